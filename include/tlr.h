@@ -1,0 +1,252 @@
+/*
+ * tlr.h -- C ABI of the GB300 (sm_103a) Tile Low-Rank Matern log-likelihood.
+ *
+ * The library evaluates the Gaussian log-likelihood of Eq. 1.2,
+ *     l(theta) = -n/2 log(2 pi) - 1/2 log|Sigma(theta)| - 1/2 Z' Sigma(theta)^-1 Z,
+ * for the Matern covariance of Eq. 4.2 (theta = sigma2, beta, nu), under the
+ * Tile Low-Rank (TLR) approximation of Sec. 2 and after one of the spatial
+ * orderings of Sec. 3.  Every step runs in CUDA kernels of this library.
+ *
+ * Conventions shared by every call
+ *  - Return value: TLR_OK (0) or one TLR_ERR_* code.  A failing call leaves a
+ *    message in tlr_last_error(ctx).  No C++ exception crosses this boundary.
+ *  - "device" pointers are CUDA global-memory pointers of the context's
+ *    device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *    pointer it passes; the library keeps none of them after the call returns.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are stream ordered; a call syncs the stream only where it
+ *    returns a value on the host (documented per call).
+ *  - Locations are SoA float64: xy[0..n) = x, xy[n..2n) = y.
+ *  - Matrix tiles are column major.  The tile size is nb; NT = ceil(n / nb);
+ *    tile t covers rows [t nb, min(n, (t+1) nb)) and has m_t rows.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef TLR_H
+#define TLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define TLR_OK            0
+#define TLR_ERR_ARG       1  /* invalid argument (sizes, pointers, theta, flags) */
+#define TLR_ERR_CUDA      2  /* a CUDA runtime call failed */
+#define TLR_ERR_OOM       3  /* device memory could not be allocated */
+#define TLR_ERR_RANK      4  /* an off-diagonal tile needs rank > maxrank (Sec. 5.2, Table 1 "NA") */
+#define TLR_ERR_NOT_SPD   5  /* non-positive pivot in a Cholesky factorisation */
+#define TLR_ERR_TIMEOUT   6  /* a bounded device wait gave up */
+#define TLR_ERR_NAN       7  /* a non-finite value was produced */
+
+/* ---- orderings (Sec. 3) --------------------------------------------------- */
+#define TLR_ORDER_IDENTITY 0 /* generation order: the paper's "no order" (Sec. 5.1) */
+#define TLR_ORDER_RANDOM   1 /* stable sort of splitmix64(seed ^ i) >> 32 */
+#define TLR_ORDER_MORTON   2 /* Sec. 3.1.1: interleaved bits of 16-bit coordinates */
+#define TLR_ORDER_HILBERT  3 /* Sec. 3.1.2: Hilbert index, orientation of Figure 3 */
+#define TLR_ORDER_KDTREE   4 /* Sec. 3.2: median splits on the widest dimension, in-order */
+#define TLR_ORDER_MAXMIN   5 /* Sec. 3.3.1 (Guinness 2018): maximum-minimum distance */
+
+/* tlr_order flags */
+#define TLR_ORDER_QUANTIZE 1u /* xy_out holds decoded coordinates q / 65535 (Sec. 3.1, "Decoding") */
+
+/* precision of the off-diagonal products (tlr_opts.precision) */
+#define TLR_PREC_FP64 0
+
+typedef struct tlr_ctx tlr_ctx; /* device, workspace pool, last error, timers */
+typedef struct tlr_mat tlr_mat; /* a TLR matrix or TLR Cholesky factor on the device */
+
+typedef struct {
+    double sigma2; /* variance, > 0 */
+    double beta;   /* range, > 0 */
+    double nu;     /* smoothness, > 0 */
+} tlr_theta;
+
+typedef struct {
+    int32_t nb;        /* tile size, 16 <= nb <= 1024 */
+    int32_t maxrank;   /* largest off-diagonal rank stored; <= 0 selects nb / 2 (Sec. 3) */
+    double eps;        /* TLR accuracy: singular values <= eps * sigma2 are dropped */
+    int32_t precision; /* TLR_PREC_* */
+    uint32_t flags;    /* reserved, 0 */
+} tlr_opts;
+
+typedef struct {
+    double loglik;        /* Eq. 1.2 */
+    double logdet;        /* log|Sigma| = 2 sum log L_ii */
+    double quad;          /* Z' Sigma^-1 Z = |L^-1 Z|^2 */
+    int64_t info;         /* NOT_SPD: global row of the failing pivot; RANK: tile i*NT+j; else -1 */
+    int32_t max_rank;     /* largest off-diagonal rank of the factor */
+    double mean_rank;     /* mean off-diagonal rank of the factor */
+    int64_t offdiag_bytes;/* Table 1 accounting: sum over i>j of (m_i + m_j) r_ij * 8 */
+    int64_t dense_bytes;  /* Table 1 "Dense": lower off-diagonal tiles * nb^2 * 8 */
+    double flops;         /* floating-point operations counted from the rank map */
+    float ms_total;       /* device time of the call (CUDA events on `stream`) */
+} tlr_result;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Errors: TLR_ERR_ARG (out NULL), TLR_ERR_CUDA (no such device). */
+int tlr_ctx_create(int device, tlr_ctx **out);
+
+/* Destroy a context; frees its workspace.  NULL is ignored. */
+void tlr_ctx_destroy(tlr_ctx *ctx);
+
+/* Message of the last failing call on `ctx` ("" if none).  Owned by ctx. */
+const char *tlr_last_error(const tlr_ctx *ctx);
+
+/* Library version string, e.g. "tlr-gb300 0.1 sm_103a". */
+const char *tlr_version(void);
+
+/* Number of CUDA kernels the library has launched since it was loaded (all
+ * contexts); the difference across a region counts its launches. */
+int64_t tlr_launch_count(void);
+
+/* ---- a1: spatial ordering (Sec. 3) -------------------------------------- */
+
+/* Order n locations.  Sec. 3.1 (encode, sort, decode), Sec. 3.2 (KD-tree),
+ * Sec. 3.3.1 (max-min), Sec. 5.1 (no order).
+ *   xy      device, 2n doubles, SoA; for MORTON/HILBERT each coordinate is
+ *           clamped to [0, 1] and quantised as round(v * 65535), ties to even
+ *   method  TLR_ORDER_*; seed is used by RANDOM only
+ *   perm    device, n int64 (output): position k holds original point perm[k]
+ *   codes   device, n uint32 (output, may be NULL): the sort keys of RANDOM,
+ *           MORTON and HILBERT in original order; left untouched otherwise
+ *   xy_out  device, 2n doubles (output, may be NULL): the permuted locations;
+ *           with flags & TLR_ORDER_QUANTIZE the decoded values q / 65535
+ * Ties are broken by original index; the result is bit-identical across runs.
+ * Errors: TLR_ERR_ARG (n < 0, bad method/flags, NULL perm with n > 0). */
+int tlr_order(tlr_ctx *ctx, const double *xy, int64_t n, int method, uint64_t seed,
+              uint32_t flags, int64_t *perm, uint32_t *codes, double *xy_out, void *stream);
+
+/* dst[k] = src[perm[k]] for k < n (device pointers; permutes Z like the
+ * locations).  Errors: TLR_ERR_ARG. */
+int tlr_gather(tlr_ctx *ctx, const int64_t *perm, const double *src, int64_t n, double *dst,
+               void *stream);
+
+/* ---- a2: covariance tiles (Eq. 1.1, Eq. 4.2) ---------------------------- */
+
+/* Number of doubles of the packed lower-triangular tile array of tlr_generate:
+ * NT (NT + 1) / 2 * nb * nb. */
+int64_t tlr_tiles_size(int64_t n, int nb);
+
+/* Dense lower-triangular covariance tiles Sigma_ij = C(|s_i - s_j|; theta),
+ * i >= j, of the (already ordered) locations xy (device, SoA).  Tile (i, j)
+ * starts at tiles + (i (i + 1) / 2 + j) nb^2, column major with leading
+ * dimension nb; rows/columns past m_i/m_j are set to 0.  K_nu is evaluated on
+ * the device (Temme's series for x <= 2, a continued fraction with the
+ * Wronskian for 2 < x <= 25, the asymptotic expansion beyond).
+ * Errors: TLR_ERR_ARG (n <= 0, nb out of range, theta not positive). */
+int tlr_generate(tlr_ctx *ctx, const double *xy, int64_t n, int nb, tlr_theta theta,
+                 double *tiles, void *stream);
+
+/* Matern covariance for m distances (device in, device out); a probe of the
+ * device K_nu used by tlr_generate.  Errors: TLR_ERR_ARG. */
+int tlr_matern(tlr_ctx *ctx, const double *d, int64_t m, tlr_theta theta, double *out,
+               void *stream);
+
+/* ---- TLR matrices ---------------------------------------------------------- */
+
+/* Allocate a TLR matrix for n points, tile nb, off-diagonal capacity maxrank
+ * (<= 0: nb / 2).  Device storage: diagonal tiles NT nb^2 doubles; U and V
+ * each NT (NT - 1) / 2 * nb * maxrank doubles; ranks NT^2 int32.
+ * Errors: TLR_ERR_ARG, TLR_ERR_OOM. */
+int tlr_mat_create(tlr_ctx *ctx, int64_t n, int nb, int maxrank, tlr_mat **out);
+void tlr_mat_destroy(tlr_mat *mat);
+
+/* Device pointers and layout of a TLR matrix (any output may be NULL).
+ *   D      diagonal tile t at D + t nb^2 (column major, ld nb; lower triangle
+ *          holds L_tt after a factorisation)
+ *   U, V   off-diagonal tile (i, j), i > j, index k = i (i - 1) / 2 + j:
+ *          U_k at U + k nb maxrank, V_k at V + k nb maxrank, column major
+ *          with ld nb, r_ij valid columns; A_ij ~ U_k V_k'
+ *   ranks  device int32 NT x NT row major; ranks[i NT + j] = r_ij (symmetric),
+ *          the diagonal holds m_t */
+int tlr_mat_layout(const tlr_mat *mat, int64_t *n, int *nb, int *nt, int *maxrank,
+                   double **D, double **U, double **V, int32_t **ranks);
+
+/* Copy one tile to caller buffers (device, column major, ld nb): for i == j
+ * the diagonal tile into `a` (nb x nb); for i > j the factors U_ij into `a`
+ * and V_ij into `b` (nb x r each, capacity nb x maxrank).  *rank (host)
+ * receives r_ij (m_i for i == j).  Stream ordered on `stream`.
+ * Errors: TLR_ERR_ARG (i < j, out of range, NULL buffers). */
+int tlr_mat_tile(tlr_ctx *ctx, const tlr_mat *mat, int i, int j, double *a, double *b,
+                 int32_t *rank, void *stream);
+
+/* Copy the NT x NT rank map to host memory (row major).  Syncs the context's
+ * internal copy stream.  Errors: TLR_ERR_ARG, TLR_ERR_CUDA. */
+int tlr_mat_ranks(tlr_ctx *ctx, const tlr_mat *mat, int32_t *host_ranks);
+
+/* ---- a3: per-tile compression (Sec. 2, Sec. 3) -------------------------- */
+
+/* Compress the packed dense tiles of tlr_generate into `A`: diagonal tiles are
+ * copied, each off-diagonal tile is replaced by U V' with
+ * r = #{ singular values > eps_abs } (absolute threshold, normally
+ * eps * sigma2).  Randomised range finder with adaptive sample size, then an
+ * exact SVD of the projected tile.
+ * Errors: TLR_ERR_ARG; TLR_ERR_RANK if some r > maxrank (info = i NT + j). */
+int tlr_compress(tlr_ctx *ctx, const double *tiles, int64_t n, int nb, double eps_abs,
+                 tlr_mat *A, int64_t *info, void *stream);
+
+/* ---- a4: TLR Cholesky (Sec. 2, Sec. 5.3) -------------------------------- */
+
+/* Factor the TLR matrix A = L L' in place (tile algorithm of akbudak2017tile,
+ * left-looking): for each column j, every tile (i, j), i >= j, is updated
+ * with the low-rank products of the tiles already factored, the diagonal
+ * tile gets a dense Cholesky, each off-diagonal tile is recompressed at
+ * eps_abs and its V factor solved with L_jj.  On return D holds L_tt and
+ * U V' holds L_ij.
+ * Errors: TLR_ERR_NOT_SPD (info = global row), TLR_ERR_RANK (info = i NT + j). */
+int tlr_potrf(tlr_ctx *ctx, tlr_mat *A, double eps_abs, int64_t *info, void *stream);
+
+/* ---- a5: triangular solve and log-determinant (Eq. 1.2) ------------------ */
+
+/* With L from tlr_potrf: y = L^-1 z (device, n doubles each; y may alias z),
+ * *logdet = 2 sum log L_ii, *quad = y'y (host doubles).  Syncs `stream`.
+ * Errors: TLR_ERR_ARG. */
+int tlr_solve(tlr_ctx *ctx, const tlr_mat *L, const double *z, double *y, double *logdet,
+              double *quad, void *stream);
+
+/* z = L w for a factor L (device vectors): draws Z ~ N(0, L L') from white
+ * noise w.  Errors: TLR_ERR_ARG. */
+int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *stream);
+
+/* ---- the hot path: one likelihood evaluation ------------------------------ */
+
+/* l(theta) of Eq. 1.2 for ordered locations xy and observations z (device,
+ * both already permuted by tlr_order / tlr_gather).  Runs a2-a5 fused: each
+ * tile is generated from the Matern kernel directly inside its update, so the
+ * dense covariance never exists as a whole.  `L` (created for n, opts->nb,
+ * opts->maxrank) receives the factor and its rank map.  *out is filled on the
+ * host; the call syncs `stream`.
+ * Errors: TLR_ERR_ARG, TLR_ERR_NOT_SPD, TLR_ERR_RANK, TLR_ERR_OOM, TLR_ERR_CUDA. */
+int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
+               const tlr_opts *opts, tlr_mat *L, tlr_result *out, void *stream);
+
+/* ---- measurement ------------------------------------------------------------ */
+
+/* Enable (enable != 0) or disable CUDA-event timing of the panel update GEMMs
+ * (the dominant kernel of tlr_loglik), and read the figures of the last
+ * tlr_loglik call: their summed device time (ms), their FP64 flop count, the
+ * number of covariance entries their epilogues evaluated and the number of
+ * launches.  Any output may be NULL.  Errors: TLR_ERR_ARG (ctx NULL). */
+int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops,
+                double *matern_entries, int *panel_launches);
+
+/* ---- MLE (Sec. 5.1: derivative-free, bound-constrained) ------------------ */
+
+/* Maximise l(theta) over lo <= theta <= hi from theta0 with the Nelder-Mead
+ * simplex method in log(theta) (bounds by clamping), stopping when the
+ * simplex's spread in l falls below tol or after max_iter evaluations.
+ * Failed evaluations (NOT_SPD, RANK) count as l = -inf.  Outputs on host.
+ * Errors: TLR_ERR_ARG, or the first hard error of an evaluation. */
+int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tlr_opts *opts,
+            tlr_theta theta0, tlr_theta lo, tlr_theta hi, double tol, int max_iter,
+            tlr_mat *L, tlr_theta *theta_hat, double *ll_hat, int *iters, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TLR_H */

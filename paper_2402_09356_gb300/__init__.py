@@ -1,0 +1,369 @@
+"""GB300 (sm_103a) Tile Low-Rank Matern log-likelihood -- Python binding.
+
+A thin ctypes layer over the C ABI in include/tlr.h (libtlr.so, built in-tree
+by paper_2402_09356_gb300/build.py).  Every function here has the name of the
+C entry point it calls and only marshals arguments: torch tensors supply
+device memory (their data pointers) and the current CUDA stream.  All
+computation happens in the library's CUDA kernels; there is no CPU fallback:
+if libtlr.so is missing or cannot be loaded, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtlr.so")
+
+TLR_OK, TLR_ERR_ARG, TLR_ERR_CUDA, TLR_ERR_OOM, TLR_ERR_RANK, TLR_ERR_NOT_SPD, TLR_ERR_TIMEOUT, TLR_ERR_NAN = range(8)
+ORDERS = {"identity": 0, "random": 1, "morton": 2, "hilbert": 3, "kdtree": 4, "maxmin": 5}
+TLR_ORDER_QUANTIZE = 1
+TLR_PREC_FP64 = 0
+
+
+class TlrError(RuntimeError):
+    def __init__(self, code: int, msg: str, info: int = -1):
+        super().__init__("TLR error %d: %s" % (code, msg))
+        self.code = code
+        self.info = info
+
+
+class tlr_theta(ctypes.Structure):
+    _fields_ = [("sigma2", ctypes.c_double), ("beta", ctypes.c_double), ("nu", ctypes.c_double)]
+
+
+class tlr_opts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int32), ("maxrank", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class tlr_result(ctypes.Structure):
+    _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
+                ("info", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("mean_rank", ctypes.c_double),
+                ("offdiag_bytes", ctypes.c_int64), ("dense_bytes", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("ms_total", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+_SIGS = {
+    "tlr_version": (ctypes.c_char_p, []),
+    "tlr_launch_count": (ctypes.c_int64, []),
+    "tlr_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "tlr_ctx_destroy": (None, [ctypes.c_void_p]),
+    "tlr_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "tlr_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                                 ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "tlr_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_tiles_size": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int]),
+    "tlr_generate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, tlr_theta,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_matern": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, tlr_theta, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "tlr_mat_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "tlr_mat_destroy": (None, [ctypes.c_void_p]),
+    "tlr_mat_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
+    "tlr_mat_ranks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_mat_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "tlr_compress": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "tlr_potrf": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.c_void_p]),
+    "tlr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    "tlr_lmul": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_loglik": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, tlr_theta,
+                                  ctypes.POINTER(tlr_opts), ctypes.c_void_p, ctypes.POINTER(tlr_result),
+                                  ctypes.c_void_p]),
+    "tlr_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int)]),
+    "tlr_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                               ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(tlr_theta),
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtlr.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libtlr.so not built (%s); run paper_2402_09356_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _theta(theta) -> tlr_theta:
+    if isinstance(theta, tlr_theta):
+        return theta
+    s2, b, nu = theta
+    return tlr_theta(float(s2), float(b), float(nu))
+
+
+def _check_f64(name, t, numel=None):
+    import torch
+    if t.device.type != "cuda" or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TlrError(TLR_ERR_ARG, "%s must be a contiguous float64 CUDA tensor" % name)
+    if numel is not None and t.numel() != numel:
+        raise TlrError(TLR_ERR_ARG, "%s must have %d elements" % (name, numel))
+
+
+class Context:
+    """Owns a tlr_ctx on one device."""
+
+    def __init__(self, device: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        rc = lib.tlr_ctx_create(int(device), ctypes.byref(h))
+        if rc != TLR_OK:
+            raise TlrError(rc, "tlr_ctx_create failed on device %d" % device)
+        self.h = h
+        self.device = device
+
+    def check(self, rc: int, info: int = -1):
+        if rc != TLR_OK:
+            msg = load_library().tlr_last_error(self.h).decode()
+            raise TlrError(rc, msg, info)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().tlr_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TlrMatrix:
+    """Owns a tlr_mat (TLR matrix or factor) of a context."""
+
+    def __init__(self, ctx: Context, n: int, nb: int, maxrank: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx.check(load_library().tlr_mat_create(ctx.h, int(n), int(nb), int(maxrank), ctypes.byref(h)))
+        self.h = h
+        self.n, self.nb = int(n), int(nb)
+        self.nt = (self.n + self.nb - 1) // self.nb
+        self.maxrank = self.layout()["maxrank"]
+
+    def layout(self) -> dict:
+        n, nb, nt, mr = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        D, U, V, R = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        load_library().tlr_mat_layout(self.h, ctypes.byref(n), ctypes.byref(nb), ctypes.byref(nt), ctypes.byref(mr),
+                                      ctypes.byref(D), ctypes.byref(U), ctypes.byref(V), ctypes.byref(R))
+        return {"n": n.value, "nb": nb.value, "nt": nt.value, "maxrank": mr.value,
+                "D": D.value, "U": U.value, "V": V.value, "ranks": R.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().tlr_mat_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tlr_version() -> str:
+    return load_library().tlr_version().decode()
+
+
+def tlr_launch_count() -> int:
+    return int(load_library().tlr_launch_count())
+
+
+def tlr_order(ctx: Context, xy, method, seed: int = 3, flags: int = 0, perm=None, codes=None, xy_out=None,
+              stream=None):
+    """Order SoA locations xy (float64 CUDA, 2n).  Returns perm (int64 CUDA, n)."""
+    import torch
+    n = xy.numel() // 2
+    _check_f64("xy", xy, 2 * n)
+    if isinstance(method, str):
+        method = ORDERS[method]
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int64, device=xy.device)
+    rc = load_library().tlr_order(ctx.h, _ptr(xy), n, int(method), ctypes.c_uint64(seed & (2**64 - 1)),
+                                  int(flags), _ptr(perm), _ptr(codes), _ptr(xy_out), _stream(stream))
+    ctx.check(rc)
+    return perm
+
+
+def tlr_gather(ctx: Context, perm, src, dst=None, stream=None):
+    import torch
+    n = perm.numel()
+    if dst is None:
+        dst = torch.empty(n, dtype=torch.float64, device=src.device)
+    ctx.check(load_library().tlr_gather(ctx.h, _ptr(perm), _ptr(src), n, _ptr(dst), _stream(stream)))
+    return dst
+
+
+def tlr_tiles_size(n: int, nb: int) -> int:
+    return int(load_library().tlr_tiles_size(int(n), int(nb)))
+
+
+def tlr_generate(ctx: Context, xy, nb: int, theta, tiles=None, stream=None):
+    """Packed lower-triangular dense covariance tiles (float64 CUDA)."""
+    import torch
+    n = xy.numel() // 2
+    _check_f64("xy", xy, 2 * n)
+    if tiles is None:
+        tiles = torch.empty(tlr_tiles_size(n, nb), dtype=torch.float64, device=xy.device)
+    ctx.check(load_library().tlr_generate(ctx.h, _ptr(xy), n, int(nb), _theta(theta), _ptr(tiles), _stream(stream)))
+    return tiles
+
+
+def tlr_matern(ctx: Context, d, theta, out=None, stream=None):
+    import torch
+    _check_f64("d", d)
+    if out is None:
+        out = torch.empty_like(d)
+    ctx.check(load_library().tlr_matern(ctx.h, _ptr(d), d.numel(), _theta(theta), _ptr(out), _stream(stream)))
+    return out
+
+
+def tlr_mat_ranks(mat: TlrMatrix):
+    import numpy as np
+    r = np.zeros((mat.nt, mat.nt), dtype=np.int32)
+    mat.ctx.check(load_library().tlr_mat_ranks(mat.ctx.h, mat.h, ctypes.c_void_p(r.ctypes.data)))
+    return r
+
+
+def tlr_mat_tile(mat: TlrMatrix, i: int, j: int, stream=None):
+    """Tile (i, j) as torch tensors: D (m_i x m_i) for i == j, else (U, V) of the factor."""
+    import torch
+    nb = mat.nb
+    dev = torch.device("cuda", mat.ctx.device)
+    # a column-major nb x cols matrix is a row-major (cols, nb) tensor
+    a = torch.zeros((nb if i == j else mat.maxrank, nb), dtype=torch.float64, device=dev)
+    b = torch.zeros((mat.maxrank, nb), dtype=torch.float64, device=dev) if i != j else None
+    r = ctypes.c_int32()
+    rc = load_library().tlr_mat_tile(mat.ctx.h, mat.h, int(i), int(j), _ptr(a), _ptr(b), ctypes.byref(r),
+                                     _stream(stream))
+    mat.ctx.check(rc)
+    mi = min(nb, mat.n - i * nb)
+    mj = min(nb, mat.n - j * nb)
+    if i == j:
+        return a.t()[:mi, :mi]
+    return a.t()[:mi, :r.value], b.t()[:mj, :r.value]
+
+
+def tlr_compress(mat: TlrMatrix, tiles, eps_abs: float, stream=None):
+    info = ctypes.c_int64(-1)
+    rc = load_library().tlr_compress(mat.ctx.h, _ptr(tiles), mat.n, mat.nb, float(eps_abs), mat.h,
+                                     ctypes.byref(info), _stream(stream))
+    mat.ctx.check(rc, info.value)
+    return mat
+
+
+def tlr_potrf(mat: TlrMatrix, eps_abs: float, stream=None):
+    info = ctypes.c_int64(-1)
+    rc = load_library().tlr_potrf(mat.ctx.h, mat.h, float(eps_abs), ctypes.byref(info), _stream(stream))
+    mat.ctx.check(rc, info.value)
+    return mat
+
+
+def tlr_solve(mat: TlrMatrix, z, y=None, stream=None):
+    """y = L^-1 z; returns (y, logdet, quad)."""
+    import torch
+    _check_f64("z", z, mat.n)
+    if y is None:
+        y = torch.empty_like(z)
+    ld, q = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().tlr_solve(mat.ctx.h, mat.h, _ptr(z), _ptr(y), ctypes.byref(ld), ctypes.byref(q),
+                                  _stream(stream))
+    mat.ctx.check(rc)
+    return y, ld.value, q.value
+
+
+def tlr_lmul(mat: TlrMatrix, w, z=None, stream=None):
+    import torch
+    _check_f64("w", w, mat.n)
+    if z is None:
+        z = torch.empty_like(w)
+    mat.ctx.check(load_library().tlr_lmul(mat.ctx.h, mat.h, _ptr(w), _ptr(z), _stream(stream)))
+    return z
+
+
+@dataclass
+class Options:
+    nb: int = 800
+    eps: float = 1e-7
+    maxrank: int = 0
+    precision: int = TLR_PREC_FP64
+
+    def c(self) -> tlr_opts:
+        return tlr_opts(int(self.nb), int(self.maxrank), float(self.eps), int(self.precision), 0)
+
+
+def tlr_loglik(mat: TlrMatrix, xy, z, theta, opts: Options, stream=None) -> dict:
+    """l(theta) (Eq. 1.2) for ordered xy / z; `mat` receives the factor."""
+    _check_f64("xy", xy, 2 * mat.n)
+    _check_f64("z", z, mat.n)
+    res = tlr_result()
+    o = opts.c()
+    rc = load_library().tlr_loglik(mat.ctx.h, _ptr(xy), _ptr(z), mat.n, _theta(theta), ctypes.byref(o), mat.h,
+                                   ctypes.byref(res), _stream(stream))
+    mat.ctx.check(rc, res.info)
+    return res.as_dict()
+
+
+def tlr_profile(ctx: Context, enable: bool = True) -> dict:
+    ms, fl, me, pl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    ctx.check(load_library().tlr_profile(ctx.h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(fl),
+                                         ctypes.byref(me), ctypes.byref(pl)))
+    return {"gemm_ms": ms.value, "gemm_flops": fl.value, "matern_entries": me.value, "panel_launches": pl.value}
+
+
+def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1e-9, max_iter: int = 500,
+            stream=None) -> dict:
+    th, ll, it = tlr_theta(), ctypes.c_double(), ctypes.c_int()
+    o = opts.c()
+    rc = load_library().tlr_mle(mat.ctx.h, _ptr(xy), _ptr(z), mat.n, ctypes.byref(o), _theta(theta0), _theta(lo),
+                                _theta(hi), float(tol), int(max_iter), mat.h, ctypes.byref(th), ctypes.byref(ll),
+                                ctypes.byref(it), _stream(stream))
+    mat.ctx.check(rc)
+    return {"theta": (th.sigma2, th.beta, th.nu), "loglik": ll.value, "iters": it.value}
+
+
+def loglik_log2pi(n: int) -> float:
+    return -0.5 * n * math.log(2 * math.pi)

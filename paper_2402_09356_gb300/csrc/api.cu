@@ -1,0 +1,495 @@
+// C ABI of the TLR library (include/tlr.h).  Every entry point validates its
+// arguments, runs its kernels on the caller's stream and turns any internal
+// error into a status code plus a message in the context.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "compress.cuh"
+#include "matern.cuh"
+#include "tlr_internal.cuh"
+
+namespace tlr {
+
+std::atomic<long long> g_launch_count{0};
+
+void status_reset(tlr_ctx *ctx, cudaStream_t s) {
+    TLR_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, sizeof(DevStatus), s));
+}
+
+int status_fetch(tlr_ctx *ctx, cudaStream_t s, long long *info) {
+    TLR_CUDA_TRY(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    if (info) *info = ctx->h_status->info;
+    return ctx->h_status->code;
+}
+
+void profile_events(tlr_ctx *ctx, int count) {
+    while ((int)ctx->prof_events.size() < count) {
+        cudaEvent_t e;
+        TLR_CUDA_TRY(cudaEventCreate(&e));
+        ctx->prof_events.push_back(e);
+    }
+}
+
+static int fail(tlr_ctx *ctx, const Error &e) {
+    if (ctx) ctx->err = e.msg;
+    return e.code;
+}
+
+template <class F>
+static int guarded(tlr_ctx *ctx, F &&f) {
+    if (!ctx) return TLR_ERR_ARG;
+    try {
+        TLR_CUDA_TRY(cudaSetDevice(ctx->device));
+        ctx->err.clear();
+        f();
+        return TLR_OK;
+    } catch (const Error &e) {
+        return fail(ctx, e);
+    } catch (const std::exception &e) {
+        return fail(ctx, Error{TLR_ERR_CUDA, e.what()});
+    }
+}
+
+static void check_arg(bool ok, const char *what) {
+    if (!ok) throw make_error(TLR_ERR_ARG, "invalid argument: %s", what);
+}
+
+static MaternParams params_of(tlr_theta th) {
+    MaternParams P;
+    if (!make_matern_params(th.sigma2, th.beta, th.nu, &P))
+        throw make_error(TLR_ERR_ARG, "theta must be positive and finite (sigma2=%g beta=%g nu=%g)",
+                         th.sigma2, th.beta, th.nu);
+    return P;
+}
+
+}  // namespace tlr
+
+using namespace tlr;
+
+extern "C" {
+
+const char *tlr_version(void) { return "tlr-gb300 0.1 sm_103a"; }
+
+int64_t tlr_launch_count(void) { return g_launch_count.load(); }
+
+int tlr_ctx_create(int device, tlr_ctx **out) {
+    if (!out) return TLR_ERR_ARG;
+    *out = nullptr;
+    auto *ctx = new tlr_ctx();
+    ctx->device = device;
+    int rc = guarded(ctx, [&] {
+        int count = 0;
+        TLR_CUDA_TRY(cudaGetDeviceCount(&count));
+        if (device < 0 || device >= count) throw make_error(TLR_ERR_ARG, "no CUDA device %d", device);
+        TLR_CUDA_TRY(cudaSetDevice(device));
+        TLR_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
+        TLR_CUDA_TRY(cudaMalloc(&ctx->d_status, sizeof(DevStatus)));
+        TLR_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(DevStatus)));
+        TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_status, sizeof(DevStatus), cudaHostAllocDefault));
+        TLR_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        TLR_CUDA_TRY(cudaEventCreate(&ctx->ev_a));
+        TLR_CUDA_TRY(cudaEventCreate(&ctx->ev_b));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+        ctx->stage_cap = (size_t)16 << 20;
+        TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_stage, ctx->stage_cap, cudaHostAllocDefault));
+        TLR_CUDA_TRY(cudaMalloc(&ctx->d_stage, ctx->stage_cap));
+    });
+    if (rc != TLR_OK) {
+        tlr_ctx_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return TLR_OK;
+}
+
+void tlr_ctx_destroy(tlr_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    for (cudaEvent_t e : {ctx->ev_a, ctx->ev_b, ctx->ev_fork, ctx->ev_join})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->d_omega) cudaFree(ctx->d_omega);
+    delete ctx;
+}
+
+const char *tlr_last_error(const tlr_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tlr_order(tlr_ctx *ctx, const double *xy, int64_t n, int method, uint64_t seed, uint32_t flags,
+              int64_t *perm, uint32_t *codes, double *xy_out, void *stream) {
+    return guarded(ctx, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        check_arg(n >= 0 && n < ((int64_t)1 << 31), "n");
+        check_arg(method >= TLR_ORDER_IDENTITY && method <= TLR_ORDER_MAXMIN, "method");
+        check_arg((flags & ~TLR_ORDER_QUANTIZE) == 0, "flags");
+        check_arg(n == 0 || (xy && perm), "xy/perm");
+        if (n == 0) return;
+        switch (method) {
+        case TLR_ORDER_IDENTITY: order_identity(n, perm, s); break;
+        case TLR_ORDER_RANDOM:
+        case TLR_ORDER_MORTON:
+        case TLR_ORDER_HILBERT: order_sfc(xy, n, method, seed, perm, codes, s); break;
+        case TLR_ORDER_KDTREE: order_kdtree(xy, n, perm, s); break;
+        case TLR_ORDER_MAXMIN: order_maxmin(xy, n, perm, s, ctx->num_sms); break;
+        }
+        if (xy_out) permute_xy(xy, perm, n, (flags & TLR_ORDER_QUANTIZE) ? 1 : 0, xy_out, s);
+    });
+}
+
+int tlr_gather(tlr_ctx *ctx, const int64_t *perm, const double *src, int64_t n, double *dst, void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(n >= 0 && (n == 0 || (perm && src && dst)), "gather");
+        gather(perm, src, n, dst, (cudaStream_t)stream);
+    });
+}
+
+int64_t tlr_tiles_size(int64_t n, int nb) {
+    if (n <= 0 || nb <= 0) return 0;
+    int64_t nt = (n + nb - 1) / nb;
+    return nt * (nt + 1) / 2 * (int64_t)nb * nb;
+}
+
+int tlr_generate(tlr_ctx *ctx, const double *xy, int64_t n, int nb, tlr_theta theta, double *tiles,
+                 void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(n > 0 && xy && tiles, "n/xy/tiles");
+        check_arg(nb >= 16 && nb <= kMaxTile, "nb");
+        MaternParams P = params_of(theta);
+        generate_tiles(xy, n, nb, P, tiles, (cudaStream_t)stream);
+    });
+}
+
+int tlr_matern(tlr_ctx *ctx, const double *d, int64_t m, tlr_theta theta, double *out, void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(m >= 0 && (m == 0 || (d && out)), "d/out");
+        MaternParams P = params_of(theta);
+        matern_vec(d, m, P, out, (cudaStream_t)stream);
+    });
+}
+
+int tlr_mat_create(tlr_ctx *ctx, int64_t n, int nb, int maxrank, tlr_mat **out) {
+    return guarded(ctx, [&] {
+        check_arg(out != nullptr, "out");
+        *out = nullptr;
+        check_arg(n > 0 && nb >= 16 && nb <= kMaxTile, "n/nb");
+        if (maxrank <= 0) maxrank = nb / 2;
+        check_arg(maxrank <= nb, "maxrank");
+        auto *M = new tlr_mat();
+        M->device = ctx->device;
+        M->n = n;
+        M->nb = nb;
+        M->nt = (int)((n + nb - 1) / nb);
+        M->maxrank = maxrank;
+        int64_t noff = (int64_t)M->nt * (M->nt - 1) / 2;
+        size_t dbytes = (size_t)M->nt * nb * nb * sizeof(double);
+        size_t uvbytes = (size_t)std::max<int64_t>(noff, 1) * nb * maxrank * sizeof(double);
+        cudaError_t e1 = cudaMalloc(&M->D, dbytes);
+        cudaError_t e2 = cudaMalloc(&M->U, uvbytes);
+        cudaError_t e3 = cudaMalloc(&M->V, uvbytes);
+        cudaError_t e4 = cudaMalloc(&M->ranks, (size_t)M->nt * M->nt * sizeof(int32_t));
+        if (e1 || e2 || e3 || e4) {
+            tlr_mat_destroy(M);
+            cudaGetLastError();
+            throw make_error(TLR_ERR_OOM, "cannot allocate TLR matrix (%zu + 2 x %zu bytes)", dbytes, uvbytes);
+        }
+        // padding rows of U / V must read as zero
+        TLR_CUDA_TRY(cudaMemset(M->D, 0, dbytes));
+        TLR_CUDA_TRY(cudaMemset(M->U, 0, uvbytes));
+        TLR_CUDA_TRY(cudaMemset(M->V, 0, uvbytes));
+        TLR_CUDA_TRY(cudaMemset(M->ranks, 0, (size_t)M->nt * M->nt * sizeof(int32_t)));
+        *out = M;
+    });
+}
+
+void tlr_mat_destroy(tlr_mat *M) {
+    if (!M) return;
+    cudaSetDevice(M->device);
+    cudaDeviceSynchronize();
+    if (M->D) cudaFree(M->D);
+    if (M->U) cudaFree(M->U);
+    if (M->V) cudaFree(M->V);
+    if (M->ranks) cudaFree(M->ranks);
+    delete M;
+}
+
+int tlr_mat_layout(const tlr_mat *M, int64_t *n, int *nb, int *nt, int *maxrank, double **D, double **U,
+                   double **V, int32_t **ranks) {
+    if (!M) return TLR_ERR_ARG;
+    if (n) *n = M->n;
+    if (nb) *nb = M->nb;
+    if (nt) *nt = M->nt;
+    if (maxrank) *maxrank = M->maxrank;
+    if (D) *D = M->D;
+    if (U) *U = M->U;
+    if (V) *V = M->V;
+    if (ranks) *ranks = M->ranks;
+    return TLR_OK;
+}
+
+int tlr_mat_tile(tlr_ctx *ctx, const tlr_mat *M, int i, int j, double *a, double *b, int32_t *rank,
+                 void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(M && a && rank, "mat/a/rank");
+        check_arg(i >= 0 && j >= 0 && i < M->nt && j <= i, "tile index");
+        cudaStream_t s = (cudaStream_t)stream;
+        size_t nb = M->nb;
+        if (i == j) {
+            TLR_CUDA_TRY(cudaMemcpyAsync(a, M->D + (int64_t)i * nb * nb, nb * nb * sizeof(double),
+                                         cudaMemcpyDeviceToDevice, s));
+            *rank = tile_rows(M->n, M->nb, i);
+            return;
+        }
+        check_arg(b != nullptr, "b");
+        int r = M->h_ranks.size() == (size_t)M->nt * M->nt ? M->h_ranks[(size_t)i * M->nt + j] : 0;
+        size_t off = (size_t)off_index(i, j) * nb * M->maxrank;
+        if (r > 0) {
+            TLR_CUDA_TRY(cudaMemcpyAsync(a, M->U + off, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            TLR_CUDA_TRY(cudaMemcpyAsync(b, M->V + off, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        }
+        *rank = r;
+    });
+}
+
+int tlr_mat_ranks(tlr_ctx *ctx, const tlr_mat *M, int32_t *host_ranks) {
+    return guarded(ctx, [&] {
+        check_arg(M && host_ranks, "mat/host_ranks");
+        TLR_CUDA_TRY(cudaMemcpy(host_ranks, M->ranks, (size_t)M->nt * M->nt * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost));
+    });
+}
+
+int tlr_compress(tlr_ctx *ctx, const double *tiles, int64_t n, int nb, double eps_abs, tlr_mat *A,
+                 int64_t *info, void *stream) {
+    long long inf = -1;
+    int rc = guarded(ctx, [&] {
+        check_arg(tiles && A, "tiles/A");
+        check_arg(A->n == n && A->nb == nb, "A does not match n/nb");
+        check_arg(eps_abs >= 0 && std::isfinite(eps_abs), "eps_abs");
+        compress_packed(ctx, (cudaStream_t)stream, tiles, A, eps_abs, &inf);
+    });
+    if (info) *info = inf;
+    return rc;
+}
+
+int tlr_potrf(tlr_ctx *ctx, tlr_mat *A, double eps_abs, int64_t *info, void *stream) {
+    long long inf = -1;
+    int rc = guarded(ctx, [&] {
+        check_arg(A != nullptr, "A");
+        check_arg(eps_abs >= 0 && std::isfinite(eps_abs), "eps_abs");
+        cudaStream_t s = (cudaStream_t)stream;
+        status_reset(ctx, s);
+        FactorStats st;
+        factor(ctx, s, A, FactorMode::Tlr, nullptr, nullptr, eps_abs, &st, &inf);
+    });
+    if (info) *info = inf;
+    return rc;
+}
+
+int tlr_solve(tlr_ctx *ctx, const tlr_mat *L, const double *z, double *y, double *logdet, double *quad,
+              void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(L && z && y, "L/z/y");
+        cudaStream_t s = (cudaStream_t)stream;
+        check_arg(L->h_ranks.size() == (size_t)L->nt * L->nt, "L holds no factor");
+        DevBuf acc(2 * sizeof(double), s);
+        TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 2 * sizeof(double), s));
+        status_reset(ctx, s);
+        forward_solve(ctx, s, L, z, y, acc.as<double>());
+        double h[2];
+        TLR_CUDA_TRY(cudaMemcpyAsync(h, acc.as<double>(), sizeof h, cudaMemcpyDeviceToHost, s));
+        TLR_CUDA_TRY(cudaStreamSynchronize(s));
+        if (logdet) *logdet = 2.0 * h[0];
+        if (quad) *quad = h[1];
+    });
+}
+
+int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(L && w && z && w != z, "L/w/z");
+        check_arg(L->h_ranks.size() == (size_t)L->nt * L->nt, "L holds no factor");
+        lmul(ctx, (cudaStream_t)stream, L, w, z);
+    });
+}
+
+static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
+                        const tlr_opts *opts, tlr_mat *L, tlr_result *out, cudaStream_t s) {
+    check_arg(xy && z && opts && L && out, "xy/z/opts/L/out");
+    check_arg(n > 0 && L->n == n && L->nb == opts->nb, "L does not match n/nb");
+    check_arg(opts->eps >= 0 && std::isfinite(opts->eps), "eps");
+    check_arg(opts->precision == TLR_PREC_FP64, "precision");
+    MaternParams P = params_of(theta);
+    std::memset(out, 0, sizeof *out);
+    out->info = -1;
+    TLR_CUDA_TRY(cudaEventRecord(ctx->ev_a, s));
+    status_reset(ctx, s);
+    FactorStats st;
+    long long inf = -1;
+    try {
+        factor(ctx, s, L, FactorMode::Matern, xy, &P, opts->eps * theta.sigma2, &st, &inf);
+    } catch (const Error &) {
+        out->info = inf;
+        throw;
+    }
+    DevBuf acc(2 * sizeof(double), s), y((size_t)n * sizeof(double), s);
+    TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 2 * sizeof(double), s));
+    forward_solve(ctx, s, L, z, y.as<double>(), acc.as<double>());
+    double h[2];
+    TLR_CUDA_TRY(cudaMemcpyAsync(h, acc.as<double>(), sizeof h, cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaEventRecord(ctx->ev_b, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    long long sinfo = -1;
+    int sc = status_fetch(ctx, s, &sinfo);
+    if (sc) {
+        out->info = sinfo;
+        throw make_error(sc, "likelihood: device status %d (info %lld)", sc, sinfo);
+    }
+    out->logdet = 2.0 * h[0];
+    out->quad = h[1];
+    out->loglik = -0.5 * (double)n * std::log(2.0 * M_PI) - 0.5 * out->logdet - 0.5 * out->quad;
+    if (!std::isfinite(out->loglik)) throw make_error(TLR_ERR_NAN, "likelihood is not finite");
+    int nt = L->nt;
+    double sum = 0;
+    int cnt = 0, mx = 0;
+    int64_t bytes = 0;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < i; ++j) {
+            int r = L->h_ranks[(size_t)i * nt + j];
+            sum += r;
+            ++cnt;
+            mx = std::max(mx, r);
+            bytes += (int64_t)(tile_rows(n, L->nb, i) + tile_rows(n, L->nb, j)) * r * 8;
+        }
+    out->max_rank = mx;
+    out->mean_rank = cnt ? sum / cnt : 0.0;
+    out->offdiag_bytes = bytes;
+    out->dense_bytes = (int64_t)nt * (nt - 1) / 2 * L->nb * L->nb * 8;
+    out->flops = st.flops;
+    float ms = 0.f;
+    TLR_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b));
+    out->ms_total = ms;
+    ctx->last_gemm_ms = st.gemm_ms;
+    ctx->last_gemm_flops = st.gemm_flops;
+    ctx->last_matern_entries = st.matern_entries;
+    ctx->last_panel_launches = st.panel_launches;
+}
+
+int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
+               const tlr_opts *opts, tlr_mat *L, tlr_result *out, void *stream) {
+    return guarded(ctx, [&] { loglik_impl(ctx, xy, z, n, theta, opts, L, out, (cudaStream_t)stream); });
+}
+
+int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops, double *matern_entries,
+                int *panel_launches) {
+    if (!ctx) return TLR_ERR_ARG;
+    ctx->profile = enable != 0;
+    if (gemm_ms) *gemm_ms = ctx->last_gemm_ms;
+    if (gemm_flops) *gemm_flops = ctx->last_gemm_flops;
+    if (matern_entries) *matern_entries = ctx->last_matern_entries;
+    if (panel_launches) *panel_launches = ctx->last_panel_launches;
+    return TLR_OK;
+}
+
+int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tlr_opts *opts,
+            tlr_theta theta0, tlr_theta lo, tlr_theta hi, double tol, int max_iter, tlr_mat *L,
+            tlr_theta *theta_hat, double *ll_hat, int *iters, void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(theta_hat && ll_hat && iters && max_iter > 0 && tol > 0, "mle outputs");
+        check_arg(lo.sigma2 > 0 && lo.beta > 0 && lo.nu > 0 && hi.sigma2 >= lo.sigma2 && hi.beta >= lo.beta &&
+                      hi.nu >= lo.nu, "bounds");
+        cudaStream_t s = (cudaStream_t)stream;
+        const double llo[3] = {std::log(lo.sigma2), std::log(lo.beta), std::log(lo.nu)};
+        const double lhi[3] = {std::log(hi.sigma2), std::log(hi.beta), std::log(hi.nu)};
+        int evals = 0;
+        auto clampv = [&](double *v) {
+            for (int d = 0; d < 3; ++d) v[d] = std::min(lhi[d], std::max(llo[d], v[d]));
+        };
+        // f = -l(theta) in log coordinates; failed evaluations are +inf
+        auto f = [&](const double *v) -> double {
+            tlr_theta th{std::exp(v[0]), std::exp(v[1]), std::exp(v[2])};
+            tlr_result r;
+            ++evals;
+            try {
+                loglik_impl(ctx, xy, z, n, th, opts, L, &r, s);
+            } catch (const Error &e) {
+                if (e.code == TLR_ERR_NOT_SPD || e.code == TLR_ERR_RANK || e.code == TLR_ERR_NAN) {
+                    cudaStreamSynchronize(s);
+                    return INFINITY;
+                }
+                throw;
+            }
+            return -r.loglik;
+        };
+        double x[4][3], fx[4];
+        double v0[3] = {std::log(theta0.sigma2), std::log(theta0.beta), std::log(theta0.nu)};
+        clampv(v0);
+        for (int p = 0; p < 4; ++p) {
+            for (int d = 0; d < 3; ++d) x[p][d] = v0[d];
+            if (p > 0) x[p][p - 1] += 0.1;
+            clampv(x[p]);
+            fx[p] = f(x[p]);
+        }
+        // Nelder-Mead (reflection 1, expansion 2, contraction 1/2, shrink 1/2)
+        while (evals < max_iter) {
+            int idx[4] = {0, 1, 2, 3};
+            std::sort(idx, idx + 4, [&](int a, int b) { return fx[a] < fx[b]; });
+            double xs[4][3], fs[4];
+            for (int p = 0; p < 4; ++p) {
+                fs[p] = fx[idx[p]];
+                for (int d = 0; d < 3; ++d) xs[p][d] = x[idx[p]][d];
+            }
+            std::memcpy(x, xs, sizeof x);
+            std::memcpy(fx, fs, sizeof fx);
+            if (std::isfinite(fx[3]) && std::fabs(fx[3] - fx[0]) <= tol * (1.0 + std::fabs(fx[0]))) break;
+            double c[3] = {0, 0, 0};
+            for (int p = 0; p < 3; ++p)
+                for (int d = 0; d < 3; ++d) c[d] += x[p][d] / 3.0;
+            double xr[3], xe[3], xc[3];
+            for (int d = 0; d < 3; ++d) xr[d] = c[d] + (c[d] - x[3][d]);
+            clampv(xr);
+            double fr = f(xr);
+            if (fr < fx[0]) {
+                for (int d = 0; d < 3; ++d) xe[d] = c[d] + 2.0 * (c[d] - x[3][d]);
+                clampv(xe);
+                double fe = f(xe);
+                if (fe < fr) { std::memcpy(x[3], xe, sizeof xe); fx[3] = fe; }
+                else { std::memcpy(x[3], xr, sizeof xr); fx[3] = fr; }
+            } else if (fr < fx[2]) {
+                std::memcpy(x[3], xr, sizeof xr);
+                fx[3] = fr;
+            } else {
+                bool outside = fr < fx[3];
+                for (int d = 0; d < 3; ++d)
+                    xc[d] = outside ? c[d] + 0.5 * (xr[d] - c[d]) : c[d] + 0.5 * (x[3][d] - c[d]);
+                clampv(xc);
+                double fc = f(xc);
+                if (fc < (outside ? fr : fx[3])) {
+                    std::memcpy(x[3], xc, sizeof xc);
+                    fx[3] = fc;
+                } else {
+                    for (int p = 1; p < 4; ++p) {
+                        for (int d = 0; d < 3; ++d) x[p][d] = x[0][d] + 0.5 * (x[p][d] - x[0][d]);
+                        fx[p] = f(x[p]);
+                    }
+                }
+            }
+        }
+        int best = 0;
+        for (int p = 1; p < 4; ++p)
+            if (fx[p] < fx[best]) best = p;
+        if (!std::isfinite(fx[best])) throw make_error(TLR_ERR_NOT_SPD, "no feasible likelihood evaluation");
+        *theta_hat = tlr_theta{std::exp(x[best][0]), std::exp(x[best][1]), std::exp(x[best][2])};
+        *ll_hat = -fx[best];
+        *iters = evals;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Internal definitions shared by the CUDA translation units of the TLR library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <utility>
+#include <string>
+#include <vector>
+
+#include "../../include/tlr.h"
+
+namespace tlr {
+
+// Device-side status word: the first failing kernel wins the atomicCAS on
+// `code`; `info` carries the failing row / tile.
+struct DevStatus {
+    int code;
+    int pad;
+    long long info;
+};
+
+__device__ inline void set_status(DevStatus *st, int code, long long info) {
+    if (atomicCAS(&st->code, 0, code) == 0) st->info = info;
+}
+
+// Error carried back to the C ABI.
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define TLR_CUDA_TRY(expr)                                                               \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            throw ::tlr::Error{e_ == cudaErrorMemoryAllocation ? TLR_ERR_OOM : TLR_ERR_CUDA, \
+                               std::string(#expr) + ": " + cudaGetErrorString(e_)};     \
+    } while (0)
+
+#define TLR_CHECK_LAUNCH() TLR_CUDA_TRY(cudaGetLastError())
+
+inline Error make_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    return Error{code, buf};
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Number of kernels this library has launched (all contexts, all devices).
+extern std::atomic<long long> g_launch_count;
+
+// Every kernel of the library is launched through here so that launches can
+// be counted.
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   Args &&...args) {
+    kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+}
+
+// Stream-ordered device buffer from the CUDA memory pool.
+class DevBuf {
+public:
+    DevBuf() = default;
+    DevBuf(size_t bytes, cudaStream_t s) { alloc(bytes, s); }
+    ~DevBuf() { release(); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    void alloc(size_t bytes, cudaStream_t s) {
+        release();
+        stream_ = s;
+        bytes_ = bytes;
+        if (bytes) TLR_CUDA_TRY(cudaMallocAsync(&ptr_, bytes, s));
+    }
+    void release() {
+        if (ptr_) cudaFreeAsync(ptr_, stream_);
+        ptr_ = nullptr;
+        bytes_ = 0;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(ptr_); }
+    size_t bytes() const { return bytes_; }
+
+private:
+    void *ptr_ = nullptr;
+    size_t bytes_ = 0;
+    cudaStream_t stream_ = nullptr;
+};
+
+}  // namespace tlr
+
+struct tlr_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    tlr::DevStatus *d_status = nullptr;   // device status word
+    tlr::DevStatus *h_status = nullptr;   // pinned host mirror
+    cudaStream_t aux = nullptr;           // second stream for concurrent tile work
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_fork = nullptr, ev_join = nullptr;
+    // descriptor staging: pinned host ring mirrored into device memory
+    char *h_stage = nullptr;
+    char *d_stage = nullptr;
+    size_t stage_cap = 0;
+    size_t stage_off = 0;
+    // fixed Gaussian test matrices of the randomised range finder
+    double *d_omega = nullptr;
+    int omega_rows = 0, omega_cols = 0;
+    // timing of the dominant kernel (panel update GEMMs)
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_events;
+    double last_gemm_ms = 0.0, last_gemm_flops = 0.0, last_matern_entries = 0.0;
+    int last_panel_launches = 0;
+};
+
+struct tlr_mat {
+    int device = 0;
+    int64_t n = 0;
+    int nb = 0;
+    int nt = 0;
+    int maxrank = 0;
+    double *D = nullptr;        // nt * nb * nb
+    double *U = nullptr;        // noff * nb * maxrank
+    double *V = nullptr;        // noff * nb * maxrank
+    int32_t *ranks = nullptr;   // nt * nt
+    std::vector<int32_t> h_ranks;  // host mirror, refreshed after compress / factor
+};
+
+namespace tlr {
+
+inline int64_t off_index(int i, int j) { return (int64_t)i * (i - 1) / 2 + j; }
+inline int tile_rows(int64_t n, int nb, int t) {
+    int64_t r = n - (int64_t)t * nb;
+    return (int)(r < nb ? r : nb);
+}
+
+// Copies `bytes` of host data into the staging ring and returns the device
+// address of the copy (stream ordered on `s`).
+void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s);
+
+// Status word helpers (host side).
+void status_reset(tlr_ctx *ctx, cudaStream_t s);
+// Copies the status word to the host and syncs `s`; returns the device code.
+int status_fetch(tlr_ctx *ctx, cudaStream_t s, long long *info);
+
+}  // namespace tlr

@@ -1,0 +1,451 @@
+// a3: per-tile low-rank compression at an absolute accuracy tau (Sec. 2-3:
+// the accuracy threshold decides how many singular values are kept).
+//
+// For a dense tile T (m x k) the rank is r = #{sigma_i(T) > tau} and the
+// factors satisfy T ~ U V' with |T - U V'|_2 ~ sigma_{r+1}.  Computing the
+// full SVD of every nb x nb tile would cost O(nb^3); instead, per tile:
+//   1. Y = T Omega (Omega: k x s Gaussian, s = guessed rank + margin) and
+//      four probe columns Y_g = T g (batched GEMMs, whole GPU);
+//   2. Q = orth(Y) by Householder QR with explicit Q (one CTA per tile); the
+//      probes give |T g - Q Q' T g|, an a-posteriori estimate of the range
+//      error (Halko, Martinsson, Tropp 2011, Sec. 4.3);
+//   3. Bt = T' Q (batched GEMM), Bt = Q2 R (Householder QR);
+//   4. one-sided Jacobi SVD of R' = W S Z' (one CTA per tile), so that
+//      T ~ Q Q' T = (Q W) S (Q2 Z)'.
+// If the probe residual exceeds 5% of tau the sample was too small: s is
+// doubled and the tile redone.  Otherwise the singular values S are those of
+// Q Q' T, which differ from those of T by at most the (small) residual, and
+// the rank decision is an exact SVD count.  U = Q (W S)[:, :r], V = Q2 Z[:, :r].
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "compress.cuh"
+#include "gemm.cuh"
+
+namespace tlr {
+
+constexpr int kProbes = 4;
+constexpr int kQrThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+    return t;
+}
+
+struct QrJob {
+    double *A;     // m x s, in place (reflectors below the diagonal)
+    int lda;
+    double *Q;     // m x s output (explicit Q)
+    int ldq;
+    double *R;     // s x s upper output (may be null), ld s
+    const double *probe;  // m x kProbes probe columns (may be null), ld lda
+    double *resid;        // output: max probe residual norm (if probe)
+    int m, s;
+};
+
+// Householder QR of one m x s matrix per CTA with explicit Q.
+__global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrJob *__restrict__ jobs) {
+    __shared__ double red[32];
+    __shared__ double s_tau, s_beta;
+    extern __shared__ double s_dyn[];  // s betas, then s taus, then s probe coefficients
+    const QrJob J = jobs[blockIdx.x];
+    const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kQrThreads / 32;
+    double *betas = s_dyn, *taus = s_dyn + s, *coef = s_dyn + 2 * s;
+    double *A = J.A;
+    const int64_t lda = J.lda;
+    // factorisation
+    for (int c = 0; c < s; ++c) {
+        double *col = A + (int64_t)c * lda;
+        double part = 0.0;
+        for (int r = c + tid; r < m; r += kQrThreads) part += col[r] * col[r];
+        double nrm2 = block_sum(part, red);
+        if (tid == 0) {
+            double alpha = (c < m) ? col[c] : 0.0;
+            double nrm = sqrt(nrm2);
+            if (nrm == 0.0 || c >= m) {
+                s_tau = 0.0;
+                s_beta = 0.0;
+            } else {
+                double beta = -copysign(nrm, alpha);
+                double v0 = alpha - beta;
+                double vtv = nrm2 - alpha * alpha + v0 * v0;
+                s_tau = 2.0 / vtv;
+                s_beta = beta;
+                col[c] = v0;
+            }
+            taus[c] = s_tau;
+            betas[c] = s_beta;
+        }
+        __syncthreads();
+        const double tau = s_tau;
+        if (tau != 0.0) {
+            for (int cc = c + 1 + warp; cc < s; cc += nw) {
+                double *dst = A + (int64_t)cc * lda;
+                double w = 0.0;
+                for (int r = c + lane; r < m; r += 32) w += col[r] * dst[r];
+                w = warp_sum(w) * tau;
+                for (int r = c + lane; r < m; r += 32) dst[r] -= w * col[r];
+            }
+        }
+        __syncthreads();
+    }
+    // R (upper triangle, diagonal = betas)
+    if (J.R) {
+        for (int e = tid; e < s * s; e += kQrThreads) {
+            int i = e % s, j = e / s;
+            double v = 0.0;
+            if (i < j) v = A[(int64_t)j * lda + i];
+            else if (i == j) v = betas[i];
+            J.R[(int64_t)j * s + i] = v;
+        }
+    }
+    // explicit Q = H_0 ... H_{s-1} [I; 0]
+    double *Q = J.Q;
+    const int64_t ldq = J.ldq;
+    for (int e = tid; e < m * s; e += kQrThreads) {
+        int r = e % m, j = e / m;
+        Q[(int64_t)j * ldq + r] = (r == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int c = s - 1; c >= 0; --c) {
+        const double tau = taus[c];
+        if (tau == 0.0) continue;
+        const double *v = A + (int64_t)c * lda;
+        for (int cc = c + warp; cc < s; cc += nw) {
+            double *dst = Q + (int64_t)cc * ldq;
+            double w = 0.0;
+            for (int r = c + lane; r < m; r += 32) w += v[r] * dst[r];
+            w = warp_sum(w) * tau;
+            for (int r = c + lane; r < m; r += 32) dst[r] -= w * v[r];
+        }
+        __syncthreads();
+    }
+    // probe residuals |y - Q Q' y|
+    if (J.probe) {
+        double worst = 0.0;
+        for (int g = 0; g < kProbes; ++g) {
+            const double *y = J.probe + (int64_t)g * lda;
+            for (int u = warp; u < s; u += nw) {
+                const double *q = Q + (int64_t)u * ldq;
+                double w = 0.0;
+                for (int r = lane; r < m; r += 32) w += q[r] * y[r];
+                w = warp_sum(w);
+                if (lane == 0) coef[u] = w;
+            }
+            __syncthreads();
+            double part = 0.0;
+            for (int r = tid; r < m; r += kQrThreads) {
+                double v = y[r];
+                for (int u = 0; u < s; ++u) v -= Q[(int64_t)u * ldq + r] * coef[u];
+                part += v * v;
+            }
+            double r2 = block_sum(part, red);
+            worst = fmax(worst, sqrt(r2));
+            __syncthreads();
+        }
+        if (tid == 0) *J.resid = worst;
+    }
+}
+
+struct SvdJob {
+    const double *R;  // s x s upper (ld s), input
+    double *A;        // s x s work: R' rotated to W S
+    double *Z;        // s x s work: accumulated right rotations
+    double *WS;       // s x s output: W S, columns sorted by S descending
+    double *Zs;       // s x s output: Z, columns sorted alike
+    double *S;        // s singular values (output, descending)
+    int *rank;        // #{S > tau}
+    int s;
+};
+
+// One-sided (Hestenes) Jacobi SVD of R' per CTA: cyclic tournament ordering,
+// one warp per column pair.
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_svd(const SvdJob *__restrict__ jobs, double tau) {
+    __shared__ int s_rot;
+    extern __shared__ double s_dyn[];  // norms (s), order (s ints)
+    const SvdJob J = jobs[blockIdx.x];
+    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / 32;
+    double *A = J.A, *Z = J.Z;
+    for (int e = tid; e < s * s; e += kQrThreads) {
+        int i = e % s, j = e / s;
+        A[(int64_t)j * s + i] = J.R[(int64_t)i * s + j];  // A = R'
+        Z[(int64_t)j * s + i] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int np = s + (s & 1);  // players (pad to even; index s is a bye)
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pr = warp; pr < np / 2; pr += nw) {
+                // round-robin pairing: player 0 fixed, others rotate
+                int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (np - 1);
+                int b = 1 + (np - 2 - pr + round) % (np - 1);
+                if (a >= s || b >= s) continue;
+                int p = min(a, b), q = max(a, b);
+                double *ap = A + (int64_t)p * s, *aq = A + (int64_t)q * s;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int r = lane; r < s; r += 32) {
+                    double x = ap[r], y = aq[r];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int r = lane; r < s; r += 32) {
+                    double x = ap[r], y = aq[r];
+                    ap[r] = c * x - sn * y;
+                    aq[r] = sn * x + c * y;
+                }
+                double *zp = Z + (int64_t)p * s, *zq = Z + (int64_t)q * s;
+                for (int r = lane; r < s; r += 32) {
+                    double x = zp[r], y = zq[r];
+                    zp[r] = c * x - sn * y;
+                    zq[r] = sn * x + c * y;
+                }
+                if (lane == 0) s_rot = 1;
+            }
+            __syncthreads();
+        }
+        if (!s_rot) break;
+        __syncthreads();
+    }
+    // singular values = column norms
+    double *nrm = s_dyn;
+    int *ord = (int *)(s_dyn + s);
+    for (int u = warp; u < s; u += nw) {
+        double v = 0.0;
+        const double *au = A + (int64_t)u * s;
+        for (int r = lane; r < s; r += 32) v += au[r] * au[r];
+        v = warp_sum(v);
+        if (lane == 0) nrm[u] = sqrt(v);
+    }
+    __syncthreads();
+    // descending order, ties by index
+    for (int u = tid; u < s; u += kQrThreads) {
+        int pos = 0;
+        for (int w = 0; w < s; ++w) pos += (nrm[w] > nrm[u]) || (nrm[w] == nrm[u] && w < u);
+        ord[pos] = u;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int r = 0;
+        for (int u = 0; u < s; ++u) r += nrm[u] > tau;
+        *J.rank = r;
+    }
+    for (int e = tid; e < s * s; e += kQrThreads) {
+        int r = e % s, u = e / s, src = ord[u];
+        J.WS[(int64_t)u * s + r] = A[(int64_t)src * s + r];
+        J.Zs[(int64_t)u * s + r] = Z[(int64_t)src * s + r];
+        if (r == 0) J.S[u] = nrm[src];
+    }
+}
+
+__global__ void k_gaussian(double *__restrict__ a, int64_t count, uint64_t seed) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    auto mix = [](uint64_t z) {
+        z += 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    uint64_t u1 = mix(seed ^ (2 * (uint64_t)i)), u2 = mix(seed ^ (2 * (uint64_t)i + 1));
+    double a1 = ((double)(u1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double a2 = (double)(u2 >> 11) * (1.0 / 9007199254740992.0);
+    a[i] = sqrt(-2.0 * log(a1)) * cospi(2.0 * a2);
+}
+
+void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
+    if (ctx->d_omega) return;
+    ctx->omega_rows = kMaxTile;
+    ctx->omega_cols = kMaxSample + kProbes;
+    int64_t cnt = (int64_t)ctx->omega_rows * ctx->omega_cols;
+    TLR_CUDA_TRY(cudaMalloc(&ctx->d_omega, cnt * sizeof(double)));
+    launch(k_gaussian, (unsigned)ceil_div(cnt, 256), 256, 0, s, ctx->d_omega, cnt, 0x243F6A8885A308D3ull);
+    TLR_CHECK_LAUNCH();
+}
+
+void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
+                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile) {
+    ensure_omega(ctx, st);
+    const int nj = (int)jobs.size();
+    ranks.assign(nj, 0);
+    *bad_tile = -1;
+    *nan_tile = -1;
+    std::vector<int> sz(nj), pending;
+    for (int q = 0; q < nj; ++q) {
+        const CompressJob &J = jobs[q];
+        int full = std::min(J.m, J.k);
+        int g = std::max(16, ((J.s_guess + 16 + 7) / 8) * 8);
+        sz[q] = std::min(full, std::min(g, kMaxSample));
+        if (full > 0) pending.push_back(q);
+    }
+    const double *omega = ctx->d_omega;
+    const int ldo = ctx->omega_rows;
+    const double *probe_cols = ctx->d_omega + (int64_t)kMaxSample * ldo;
+    while (!pending.empty()) {
+        // workspace offsets (doubles)
+        std::vector<int64_t> oY(pending.size()), oQ(pending.size()), oB(pending.size()), oQ2(pending.size()),
+            oR(pending.size()), oA(pending.size()), oZ(pending.size()), oS(pending.size()),
+            oWS(pending.size()), oZs(pending.size());
+        int64_t tot = 0;
+        for (size_t u = 0; u < pending.size(); ++u) {
+            const CompressJob &J = jobs[pending[u]];
+            int s = sz[pending[u]];
+            auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
+            oY[u] = take((int64_t)J.m * (s + kProbes));
+            oQ[u] = take((int64_t)J.m * s);
+            oB[u] = take((int64_t)J.k * s);
+            oQ2[u] = take((int64_t)J.k * s);
+            oR[u] = take((int64_t)s * s);
+            oA[u] = take((int64_t)s * s);
+            oZ[u] = take((int64_t)s * s);
+            oS[u] = take(s);
+            oWS[u] = take((int64_t)s * s);
+            oZs[u] = take((int64_t)s * s);
+        }
+        size_t np = pending.size();
+        DevBuf ws(tot * sizeof(double) + np * (sizeof(double) + sizeof(int)) + 256, st);
+        double *W = ws.as<double>();
+        double *d_resid = W + tot;
+        int *d_rank = (int *)(d_resid + np);
+        // 1. Y = T [Omega_s | G]
+        std::vector<GemmProb> g1;
+        for (size_t u = 0; u < np; ++u) {
+            const CompressJob &J = jobs[pending[u]];
+            int s = sz[pending[u]];
+            GemmProb a{};
+            a.A = J.T; a.lda = J.ldt; a.m = J.m; a.k = J.k;
+            a.B = omega; a.ldb = ldo; a.n = s;
+            a.C = W + oY[u]; a.ldc = J.m;
+            g1.push_back(a);
+            GemmProb b = a;
+            b.B = probe_cols; b.n = kProbes;
+            b.C = W + oY[u] + (int64_t)J.m * s;
+            g1.push_back(b);
+        }
+        gemm_batched(ctx, st, false, false, g1, 1.0, 0.0);
+        // 2. Q = orth(Y_s), probe residuals
+        std::vector<QrJob> q1(np);
+        int smax = 0;
+        for (size_t u = 0; u < np; ++u) {
+            const CompressJob &J = jobs[pending[u]];
+            int s = sz[pending[u]];
+            smax = std::max(smax, s);
+            q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, W + oY[u] + (int64_t)J.m * s,
+                          d_resid + u, J.m, s};
+        }
+        auto *dq1 = (const QrJob *)stage_push(ctx, q1.data(), np * sizeof(QrJob), st);
+        size_t shq = (size_t)3 * smax * sizeof(double);
+        if (shq > 48 * 1024)
+            TLR_CUDA_TRY(cudaFuncSetAttribute(k_house_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shq));
+        launch(k_house_qr, (unsigned)np, kQrThreads, shq, st, dq1);
+        TLR_CHECK_LAUNCH();
+        // 3. Bt = T' Q, Bt = Q2 R
+        std::vector<GemmProb> g2;
+        for (size_t u = 0; u < np; ++u) {
+            const CompressJob &J = jobs[pending[u]];
+            int s = sz[pending[u]];
+            GemmProb a{};
+            a.A = J.T; a.lda = J.ldt; a.m = J.k; a.k = J.m;
+            a.B = W + oQ[u]; a.ldb = J.m; a.n = s;
+            a.C = W + oB[u]; a.ldc = J.k;
+            g2.push_back(a);
+        }
+        gemm_batched(ctx, st, true, false, g2, 1.0, 0.0);
+        std::vector<QrJob> q2(np);
+        for (size_t u = 0; u < np; ++u) {
+            const CompressJob &J = jobs[pending[u]];
+            int s = sz[pending[u]];
+            q2[u] = QrJob{W + oB[u], J.k, W + oQ2[u], J.k, W + oR[u], nullptr, nullptr, J.k, s};
+        }
+        auto *dq2 = (const QrJob *)stage_push(ctx, q2.data(), np * sizeof(QrJob), st);
+        launch(k_house_qr, (unsigned)np, kQrThreads, shq, st, dq2);
+        TLR_CHECK_LAUNCH();
+        // 4. SVD of R'
+        std::vector<SvdJob> sv(np);
+        for (size_t u = 0; u < np; ++u) {
+            int s = sz[pending[u]];
+            sv[u] = SvdJob{W + oR[u], W + oA[u], W + oZ[u], W + oWS[u], W + oZs[u], W + oS[u], d_rank + u, s};
+        }
+        auto *dsv = (const SvdJob *)stage_push(ctx, sv.data(), np * sizeof(SvdJob), st);
+        size_t shs = (size_t)smax * (sizeof(double) + sizeof(int));
+        if (shs > 48 * 1024)
+            TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shs));
+        launch(k_jacobi_svd, (unsigned)np, kQrThreads, shs, st, dsv, tau);
+        TLR_CHECK_LAUNCH();
+        // decisions on the host
+        std::vector<double> h_resid(np);
+        std::vector<int> h_rank(np);
+        TLR_CUDA_TRY(cudaMemcpyAsync(h_resid.data(), d_resid, np * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+        TLR_CUDA_TRY(cudaStreamSynchronize(st));
+        ctx->stage_off = 0;
+        std::vector<int> next;
+        std::vector<GemmProb> gu, gv;
+        for (size_t u = 0; u < np; ++u) {
+            int q = pending[u];
+            const CompressJob &J = jobs[q];
+            int s = sz[q];
+            int full = std::min(J.m, J.k);
+            if (!std::isfinite(h_resid[u])) {
+                if (*nan_tile < 0) *nan_tile = J.tile_id;
+                continue;
+            }
+            bool conv = (s >= full) || (h_resid[u] <= 0.05 * tau);
+            if (!conv) {
+                if (s >= kMaxSample || s >= maxrank + 64) {
+                    if (*bad_tile < 0) *bad_tile = J.tile_id;
+                    continue;
+                }
+                sz[q] = std::min(full, std::min(2 * s, kMaxSample));
+                next.push_back(q);
+                continue;
+            }
+            int r = h_rank[u];
+            if (r > maxrank) {
+                if (*bad_tile < 0) *bad_tile = J.tile_id;
+                continue;
+            }
+            ranks[q] = r;
+            if (r == 0) continue;
+            GemmProb a{};
+            a.A = W + oQ[u]; a.lda = J.m; a.m = J.m; a.k = s;
+            a.B = W + oWS[u]; a.ldb = s; a.n = r;
+            a.C = J.U; a.ldc = J.ldu;
+            gu.push_back(a);
+            GemmProb b{};
+            b.A = W + oQ2[u]; b.lda = J.k; b.m = J.k; b.k = s;
+            b.B = W + oZs[u]; b.ldb = s; b.n = r;
+            b.C = J.V; b.ldc = J.ldv;
+            gv.push_back(b);
+        }
+        gemm_batched(ctx, st, false, false, gu, 1.0, 0.0);
+        gemm_batched(ctx, st, false, false, gv, 1.0, 0.0);
+        // the workspace is released stream-ordered after these GEMMs
+        pending.swap(next);
+    }
+}
+
+}  // namespace tlr

@@ -1,0 +1,31 @@
+// Dense FP64 tile operations (declarations; see dense.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace tlr {
+
+// One right-hand side matrix of a batched triangular solve: m x ncols, column
+// major with leading dimension ld, solved in place.
+struct RhsDesc {
+    double *B;
+    int ncols;
+    int ld;
+};
+
+// In-place Cholesky A = L L' of the m x m matrix A (lower triangle used and
+// returned, strict upper triangle zeroed).  A non-positive pivot sets the
+// context status to TLR_ERR_NOT_SPD with info = row_base + local row.
+void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long long row_base);
+
+// B <- L^-1 B for every right-hand side matrix (L lower triangular m x m).
+void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int m,
+                     const std::vector<RhsDesc> &rhs);
+
+// acc[0] += sum_r log A[r, r] (skipped once the status word holds an error).
+void diag_logsum(cudaStream_t s, const double *A, int lda, int m, double *acc, const DevStatus *st);
+
+// acc[0] += |v|^2
+void sumsq(cudaStream_t s, const double *v, int m, double *acc);
+
+}  // namespace tlr

@@ -1,0 +1,61 @@
+// Batched FP64 GEMM launchers and the descriptor staging buffers of a context.
+#include <cstring>
+
+#include "gemm.cuh"
+
+namespace tlr {
+
+void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s) {
+    size_t need = (bytes + 255) & ~(size_t)255;
+    if (need > ctx->stage_cap) throw make_error(TLR_ERR_ARG, "descriptor batch too large (%zu bytes)", bytes);
+    if (ctx->stage_off + need > ctx->stage_cap) {
+        // every reader of the staging area runs on `s` or on the aux stream
+        TLR_CUDA_TRY(cudaStreamSynchronize(s));
+        TLR_CUDA_TRY(cudaStreamSynchronize(ctx->aux));
+        ctx->stage_off = 0;
+    }
+    char *h = ctx->h_stage + ctx->stage_off;
+    char *d = ctx->d_stage + ctx->stage_off;
+    std::memcpy(h, data, bytes);
+    TLR_CUDA_TRY(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
+    ctx->stage_off += need;
+    return d;
+}
+
+template <class Epi>
+static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                   double alpha, const Epi &epi) {
+    if (probs.empty()) return;
+    std::vector<int> off(probs.size() + 1, 0);
+    for (size_t b = 0; b < probs.size(); ++b) {
+        const GemmProb &p = probs[b];
+        int tiles = (p.m > 0 && p.n > 0) ? (int)(ceil_div(p.m, kGemmBM) * ceil_div(p.n, kGemmBN)) : 0;
+        off[b + 1] = off[b] + tiles;
+    }
+    int total = off.back();
+    if (total == 0) return;
+    auto *dp = (const GemmProb *)stage_push(ctx, probs.data(), probs.size() * sizeof(GemmProb), s);
+    auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
+    int np = (int)probs.size();
+    if (!ta && !tb) launch(k_gemm_f64<false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else if (!ta && tb) launch(k_gemm_f64<false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else if (ta && !tb) launch(k_gemm_f64<true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else launch(k_gemm_f64<true, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    TLR_CHECK_LAUNCH();
+}
+
+void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                  double alpha, double beta) {
+    launch_gemm(ctx, s, ta, tb, probs, alpha, EpiLinear{beta});
+}
+
+void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
+                         double alpha, const double *xy, int64_t n, const MaternParams &P) {
+    EpiMatern e;
+    e.xy = xy;
+    e.n = n;
+    e.P = P;
+    launch_gemm(ctx, s, false, tb, probs, alpha, e);
+}
+
+}  // namespace tlr

@@ -1,0 +1,393 @@
+// a4 + a5: TLR Cholesky factorisation, forward solve and log-determinant.
+//
+// Left-looking tile Cholesky (the tile DAG of Sec. 2 executed column by
+// column on one GPU).  For column j, with L_ik = U_ik V_ik' for k < j:
+//   T_ij = A_ij - sum_{k<j} L_ik L_jk'          (i >= j)
+//        = A_ij - P_ij Q_j',  Q_j = [U_j0 | ... | U_j,j-1],
+//                             P_ij = [U_i0 (V_i0' V_j0) | ... ].
+// The update of the whole column panel is ONE batched GEMM (all i share Q_j);
+// in the likelihood path A_ij is never stored: the GEMM epilogue evaluates
+// the Matern covariance of the two locations (Eq. 4.2) and subtracts the
+// product, so generation and Schur update are fused.  Then
+//   L_jj = chol(T_jj)                  (dense FP64),
+//   T_ij ~ U V' at accuracy tau        (recompression of the updated tile),
+//   V <- L_jj^-1 V                     (so that L_ij = T_ij L_jj^-T = U V').
+// Each updated tile is compressed once, after all its updates (HiCMA-style
+// codes recompress after every single low-rank update instead).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "compress.cuh"
+#include "dense.cuh"
+#include "gemm.cuh"
+#include "matern.cuh"
+#include "tlr_internal.cuh"
+
+namespace tlr {
+
+__global__ void k_copy_batched(const CopyDesc *__restrict__ d) {
+    const CopyDesc c = d[blockIdx.x];
+    for (int64_t e = threadIdx.x; e < (int64_t)c.m * c.n; e += blockDim.x) {
+        int r = (int)(e % c.m), col = (int)(e / c.m);
+        c.dst[(int64_t)col * c.ldd + r] = c.src ? c.src[(int64_t)col * c.lds + r] : 0.0;
+    }
+}
+
+void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &descs) {
+    std::vector<CopyDesc> act;
+    for (const CopyDesc &c : descs)
+        if (c.m > 0 && c.n > 0) act.push_back(c);
+    if (act.empty()) return;
+    auto *dd = (const CopyDesc *)stage_push(ctx, act.data(), act.size() * sizeof(CopyDesc), s);
+    launch(k_copy_batched, (unsigned)act.size(), 256, 0, s, dd);
+    TLR_CHECK_LAUNCH();
+}
+
+static inline double *Uslot(tlr_mat *M, int i, int j) {
+    return M->U + off_index(i, j) * (int64_t)M->nb * M->maxrank;
+}
+static inline double *Vslot(tlr_mat *M, int i, int j) {
+    return M->V + off_index(i, j) * (int64_t)M->nb * M->maxrank;
+}
+static inline const double *Uslot(const tlr_mat *M, int i, int j) {
+    return M->U + off_index(i, j) * (int64_t)M->nb * M->maxrank;
+}
+static inline const double *Vslot(const tlr_mat *M, int i, int j) {
+    return M->V + off_index(i, j) * (int64_t)M->nb * M->maxrank;
+}
+
+void upload_ranks(tlr_mat *M, cudaStream_t s) {
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    TLR_CUDA_TRY(cudaMemcpy(M->ranks, M->h_ranks.data(), M->h_ranks.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice));
+}
+
+void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const double *xy,
+            const MaternParams *P, double tau, FactorStats *stats, long long *info) {
+    const int nt = M->nt, nb = M->nb;
+    const int64_t n = M->n;
+    *info = -1;
+    std::vector<int32_t> &R = M->h_ranks;  // r_ij of the factor, filled column by column
+    std::vector<int32_t> prev = R;         // previous ranks (input ranks for FactorMode::Tlr)
+    bool have_prev = !prev.empty() && prev.size() == (size_t)nt * nt;
+    if (mode == FactorMode::Tlr && !have_prev) throw make_error(TLR_ERR_ARG, "matrix holds no compressed input");
+    int prof_used = 0;
+    R.assign((size_t)nt * nt, 0);
+    for (int t = 0; t < nt; ++t) R[(size_t)t * nt + t] = tile_rows(n, nb, t);
+    auto r_of = [&](int i, int k) { return (int)R[(size_t)i * nt + k]; };
+    DevBuf panel((size_t)nt * nb * nb * sizeof(double), st);
+    double *Tp = panel.as<double>();
+
+    for (int j = 0; j < nt; ++j) {
+        const int mj = tile_rows(n, nb, j);
+        const int64_t Mp = (int64_t)(nt - j) * nb;  // panel leading dimension
+        // --- Q_j = [U_j0 | ... ] and offsets
+        std::vector<int> off(j + 1, 0);
+        for (int k = 0; k < j; ++k) off[k + 1] = off[k] + r_of(j, k);
+        const int Rj = off[j];
+        DevBuf qbuf((size_t)nb * std::max(Rj, 1) * sizeof(double), st);
+        DevBuf pbuf((size_t)Mp * std::max(Rj, 1) * sizeof(double), st);
+        double *Qj = qbuf.as<double>(), *Pj = pbuf.as<double>();
+        if (Rj > 0) {
+            std::vector<CopyDesc> cq;
+            for (int k = 0; k < j; ++k)
+                if (r_of(j, k) > 0)
+                    cq.push_back(CopyDesc{Uslot(M, j, k), nb, Qj + (int64_t)off[k] * nb, nb, mj, r_of(j, k)});
+            copy_batched(ctx, st, cq);
+            TLR_CUDA_TRY(cudaMemsetAsync(Pj, 0, (size_t)Mp * Rj * sizeof(double), st));
+            // W_ik = V_ik' V_jk, then P block (i, k) = U_ik W_ik
+            std::vector<int64_t> woff;
+            int64_t wtot = 0;
+            struct Pair { int i, k; int64_t w; };
+            std::vector<Pair> pairs;
+            for (int i = j; i < nt; ++i)
+                for (int k = 0; k < j; ++k)
+                    if (r_of(i, k) > 0 && r_of(j, k) > 0) {
+                        pairs.push_back(Pair{i, k, wtot});
+                        wtot += (int64_t)r_of(i, k) * r_of(j, k);
+                    }
+            DevBuf wbuf((size_t)std::max<int64_t>(wtot, 1) * sizeof(double), st);
+            double *Wb = wbuf.as<double>();
+            std::vector<GemmProb> gw, gp;
+            for (const Pair &pp : pairs) {
+                int rik = r_of(pp.i, pp.k), rjk = r_of(j, pp.k), mk = tile_rows(n, nb, pp.k);
+                GemmProb a{};
+                a.A = Vslot(M, pp.i, pp.k); a.lda = nb; a.m = rik; a.k = mk;
+                a.B = Vslot(M, j, pp.k); a.ldb = nb; a.n = rjk;
+                a.C = Wb + pp.w; a.ldc = rik;
+                gw.push_back(a);
+                GemmProb b{};
+                b.A = Uslot(M, pp.i, pp.k); b.lda = nb; b.m = tile_rows(n, nb, pp.i); b.k = rik;
+                b.B = Wb + pp.w; b.ldb = rik; b.n = rjk;
+                b.C = Pj + (int64_t)off[pp.k] * Mp + (int64_t)(pp.i - j) * nb; b.ldc = (int)Mp;
+                gp.push_back(b);
+                stats->flops += 2.0 * mk * rik * rjk + 2.0 * b.m * rik * rjk;
+            }
+            gemm_batched(ctx, st, true, false, gw, 1.0, 0.0);
+            gemm_batched(ctx, st, false, false, gp, 1.0, 0.0);
+        }
+        // --- panel: T_{:,j} = A_{:,j} - P_j Q_j'
+        const int64_t rows_valid = n - (int64_t)j * nb;
+        if (mode == FactorMode::Matern) {
+            GemmProb g{};
+            g.A = Pj; g.lda = (int)Mp; g.m = (int)Mp; g.k = Rj;
+            g.B = Qj; g.ldb = nb; g.n = mj;
+            g.C = Tp; g.ldc = (int)Mp;
+            g.ri0 = (int64_t)j * nb; g.ci0 = (int64_t)j * nb;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ctx->profile) {
+                profile_events(ctx, prof_used + 2);
+                e0 = ctx->prof_events[prof_used];
+                e1 = ctx->prof_events[prof_used + 1];
+                prof_used += 2;
+                TLR_CUDA_TRY(cudaEventRecord(e0, st));
+            }
+            gemm_batched_matern(ctx, st, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P);
+            if (ctx->profile) TLR_CUDA_TRY(cudaEventRecord(e1, st));
+            stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
+            stats->matern_entries += (double)rows_valid * mj;
+            stats->panel_launches += 1;
+        } else {
+            // densify the compressed input column: T_jj = D_jj, T_ij = U_ij V_ij'
+            TLR_CUDA_TRY(cudaMemsetAsync(Tp, 0, (size_t)Mp * nb * sizeof(double), st));
+            copy_batched(ctx, st, {CopyDesc{M->D + (int64_t)j * nb * nb, nb, Tp, (int)Mp, mj, mj}});
+            std::vector<GemmProb> gd;
+            for (int i = j + 1; i < nt; ++i) {
+                int rin = prev[(size_t)i * nt + j];
+                if (rin <= 0) continue;
+                GemmProb a{};
+                a.A = Uslot(M, i, j); a.lda = nb; a.m = tile_rows(n, nb, i); a.k = rin;
+                a.B = Vslot(M, i, j); a.ldb = nb; a.n = mj;
+                a.C = Tp + (int64_t)(i - j) * nb; a.ldc = (int)Mp;
+                gd.push_back(a);
+            }
+            gemm_batched(ctx, st, false, true, gd, 1.0, 0.0);
+            if (Rj > 0) {
+                GemmProb g{};
+                g.A = Pj; g.lda = (int)Mp; g.m = (int)Mp; g.k = Rj;
+                g.B = Qj; g.ldb = nb; g.n = mj;
+                g.C = Tp; g.ldc = (int)Mp;
+                gemm_batched(ctx, st, false, true, std::vector<GemmProb>{g}, -1.0, 1.0);
+            }
+            stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
+        }
+        stats->flops += 2.0 * (double)rows_valid * mj * Rj;
+        // --- L_jj = chol(T_jj) into D_j
+        double *Dj = M->D + (int64_t)j * nb * nb;
+        copy_batched(ctx, st, {CopyDesc{Tp, (int)Mp, Dj, nb, mj, mj}});
+        potrf_dense(ctx, st, Dj, nb, mj, (long long)j * nb);
+        stats->flops += (double)mj * mj * mj / 3.0;
+        // --- compress T_ij, i > j
+        std::vector<CompressJob> jobs;
+        for (int i = j + 1; i < nt; ++i) {
+            CompressJob c{};
+            c.T = Tp + (int64_t)(i - j) * nb;
+            c.ldt = (int)Mp;
+            c.m = tile_rows(n, nb, i);
+            c.k = mj;
+            c.U = Uslot(M, i, j);
+            c.ldu = nb;
+            c.V = Vslot(M, i, j);
+            c.ldv = nb;
+            c.s_guess = have_prev ? prev[(size_t)i * nt + j] : 32;
+            c.tile_id = (long long)i * nt + j;
+            jobs.push_back(c);
+        }
+        if (!jobs.empty()) {
+            std::vector<int> rk;
+            long long bad = -1, nan = -1;
+            compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan);
+            long long sinfo = -1;
+            int sc = status_fetch(ctx, st, &sinfo);
+            if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
+            if (nan >= 0) {
+                *info = nan;
+                throw make_error(TLR_ERR_NAN, "tile (%lld, %lld) holds non-finite values", nan / nt, nan % nt);
+            }
+            if (bad >= 0) {
+                *info = bad;
+                throw make_error(TLR_ERR_RANK, "tile (%lld, %lld) needs rank > maxrank %d",
+                                 bad / nt, bad % nt, M->maxrank);
+            }
+            for (size_t q = 0; q < jobs.size(); ++q) {
+                int i = j + 1 + (int)q;
+                R[(size_t)i * nt + j] = R[(size_t)j * nt + i] = rk[q];
+                double m = jobs[q].m, k = jobs[q].k;
+                stats->flops += 8.0 * m * k * (rk[q] + 8);  // sampling + projection GEMMs (approx.)
+            }
+            // --- V_ij <- L_jj^-1 V_ij
+            std::vector<RhsDesc> rhs;
+            for (int i = j + 1; i < nt; ++i)
+                if (r_of(i, j) > 0) rhs.push_back(RhsDesc{Vslot(M, i, j), r_of(i, j), nb});
+            trsm_left_lower(ctx, st, Dj, nb, mj, rhs);
+            for (const RhsDesc &d : rhs) stats->flops += (double)mj * mj * d.ncols;
+        } else {
+            long long sinfo = -1;
+            int sc = status_fetch(ctx, st, &sinfo);
+            if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
+        }
+    }
+    upload_ranks(M, st);
+    if (ctx->profile) {
+        float tot = 0.f;
+        for (int e = 0; e < prof_used; e += 2) {
+            float ms = 0.f;
+            TLR_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_events[e], ctx->prof_events[e + 1]));
+            tot += ms;
+        }
+        stats->gemm_ms += tot;
+    }
+}
+
+// y = L^-1 z tile by tile; acc[0] += sum log L_ii, acc[1] += |y|^2.
+void forward_solve(tlr_ctx *ctx, cudaStream_t st, const tlr_mat *M, const double *z, double *y,
+                   double *acc) {
+    const int nt = M->nt, nb = M->nb;
+    const int64_t n = M->n;
+    auto r_of = [&](int i, int k) { return (int)M->h_ranks[(size_t)i * nt + k]; };
+    if (y != z) TLR_CUDA_TRY(cudaMemcpyAsync(y, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int maxR = 0;
+    for (int j = 0; j < nt; ++j) {
+        int Rj = 0;
+        for (int k = 0; k < j; ++k) Rj += r_of(j, k);
+        maxR = std::max(maxR, Rj);
+    }
+    DevBuf cbuf((size_t)std::max(maxR, 1) * sizeof(double), st);
+    double *c = cbuf.as<double>();
+    for (int j = 0; j < nt; ++j) {
+        const int mj = tile_rows(n, nb, j);
+        double *yj = y + (int64_t)j * nb;
+        std::vector<GemmProb> gc, gu;
+        int o = 0;
+        for (int k = 0; k < j; ++k) {
+            int r = r_of(j, k);
+            if (r <= 0) continue;
+            GemmProb a{};  // c_k = V_jk' y_k
+            a.A = Vslot(M, j, k); a.lda = nb; a.m = r; a.k = tile_rows(n, nb, k);
+            a.B = y + (int64_t)k * nb; a.ldb = nb; a.n = 1;
+            a.C = c + o; a.ldc = r;
+            gc.push_back(a);
+            o += r;
+        }
+        if (o > 0) {
+            gemm_batched(ctx, st, true, false, gc, 1.0, 0.0);
+            // y_j -= [U_j0 ...] c, accumulated one k at a time (distinct outputs per launch)
+            o = 0;
+            for (int k = 0; k < j; ++k) {
+                int r = r_of(j, k);
+                if (r <= 0) continue;
+                GemmProb b{};
+                b.A = Uslot(M, j, k); b.lda = nb; b.m = mj; b.k = r;
+                b.B = c + o; b.ldb = r; b.n = 1;
+                b.C = yj; b.ldc = nb;
+                gemm_batched(ctx, st, false, false, std::vector<GemmProb>{b}, -1.0, 1.0);
+                o += r;
+            }
+        }
+        const double *Dj = M->D + (int64_t)j * nb * nb;
+        trsm_left_lower(ctx, st, Dj, nb, mj, {RhsDesc{yj, 1, nb}});
+        diag_logsum(st, Dj, nb, mj, acc, ctx->d_status);
+        sumsq(st, yj, mj, acc + 1);
+    }
+}
+
+// z = L w
+void lmul(tlr_ctx *ctx, cudaStream_t st, const tlr_mat *M, const double *w, double *z) {
+    const int nt = M->nt, nb = M->nb;
+    const int64_t n = M->n;
+    auto r_of = [&](int i, int k) { return (int)M->h_ranks[(size_t)i * nt + k]; };
+    std::vector<GemmProb> gd;
+    for (int i = 0; i < nt; ++i) {
+        GemmProb a{};
+        a.A = M->D + (int64_t)i * nb * nb; a.lda = nb; a.m = tile_rows(n, nb, i); a.k = a.m;
+        a.B = w + (int64_t)i * nb; a.ldb = nb; a.n = 1;
+        a.C = z + (int64_t)i * nb; a.ldc = nb;
+        gd.push_back(a);
+    }
+    gemm_batched(ctx, st, false, false, gd, 1.0, 0.0);
+    // c_ik = V_ik' w_k for all i > k
+    int64_t tot = 0;
+    std::vector<int64_t> co((size_t)nt * nt, -1);
+    for (int i = 0; i < nt; ++i)
+        for (int k = 0; k < i; ++k)
+            if (r_of(i, k) > 0) { co[(size_t)i * nt + k] = tot; tot += r_of(i, k); }
+    if (tot == 0) return;
+    DevBuf cbuf((size_t)tot * sizeof(double), st);
+    double *c = cbuf.as<double>();
+    std::vector<GemmProb> gc;
+    for (int i = 0; i < nt; ++i)
+        for (int k = 0; k < i; ++k) {
+            int r = r_of(i, k);
+            if (r <= 0) continue;
+            GemmProb a{};
+            a.A = Vslot(M, i, k); a.lda = nb; a.m = r; a.k = tile_rows(n, nb, k);
+            a.B = w + (int64_t)k * nb; a.ldb = nb; a.n = 1;
+            a.C = c + co[(size_t)i * nt + k]; a.ldc = r;
+            gc.push_back(a);
+        }
+    gemm_batched(ctx, st, true, false, gc, 1.0, 0.0);
+    for (int k = 0; k < nt; ++k) {
+        std::vector<GemmProb> gu;
+        for (int i = k + 1; i < nt; ++i) {
+            int r = r_of(i, k);
+            if (r <= 0) continue;
+            GemmProb b{};
+            b.A = Uslot(M, i, k); b.lda = nb; b.m = tile_rows(n, nb, i); b.k = r;
+            b.B = c + co[(size_t)i * nt + k]; b.ldb = r; b.n = 1;
+            b.C = z + (int64_t)i * nb; b.ldc = nb;
+            gu.push_back(b);
+        }
+        gemm_batched(ctx, st, false, false, gu, 1.0, 1.0);
+    }
+}
+
+// Compress packed dense tiles (tlr_generate layout) into M.
+void compress_packed(tlr_ctx *ctx, cudaStream_t st, const double *tiles, tlr_mat *M, double tau,
+                     long long *info) {
+    const int nt = M->nt, nb = M->nb;
+    const int64_t n = M->n;
+    std::vector<int32_t> prev = M->h_ranks;
+    bool have_prev = prev.size() == (size_t)nt * nt;
+    auto tile = [&](int i, int j) { return tiles + ((int64_t)i * (i + 1) / 2 + j) * nb * nb; };
+    std::vector<CopyDesc> cd;
+    for (int t = 0; t < nt; ++t)
+        cd.push_back(CopyDesc{tile(t, t), nb, M->D + (int64_t)t * nb * nb, nb, nb, nb});
+    copy_batched(ctx, st, cd);
+    std::vector<CompressJob> jobs;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < i; ++j) {
+            CompressJob c{};
+            c.T = tile(i, j); c.ldt = nb;
+            c.m = tile_rows(n, nb, i); c.k = tile_rows(n, nb, j);
+            c.U = Uslot(M, i, j); c.ldu = nb;
+            c.V = Vslot(M, i, j); c.ldv = nb;
+            c.s_guess = have_prev ? prev[(size_t)i * nt + j] : 32;
+            c.tile_id = (long long)i * nt + j;
+            jobs.push_back(c);
+        }
+    std::vector<int32_t> &R = M->h_ranks;
+    R.assign((size_t)nt * nt, 0);
+    for (int t = 0; t < nt; ++t) R[(size_t)t * nt + t] = tile_rows(n, nb, t);
+    *info = -1;
+    if (!jobs.empty()) {
+        std::vector<int> rk;
+        long long bad = -1, nan = -1;
+        compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan);
+        if (nan >= 0) {
+            *info = nan;
+            throw make_error(TLR_ERR_NAN, "tile (%lld, %lld) holds non-finite values", nan / nt, nan % nt);
+        }
+        if (bad >= 0) {
+            *info = bad;
+            throw make_error(TLR_ERR_RANK, "tile (%lld, %lld) needs rank > maxrank %d", bad / nt,
+                             bad % nt, M->maxrank);
+        }
+        size_t q = 0;
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < i; ++j, ++q) R[(size_t)i * nt + j] = R[(size_t)j * nt + i] = rk[q];
+    }
+    upload_ranks(M, st);
+}
+
+}  // namespace tlr

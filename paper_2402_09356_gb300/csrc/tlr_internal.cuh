@@ -1,0 +1,56 @@
+// Internal interfaces between the TLR driver (tlr.cu) and the C ABI (api.cu).
+#pragma once
+
+#include "common.cuh"
+#include "matern.cuh"
+
+namespace tlr {
+
+// A batched matrix copy: dst (m x n, ld ldd) = src (ld lds), or 0 if src is null.
+struct CopyDesc {
+    const double *src;
+    int lds;
+    double *dst;
+    int ldd;
+    int m, n;
+};
+
+void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &descs);
+
+enum class FactorMode {
+    Matern,  // tiles generated from the Matern kernel inside the panel update (likelihood path)
+    Tlr      // tiles taken from the compressed input held in the matrix (tlr_potrf)
+};
+
+struct FactorStats {
+    double flops = 0.0;           // floating-point operations counted from the rank map
+    double gemm_flops = 0.0;      // of which: panel update GEMMs
+    double matern_entries = 0.0;  // covariance entries evaluated in the panel epilogues
+    int panel_launches = 0;
+    float gemm_ms = 0.f;          // device time of the panel GEMMs (when ctx->profile)
+};
+
+void profile_events(tlr_ctx *ctx, int count);
+void upload_ranks(tlr_mat *M, cudaStream_t s);
+void factor(tlr_ctx *ctx, cudaStream_t s, tlr_mat *M, FactorMode mode, const double *xy,
+            const MaternParams *P, double tau, FactorStats *stats, long long *info);
+void forward_solve(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *z, double *y,
+                   double *acc);
+void lmul(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *w, double *z);
+void compress_packed(tlr_ctx *ctx, cudaStream_t s, const double *tiles, tlr_mat *M, double tau,
+                     long long *info);
+
+// ordering (order.cu)
+void order_sfc(const double *xy, int64_t n, int method, uint64_t seed, int64_t *perm, uint32_t *codes,
+               cudaStream_t s);
+void order_kdtree(const double *xy, int64_t n, int64_t *perm, cudaStream_t s);
+void order_maxmin(const double *xy, int64_t n, int64_t *perm, cudaStream_t s, int num_sms);
+void order_identity(int64_t n, int64_t *perm, cudaStream_t s);
+void permute_xy(const double *xy, const int64_t *perm, int64_t n, int quantize, double *out, cudaStream_t s);
+void gather(const int64_t *perm, const double *src, int64_t n, double *dst, cudaStream_t s);
+
+// covariance (matern.cu)
+void generate_tiles(const double *xy, int64_t n, int nb, const MaternParams &P, double *tiles, cudaStream_t s);
+void matern_vec(const double *d, int64_t m, const MaternParams &P, double *out, cudaStream_t s);
+
+}  // namespace tlr

@@ -16,3 +16,19 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """A library context on cuda:0 (GPU tests only)."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    from paper_2402_09356_gb300 import build as tlr_build
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    tlr_build.build()
+    torch.cuda.init()
+    c = tlr.Context(0)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
