@@ -156,6 +156,7 @@ def run_gpu(args):
     tlr.tlr_profile(ctx, True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     results, gemm_ms, gemm_flops, panel_launches = [], 0.0, 0.0, 0
+    stage_ms = {k: 0.0 for k in tlr.STAGES}
     clocks = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -171,6 +172,8 @@ def run_gpu(args):
         gemm_ms += prof["gemm_ms"]
         gemm_flops += prof["gemm_flops"]
         panel_launches += prof["panel_launches"]
+        for k, v in tlr.tlr_stage_times(ctx).items():
+            stage_ms[k] += v / args.steps
         results.append(r)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -233,6 +236,7 @@ def run_gpu(args):
                    "theta_walk": "log-space, scale 0.05/step, seed 7",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "stage_ms_per_step": stage_ms,
         "loglik_last": results[-1]["loglik"],
         "max_rank_last": results[-1]["max_rank"],
         "mean_rank_last": results[-1]["mean_rank"],

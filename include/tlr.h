@@ -234,6 +234,13 @@ int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_t
 int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops,
                 double *matern_entries, int *panel_launches);
 
+/* Per-stage device time (ms) of the last profiled tlr_loglik factorisation,
+ * summed over all columns, written to ms[0..4]: building the low-rank update
+ * operands, the panel update GEMM (with Matern generation), the dense POTRF of
+ * the diagonal tile, the compression of the off-diagonal tiles, and the TRSM
+ * of their V factors.  Errors: TLR_ERR_ARG. */
+int tlr_stage_times(tlr_ctx *ctx, double *ms);
+
 /* ---- MLE (Sec. 5.1: derivative-free, bound-constrained) ------------------ */
 
 /* Maximise l(theta) over lo <= theta <= hi from theta0 with the Nelder-Mead

@@ -90,6 +90,7 @@ _SIGS = {
     "tlr_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int)]),
+    "tlr_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(tlr_theta),
@@ -352,6 +353,15 @@ def tlr_profile(ctx: Context, enable: bool = True) -> dict:
     ctx.check(load_library().tlr_profile(ctx.h, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(fl),
                                          ctypes.byref(me), ctypes.byref(pl)))
     return {"gemm_ms": ms.value, "gemm_flops": fl.value, "matern_entries": me.value, "panel_launches": pl.value}
+
+
+STAGES = ("build", "panel", "potrf", "compress", "trsm")
+
+
+def tlr_stage_times(ctx: Context) -> dict:
+    a = (ctypes.c_double * 5)()
+    ctx.check(load_library().tlr_stage_times(ctx.h, a))
+    return {k: a[i] for i, k in enumerate(STAGES)}
 
 
 def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1e-9, max_iter: int = 500,

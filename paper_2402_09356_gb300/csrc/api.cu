@@ -380,6 +380,7 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     ctx->last_gemm_flops = st.gemm_flops;
     ctx->last_matern_entries = st.matern_entries;
     ctx->last_panel_launches = st.panel_launches;
+    for (int k = 0; k < kStages; ++k) ctx->last_stage_ms[k] = st.stage_ms[k];
 }
 
 int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
@@ -395,6 +396,12 @@ int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops, d
     if (gemm_flops) *gemm_flops = ctx->last_gemm_flops;
     if (matern_entries) *matern_entries = ctx->last_matern_entries;
     if (panel_launches) *panel_launches = ctx->last_panel_launches;
+    return TLR_OK;
+}
+
+int tlr_stage_times(tlr_ctx *ctx, double *ms) {
+    if (!ctx || !ms) return TLR_ERR_ARG;
+    for (int k = 0; k < kStages; ++k) ms[k] = ctx->last_stage_ms[k];
     return TLR_OK;
 }
 

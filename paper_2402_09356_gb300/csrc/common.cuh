@@ -117,6 +117,7 @@ struct tlr_ctx {
     std::vector<cudaEvent_t> prof_events;
     double last_gemm_ms = 0.0, last_gemm_flops = 0.0, last_matern_entries = 0.0;
     int last_panel_launches = 0;
+    double last_stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 struct tlr_mat {

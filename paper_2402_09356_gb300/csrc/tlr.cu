@@ -79,9 +79,19 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     DevBuf panel((size_t)nt * nb * nb * sizeof(double), st);
     double *Tp = panel.as<double>();
 
+    // stage boundary events (profiling): 6 marks per column
+    std::vector<cudaEvent_t> marks;
+    auto mark = [&]() {
+        if (!ctx->profile) return;
+        profile_events(ctx, prof_used + 1);
+        cudaEvent_t e = ctx->prof_events[prof_used++];
+        TLR_CUDA_TRY(cudaEventRecord(e, st));
+        marks.push_back(e);
+    };
     for (int j = 0; j < nt; ++j) {
         const int mj = tile_rows(n, nb, j);
         const int64_t Mp = (int64_t)(nt - j) * nb;  // panel leading dimension
+        mark();
         // --- Q_j = [U_j0 | ... ] and offsets
         std::vector<int> off(j + 1, 0);
         for (int k = 0; k < j; ++k) off[k + 1] = off[k] + r_of(j, k);
@@ -127,6 +137,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             gemm_batched(ctx, st, true, false, gw, 1.0, 0.0);
             gemm_batched(ctx, st, false, false, gp, 1.0, 0.0);
         }
+        mark();
         // --- panel: T_{:,j} = A_{:,j} - P_j Q_j'
         const int64_t rows_valid = n - (int64_t)j * nb;
         if (mode == FactorMode::Matern) {
@@ -135,16 +146,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             g.B = Qj; g.ldb = nb; g.n = mj;
             g.C = Tp; g.ldc = (int)Mp;
             g.ri0 = (int64_t)j * nb; g.ci0 = (int64_t)j * nb;
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (ctx->profile) {
-                profile_events(ctx, prof_used + 2);
-                e0 = ctx->prof_events[prof_used];
-                e1 = ctx->prof_events[prof_used + 1];
-                prof_used += 2;
-                TLR_CUDA_TRY(cudaEventRecord(e0, st));
-            }
             gemm_batched_matern(ctx, st, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P);
-            if (ctx->profile) TLR_CUDA_TRY(cudaEventRecord(e1, st));
             stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
             stats->matern_entries += (double)rows_valid * mj;
             stats->panel_launches += 1;
@@ -173,11 +175,13 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
         }
         stats->flops += 2.0 * (double)rows_valid * mj * Rj;
+        mark();
         // --- L_jj = chol(T_jj) into D_j
         double *Dj = M->D + (int64_t)j * nb * nb;
         copy_batched(ctx, st, {CopyDesc{Tp, (int)Mp, Dj, nb, mj, mj}});
         potrf_dense(ctx, st, Dj, nb, mj, (long long)j * nb);
         stats->flops += (double)mj * mj * mj / 3.0;
+        mark();
         // --- compress T_ij, i > j
         std::vector<CompressJob> jobs;
         for (int i = j + 1; i < nt; ++i) {
@@ -216,27 +220,33 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 double m = jobs[q].m, k = jobs[q].k;
                 stats->flops += 8.0 * m * k * (rk[q] + 8);  // sampling + projection GEMMs (approx.)
             }
+            mark();
             // --- V_ij <- L_jj^-1 V_ij
             std::vector<RhsDesc> rhs;
             for (int i = j + 1; i < nt; ++i)
                 if (r_of(i, j) > 0) rhs.push_back(RhsDesc{Vslot(M, i, j), r_of(i, j), nb});
             trsm_left_lower(ctx, st, Dj, nb, mj, rhs);
             for (const RhsDesc &d : rhs) stats->flops += (double)mj * mj * d.ncols;
+            mark();
         } else {
             long long sinfo = -1;
             int sc = status_fetch(ctx, st, &sinfo);
             if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
+            mark();
+            mark();
         }
     }
     upload_ranks(M, st);
     if (ctx->profile) {
-        float tot = 0.f;
-        for (int e = 0; e < prof_used; e += 2) {
-            float ms = 0.f;
-            TLR_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->prof_events[e], ctx->prof_events[e + 1]));
-            tot += ms;
-        }
-        stats->gemm_ms += tot;
+        // marks: 6 per column (start, after build, after panel, after potrf,
+        // after compress, after trsm); panel interval = stage 1
+        for (size_t c = 0; c + 5 < marks.size(); c += 6)
+            for (int k = 0; k < kStages; ++k) {
+                float ms = 0.f;
+                TLR_CUDA_TRY(cudaEventElapsedTime(&ms, marks[c + k], marks[c + k + 1]));
+                stats->stage_ms[k] += ms;
+            }
+        stats->gemm_ms += stats->stage_ms[1];
     }
 }
 

@@ -17,6 +17,8 @@ struct CopyDesc {
 
 void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &descs);
 
+constexpr int kStages = 5;
+
 enum class FactorMode {
     Matern,  // tiles generated from the Matern kernel inside the panel update (likelihood path)
     Tlr      // tiles taken from the compressed input held in the matrix (tlr_potrf)
@@ -28,6 +30,9 @@ struct FactorStats {
     double matern_entries = 0.0;  // covariance entries evaluated in the panel epilogues
     int panel_launches = 0;
     float gemm_ms = 0.f;          // device time of the panel GEMMs (when ctx->profile)
+    // device time per stage (when ctx->profile): low-rank operand build, panel
+    // update GEMM, diagonal POTRF, compression, TRSM of V
+    float stage_ms[kStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
 };
 
 void profile_events(tlr_ctx *ctx, int count);

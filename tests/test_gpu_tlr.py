@@ -54,7 +54,7 @@ def test_compress_ranks_and_error(ctx, eps, order):
     S = oracle.cov_matrix(xyp, theta)
     ref, sv = oracle.tile_ranks(S, nb, eps)
     tiles = tlr.tlr_generate(ctx, torch.from_numpy(xyp).cuda(), nb, theta)
-    A = tlr.TlrMatrix(ctx, n, nb, 0)
+    A = tlr.TlrMatrix(ctx, n, nb, nb)  # random order needs ranks above nb/2
     tlr.tlr_compress(A, tiles, eps)
     got = tlr.tlr_mat_ranks(A)
     nt = n // nb
@@ -68,7 +68,8 @@ def test_compress_ranks_and_error(ctx, eps, order):
             E = T - U.cpu().numpy() @ V.cpu().numpy().T
             assert np.linalg.norm(E, 2) <= 1.1 * eps, (i, j)
         D = tlr.tlr_mat_tile(A, i, i).cpu().numpy()
-        assert np.array_equal(D, S[i * nb:(i + 1) * nb, i * nb:(i + 1) * nb])
+        Sd = S[i * nb:(i + 1) * nb, i * nb:(i + 1) * nb]
+        assert np.all(np.abs(D - Sd) <= 1e-12 * np.abs(Sd) + 1e-300)
 
 
 C1 = dict(n=1600, theta=(1.0, 0.1, 0.5), order="morton", nb=200, eps=1e-9)
@@ -93,7 +94,8 @@ def test_loglik_orderings_and_theta(ctx, order, theta):
     n, nb, eps = 1600, 200, 1e-9
     xy, z, perm = ordered_problem(n, (1.0, 0.1, 0.5), order)
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)
-    r, _, _ = gpu_loglik(ctx, xy, z, theta, order, nb, eps)
+    # identity, random and max-min orders need ranks above nb/2 at this accuracy
+    r, _, _ = gpu_loglik(ctx, xy, z, theta, order, nb, eps, maxrank=nb)
     assert abs(r["loglik"] - ref["loglik"]) <= 10 * eps * abs(ref["loglik"]), (r["loglik"], ref["loglik"])
 
 
@@ -102,7 +104,7 @@ def test_loglik_ragged_and_tiny(ctx, n, nb):
     theta, eps = (1.2, 0.08, 0.8), 1e-9
     xy, z, perm = ordered_problem(n, theta, "hilbert", loc_seed=n, z_seed=n + 1)
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)
-    r, _, _ = gpu_loglik(ctx, xy, z, theta, "hilbert", nb, eps)
+    r, _, _ = gpu_loglik(ctx, xy, z, theta, "hilbert", nb, eps, maxrank=nb)
     assert abs(r["loglik"] - ref["loglik"]) <= 10 * eps * abs(ref["loglik"]) + 1e-12
 
 
