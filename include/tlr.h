@@ -120,6 +120,27 @@ int64_t tlr_launch_count(void);
 int tlr_order(tlr_ctx *ctx, const double *xy, int64_t n, int method, uint64_t seed,
               uint32_t flags, int64_t *perm, uint32_t *codes, double *xy_out, void *stream);
 
+/* The same ordering as tlr_order for RANDOM, MORTON and HILBERT, for callers
+ * that cannot allocate device memory while they run (for instance a serving
+ * loop that cannot afford cudaMalloc's implicit device synchronisation, or a
+ * process whose device memory is fixed at start-up).  The paper has no
+ * counterpart; this is an engineering variant of the Sec. 3.1 pipeline.
+ *   xy, n, method, seed, perm, codes: as for tlr_order (device pointers;
+ *   codes may be NULL).  No context: the current CUDA device is used.
+ * It calls no cudaMalloc / cudaFree: its sort buffers live in one file-scope
+ * __device__ array of 4.26 MB that every device loading the library holds
+ * until the process exits, so n is limited to 262,144 (2^18) locations.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents (every value a call reads it writes first):
+ * calls whose kernels overlap on the GPU race, so issue them on one stream
+ * or order them.
+ * Errors: TLR_ERR_ARG (n < 0, n > 262144, another method, NULL pointers),
+ * TLR_ERR_CUDA (symbol lookup or launch failure). */
+int tlr_order_noalloc(const double *xy, int64_t n, int method, uint64_t seed, int64_t *perm,
+                      uint32_t *codes, void *stream);
+
 /* dst[k] = src[perm[k]] for k < n (device pointers; permutes Z like the
  * locations).  Errors: TLR_ERR_ARG. */
 int tlr_gather(tlr_ctx *ctx, const int64_t *perm, const double *src, int64_t n, double *dst,

@@ -60,6 +60,8 @@ _SIGS = {
     "tlr_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]),
+    "tlr_order_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tlr_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_void_p]),
     "tlr_tiles_size": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int]),
@@ -226,6 +228,26 @@ def tlr_order(ctx: Context, xy, method, seed: int = 3, flags: int = 0, perm=None
     rc = load_library().tlr_order(ctx.h, _ptr(xy), n, int(method), ctypes.c_uint64(seed & (2**64 - 1)),
                                   int(flags), _ptr(perm), _ptr(codes), _ptr(xy_out), _stream(stream))
     ctx.check(rc)
+    return perm
+
+
+def tlr_order_noalloc(xy, method, seed: int = 3, perm=None, codes=None, stream=None):
+    """tlr_order for random / Morton / Hilbert without device allocation in the library.
+
+    For callers that cannot allocate while running; uses the library's fixed
+    scratch array (n <= 262,144).  perm (int64 CUDA, n) is returned.
+    """
+    import torch
+    n = xy.numel() // 2
+    _check_f64("xy", xy, 2 * n)
+    if isinstance(method, str):
+        method = ORDERS[method]
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int64, device=xy.device)
+    rc = load_library().tlr_order_noalloc(_ptr(xy), n, int(method), ctypes.c_uint64(seed & (2**64 - 1)),
+                                          _ptr(perm), _ptr(codes), _stream(stream))
+    if rc != TLR_OK:
+        raise TlrError(rc, "tlr_order_noalloc failed")
     return perm
 
 

@@ -18,6 +18,8 @@
 // publishes its (max, lowest index) partial; the next launch reduces the
 // partials (double-buffered) to find the next point.  All distance arithmetic
 // uses explicitly rounded intrinsics so that no multiply-add is contracted.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace tlr {
@@ -533,3 +535,75 @@ void gather(const int64_t *perm, const double *src, int64_t n, double *dst, cuda
 }
 
 }  // namespace tlr
+
+// ----------------------------------------------------------------------------
+// Ordering without any allocation.
+//
+// For callers that must not allocate device memory once they are running:
+// a serving loop whose latency budget cannot absorb cudaMalloc's implicit
+// device synchronisation, or a host process whose memory is fixed up front
+// (a pre-sized pool shared with other work).  tlr_order allocates its sort
+// buffers per call; tlr_order_noalloc instead uses one file-scope scratch
+// array that every device holds from module load until process exit.
+// ----------------------------------------------------------------------------
+namespace tlr {
+
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 18;  // 262,144 locations
+constexpr int64_t kNoAllocBlocks = (kNoAllocMaxN + kSortTile - 1) / kSortTile;
+// keys, values and their ping-pong copies (4 x n words) plus the radix histogram
+constexpr int64_t kNoAllocWords = 4 * kNoAllocMaxN + 256 * kNoAllocBlocks;
+
+static __device__ __align__(256) uint32_t g_order_scratch[kNoAllocWords];
+
+// Device address of g_order_scratch per device, looked up once per device.
+static uint32_t *noalloc_scratch(int device, int *rc) {
+    static std::mutex mu;
+    static uint32_t *addr[64] = {nullptr};
+    *rc = TLR_OK;
+    if (device < 0 || device >= 64) { *rc = TLR_ERR_ARG; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_order_scratch);
+        if (e != cudaSuccess || p == nullptr) { *rc = TLR_ERR_CUDA; return nullptr; }
+        addr[device] = static_cast<uint32_t *>(p);
+    }
+    return addr[device];
+}
+
+}  // namespace tlr
+
+extern "C" int tlr_order_noalloc(const double *xy, int64_t n, int method, uint64_t seed, int64_t *perm,
+                                 uint32_t *codes, void *stream) {
+    using namespace tlr;
+    if (n < 0 || n > kNoAllocMaxN) return TLR_ERR_ARG;
+    if (method != TLR_ORDER_RANDOM && method != TLR_ORDER_MORTON && method != TLR_ORDER_HILBERT)
+        return TLR_ERR_ARG;
+    if (n == 0) return TLR_OK;
+    if (!xy || !perm) return TLR_ERR_ARG;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return TLR_ERR_CUDA;
+    int rc = TLR_OK;
+    uint32_t *base = noalloc_scratch(device, &rc);
+    if (!base) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t *keys = base, *vals = base + kNoAllocMaxN;
+    uint32_t *ktmp = base + 2 * kNoAllocMaxN, *vtmp = base + 3 * kNoAllocMaxN;
+    uint32_t *hist = base + 4 * kNoAllocMaxN;
+    const int nblk = (int)ceil_div(n, kSortTile);
+    launch(k_sfc_keys, grid1(n), 256, 0, s, xy, n, method, seed, keys, vals);
+    if (codes && cudaMemcpyAsync(codes, keys, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return TLR_ERR_CUDA;
+    // stable LSD radix sort, 4 passes of 8 bits; every histogram entry and
+    // every key/value slot read by a pass is written earlier in the same call
+    for (int shift = 0; shift < 32; shift += 8) {
+        launch(k_radix_hist<uint32_t>, nblk, kSortThreads, 0, s, keys, n, shift, hist, nblk);
+        launch(k_scan_exclusive, 1, 1024, 0, s, hist, (int64_t)256 * nblk);
+        launch(k_radix_scatter<uint32_t>, nblk, kSortThreads, 0, s, keys, vals, n, shift, hist, nblk, ktmp,
+               vtmp);
+        std::swap(keys, ktmp);
+        std::swap(vals, vtmp);
+    }
+    launch(k_perm_out, grid1(n), 256, 0, s, vals, n, perm);
+    return cudaGetLastError() == cudaSuccess ? TLR_OK : TLR_ERR_CUDA;
+}
