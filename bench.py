@@ -172,8 +172,8 @@ def run_gpu(args):
         gemm_ms += prof["gemm_ms"]
         gemm_flops += prof["gemm_flops"]
         panel_launches += prof["panel_launches"]
-        for k, v in tlr.tlr_stage_times(ctx).items():
-            stage_ms[k] += v / args.steps
+        for name, v in tlr.tlr_stage_times(ctx).items():
+            stage_ms[name] += v / args.steps
         results.append(r)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -230,8 +230,8 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "ordering study FP64, n=40,000 (200x200 perturbed grid), Matern sigma2=1 "
-                               "beta=0.1 nu=0.5 walk start, Hilbert, tile 800, eps 1e-7",
+        "config": {"workload": "ordering study FP64, n=%d (perturbed grid), Matern sigma2=1 beta=0.1 nu=0.5 "
+                               "walk start, %s, tile %d, eps %g" % (N_POINTS, ORDER, NB, EPS),
                    "n": N_POINTS, "nb": NB, "eps": EPS, "ordering": ORDER, "theta0": list(THETA0),
                    "theta_walk": "log-space, scale 0.05/step, seed 7",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
@@ -318,13 +318,19 @@ def run_reference(args):
 
 
 def main():
+    global N_POINTS, NB, EPS, ORDER
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_POINTS, help="locations (profiling of smaller cases)")
+    ap.add_argument("--nb", type=int, default=NB)
+    ap.add_argument("--eps", type=float, default=EPS)
+    ap.add_argument("--order", default=ORDER)
     args = ap.parse_args()
+    N_POINTS, NB, EPS, ORDER = args.n, args.nb, args.eps, args.order
     if args.impl == "reference":
         run_reference(args)
         return

@@ -266,7 +266,9 @@ int tlr_stage_times(tlr_ctx *ctx, double *ms);
 
 /* Maximise l(theta) over lo <= theta <= hi from theta0 with the Nelder-Mead
  * simplex method in log(theta) (bounds by clamping), stopping when the
- * simplex's spread in l falls below tol or after max_iter evaluations.
+ * simplex's spread in l falls below tol * (1 + |l|), when its size in
+ * log(theta) falls below 1e-8, or after max_iter evaluations.  L holds the
+ * factor of the last evaluated theta on return.
  * Failed evaluations (NOT_SPD, RANK) count as l = -inf.  Outputs on host.
  * Errors: TLR_ERR_ARG, or the first hard error of an evaluation. */
 int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tlr_opts *opts,

@@ -94,9 +94,12 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
         TLR_CUDA_TRY(cudaEventCreate(&ctx->ev_b));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
-        ctx->stage_cap = (size_t)16 << 20;
-        TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_stage, ctx->stage_cap, cudaHostAllocDefault));
-        TLR_CUDA_TRY(cudaMalloc(&ctx->d_stage, ctx->stage_cap));
+        for (StageRing &R : ctx->stage) {
+            R.cap = (size_t)16 << 20;
+            TLR_CUDA_TRY(cudaHostAlloc(&R.h, R.cap, cudaHostAllocDefault));
+            TLR_CUDA_TRY(cudaMalloc(&R.d, R.cap));
+        }
+        TLR_CUDA_TRY(cudaMalloc(&ctx->d_mtab, 2 * (size_t)kTabIntervals * kTabCoef * sizeof(double)));
     });
     if (rc != TLR_OK) {
         tlr_ctx_destroy(ctx);
@@ -116,9 +119,12 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     for (cudaEvent_t e : {ctx->ev_a, ctx->ev_b, ctx->ev_fork, ctx->ev_join})
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
-    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
-    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    for (StageRing &R : ctx->stage) {
+        if (R.h) cudaFreeHost(R.h);
+        if (R.d) cudaFree(R.d);
+    }
     if (ctx->d_omega) cudaFree(ctx->d_omega);
+    if (ctx->d_mtab) cudaFree(ctx->d_mtab);
     delete ctx;
 }
 
@@ -164,6 +170,7 @@ int tlr_generate(tlr_ctx *ctx, const double *xy, int64_t n, int nb, tlr_theta th
         check_arg(n > 0 && xy && tiles, "n/xy/tiles");
         check_arg(nb >= 16 && nb <= kMaxTile, "nb");
         MaternParams P = params_of(theta);
+        build_matern_table(&P, ctx->d_mtab, (cudaStream_t)stream);
         generate_tiles(xy, n, nb, P, tiles, (cudaStream_t)stream);
     });
 }
@@ -330,6 +337,7 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     std::memset(out, 0, sizeof *out);
     out->info = -1;
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_a, s));
+    build_matern_table(&P, ctx->d_mtab, s);
     status_reset(ctx, s);
     FactorStats st;
     long long inf = -1;
@@ -456,6 +464,10 @@ int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tl
             std::memcpy(x, xs, sizeof x);
             std::memcpy(fx, fs, sizeof fx);
             if (std::isfinite(fx[3]) && std::fabs(fx[3] - fx[0]) <= tol * (1.0 + std::fabs(fx[0]))) break;
+            double diam = 0.0;  // simplex size in log(theta)
+            for (int p = 1; p < 4; ++p)
+                for (int d = 0; d < 3; ++d) diam = std::max(diam, std::fabs(x[p][d] - x[0][d]));
+            if (diam < 1e-8) break;
             double c[3] = {0, 0, 0};
             for (int p = 0; p < 3; ++p)
                 for (int d = 0; d < 3; ++d) c[d] += x[p][d] / 3.0;

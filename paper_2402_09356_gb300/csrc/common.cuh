@@ -94,6 +94,16 @@ private:
     cudaStream_t stream_ = nullptr;
 };
 
+// A pinned host ring mirrored in device memory for kernel descriptors.  One
+// ring per stream that launches kernels reading descriptors, so that a ring
+// is only reset after a sync of the one stream whose kernels read it.
+struct StageRing {
+    char *h = nullptr;
+    char *d = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+};
+
 }  // namespace tlr
 
 struct tlr_ctx {
@@ -104,14 +114,13 @@ struct tlr_ctx {
     tlr::DevStatus *h_status = nullptr;   // pinned host mirror
     cudaStream_t aux = nullptr;           // second stream for concurrent tile work
     cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_fork = nullptr, ev_join = nullptr;
-    // descriptor staging: pinned host ring mirrored into device memory
-    char *h_stage = nullptr;
-    char *d_stage = nullptr;
-    size_t stage_cap = 0;
-    size_t stage_off = 0;
+    // descriptor staging: ring 0 for the caller's stream, ring 1 for `aux`
+    tlr::StageRing stage[2];
     // fixed Gaussian test matrices of the randomised range finder
     double *d_omega = nullptr;
     int omega_rows = 0, omega_cols = 0;
+    // per-theta Matern interpolation table (+ node scratch)
+    double *d_mtab = nullptr;
     // timing of the dominant kernel (panel update GEMMs)
     bool profile = false;
     std::vector<cudaEvent_t> prof_events;
@@ -135,15 +144,20 @@ struct tlr_mat {
 
 namespace tlr {
 
+inline void stage_reset_main(tlr_ctx *ctx) { ctx->stage[0].off = 0; }
+
 inline int64_t off_index(int i, int j) { return (int64_t)i * (i - 1) / 2 + j; }
 inline int tile_rows(int64_t n, int nb, int t) {
     int64_t r = n - (int64_t)t * nb;
     return (int)(r < nb ? r : nb);
 }
 
-// Copies `bytes` of host data into the staging ring and returns the device
-// address of the copy (stream ordered on `s`).
+// Copies `bytes` of host data into the staging ring of stream `s` (ring 1 for
+// ctx->aux, ring 0 otherwise) and returns the device address of the copy
+// (stream ordered on `s`).
 void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s);
+// Marks ring 0 empty; only valid right after a sync of the stream that uses it.
+inline void stage_reset_main(tlr_ctx *ctx);
 
 // Status word helpers (host side).
 void status_reset(tlr_ctx *ctx, cudaStream_t s);

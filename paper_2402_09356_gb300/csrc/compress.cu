@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "compress.cuh"
 #include "gemm.cuh"
@@ -257,8 +259,12 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_svd(const SvdJob *__restr
     __syncthreads();
     if (tid == 0) {
         int r = 0;
-        for (int u = 0; u < s; ++u) r += nrm[u] > tau;
-        *J.rank = r;
+        bool bad = false;
+        for (int u = 0; u < s; ++u) {
+            r += nrm[u] > tau;
+            bad |= !(nrm[u] <= 1.7e308);
+        }
+        *J.rank = bad ? -1 : r;
     }
     for (int e = tid; e < s * s; e += kQrThreads) {
         int r = e % s, u = e / s, src = min(max(ord[u], 0), s - 1);
@@ -266,6 +272,269 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_svd(const SvdJob *__restr
         J.Zs[(int64_t)u * s + r] = Z[(int64_t)src * s + r];
         if (r == 0) J.S[u] = nrm[src];
     }
+}
+
+// ---------------------------------------------------------------------------
+// Cluster versions for large samples.  One FP64 tile factorisation on a single
+// SM is slow on GB300 (2 DFMA/clk/SM), and the highest-rank tile of a column
+// is the critical path of the whole factorisation, so each large tile is
+// spread over a cluster of kCl CTAs: the QR splits rows across the CTAs and
+// exchanges partial dot products through distributed shared memory; the
+// Jacobi SVD splits each round's column pairs across the cluster's warps.
+// Every loop bound and every branch around a cluster barrier depends only on
+// the job (identical for all CTAs of a cluster), so all CTAs execute the same
+// sequence of barriers.  Data written by another CTA is read with __ldcg.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+template <int kCl>
+__global__ void __launch_bounds__(kQrThreads) k_house_qr_cl(const QrJob *__restrict__ jobs) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const QrJob J = jobs[blockIdx.x / kCl];
+    const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kQrThreads / 32;
+    const int per = (m + kCl - 1) / kCl;
+    const int r0 = min(m, rank * per), r1 = min(m, r0 + per);
+    __shared__ double red[32];
+    __shared__ double s_norm;
+    extern __shared__ double s_dyn[];  // taus (s), betas (s), partial dots (2 x s)
+    double *taus = s_dyn, *betas = s_dyn + s, *part = s_dyn + 2 * s;
+    double *A = J.A;
+    const int64_t lda = J.lda;
+    for (int c = 0; c < s; ++c) {
+        double *col = A + (int64_t)c * lda;
+        const int rb = max(r0, c);
+        double p = 0.0;
+        for (int r = rb + tid; r < r1; r += kQrThreads) p += col[r] * col[r];
+        p = block_sum(p, red);
+        if (tid == 0) s_norm = p;
+        cl.sync();
+        double nrm2 = 0.0;
+        for (int k = 0; k < kCl; ++k) nrm2 += *cl.map_shared_rank(&s_norm, k);
+        const double alpha = __ldcg(col + c);
+        const double nrm = sqrt(nrm2);
+        double tau = 0.0, beta = 0.0, v0 = 0.0;
+        if (nrm != 0.0) {
+            beta = -copysign(nrm, alpha);
+            v0 = alpha - beta;
+            tau = 2.0 / (nrm2 - alpha * alpha + v0 * v0);
+        }
+        if (tid == 0) { taus[c] = tau; betas[c] = beta; }
+        if (tau != 0.0) {
+            for (int cc = c + 1 + warp; cc < s; cc += nw) {
+                const double *dst = A + (int64_t)cc * lda;
+                double w = 0.0;
+                for (int r = rb + lane; r < r1; r += 32) w += (r == c ? v0 : col[r]) * dst[r];
+                w = warp_sum(w);
+                if (lane == 0) part[cc] = w;
+            }
+        }
+        cl.sync();
+        if (tau != 0.0) {
+            for (int cc = c + 1 + warp; cc < s; cc += nw) {
+                double w = 0.0;
+                for (int k = 0; k < kCl; ++k) w += cl.map_shared_rank(part, k)[cc];
+                w *= tau;
+                double *dst = A + (int64_t)cc * lda;
+                for (int r = rb + lane; r < r1; r += 32) dst[r] -= w * (r == c ? v0 : col[r]);
+            }
+            __syncthreads();
+            if (tid == 0 && c >= r0 && c < r1) col[c] = v0;  // reflector stored in place
+        }
+    }
+    cl.sync();  // every CTA is done with the factorisation's partials
+    if (J.R) {
+        for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
+            int i = r0 + e % (r1 - r0), j = e / (r1 - r0);
+            if (i >= s) continue;
+            double v = 0.0;
+            if (i < j) v = A[(int64_t)j * lda + i];
+            else if (i == j) v = betas[i];
+            J.R[(int64_t)j * s + i] = v;
+        }
+    }
+    // explicit Q = H_0 ... H_{s-1} [I; 0], own rows, double-buffered partials
+    double *Q = J.Q;
+    const int64_t ldq = J.ldq;
+    for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
+        int r = r0 + e % (r1 - r0), j = e / (r1 - r0);
+        Q[(int64_t)j * ldq + r] = (r == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int active = 0;  // parity of the partial buffer alternates over applied reflectors
+    for (int c = s - 1; c >= 0; --c) {
+        const double tau = taus[c];
+        if (tau == 0.0) continue;  // identical on every CTA of the cluster
+        const double *v = A + (int64_t)c * lda;
+        double *pb = part + (active & 1) * s;
+        ++active;
+        const int rb = max(r0, c);
+        for (int cc = c + warp; cc < s; cc += nw) {
+            const double *dst = Q + (int64_t)cc * ldq;
+            double w = 0.0;
+            for (int r = rb + lane; r < r1; r += 32) w += v[r] * dst[r];
+            w = warp_sum(w);
+            if (lane == 0) pb[cc] = w;
+        }
+        cl.sync();
+        for (int cc = c + warp; cc < s; cc += nw) {
+            double w = 0.0;
+            for (int k = 0; k < kCl; ++k) w += cl.map_shared_rank(pb, k)[cc];
+            w *= tau;
+            double *dst = Q + (int64_t)cc * ldq;
+            for (int r = rb + lane; r < r1; r += 32) dst[r] -= w * v[r];
+        }
+        __syncthreads();  // the next reflector's dot products read columns other warps just wrote
+    }
+    cl.sync();  // no CTA leaves while another may still read its partials
+}
+
+template <int kCl>
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_svd_cl(const SvdJob *__restrict__ jobs, double tau) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ int s_rot;
+    extern __shared__ double s_dyn[];  // norms (s), order (s ints)
+    const SvdJob J = jobs[blockIdx.x / kCl];
+    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / 32;
+    double *A = J.A, *Z = J.Z;
+    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
+        int i = e % s, j = e / s;
+        __stcg(A + (int64_t)j * s + i, __ldcg(J.R + (int64_t)i * s + j));
+        __stcg(Z + (int64_t)j * s + i, (i == j) ? 1.0 : 0.0);
+    }
+    const int np = s + (s & 1);
+    const int gw = rank * nw + warp, ngw = kCl * nw;
+    cl.sync();
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pr = gw; pr < np / 2; pr += ngw) {
+                int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (np - 1);
+                int b = 1 + (np - 2 - pr + round) % (np - 1);
+                if (a >= s || b >= s) continue;
+                int p = min(a, b), q = max(a, b);
+                double *ap = A + (int64_t)p * s, *aq = A + (int64_t)q * s;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int r = lane; r < s; r += 32) {
+                    double x = __ldcg(ap + r), y = __ldcg(aq + r);
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int r = lane; r < s; r += 32) {
+                    double x = __ldcg(ap + r), y = __ldcg(aq + r);
+                    __stcg(ap + r, c * x - sn * y);
+                    __stcg(aq + r, sn * x + c * y);
+                }
+                double *zp = Z + (int64_t)p * s, *zq = Z + (int64_t)q * s;
+                for (int r = lane; r < s; r += 32) {
+                    double x = __ldcg(zp + r), y = __ldcg(zq + r);
+                    __stcg(zp + r, c * x - sn * y);
+                    __stcg(zq + r, sn * x + c * y);
+                }
+                if (lane == 0) s_rot = 1;
+            }
+            cl.sync();
+        }
+        int any = 0;
+        for (int k = 0; k < kCl; ++k) any |= *cl.map_shared_rank(&s_rot, k);
+        cl.sync();  // every CTA has read the flags before any resets its own
+        if (!any) break;
+    }
+    // every CTA computes all norms and the same order; each writes its share
+    double *nrm = s_dyn;
+    int *ord = (int *)(s_dyn + s);
+    for (int u = warp; u < s; u += nw) {
+        double v = 0.0;
+        const double *au = A + (int64_t)u * s;
+        for (int r = lane; r < s; r += 32) { double x = __ldcg(au + r); v += x * x; }
+        v = warp_sum(v);
+        if (lane == 0) nrm[u] = sqrt(v);
+    }
+    __syncthreads();
+    for (int u = tid; u < s; u += kQrThreads) {
+        double ku = nrm[u] <= 1.7e308 ? nrm[u] : -1.0;
+        int pos = 0;
+        for (int w = 0; w < s; ++w) {
+            double kw = nrm[w] <= 1.7e308 ? nrm[w] : -1.0;
+            pos += (kw > ku) || (kw == ku && w < u);
+        }
+        ord[pos] = u;
+    }
+    __syncthreads();
+    if (rank == 0 && tid == 0) {
+        int r = 0;
+        bool bad = false;
+        for (int u = 0; u < s; ++u) {
+            r += nrm[u] > tau;
+            bad |= !(nrm[u] <= 1.7e308);
+        }
+        *J.rank = bad ? -1 : r;
+    }
+    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
+        int r = e % s, u = e / s, src = min(max(ord[u], 0), s - 1);
+        J.WS[(int64_t)u * s + r] = __ldcg(A + (int64_t)src * s + r);
+        J.Zs[(int64_t)u * s + r] = __ldcg(Z + (int64_t)src * s + r);
+        if (r == 0) J.S[u] = nrm[src];
+    }
+}
+
+template <class K, class... Args>
+static void launch_cluster(K kernel, int csize, int nclusters, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * csize));
+    cfg.blockDim = dim3(kQrThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, args...));
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+}
+
+// Whether clusters of 16 CTAs (a non-portable size) can run on this device.
+static bool cluster16_ok() {
+    static int state = -1;
+    if (state < 0) {
+        state = 0;
+        if (cudaFuncSetAttribute(k_house_qr_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_jacobi_svd_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(kQrThreads);
+            cfg.dynamicSmemBytes = 16 * 1024;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 16;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int n1 = 0, n2 = 0;
+            if (cudaOccupancyMaxActiveClusters(&n1, k_house_qr_cl<16>, &cfg) == cudaSuccess &&
+                cudaOccupancyMaxActiveClusters(&n2, k_jacobi_svd_cl<16>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
+                state = 1;
+        }
+        cudaGetLastError();  // clear any error of the queries
+    }
+    return state == 1;
 }
 
 __global__ void k_gaussian(double *__restrict__ a, int64_t count, uint64_t seed) {
@@ -293,6 +562,43 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
     TLR_CHECK_LAUNCH();
 }
 
+// Launch one stage for a list of jobs: samples below kClusterMinS on one CTA
+// each, larger ones on a cluster of kCl CTAs.
+constexpr int kClusterMinS = 48;
+
+constexpr int kCluster16MinS = 128;
+
+// Launch one stage for a list of jobs by sample size: one CTA each below
+// kClusterMinS, clusters of 8 CTAs up to kCluster16MinS, clusters of 16 above
+// (when the device runs them; else 8).
+template <class Job, class... Extra>
+static void split_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<Job> &jobs,
+                         const std::vector<int> &sizes, void (*one)(const Job *, Extra...),
+                         void (*c8)(const Job *, Extra...), void (*c16)(const Job *, Extra...),
+                         size_t smem_per_s, Extra... extra) {
+    const bool big_ok = cluster16_ok();
+    std::vector<Job> part[3];
+    int smax[3] = {0, 0, 0};
+    for (size_t u = 0; u < jobs.size(); ++u) {
+        int cls = sizes[u] < kClusterMinS ? 0 : ((sizes[u] < kCluster16MinS || !big_ok) ? 1 : 2);
+        part[cls].push_back(jobs[u]);
+        smax[cls] = std::max(smax[cls], sizes[u]);
+    }
+    if (!part[0].empty()) {
+        auto *d = (const Job *)stage_push(ctx, part[0].data(), part[0].size() * sizeof(Job), st);
+        launch(one, (unsigned)part[0].size(), kQrThreads, smem_per_s * smax[0], st, d, extra...);
+        TLR_CHECK_LAUNCH();
+    }
+    if (!part[1].empty()) {
+        auto *d = (const Job *)stage_push(ctx, part[1].data(), part[1].size() * sizeof(Job), st);
+        launch_cluster(c8, 8, (int)part[1].size(), smem_per_s * smax[1], st, d, extra...);
+    }
+    if (!part[2].empty()) {
+        auto *d = (const Job *)stage_push(ctx, part[2].data(), part[2].size() * sizeof(Job), st);
+        launch_cluster(c16, 16, (int)part[2].size(), smem_per_s * smax[2], st, d, extra...);
+    }
+}
+
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile) {
     ensure_omega(ctx, st);
@@ -310,18 +616,18 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
     }
     const double *omega = ctx->d_omega;
     const int ldo = ctx->omega_rows;
-    const double *probe_cols = ctx->d_omega + (int64_t)kMaxSample * ldo;
     while (!pending.empty()) {
+        const size_t np = pending.size();
         // workspace offsets (doubles)
-        std::vector<int64_t> oY(pending.size()), oQ(pending.size()), oB(pending.size()), oQ2(pending.size()),
-            oR(pending.size()), oA(pending.size()), oZ(pending.size()), oS(pending.size()),
-            oWS(pending.size()), oZs(pending.size());
+        std::vector<int64_t> oY(np), oQ(np), oB(np), oQ2(np), oR(np), oA(np), oZ(np), oS(np), oWS(np), oZs(np);
+        std::vector<int> ps(np);
         int64_t tot = 0;
-        for (size_t u = 0; u < pending.size(); ++u) {
+        auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
+        for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
             int s = sz[pending[u]];
-            auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
-            oY[u] = take((int64_t)J.m * (s + kProbes));
+            ps[u] = s;
+            oY[u] = take((int64_t)J.m * s);
             oQ[u] = take((int64_t)J.m * s);
             oB[u] = take((int64_t)J.k * s);
             oQ2[u] = take((int64_t)J.k * s);
@@ -332,51 +638,34 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oWS[u] = take((int64_t)s * s);
             oZs[u] = take((int64_t)s * s);
         }
-        size_t np = pending.size();
-        DevBuf ws(tot * sizeof(double) + np * (sizeof(double) + sizeof(int)) + 256, st);
+        DevBuf ws(tot * sizeof(double) + np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
-        double *d_resid = W + tot;
-        int *d_rank = (int *)(d_resid + np);
-        // 1. Y = T [Omega_s | G]
+        int *d_rank = (int *)(W + tot);
+        // 1. Y = T Omega_s
         std::vector<GemmProb> g1;
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            int s = sz[pending[u]];
             GemmProb a{};
             a.A = J.T; a.lda = J.ldt; a.m = J.m; a.k = J.k;
-            a.B = omega; a.ldb = ldo; a.n = s;
+            a.B = omega; a.ldb = ldo; a.n = ps[u];
             a.C = W + oY[u]; a.ldc = J.m;
             g1.push_back(a);
-            GemmProb b = a;
-            b.B = probe_cols; b.n = kProbes;
-            b.C = W + oY[u] + (int64_t)J.m * s;
-            g1.push_back(b);
         }
         gemm_batched(ctx, st, false, false, g1, 1.0, 0.0);
-        // 2. Q = orth(Y_s), probe residuals
+        // 2. Q = orth(Y)
         std::vector<QrJob> q1(np);
-        int smax = 0;
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            int s = sz[pending[u]];
-            smax = std::max(smax, s);
-            q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, W + oY[u] + (int64_t)J.m * s,
-                          d_resid + u, J.m, s};
+            q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, nullptr, nullptr, J.m, ps[u]};
         }
-        auto *dq1 = (const QrJob *)stage_push(ctx, q1.data(), np * sizeof(QrJob), st);
-        size_t shq = (size_t)3 * smax * sizeof(double);
-        if (shq > 48 * 1024)
-            TLR_CUDA_TRY(cudaFuncSetAttribute(k_house_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shq));
-        launch(k_house_qr, (unsigned)np, kQrThreads, shq, st, dq1);
-        TLR_CHECK_LAUNCH();
+        split_launch(ctx, st, q1, ps, k_house_qr, k_house_qr_cl<8>, k_house_qr_cl<16>, 4 * sizeof(double));
         // 3. Bt = T' Q, Bt = Q2 R
         std::vector<GemmProb> g2;
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            int s = sz[pending[u]];
             GemmProb a{};
             a.A = J.T; a.lda = J.ldt; a.m = J.k; a.k = J.m;
-            a.B = W + oQ[u]; a.ldb = J.m; a.n = s;
+            a.B = W + oQ[u]; a.ldb = J.m; a.n = ps[u];
             a.C = W + oB[u]; a.ldc = J.k;
             g2.push_back(a);
         }
@@ -384,40 +673,29 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         std::vector<QrJob> q2(np);
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            int s = sz[pending[u]];
-            q2[u] = QrJob{W + oB[u], J.k, W + oQ2[u], J.k, W + oR[u], nullptr, nullptr, J.k, s};
+            q2[u] = QrJob{W + oB[u], J.k, W + oQ2[u], J.k, W + oR[u], nullptr, nullptr, J.k, ps[u]};
         }
-        auto *dq2 = (const QrJob *)stage_push(ctx, q2.data(), np * sizeof(QrJob), st);
-        launch(k_house_qr, (unsigned)np, kQrThreads, shq, st, dq2);
-        TLR_CHECK_LAUNCH();
+        split_launch(ctx, st, q2, ps, k_house_qr, k_house_qr_cl<8>, k_house_qr_cl<16>, 4 * sizeof(double));
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
-        for (size_t u = 0; u < np; ++u) {
-            int s = sz[pending[u]];
-            sv[u] = SvdJob{W + oR[u], W + oA[u], W + oZ[u], W + oWS[u], W + oZs[u], W + oS[u], d_rank + u, s};
-        }
-        auto *dsv = (const SvdJob *)stage_push(ctx, sv.data(), np * sizeof(SvdJob), st);
-        size_t shs = (size_t)smax * (sizeof(double) + sizeof(int));
-        if (shs > 48 * 1024)
-            TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shs));
-        launch(k_jacobi_svd, (unsigned)np, kQrThreads, shs, st, dsv, tau);
-        TLR_CHECK_LAUNCH();
+        for (size_t u = 0; u < np; ++u)
+            sv[u] = SvdJob{W + oR[u], W + oA[u], W + oZ[u], W + oWS[u], W + oZs[u], W + oS[u], d_rank + u, ps[u]};
+        split_launch(ctx, st, sv, ps, k_jacobi_svd, k_jacobi_svd_cl<8>, k_jacobi_svd_cl<16>,
+                     sizeof(double) + sizeof(int), tau);
         // decisions on the host
-        std::vector<double> h_resid(np);
         std::vector<int> h_rank(np);
-        TLR_CUDA_TRY(cudaMemcpyAsync(h_resid.data(), d_resid, np * sizeof(double), cudaMemcpyDeviceToHost, st));
         TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, np * sizeof(int), cudaMemcpyDeviceToHost, st));
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
-        ctx->stage_off = 0;
+        if (st != ctx->aux) stage_reset_main(ctx);
         std::vector<int> next;
         std::vector<GemmProb> gu, gv;
         for (size_t u = 0; u < np; ++u) {
             int q = pending[u];
             const CompressJob &J = jobs[q];
-            int s = sz[q];
+            int s = ps[u];
             int full = std::min(J.m, J.k);
             int r = h_rank[u];
-            if (!std::isfinite(h_resid[u])) {
+            if (r < 0) {  // non-finite singular values
                 if (*nan_tile < 0) *nan_tile = J.tile_id;
                 continue;
             }

@@ -6,19 +6,19 @@
 namespace tlr {
 
 void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s) {
+    StageRing &R = ctx->stage[(s == ctx->aux) ? 1 : 0];
     size_t need = (bytes + 255) & ~(size_t)255;
-    if (need > ctx->stage_cap) throw make_error(TLR_ERR_ARG, "descriptor batch too large (%zu bytes)", bytes);
-    if (ctx->stage_off + need > ctx->stage_cap) {
-        // every reader of the staging area runs on `s` or on the aux stream
+    if (need > R.cap) throw make_error(TLR_ERR_ARG, "descriptor batch too large (%zu bytes)", bytes);
+    if (R.off + need > R.cap) {
+        // every reader of this ring runs on `s`
         TLR_CUDA_TRY(cudaStreamSynchronize(s));
-        TLR_CUDA_TRY(cudaStreamSynchronize(ctx->aux));
-        ctx->stage_off = 0;
+        R.off = 0;
     }
-    char *h = ctx->h_stage + ctx->stage_off;
-    char *d = ctx->d_stage + ctx->stage_off;
+    char *h = R.h + R.off;
+    char *d = R.d + R.off;
     std::memcpy(h, data, bytes);
     TLR_CUDA_TRY(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s));
-    ctx->stage_off += need;
+    R.off += need;
     return d;
 }
 

@@ -55,6 +55,7 @@ bool make_matern_params(double sigma2, double beta, double nu, MaternParams *P) 
         return false;
     P->sigma2 = sigma2;
     P->inv_beta = 1.0 / beta;
+    P->tab = nullptr;
     P->nu = nu;
     int m = (int)std::floor(nu + 0.5);
     double mu = nu - m;
@@ -124,7 +125,53 @@ __global__ void k_matern_vec(const double *__restrict__ d, int64_t m, MaternPara
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
     double v = d[k];
-    out[k] = (v == 0.0) ? P.sigma2 : P.sigma2 * matern_corr_x(v * P.inv_beta, P);
+    if (v == 0.0) out[k] = P.sigma2;
+    else if (P.tab) out[k] = P.sigma2 * matern_corr_s(v * v, P);
+    else out[k] = P.sigma2 * matern_corr_x(v * P.inv_beta, P);
+}
+
+// Table nodes: log C/sigma2 at the Chebyshev points of every interval.
+__global__ void k_table_nodes(MaternParams P, double *__restrict__ g) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kTabIntervals * kTabCoef) return;
+    int iv = q / kTabCoef, k = q % kTabCoef;
+    int e = kTabEmin + iv / kTabSub, sub = iv % kTabSub;
+    double lo = ldexp(1.0 + (double)sub / kTabSub, e), hi = ldexp(1.0 + (double)(sub + 1) / kTabSub, e);
+    double node = cospi((k + 0.5) / kTabCoef);
+    double sv = lo + 0.5 * (node + 1.0) * (hi - lo);
+    double c = matern_corr_x(sqrt(sv) * P.inv_beta, P);
+    g[q] = (c > 1e-280) ? log(c) : __longlong_as_double(0x7FF8000000000000ll);
+}
+
+// Chebyshev coefficients c_j = (2/N) sum_k g_k cos(j pi (k + 1/2) / N), c_0 halved;
+// an interval with a non-finite node value keeps c_0 = NaN (direct evaluation).
+__global__ void k_table_coefs(const double *__restrict__ g, double *__restrict__ tab) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kTabIntervals * kTabCoef) return;
+    int iv = q / kTabCoef, j = q % kTabCoef;
+    const double *gi = g + iv * kTabCoef;
+    double acc = 0.0;
+    bool bad = false;
+    for (int k = 0; k < kTabCoef; ++k) {
+        double v = gi[k];
+        bad |= !(v == v);
+        acc += v * cospi((double)j * (k + 0.5) / kTabCoef);
+    }
+    acc *= 2.0 / kTabCoef;
+    if (j == 0) acc *= 0.5;
+    if (bad && j == 0) acc = __longlong_as_double(0x7FF8000000000000ll);
+    tab[q] = acc;
+}
+
+void build_matern_table(MaternParams *P, double *tab, cudaStream_t s) {
+    const int cnt = kTabIntervals * kTabCoef;
+    double *g = tab + cnt;  // scratch: the caller provides 2 * cnt doubles
+    MaternParams direct = *P;
+    direct.tab = nullptr;
+    launch(k_table_nodes, (unsigned)ceil_div(cnt, 128), 128, 0, s, direct, g);
+    launch(k_table_coefs, (unsigned)ceil_div(cnt, 128), 128, 0, s, g, tab);
+    TLR_CHECK_LAUNCH();
+    P->tab = tab;
 }
 
 void generate_tiles(const double *xy, int64_t n, int nb, const MaternParams &P, double *tiles,

@@ -34,6 +34,16 @@ __global__ void k_copy_batched(const CopyDesc *__restrict__ d) {
     }
 }
 
+__global__ void k_set_identity(double *__restrict__ X, int ld, int m) {
+    int c = blockIdx.x;
+    for (int r = threadIdx.x; r < ld; r += blockDim.x) X[(int64_t)c * ld + r] = (r == c && c < m) ? 1.0 : 0.0;
+}
+
+void set_identity(cudaStream_t s, double *X, int ld, int m) {
+    launch(k_set_identity, ld, 128, 0, s, X, ld, m);
+    TLR_CHECK_LAUNCH();
+}
+
 void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &descs) {
     std::vector<CopyDesc> act;
     for (const CopyDesc &c : descs)
@@ -78,6 +88,12 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     auto r_of = [&](int i, int k) { return (int)R[(size_t)i * nt + k]; };
     DevBuf panel((size_t)nt * nb * nb * sizeof(double), st);
     double *Tp = panel.as<double>();
+    DevBuf xinv((size_t)nb * nb * sizeof(double), st);
+    double *Xinv = xinv.as<double>();
+    std::vector<cudaEvent_t> aux_marks;  // potrf + inverse on the side stream (profiling)
+    // the side stream must not start before the buffers above exist
+    TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+    TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
 
     // stage boundary events (profiling): 6 marks per column
     std::vector<cudaEvent_t> marks;
@@ -176,13 +192,29 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         }
         stats->flops += 2.0 * (double)rows_valid * mj * Rj;
         mark();
-        // --- L_jj = chol(T_jj) into D_j
+        // --- L_jj = chol(T_jj) into D_j and X = L_jj^-1, on the side stream:
+        // they are independent of the compression of the column's other tiles
         double *Dj = M->D + (int64_t)j * nb * nb;
         copy_batched(ctx, st, {CopyDesc{Tp, (int)Mp, Dj, nb, mj, mj}});
-        potrf_dense(ctx, st, Dj, nb, mj, (long long)j * nb);
-        stats->flops += (double)mj * mj * mj / 3.0;
+        TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+        TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        if (ctx->profile) {
+            profile_events(ctx, prof_used + 1);
+            TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
+            aux_marks.push_back(ctx->prof_events[prof_used++]);
+        }
+        potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
+        set_identity(ctx->aux, Xinv, nb, mj);
+        trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
+        if (ctx->profile) {
+            profile_events(ctx, prof_used + 1);
+            TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
+            aux_marks.push_back(ctx->prof_events[prof_used++]);
+        }
+        TLR_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
+        stats->flops += (double)mj * mj * mj / 3.0 + (double)mj * mj * mj / 3.0;
         mark();
-        // --- compress T_ij, i > j
+        // --- compress T_ij, i > j (main stream, concurrently with the above)
         std::vector<CompressJob> jobs;
         for (int i = j + 1; i < nt; ++i) {
             CompressJob c{};
@@ -198,43 +230,53 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             c.tile_id = (long long)i * nt + j;
             jobs.push_back(c);
         }
-        if (!jobs.empty()) {
-            std::vector<int> rk;
-            long long bad = -1, nan = -1;
-            compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan);
-            long long sinfo = -1;
-            int sc = status_fetch(ctx, st, &sinfo);
-            if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
-            if (nan >= 0) {
-                *info = nan;
-                throw make_error(TLR_ERR_NAN, "tile (%lld, %lld) holds non-finite values", nan / nt, nan % nt);
-            }
-            if (bad >= 0) {
-                *info = bad;
-                throw make_error(TLR_ERR_RANK, "tile (%lld, %lld) needs rank > maxrank %d",
-                                 bad / nt, bad % nt, M->maxrank);
-            }
-            for (size_t q = 0; q < jobs.size(); ++q) {
-                int i = j + 1 + (int)q;
-                R[(size_t)i * nt + j] = R[(size_t)j * nt + i] = rk[q];
-                double m = jobs[q].m, k = jobs[q].k;
-                stats->flops += 8.0 * m * k * (rk[q] + 8);  // sampling + projection GEMMs (approx.)
-            }
-            mark();
-            // --- V_ij <- L_jj^-1 V_ij
-            std::vector<RhsDesc> rhs;
-            for (int i = j + 1; i < nt; ++i)
-                if (r_of(i, j) > 0) rhs.push_back(RhsDesc{Vslot(M, i, j), r_of(i, j), nb});
-            trsm_left_lower(ctx, st, Dj, nb, mj, rhs);
-            for (const RhsDesc &d : rhs) stats->flops += (double)mj * mj * d.ncols;
-            mark();
-        } else {
-            long long sinfo = -1;
-            int sc = status_fetch(ctx, st, &sinfo);
-            if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
-            mark();
-            mark();
+        std::vector<int> rk;
+        long long bad = -1, nan = -1;
+        if (!jobs.empty()) compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan);
+        mark();
+        TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+        long long sinfo = -1;
+        int sc = status_fetch(ctx, st, &sinfo);  // syncs st, after the side stream's work
+        if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
+        if (nan >= 0) {
+            *info = nan;
+            throw make_error(TLR_ERR_NAN, "tile (%lld, %lld) holds non-finite values", nan / nt, nan % nt);
         }
+        if (bad >= 0) {
+            *info = bad;
+            throw make_error(TLR_ERR_RANK, "tile (%lld, %lld) needs rank > maxrank %d", bad / nt, bad % nt,
+                             M->maxrank);
+        }
+        for (size_t q = 0; q < jobs.size(); ++q) {
+            int i = j + 1 + (int)q;
+            R[(size_t)i * nt + j] = R[(size_t)j * nt + i] = rk[q];
+            double m = jobs[q].m, k = jobs[q].k;
+            stats->flops += 8.0 * m * k * (rk[q] + 8);  // sampling + projection GEMMs (approx.)
+        }
+        // --- V_ij <- L_jj^-1 V_ij as one batched GEMM into a scratch panel, then copied back
+        {
+            std::vector<GemmProb> gt;
+            std::vector<CopyDesc> cb;
+            int64_t off_c = 0;
+            for (int i = j + 1; i < nt; ++i) off_c += r_of(i, j);
+            DevBuf vtmp((size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(double), st);
+            off_c = 0;
+            for (int i = j + 1; i < nt; ++i) {
+                int r = r_of(i, j);
+                if (r <= 0) continue;
+                GemmProb g{};
+                g.A = Xinv; g.lda = nb; g.m = mj; g.k = mj;
+                g.B = Vslot(M, i, j); g.ldb = nb; g.n = r;
+                g.C = vtmp.as<double>() + off_c * nb; g.ldc = nb;
+                gt.push_back(g);
+                cb.push_back(CopyDesc{vtmp.as<double>() + off_c * nb, nb, Vslot(M, i, j), nb, mj, r});
+                off_c += r;
+                stats->flops += 2.0 * mj * mj * r;
+            }
+            gemm_batched(ctx, st, false, false, gt, 1.0, 0.0);
+            copy_batched(ctx, st, cb);
+        }
+        mark();
     }
     upload_ranks(M, st);
     if (ctx->profile) {
@@ -246,6 +288,12 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 TLR_CUDA_TRY(cudaEventElapsedTime(&ms, marks[c + k], marks[c + k + 1]));
                 stats->stage_ms[k] += ms;
             }
+        stats->stage_ms[2] = 0.f;
+        for (size_t c = 0; c + 1 < aux_marks.size(); c += 2) {
+            float ms = 0.f;
+            TLR_CUDA_TRY(cudaEventElapsedTime(&ms, aux_marks[c], aux_marks[c + 1]));
+            stats->stage_ms[2] += ms;
+        }
         stats->gemm_ms += stats->stage_ms[1];
     }
 }

@@ -91,12 +91,32 @@ def test_loglik_small_config(ctx):
 @pytest.mark.parametrize("order", ["identity", "random", "morton", "hilbert", "kdtree", "maxmin"])
 @pytest.mark.parametrize("theta", [(1.0, 0.03, 0.5), (1.0, 0.3, 0.5), (1.5, 0.1, 1.0), (0.7, 0.1, 1.5)])
 def test_loglik_orderings_and_theta(ctx, order, theta):
+    """Z drawn from the model at the evaluated theta (the regime of an MLE near its optimum)."""
     n, nb, eps = 1600, 200, 1e-9
-    xy, z, perm = ordered_problem(n, (1.0, 0.1, 0.5), order)
+    xy, z, perm = ordered_problem(n, theta, order)
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)
     # identity, random and max-min orders need ranks above nb/2 at this accuracy
     r, _, _ = gpu_loglik(ctx, xy, z, theta, order, nb, eps, maxrank=nb)
     assert abs(r["loglik"] - ref["loglik"]) <= 10 * eps * abs(ref["loglik"]), (r["loglik"], ref["loglik"])
+
+
+@pytest.mark.parametrize("order", ["identity", "hilbert"])
+def test_loglik_misspecified_theta(ctx, order):
+    """Z from nu = 0.5 evaluated at the smooth nu = 1.5: Sigma is ill conditioned and
+    |l| is dominated by Z' Sigma^-1 Z.  A tile perturbation of at most eps moves
+    Sigma by at most NT eps in norm, so |dl| <= 1/2 NT eps (|Sigma^-1|_2 n + |Sigma^-1 Z|^2)
+    to first order; the test uses that bound (from the oracle's Sigma) with factor 2."""
+    n, nb, eps = 1600, 200, 1e-9
+    theta = (0.7, 0.1, 1.5)
+    xy, z, perm = ordered_problem(n, (1.0, 0.1, 0.5), order)
+    xyp, zp = oracle.permute_xy(xy, perm), z[perm]
+    S = oracle.cov_matrix(xyp, theta)
+    ref = oracle.loglik_from_cov(S, zp)
+    lam_min = np.linalg.eigvalsh(S)[0]
+    sol = np.linalg.solve(S, zp)
+    bound = 0.5 * (n // nb) * eps * (n / lam_min + sol @ sol)
+    r, _, _ = gpu_loglik(ctx, xy, z, theta, order, nb, eps, maxrank=nb)
+    assert abs(r["loglik"] - ref["loglik"]) <= 2 * bound, (r["loglik"], ref["loglik"], bound)
 
 
 @pytest.mark.parametrize("n,nb", [(1, 16), (17, 16), (200, 200), (1000, 96), (2113, 128)])
