@@ -96,12 +96,32 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(total_ms: float, steps: int, world: int, device=None) -> tuple:
+    """Whole-job throughput of `world` replicas: every rank ran `steps`
+    evaluations; the job's time is the slowest rank's (max over ranks).
+    Returns (evals_per_s, max_total_ms).  With world > 1 a process group must
+    be initialised (NCCL on GPUs, gloo on CPUs)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1000.0), total_ms
+
+
+def dataset_seeds(rank: int) -> tuple:
+    """Replica r evaluates its own dataset: locations seed 1 + r, w seed 2 + r."""
+    return 1 + rank, 2 + rank
+
+
 def make_inputs(tlr, ctx, torch, dev, rank: int):
     """Locations (generation order) and Z = L(theta0) w drawn with the library's factor."""
     import numpy as np
     import synth
-    xy_h = synth.jittered_grid(N_POINTS, seed=1 + rank)
-    w_h = synth.standard_normal(N_POINTS, seed=2 + rank)
+    s_loc, s_w = dataset_seeds(rank)
+    xy_h = synth.jittered_grid(N_POINTS, seed=s_loc)
+    w_h = synth.standard_normal(N_POINTS, seed=s_w)
     xy = torch.from_numpy(xy_h).to(dev)
     w = torch.from_numpy(w_h).to(dev)
     xyo = torch.empty_like(xy)
@@ -179,13 +199,9 @@ def run_gpu(args):
     clk = clocks.stop()
     launches = tlr.tlr_launch_count() - launches0
     times = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(times)
+    value, total_ms = aggregate(sum(times), args.steps, world, device=dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
         torch.distributed.barrier()
-    value = world * args.steps / (total_ms / 1000.0)
 
     # end to end through the public API with host buffers: pinned host inputs
     # copied in every step, the result read back on the host

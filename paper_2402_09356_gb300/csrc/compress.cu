@@ -489,6 +489,269 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_svd_cl(const SvdJob *__re
     }
 }
 
+// Householder QR on a cluster with ONE cluster barrier per column: each CTA
+// reduces, over its own rows r >= c, the squared norm of column c and the raw
+// products d_cc = sum_r A[r][c] A[r][cc]; the CTA that owns row c also
+// publishes that row.  After the barrier every CTA forms the reflector
+// (v = A[:, c] with v[c] = v0) and w_cc = tau (d_cc + (v0 - alpha) A[c][cc]),
+// then updates its own rows.  Buffers alternate by column parity, so a CTA
+// never overwrites values another CTA may still be reading.
+template <int kCl>
+__global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restrict__ jobs) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const QrJob J = jobs[blockIdx.x / kCl];
+    const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kQrThreads / 32;
+    const int per = (m + kCl - 1) / kCl;
+    const int r0 = min(m, rank * per), r1 = min(m, r0 + per);
+    __shared__ double red[32];
+    __shared__ double s_norm[2];
+    // taus (s), betas (s), dots (2 x s), row c of the owner (2 x s)
+    extern __shared__ double s_dyn[];
+    double *taus = s_dyn, *betas = s_dyn + s, *dots = s_dyn + 2 * s, *prow = s_dyn + 4 * s;
+    double *A = J.A;
+    const int64_t lda = J.lda;
+    for (int c = 0; c < s; ++c) {
+        const int par = c & 1;
+        double *col = A + (int64_t)c * lda;
+        const int rb = max(r0, c);
+        double *pd = dots + par * s, *pr = prow + par * s;
+        double p = 0.0;
+        for (int r = rb + tid; r < r1; r += kQrThreads) p += col[r] * col[r];
+        p = block_sum(p, red);
+        if (tid == 0) s_norm[par] = p;
+        for (int cc = c + 1 + warp; cc < s; cc += nw) {
+            const double *dst = A + (int64_t)cc * lda;
+            double w = 0.0;
+            for (int r = rb + lane; r < r1; r += 32) w += col[r] * dst[r];
+            w = warp_sum(w);
+            if (lane == 0) pd[cc] = w;
+        }
+        const int owner = c / per;
+        if (rank == owner)
+            for (int cc = c + tid; cc < s; cc += kQrThreads) pr[cc] = A[(int64_t)cc * lda + c];
+        cl.sync();
+        double nrm2 = 0.0;
+        for (int k = 0; k < kCl; ++k) nrm2 += cl.map_shared_rank(s_norm, k)[par];
+        const double *orow = cl.map_shared_rank(pr, owner);
+        const double alpha = orow[c];
+        const double nrm = sqrt(nrm2);
+        double tau = 0.0, beta = 0.0, v0 = 0.0;
+        if (nrm != 0.0) {
+            beta = -copysign(nrm, alpha);
+            v0 = alpha - beta;
+            tau = 2.0 / (nrm2 - alpha * alpha + v0 * v0);
+        }
+        if (tid == 0) { taus[c] = tau; betas[c] = beta; }
+        if (tau != 0.0) {
+            for (int cc = c + 1 + warp; cc < s; cc += nw) {
+                double d = 0.0;
+                for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pd, k)[cc];
+                const double w = tau * (d + (v0 - alpha) * orow[cc]);
+                double *dst = A + (int64_t)cc * lda;
+                for (int r = rb + lane; r < r1; r += 32) dst[r] -= w * (r == c ? v0 : col[r]);
+            }
+        }
+        __syncthreads();
+        if (tau != 0.0 && tid == 0 && c >= r0 && c < r1) col[c] = v0;  // reflector stored in place
+        __syncthreads();
+    }
+    cl.sync();  // partial buffers are reused below
+    if (J.R) {
+        for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
+            int i = r0 + e % (r1 - r0), j = e / (r1 - r0);
+            if (i >= s) continue;
+            double v = 0.0;
+            if (i < j) v = A[(int64_t)j * lda + i];
+            else if (i == j) v = betas[i];
+            J.R[(int64_t)j * s + i] = v;
+        }
+    }
+    double *Q = J.Q;
+    const int64_t ldq = J.ldq;
+    for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
+        int r = r0 + e % (r1 - r0), j = e / (r1 - r0);
+        Q[(int64_t)j * ldq + r] = (r == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    int active = 0;
+    for (int c = s - 1; c >= 0; --c) {
+        const double tau = taus[c];
+        if (tau == 0.0) continue;  // identical on every CTA of the cluster
+        const double *v = A + (int64_t)c * lda;
+        double *pb = dots + (active & 1) * s;
+        ++active;
+        const int rb = max(r0, c);
+        for (int cc = c + warp; cc < s; cc += nw) {
+            const double *dst = Q + (int64_t)cc * ldq;
+            double w = 0.0;
+            for (int r = rb + lane; r < r1; r += 32) w += v[r] * dst[r];
+            w = warp_sum(w);
+            if (lane == 0) pb[cc] = w;
+        }
+        cl.sync();
+        for (int cc = c + warp; cc < s; cc += nw) {
+            double w = 0.0;
+            for (int k = 0; k < kCl; ++k) w += cl.map_shared_rank(pb, k)[cc];
+            w *= tau;
+            double *dst = Q + (int64_t)cc * ldq;
+            for (int r = rb + lane; r < r1; r += 32) dst[r] -= w * v[r];
+        }
+        __syncthreads();
+    }
+    cl.sync();
+}
+
+// One-sided Jacobi SVD with a block schedule: the s columns (padded to
+// 2 kCl b with virtual zero columns) form 2 kCl blocks of b columns; every
+// CTA holds two blocks of A and Z in shared memory and rotates all pairs
+// between them (and, in the first block round of a sweep, inside them) with
+// only block barriers; blocks then move through L2 following a round-robin
+// tournament, so each block pair meets once per sweep at the cost of one
+// cluster barrier per block round.
+template <int kCl>
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_blk(const SvdJob *__restrict__ jobs, double tau) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ int s_rot;
+    extern __shared__ double s_dyn[];
+    const SvdJob J = jobs[blockIdx.x / kCl];
+    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / 32;
+    const int nblk = 2 * kCl;
+    const int b = (s + nblk - 1) / nblk;
+    double *Ab = s_dyn;          // [2][b][s]
+    double *Zb = s_dyn + 2 * b * s;  // [2][b][s]
+    double *A = J.A, *Z = J.Z;
+    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
+        int i = e % s, j = e / s;
+        __stcg(A + (int64_t)j * s + i, __ldcg(J.R + (int64_t)i * s + j));
+        __stcg(Z + (int64_t)j * s + i, (i == j) ? 1.0 : 0.0);
+    }
+    cl.sync();
+    auto block_at = [&](int pos, int round) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (nblk - 1); };
+    // rotate column pair (x, y) of the local buffers; virtual (zero) columns are skipped
+    auto rotate = [&](double *ax, double *ay, double *zx, double *zy) {
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < s; r += 32) {
+            double x = ax[r], y = ay[r];
+            al += x * x;
+            be += y * y;
+            ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) return;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+        for (int r = lane; r < s; r += 32) {
+            double x = ax[r], y = ay[r];
+            ax[r] = cs * x - sn * y;
+            ay[r] = sn * x + cs * y;
+            double u = zx[r], v = zy[r];
+            zx[r] = cs * u - sn * v;
+            zy[r] = sn * u + cs * v;
+        }
+        if (lane == 0) s_rot = 1;
+    };
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        for (int round = 0; round < nblk - 1; ++round) {
+            const int bx = block_at(rank, round), by = block_at(nblk - 1 - rank, round);
+            // load the two blocks (virtual columns as zeros)
+            for (int e = tid; e < 2 * b * s; e += kQrThreads) {
+                int slot = e / (b * s), rem = e % (b * s), jj = rem / s, r = rem % s;
+                int gcol = (slot ? by : bx) * b + jj;
+                Ab[e] = gcol < s ? __ldcg(A + (int64_t)gcol * s + r) : 0.0;
+                Zb[e] = gcol < s ? __ldcg(Z + (int64_t)gcol * s + r) : 0.0;
+            }
+            __syncthreads();
+            if (round == 0) {
+                // pairs inside each of the two blocks: round robin over b (padded to even)
+                const int bp = b + (b & 1);
+                for (int ir = 0; ir < bp - 1; ++ir) {
+                    for (int pr = warp; pr < bp; pr += nw) {  // bp/2 pairs per block, two blocks
+                        int slot = pr / (bp / 2), q = pr % (bp / 2);
+                        int a = (q == 0) ? 0 : 1 + (q - 1 + ir) % (bp - 1);
+                        int c2 = 1 + (bp - 2 - q + ir) % (bp - 1);
+                        if (a >= b || c2 >= b) continue;
+                        int gx = (slot ? by : bx) * b + a, gy = (slot ? by : bx) * b + c2;
+                        if (gx >= s || gy >= s) continue;
+                        double *base = Ab + slot * b * s, *zb = Zb + slot * b * s;
+                        rotate(base + min(a, c2) * s, base + max(a, c2) * s, zb + min(a, c2) * s,
+                               zb + max(a, c2) * s);
+                    }
+                    __syncthreads();
+                }
+            }
+            // pairs across the two blocks: b shifts of b disjoint pairs
+            for (int k = 0; k < b; ++k) {
+                for (int i = warp; i < b; i += nw) {
+                    int jy = (i + k) % b;
+                    int gx = bx * b + i, gy = by * b + jy;
+                    if (gx >= s || gy >= s) continue;
+                    // keep the lower global index as the first column of the pair
+                    if (gx < gy) rotate(Ab + i * s, Ab + (b + jy) * s, Zb + i * s, Zb + (b + jy) * s);
+                    else rotate(Ab + (b + jy) * s, Ab + i * s, Zb + (b + jy) * s, Zb + i * s);
+                }
+                __syncthreads();
+            }
+            // write back the real columns
+            for (int e = tid; e < 2 * b * s; e += kQrThreads) {
+                int slot = e / (b * s), rem = e % (b * s), jj = rem / s, r = rem % s;
+                int gcol = (slot ? by : bx) * b + jj;
+                if (gcol < s) {
+                    __stcg(A + (int64_t)gcol * s + r, Ab[e]);
+                    __stcg(Z + (int64_t)gcol * s + r, Zb[e]);
+                }
+            }
+            cl.sync();
+        }
+        int any = 0;
+        for (int k = 0; k < kCl; ++k) any |= *cl.map_shared_rank(&s_rot, k);
+        cl.sync();
+        if (!any) break;
+    }
+    // every CTA computes all norms and the same order; each writes its share
+    double *nrm = s_dyn;  // block buffers are free now
+    int *ord = (int *)(s_dyn + s);
+    for (int u = warp; u < s; u += nw) {
+        double v = 0.0;
+        const double *au = A + (int64_t)u * s;
+        for (int r = lane; r < s; r += 32) { double x = __ldcg(au + r); v += x * x; }
+        v = warp_sum(v);
+        if (lane == 0) nrm[u] = sqrt(v);
+    }
+    __syncthreads();
+    for (int u = tid; u < s; u += kQrThreads) {
+        double ku = nrm[u] <= 1.7e308 ? nrm[u] : -1.0;
+        int pos = 0;
+        for (int w = 0; w < s; ++w) {
+            double kw = nrm[w] <= 1.7e308 ? nrm[w] : -1.0;
+            pos += (kw > ku) || (kw == ku && w < u);
+        }
+        ord[pos] = u;
+    }
+    __syncthreads();
+    if (rank == 0 && tid == 0) {
+        int r = 0;
+        bool bad = false;
+        for (int u = 0; u < s; ++u) {
+            r += nrm[u] > tau;
+            bad |= !(nrm[u] <= 1.7e308);
+        }
+        *J.rank = bad ? -1 : r;
+    }
+    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
+        int r = e % s, u = e / s, src = min(max(ord[u], 0), s - 1);
+        J.WS[(int64_t)u * s + r] = __ldcg(A + (int64_t)src * s + r);
+        J.Zs[(int64_t)u * s + r] = __ldcg(Z + (int64_t)src * s + r);
+        if (r == 0) J.S[u] = nrm[src];
+    }
+}
+
 template <class K, class... Args>
 static void launch_cluster(K kernel, int csize, int nclusters, size_t smem, cudaStream_t st, Args... args) {
     cudaLaunchConfig_t cfg = {};
@@ -513,6 +776,10 @@ static bool cluster16_ok() {
     if (state < 0) {
         state = 0;
         if (cudaFuncSetAttribute(k_house_qr_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_house_qr_c1<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_jacobi_blk<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
                 cudaSuccess &&
             cudaFuncSetAttribute(k_jacobi_svd_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
                 cudaSuccess) {
@@ -599,6 +866,50 @@ static void split_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<Job> &
     }
 }
 
+// Shared memory of the block Jacobi: two blocks of A and of Z, b = ceil(s / 2C).
+static size_t jacobi_blk_smem(int s, int csize) {
+    int b = (s + 2 * csize - 1) / (2 * csize);
+    return (size_t)4 * b * s * sizeof(double);
+}
+
+// The SVD stage: one CTA per small sample; the block-scheduled cluster kernel
+// where its blocks fit in shared memory; the per-round cluster kernel beyond.
+static void jacobi_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs,
+                          const std::vector<int> &sizes, double tau) {
+    static bool attr_set = false;
+    const size_t smem_cap = 227 * 1024;
+    if (!attr_set) {
+        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
+        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
+        attr_set = true;
+    }
+    const bool big_ok = cluster16_ok();
+    std::vector<SvdJob> part[5];
+    int smax[5] = {0, 0, 0, 0, 0};
+    for (size_t u = 0; u < jobs.size(); ++u) {
+        int sz = sizes[u], cls;
+        int csize = (sz >= kCluster16MinS && big_ok) ? 16 : 8;
+        if (sz < kClusterMinS) cls = 0;
+        else if (jacobi_blk_smem(sz, csize) <= smem_cap) cls = (csize == 8) ? 1 : 2;
+        else cls = (csize == 8) ? 3 : 4;
+        part[cls].push_back(jobs[u]);
+        smax[cls] = std::max(smax[cls], sz);
+    }
+    const size_t per = sizeof(double) + sizeof(int);
+    for (int cls = 0; cls < 5; ++cls) {
+        if (part[cls].empty()) continue;
+        auto *d = (const SvdJob *)stage_push(ctx, part[cls].data(), part[cls].size() * sizeof(SvdJob), st);
+        int n = (int)part[cls].size();
+        switch (cls) {
+        case 0: launch(k_jacobi_svd, (unsigned)n, kQrThreads, per * smax[0], st, d, tau); TLR_CHECK_LAUNCH(); break;
+        case 1: launch_cluster(k_jacobi_blk<8>, 8, n, jacobi_blk_smem(smax[1], 8), st, d, tau); break;
+        case 2: launch_cluster(k_jacobi_blk<16>, 16, n, jacobi_blk_smem(smax[2], 16), st, d, tau); break;
+        case 3: launch_cluster(k_jacobi_svd_cl<8>, 8, n, per * smax[3], st, d, tau); break;
+        case 4: launch_cluster(k_jacobi_svd_cl<16>, 16, n, per * smax[4], st, d, tau); break;
+        }
+    }
+}
+
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile) {
     ensure_omega(ctx, st);
@@ -658,7 +969,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             const CompressJob &J = jobs[pending[u]];
             q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, nullptr, nullptr, J.m, ps[u]};
         }
-        split_launch(ctx, st, q1, ps, k_house_qr, k_house_qr_cl<8>, k_house_qr_cl<16>, 4 * sizeof(double));
+        split_launch(ctx, st, q1, ps, k_house_qr, k_house_qr_c1<8>, k_house_qr_c1<16>, 6 * sizeof(double));
         // 3. Bt = T' Q, Bt = Q2 R
         std::vector<GemmProb> g2;
         for (size_t u = 0; u < np; ++u) {
@@ -675,13 +986,12 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             const CompressJob &J = jobs[pending[u]];
             q2[u] = QrJob{W + oB[u], J.k, W + oQ2[u], J.k, W + oR[u], nullptr, nullptr, J.k, ps[u]};
         }
-        split_launch(ctx, st, q2, ps, k_house_qr, k_house_qr_cl<8>, k_house_qr_cl<16>, 4 * sizeof(double));
+        split_launch(ctx, st, q2, ps, k_house_qr, k_house_qr_c1<8>, k_house_qr_c1<16>, 6 * sizeof(double));
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
             sv[u] = SvdJob{W + oR[u], W + oA[u], W + oZ[u], W + oWS[u], W + oZs[u], W + oS[u], d_rank + u, ps[u]};
-        split_launch(ctx, st, sv, ps, k_jacobi_svd, k_jacobi_svd_cl<8>, k_jacobi_svd_cl<16>,
-                     sizeof(double) + sizeof(int), tau);
+        jacobi_launch(ctx, st, sv, ps, tau);
         // decisions on the host
         std::vector<int> h_rank(np);
         TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, np * sizeof(int), cudaMemcpyDeviceToHost, st));
