@@ -177,6 +177,7 @@ def run_gpu(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     results, gemm_ms, gemm_flops, panel_launches = [], 0.0, 0.0, 0
     stage_ms = {k: 0.0 for k in tlr.STAGES}
+    comp_ms = {k: 0.0 for k in tlr.COMPRESS_STEPS}
     clocks = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -194,6 +195,8 @@ def run_gpu(args):
         panel_launches += prof["panel_launches"]
         for name, v in tlr.tlr_stage_times(ctx).items():
             stage_ms[name] += v / args.steps
+        for name, v in tlr.tlr_compress_times(ctx).items():
+            comp_ms[name] += v / args.steps
         results.append(r)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -253,6 +256,7 @@ def run_gpu(args):
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "stage_ms_per_step": stage_ms,
+        "compress_ms_per_step": comp_ms,
         "loglik_last": results[-1]["loglik"],
         "max_rank_last": results[-1]["max_rank"],
         "mean_rank_last": results[-1]["mean_rank"],

@@ -262,6 +262,13 @@ int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops,
  * of their V factors.  Errors: TLR_ERR_ARG. */
 int tlr_stage_times(tlr_ctx *ctx, double *ms);
 
+/* Device time (ms) of the compression sub-steps of the last profiled
+ * factorisation, written to ms[0..6]: sampling GEMM (T Omega), QR of the
+ * sample, projection GEMM (T' Q), QR of the projection, SVD of the small
+ * factor, host decision (including the stream sync), U/V GEMMs.
+ * Errors: TLR_ERR_ARG. */
+int tlr_compress_times(tlr_ctx *ctx, double *ms);
+
 /* ---- MLE (Sec. 5.1: derivative-free, bound-constrained) ------------------ */
 
 /* Maximise l(theta) over lo <= theta <= hi from theta0 with the Nelder-Mead

@@ -93,6 +93,7 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int)]),
     "tlr_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "tlr_compress_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(tlr_theta),
@@ -384,6 +385,15 @@ def tlr_stage_times(ctx: Context) -> dict:
     a = (ctypes.c_double * 5)()
     ctx.check(load_library().tlr_stage_times(ctx.h, a))
     return {k: a[i] for i, k in enumerate(STAGES)}
+
+
+COMPRESS_STEPS = ("sample", "qr_y", "project", "qr_b", "svd", "host", "uv")
+
+
+def tlr_compress_times(ctx: Context) -> dict:
+    a = (ctypes.c_double * 7)()
+    ctx.check(load_library().tlr_compress_times(ctx.h, a))
+    return {k: a[i] for i, k in enumerate(COMPRESS_STEPS)}
 
 
 def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1e-9, max_iter: int = 500,

@@ -341,15 +341,15 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     status_reset(ctx, s);
     FactorStats st;
     long long inf = -1;
+    DevBuf acc(2 * sizeof(double), s), y((size_t)n * sizeof(double), s);
+    TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 2 * sizeof(double), s));
     try {
-        factor(ctx, s, L, FactorMode::Matern, xy, &P, opts->eps * theta.sigma2, &st, &inf);
+        factor(ctx, s, L, FactorMode::Matern, xy, &P, opts->eps * theta.sigma2, &st, &inf, z,
+               y.as<double>(), acc.as<double>());
     } catch (const Error &) {
         out->info = inf;
         throw;
     }
-    DevBuf acc(2 * sizeof(double), s), y((size_t)n * sizeof(double), s);
-    TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 2 * sizeof(double), s));
-    forward_solve(ctx, s, L, z, y.as<double>(), acc.as<double>());
     double h[2];
     TLR_CUDA_TRY(cudaMemcpyAsync(h, acc.as<double>(), sizeof h, cudaMemcpyDeviceToHost, s));
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_b, s));
@@ -410,6 +410,12 @@ int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops, d
 int tlr_stage_times(tlr_ctx *ctx, double *ms) {
     if (!ctx || !ms) return TLR_ERR_ARG;
     for (int k = 0; k < kStages; ++k) ms[k] = ctx->last_stage_ms[k];
+    return TLR_OK;
+}
+
+int tlr_compress_times(tlr_ctx *ctx, double *ms) {
+    if (!ctx || !ms) return TLR_ERR_ARG;
+    for (int k = 0; k < 7; ++k) ms[k] = ctx->comp_ms[k];
     return TLR_OK;
 }
 

@@ -876,12 +876,20 @@ static size_t jacobi_blk_smem(int s, int csize) {
 // where its blocks fit in shared memory; the per-round cluster kernel beyond.
 static void jacobi_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs,
                           const std::vector<int> &sizes, double tau) {
-    static bool attr_set = false;
-    const size_t smem_cap = 227 * 1024;
-    if (!attr_set) {
-        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
-        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cap));
-        attr_set = true;
+    // dynamic shared memory available to the block kernel: the device's opt-in
+    // per-block limit minus the kernel's static shared memory
+    static size_t smem_cap = 0;
+    if (smem_cap == 0) {
+        int dev = 0, optin = 0;
+        TLR_CUDA_TRY(cudaGetDevice(&dev));
+        TLR_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa8, fa16;
+        TLR_CUDA_TRY(cudaFuncGetAttributes(&fa8, k_jacobi_blk<8>));
+        TLR_CUDA_TRY(cudaFuncGetAttributes(&fa16, k_jacobi_blk<16>));
+        size_t cap = (size_t)optin - std::max(fa8.sharedSizeBytes, fa16.sharedSizeBytes);
+        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+        smem_cap = cap;
     }
     const bool big_ok = cluster16_ok();
     std::vector<SvdJob> part[5];
@@ -913,6 +921,34 @@ static void jacobi_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJo
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile) {
     ensure_omega(ctx, st);
+    // profiling marks between the sub-steps of each adaptive round
+    std::vector<cudaEvent_t> ev;
+    auto cmark = [&]() {
+        if (!ctx->profile) return;
+        size_t k = ev.size();
+        while (ctx->comp_events.size() <= k) {
+            cudaEvent_t e;
+            TLR_CUDA_TRY(cudaEventCreate(&e));
+            ctx->comp_events.push_back(e);
+        }
+        TLR_CUDA_TRY(cudaEventRecord(ctx->comp_events[k], st));
+        ev.push_back(ctx->comp_events[k]);
+    };
+    // 8 marks per round: start, after sampling, QR of Y, projection, QR of B',
+    // SVD, host decision, U/V; summed into ctx->comp_ms when the call ends
+    struct Flush {
+        tlr_ctx *ctx;
+        std::vector<cudaEvent_t> &ev;
+        ~Flush() {
+            if (!ctx->profile || ev.empty()) return;
+            if (cudaEventSynchronize(ev.back()) != cudaSuccess) return;
+            for (size_t c = 0; c + 8 <= ev.size(); c += 8)
+                for (int k = 0; k < 7; ++k) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, ev[c + k], ev[c + k + 1]) == cudaSuccess) ctx->comp_ms[k] += ms;
+                }
+        }
+    } flush{ctx, ev};
     const int nj = (int)jobs.size();
     ranks.assign(nj, 0);
     *bad_tile = -1;
@@ -952,6 +988,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         DevBuf ws(tot * sizeof(double) + np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
         int *d_rank = (int *)(W + tot);
+        cmark();
         // 1. Y = T Omega_s
         std::vector<GemmProb> g1;
         for (size_t u = 0; u < np; ++u) {
@@ -963,6 +1000,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             g1.push_back(a);
         }
         gemm_batched(ctx, st, false, false, g1, 1.0, 0.0);
+        cmark();
         // 2. Q = orth(Y)
         std::vector<QrJob> q1(np);
         for (size_t u = 0; u < np; ++u) {
@@ -970,6 +1008,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, nullptr, nullptr, J.m, ps[u]};
         }
         split_launch(ctx, st, q1, ps, k_house_qr, k_house_qr_c1<8>, k_house_qr_c1<16>, 6 * sizeof(double));
+        cmark();
         // 3. Bt = T' Q, Bt = Q2 R
         std::vector<GemmProb> g2;
         for (size_t u = 0; u < np; ++u) {
@@ -981,22 +1020,26 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             g2.push_back(a);
         }
         gemm_batched(ctx, st, true, false, g2, 1.0, 0.0);
+        cmark();
         std::vector<QrJob> q2(np);
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
             q2[u] = QrJob{W + oB[u], J.k, W + oQ2[u], J.k, W + oR[u], nullptr, nullptr, J.k, ps[u]};
         }
         split_launch(ctx, st, q2, ps, k_house_qr, k_house_qr_c1<8>, k_house_qr_c1<16>, 6 * sizeof(double));
+        cmark();
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
             sv[u] = SvdJob{W + oR[u], W + oA[u], W + oZ[u], W + oWS[u], W + oZs[u], W + oS[u], d_rank + u, ps[u]};
         jacobi_launch(ctx, st, sv, ps, tau);
+        cmark();
         // decisions on the host
         std::vector<int> h_rank(np);
         TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, np * sizeof(int), cudaMemcpyDeviceToHost, st));
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
         if (st != ctx->aux) stage_reset_main(ctx);
+        cmark();
         std::vector<int> next;
         std::vector<GemmProb> gu, gv;
         for (size_t u = 0; u < np; ++u) {
@@ -1039,6 +1082,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         }
         gemm_batched(ctx, st, false, false, gu, 1.0, 0.0);
         gemm_batched(ctx, st, false, false, gv, 1.0, 0.0);
+        cmark();
         // the workspace is released stream-ordered after these GEMMs
         pending.swap(next);
     }

@@ -24,7 +24,7 @@ void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s) {
 
 template <class Epi>
 static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
-                   double alpha, const Epi &epi) {
+                   double alpha, const Epi &epi, bool df) {
     if (probs.empty()) return;
     std::vector<int> off(probs.size() + 1, 0);
     for (size_t b = 0; b < probs.size(); ++b) {
@@ -37,25 +37,47 @@ static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const st
     auto *dp = (const GemmProb *)stage_push(ctx, probs.data(), probs.size() * sizeof(GemmProb), s);
     auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
     int np = (int)probs.size();
-    if (!ta && !tb) launch(k_gemm_f64<false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    if (df) {
+        if (!ta && !tb) launch(k_gemm_df<false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        else if (!ta && tb) launch(k_gemm_df<false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        else if (ta && !tb) launch(k_gemm_df<true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        else launch(k_gemm_df<true, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    } else if (!ta && !tb) launch(k_gemm_f64<false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
     else if (!ta && tb) launch(k_gemm_f64<false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
     else if (ta && !tb) launch(k_gemm_f64<true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
     else launch(k_gemm_f64<true, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
     TLR_CHECK_LAUNCH();
 }
 
+__global__ void k_split_f2(const double *__restrict__ src, int ld, int m, int64_t count,
+                           float2 *__restrict__ dst) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    int64_t i = e % m, j = e / m;
+    double v = src[j * ld + i];
+    float h = __double2float_rn(v);
+    dst[j * ld + i] = make_float2(h, __double2float_rn(v - (double)h));
+}
+
+void split_f2(cudaStream_t s, const double *src, int ld, int m, int n, float2 *dst) {
+    int64_t count = (int64_t)m * n;
+    if (count <= 0) return;
+    launch(k_split_f2, (unsigned)ceil_div(count, 256), 256, 0, s, src, ld, m, count, dst);
+    TLR_CHECK_LAUNCH();
+}
+
 void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
-                  double alpha, double beta) {
-    launch_gemm(ctx, s, ta, tb, probs, alpha, EpiLinear{beta});
+                  double alpha, double beta, bool df) {
+    launch_gemm(ctx, s, ta, tb, probs, alpha, EpiLinear{beta}, df);
 }
 
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
-                         double alpha, const double *xy, int64_t n, const MaternParams &P) {
+                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df) {
     EpiMatern e;
     e.xy = xy;
     e.n = n;
     e.P = P;
-    launch_gemm(ctx, s, false, tb, probs, alpha, e);
+    launch_gemm(ctx, s, false, tb, probs, alpha, e, df);
 }
 
 }  // namespace tlr

@@ -74,7 +74,8 @@ void upload_ranks(tlr_mat *M, cudaStream_t s) {
 }
 
 void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const double *xy,
-            const MaternParams *P, double tau, FactorStats *stats, long long *info) {
+            const MaternParams *P, double tau, FactorStats *stats, long long *info, const double *z,
+            double *y, double *acc) {
     const int nt = M->nt, nb = M->nb;
     const int64_t n = M->n;
     *info = -1;
@@ -83,6 +84,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     bool have_prev = !prev.empty() && prev.size() == (size_t)nt * nt;
     if (mode == FactorMode::Tlr && !have_prev) throw make_error(TLR_ERR_ARG, "matrix holds no compressed input");
     int prof_used = 0;
+    for (double &v : ctx->comp_ms) v = 0.0;
     R.assign((size_t)nt * nt, 0);
     for (int t = 0; t < nt; ++t) R[(size_t)t * nt + t] = tile_rows(n, nb, t);
     auto r_of = [&](int i, int k) { return (int)R[(size_t)i * nt + k]; };
@@ -90,6 +92,10 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     double *Tp = panel.as<double>();
     DevBuf xinv((size_t)nb * nb * sizeof(double), st);
     double *Xinv = xinv.as<double>();
+    // fused forward solve (a5): y = L^-1 z column by column
+    const bool solve = (z != nullptr && y != nullptr && acc != nullptr);
+    DevBuf ytmp(solve ? (size_t)nb * sizeof(double) : 0, st);
+    if (solve && y != z) TLR_CUDA_TRY(cudaMemcpyAsync(y, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::vector<cudaEvent_t> aux_marks;  // potrf + inverse on the side stream (profiling)
     // the side stream must not start before the buffers above exist
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
@@ -152,6 +158,26 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             }
             gemm_batched(ctx, st, true, false, gw, 1.0, 0.0);
             gemm_batched(ctx, st, false, false, gp, 1.0, 0.0);
+        }
+        if (solve && Rj > 0) {
+            // y_j -= Q_j c, c_k = V_jk' y_k (the y_k, k < j, are final)
+            DevBuf cb((size_t)Rj * sizeof(double), st);
+            std::vector<GemmProb> gc;
+            for (int k = 0; k < j; ++k) {
+                int r = r_of(j, k);
+                if (r <= 0) continue;
+                GemmProb a{};
+                a.A = Vslot(M, j, k); a.lda = nb; a.m = r; a.k = tile_rows(n, nb, k);
+                a.B = y + (int64_t)k * nb; a.ldb = nb; a.n = 1;
+                a.C = cb.as<double>() + off[k]; a.ldc = r;
+                gc.push_back(a);
+            }
+            gemm_batched(ctx, st, true, false, gc, 1.0, 0.0);
+            GemmProb g{};
+            g.A = Qj; g.lda = nb; g.m = mj; g.k = Rj;
+            g.B = cb.as<double>(); g.ldb = Rj; g.n = 1;
+            g.C = y + (int64_t)j * nb; g.ldc = nb;
+            gemm_batched(ctx, st, false, false, std::vector<GemmProb>{g}, -1.0, 1.0);
         }
         mark();
         // --- panel: T_{:,j} = A_{:,j} - P_j Q_j'
@@ -275,6 +301,17 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             }
             gemm_batched(ctx, st, false, false, gt, 1.0, 0.0);
             copy_batched(ctx, st, cb);
+        }
+        if (solve) {
+            double *yj = y + (int64_t)j * nb;
+            GemmProb g{};
+            g.A = Xinv; g.lda = nb; g.m = mj; g.k = mj;
+            g.B = yj; g.ldb = nb; g.n = 1;
+            g.C = ytmp.as<double>(); g.ldc = nb;
+            gemm_batched(ctx, st, false, false, std::vector<GemmProb>{g}, 1.0, 0.0);
+            TLR_CUDA_TRY(cudaMemcpyAsync(yj, ytmp.as<double>(), mj * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            diag_logsum(st, Dj, nb, mj, acc, ctx->d_status);
+            sumsq(st, yj, mj, acc + 1);
         }
         mark();
     }

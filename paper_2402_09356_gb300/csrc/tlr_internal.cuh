@@ -37,8 +37,12 @@ struct FactorStats {
 
 void profile_events(tlr_ctx *ctx, int count);
 void upload_ranks(tlr_mat *M, cudaStream_t s);
+// TLR Cholesky.  With z, y and acc given, the forward solve of Eq. 1.2 is fused
+// in: y = L^-1 z (z, y device, ordered; may alias), acc[0] += sum log L_ii,
+// acc[1] += |y|^2.
 void factor(tlr_ctx *ctx, cudaStream_t s, tlr_mat *M, FactorMode mode, const double *xy,
-            const MaternParams *P, double tau, FactorStats *stats, long long *info);
+            const MaternParams *P, double tau, FactorStats *stats, long long *info,
+            const double *z = nullptr, double *y = nullptr, double *acc = nullptr);
 void forward_solve(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *z, double *y,
                    double *acc);
 void lmul(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *w, double *z);
