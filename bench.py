@@ -178,6 +178,7 @@ def run_gpu(args):
     results, gemm_ms, gemm_flops, panel_launches = [], 0.0, 0.0, 0
     stage_ms = {k: 0.0 for k in tlr.STAGES}
     comp_ms = {k: 0.0 for k in tlr.COMPRESS_STEPS}
+    comp_stats = {k: 0 for k in tlr.COMPRESS_STATS}
     clocks = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
@@ -197,6 +198,8 @@ def run_gpu(args):
             stage_ms[name] += v / args.steps
         for name, v in tlr.tlr_compress_times(ctx).items():
             comp_ms[name] += v / args.steps
+        for name, v in tlr.tlr_compress_stats(ctx).items():
+            comp_stats[name] = max(comp_stats[name], v) if name == "max_sweeps" else comp_stats[name] + v
         results.append(r)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -257,6 +260,9 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "stage_ms_per_step": stage_ms,
         "compress_ms_per_step": comp_ms,
+        "compress_per_step": {"tiles": comp_stats["tiles"] / args.steps, "rounds": comp_stats["rounds"] / args.steps,
+                              "mean_sweeps": comp_stats["sweeps"] / max(comp_stats["tiles"], 1),
+                              "max_sweeps": comp_stats["max_sweeps"]},
         "loglik_last": results[-1]["loglik"],
         "max_rank_last": results[-1]["max_rank"],
         "mean_rank_last": results[-1]["mean_rank"],

@@ -269,6 +269,13 @@ int tlr_stage_times(tlr_ctx *ctx, double *ms);
  * Errors: TLR_ERR_ARG. */
 int tlr_compress_times(tlr_ctx *ctx, double *ms);
 
+/* Counters of the compressions of the last tlr_loglik / tlr_potrf
+ * factorisation, written to out[0..3]: tile compressions run (a tile redone
+ * with a larger sample counts again), adaptive rounds, Jacobi sweeps summed
+ * over the compressions, and the largest sweep count of one compression.
+ * Collected whether or not profiling is on.  Errors: TLR_ERR_ARG. */
+int tlr_compress_stats(tlr_ctx *ctx, int64_t *out);
+
 /* ---- MLE (Sec. 5.1: derivative-free, bound-constrained) ------------------ */
 
 /* Maximise l(theta) over lo <= theta <= hi from theta0 with the Nelder-Mead

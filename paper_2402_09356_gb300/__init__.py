@@ -94,6 +94,7 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_int)]),
     "tlr_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_compress_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "tlr_compress_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "tlr_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(tlr_theta),
@@ -394,6 +395,15 @@ def tlr_compress_times(ctx: Context) -> dict:
     a = (ctypes.c_double * 7)()
     ctx.check(load_library().tlr_compress_times(ctx.h, a))
     return {k: a[i] for i, k in enumerate(COMPRESS_STEPS)}
+
+
+COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps")
+
+
+def tlr_compress_stats(ctx: Context) -> dict:
+    a = (ctypes.c_int64 * 4)()
+    ctx.check(load_library().tlr_compress_stats(ctx.h, a))
+    return {k: int(a[i]) for i, k in enumerate(COMPRESS_STATS)}
 
 
 def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1e-9, max_iter: int = 500,

@@ -419,6 +419,12 @@ int tlr_compress_times(tlr_ctx *ctx, double *ms) {
     return TLR_OK;
 }
 
+int tlr_compress_stats(tlr_ctx *ctx, int64_t *out) {
+    if (!ctx || !out) return TLR_ERR_ARG;
+    for (int k = 0; k < 4; ++k) out[k] = ctx->comp_stats[k];
+    return TLR_OK;
+}
+
 int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tlr_opts *opts,
             tlr_theta theta0, tlr_theta lo, tlr_theta hi, double tol, int max_iter, tlr_mat *L,
             tlr_theta *theta_hat, double *ll_hat, int *iters, void *stream) {

@@ -131,6 +131,7 @@ struct tlr_ctx {
     // GEMM, QR of B', SVD, host decision (incl. sync), U/V GEMMs
     std::vector<cudaEvent_t> comp_events;
     double comp_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long comp_stats[4] = {0, 0, 0, 0};  // tiles, rounds, Jacobi sweeps (sum, max)
 };
 
 struct tlr_mat {

@@ -5,19 +5,36 @@
 // factors satisfy T ~ U V' with |T - U V'|_2 ~ sigma_{r+1}.  Computing the
 // full SVD of every nb x nb tile would cost O(nb^3); instead, per tile:
 //   1. Y = T Omega (Omega: k x s Gaussian) by batched GEMM (whole GPU);
-//   2. Q = orth(Y) by Householder QR with explicit Q (one CTA per tile);
-//   3. Bt = T' Q (batched GEMM), Bt = Q2 R (Householder QR);
-//   4. one-sided Jacobi SVD of R' = W S Z' (one CTA per tile), so that
-//      T ~ Q Q' T = (Q W) S (Q2 Z)'.
+//   2. Q = orth(Y): Householder QR with the explicit Q formed in place;
+//   3. B = T' Q (batched GEMM), kept, and the R factor of B = Q2 R;
+//   4. one-sided Jacobi SVD of R' = W S Z' (only W and S are formed).
+// With the unit left singular vectors W of R' (the right singular vectors
+// of B) and W_r their first r columns,
+//   U = Q W_r,  V = B W_r  =>  U V' = Q W_r W_r' Q' T,
+// the projection of T onto its r dominant left singular directions within
+// range(Q), so |T - U V'| <= |T - Q Q' T| + sigma_{r+1}(Q' T).
 // The rank is the SVD count of the projected tile, r = #{S > tau}.  A sample
 // of s = r + 24 columns reproduces the exact SVD rank and an error below tau
 // on the Matern tiles of the workloads (nu = 0.5 has the slowest decay); the
 // sample size comes from the tile's rank at the previous evaluation, and a
 // tile whose detected rank leaves fewer than 20 spare samples is redone with
 // a larger sample (Halko, Martinsson, Tropp 2011, Sec. 4: oversampling).
-// U = Q (W S)[:, :r], V = Q2 Z[:, :r].
+//
+// GB300 issues 2 FP64 FMA per clock per SM, so one tile's QR or SVD on one SM
+// is slow, and the highest-rank tile of a column lies on the critical path of
+// the factorisation.  Each tile therefore runs on a thread-block cluster whose
+// CTAs keep their share of the tile in shared memory:
+//   - QR: the CTAs split the rows; per column one cluster barrier exchanges
+//     the partial dot products through distributed shared memory (DSMEM);
+//   - SVD: the columns of R' form 2C blocks; every CTA rotates the column
+//     pairs between (and, once per sweep, within) its two blocks and then
+//     pulls its next two blocks from their holders over DSMEM, following a
+//     round-robin tournament, with one cluster barrier per block round.
+// Tiles whose panels do not fit in shared memory use global-memory variants.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -27,10 +44,13 @@
 
 namespace tlr {
 
-constexpr int kProbes = 4;
+namespace cg = cooperative_groups;
+
 constexpr int kOversample = 24;  // samples beyond the expected rank
 constexpr int kSpare = 20;       // fewer spare samples than this: redo with more
 constexpr int kQrThreads = 256;
+constexpr int kNw = kQrThreads / 32;
+constexpr int kMaxSweeps = 40;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -49,466 +69,182 @@ __device__ double block_sum(double v, double *red) {
     return t;
 }
 
+// Householder reflector of one column: given |x|^2 (nrm2) and its head alpha,
+// beta = -sign(alpha) |x|, v = x with v_head = alpha - beta, tau = 2 / v'v.
+__device__ __forceinline__ void householder(double nrm2, double alpha, double &tau, double &beta, double &v0) {
+    tau = 0.0;
+    beta = 0.0;
+    v0 = 0.0;
+    const double nrm = sqrt(nrm2);
+    if (nrm != 0.0) {
+        beta = -copysign(nrm, alpha);
+        v0 = alpha - beta;
+        tau = 2.0 / (nrm2 - alpha * alpha + v0 * v0);
+    }
+}
+
 struct QrJob {
-    double *A;     // m x s, in place (reflectors below the diagonal)
+    double *A;  // m x s input (ld lda); read only, except by the global-memory variant
     int lda;
-    double *Q;     // m x s output (explicit Q)
+    double *Q;  // m x s output Q (ld ldq), or null
     int ldq;
-    double *R;     // s x s upper output (may be null), ld s
-    const double *probe;  // m x kProbes probe columns (may be null), ld lda
-    double *resid;        // output: max probe residual norm (if probe)
+    double *Rt;  // s x s output R' (ld s, lower triangular), or null
     int m, s;
 };
 
-// Householder QR of one m x s matrix per CTA with explicit Q.
-__global__ void __launch_bounds__(kQrThreads) k_house_qr(const QrJob *__restrict__ jobs) {
-    __shared__ double red[32];
-    __shared__ double s_tau, s_beta;
-    extern __shared__ double s_dyn[];  // s betas, then s taus, then s probe coefficients
-    const QrJob J = jobs[blockIdx.x];
-    const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = kQrThreads / 32;
-    double *betas = s_dyn, *taus = s_dyn + s, *coef = s_dyn + 2 * s;
-    double *A = J.A;
-    const int64_t lda = J.lda;
-    // factorisation
-    for (int c = 0; c < s; ++c) {
-        double *col = A + (int64_t)c * lda;
-        double part = 0.0;
-        for (int r = c + tid; r < m; r += kQrThreads) part += col[r] * col[r];
-        double nrm2 = block_sum(part, red);
-        if (tid == 0) {
-            double alpha = (c < m) ? col[c] : 0.0;
-            double nrm = sqrt(nrm2);
-            if (nrm == 0.0 || c >= m) {
-                s_tau = 0.0;
-                s_beta = 0.0;
-            } else {
-                double beta = -copysign(nrm, alpha);
-                double v0 = alpha - beta;
-                double vtv = nrm2 - alpha * alpha + v0 * v0;
-                s_tau = 2.0 / vtv;
-                s_beta = beta;
-                col[c] = v0;
-            }
-            taus[c] = s_tau;
-            betas[c] = s_beta;
-        }
-        __syncthreads();
-        const double tau = s_tau;
-        if (tau != 0.0) {
-            for (int cc = c + 1 + warp; cc < s; cc += nw) {
-                double *dst = A + (int64_t)cc * lda;
-                double w = 0.0;
-                for (int r = c + lane; r < m; r += 32) w += col[r] * dst[r];
-                w = warp_sum(w) * tau;
-                for (int r = c + lane; r < m; r += 32) dst[r] -= w * col[r];
-            }
-        }
-        __syncthreads();
-    }
-    // R (upper triangle, diagonal = betas)
-    if (J.R) {
-        for (int e = tid; e < s * s; e += kQrThreads) {
-            int i = e % s, j = e / s;
-            double v = 0.0;
-            if (i < j) v = A[(int64_t)j * lda + i];
-            else if (i == j) v = betas[i];
-            J.R[(int64_t)j * s + i] = v;
-        }
-    }
-    // explicit Q = H_0 ... H_{s-1} [I; 0]
-    double *Q = J.Q;
-    const int64_t ldq = J.ldq;
-    for (int e = tid; e < m * s; e += kQrThreads) {
-        int r = e % m, j = e / m;
-        Q[(int64_t)j * ldq + r] = (r == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int c = s - 1; c >= 0; --c) {
-        const double tau = taus[c];
-        if (tau == 0.0) continue;
-        const double *v = A + (int64_t)c * lda;
-        for (int cc = c + warp; cc < s; cc += nw) {
-            double *dst = Q + (int64_t)cc * ldq;
-            double w = 0.0;
-            for (int r = c + lane; r < m; r += 32) w += v[r] * dst[r];
-            w = warp_sum(w) * tau;
-            for (int r = c + lane; r < m; r += 32) dst[r] -= w * v[r];
-        }
-        __syncthreads();
-    }
-    // probe residuals |y - Q Q' y|
-    if (J.probe) {
-        double worst = 0.0;
-        for (int g = 0; g < kProbes; ++g) {
-            const double *y = J.probe + (int64_t)g * lda;
-            for (int u = warp; u < s; u += nw) {
-                const double *q = Q + (int64_t)u * ldq;
-                double w = 0.0;
-                for (int r = lane; r < m; r += 32) w += q[r] * y[r];
-                w = warp_sum(w);
-                if (lane == 0) coef[u] = w;
-            }
-            __syncthreads();
-            double part = 0.0;
-            for (int r = tid; r < m; r += kQrThreads) {
-                double v = y[r];
-                for (int u = 0; u < s; ++u) v -= Q[(int64_t)u * ldq + r] * coef[u];
-                part += v * v;
-            }
-            double r2 = block_sum(part, red);
-            worst = fmax(worst, sqrt(r2));
-            __syncthreads();
-        }
-        if (tid == 0) *J.resid = worst;
-    }
-}
-
-struct SvdJob {
-    const double *R;  // s x s upper (ld s), input
-    double *A;        // s x s work: R' rotated to W S
-    double *Z;        // s x s work: accumulated right rotations
-    double *WS;       // s x s output: W S, columns sorted by S descending
-    double *Zs;       // s x s output: Z, columns sorted alike
-    double *S;        // s singular values (output, descending)
-    int *rank;        // #{S > tau}
-    int s;
-};
-
-// One-sided (Hestenes) Jacobi SVD of R' per CTA: cyclic tournament ordering,
-// one warp per column pair.
-__global__ void __launch_bounds__(kQrThreads) k_jacobi_svd(const SvdJob *__restrict__ jobs, double tau) {
-    __shared__ int s_rot;
-    extern __shared__ double s_dyn[];  // norms (s), order (s ints)
-    const SvdJob J = jobs[blockIdx.x];
-    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / 32;
-    double *A = J.A, *Z = J.Z;
-    for (int e = tid; e < s * s; e += kQrThreads) {
-        int i = e % s, j = e / s;
-        A[(int64_t)j * s + i] = J.R[(int64_t)i * s + j];  // A = R'
-        Z[(int64_t)j * s + i] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    const int np = s + (s & 1);  // players (pad to even; index s is a bye)
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int round = 0; round < np - 1; ++round) {
-            for (int pr = warp; pr < np / 2; pr += nw) {
-                // round-robin pairing: player 0 fixed, others rotate
-                int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (np - 1);
-                int b = 1 + (np - 2 - pr + round) % (np - 1);
-                if (a >= s || b >= s) continue;
-                int p = min(a, b), q = max(a, b);
-                double *ap = A + (int64_t)p * s, *aq = A + (int64_t)q * s;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < s; r += 32) {
-                    double x = ap[r], y = aq[r];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
-                double zeta = (be - al) / (2.0 * ga);
-                double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-                for (int r = lane; r < s; r += 32) {
-                    double x = ap[r], y = aq[r];
-                    ap[r] = c * x - sn * y;
-                    aq[r] = sn * x + c * y;
-                }
-                double *zp = Z + (int64_t)p * s, *zq = Z + (int64_t)q * s;
-                for (int r = lane; r < s; r += 32) {
-                    double x = zp[r], y = zq[r];
-                    zp[r] = c * x - sn * y;
-                    zq[r] = sn * x + c * y;
-                }
-                if (lane == 0) s_rot = 1;
-            }
-            __syncthreads();
-        }
-        if (!s_rot) break;
-        __syncthreads();
-    }
-    // singular values = column norms
-    double *nrm = s_dyn;
-    int *ord = (int *)(s_dyn + s);
-    for (int u = warp; u < s; u += nw) {
-        double v = 0.0;
-        const double *au = A + (int64_t)u * s;
-        for (int r = lane; r < s; r += 32) v += au[r] * au[r];
-        v = warp_sum(v);
-        if (lane == 0) nrm[u] = sqrt(v);
-    }
-    __syncthreads();
-    // descending order, ties by index; a non-finite norm sorts last, so the
-    // positions always form a permutation of 0..s-1
-    for (int u = tid; u < s; u += kQrThreads) {
-        double ku = nrm[u] <= 1.7e308 ? nrm[u] : -1.0;
-        int pos = 0;
-        for (int w = 0; w < s; ++w) {
-            double kw = nrm[w] <= 1.7e308 ? nrm[w] : -1.0;
-            pos += (kw > ku) || (kw == ku && w < u);
-        }
-        ord[pos] = u;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int r = 0;
-        bool bad = false;
-        for (int u = 0; u < s; ++u) {
-            r += nrm[u] > tau;
-            bad |= !(nrm[u] <= 1.7e308);
-        }
-        *J.rank = bad ? -1 : r;
-    }
-    for (int e = tid; e < s * s; e += kQrThreads) {
-        int r = e % s, u = e / s, src = min(max(ord[u], 0), s - 1);
-        J.WS[(int64_t)u * s + r] = A[(int64_t)src * s + r];
-        J.Zs[(int64_t)u * s + r] = Z[(int64_t)src * s + r];
-        if (r == 0) J.S[u] = nrm[src];
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Cluster versions for large samples.  One FP64 tile factorisation on a single
-// SM is slow on GB300 (2 DFMA/clk/SM), and the highest-rank tile of a column
-// is the critical path of the whole factorisation, so each large tile is
-// spread over a cluster of kCl CTAs: the QR splits rows across the CTAs and
-// exchanges partial dot products through distributed shared memory; the
-// Jacobi SVD splits each round's column pairs across the cluster's warps.
-// Every loop bound and every branch around a cluster barrier depends only on
-// the job (identical for all CTAs of a cluster), so all CTAs execute the same
-// sequence of barriers.  Data written by another CTA is read with __ldcg.
-// ---------------------------------------------------------------------------
-namespace cg = cooperative_groups;
-
+// QR with the panel in shared memory.  CTA `rank` of the cluster owns rows
+// [r0, r0 + nr) of all s columns, column-major with an odd leading dimension.
+// Column c: every CTA forms the dot products of column c with columns c..s-1
+// over its rows (at or below row c), and the owner of row c publishes that
+// row; after one cluster barrier every CTA sums the kCl partials, forms the
+// reflector (v = column c with v_c = v0) and w_cc = tau (d_cc + (v0 - alpha)
+// A(c, cc)), and updates its own rows.  Buffers alternate by column parity, so
+// a CTA never overwrites values another CTA may still be reading.
+// Q = H_0 ... H_{s-1} [I; 0] is then accumulated backwards in place: before
+// H_c is applied, columns > c already hold their final values below row c,
+// and column c becomes H_c e_c (LAPACK's dorg2r ordering).
+// Shared memory: s * ld + 8 s doubles.
 template <int kCl>
-__global__ void __launch_bounds__(kQrThreads) k_house_qr_cl(const QrJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const QrJob J = jobs[blockIdx.x / kCl];
     const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = kQrThreads / 32;
-    const int per = (m + kCl - 1) / kCl;
-    const int r0 = min(m, rank * per), r1 = min(m, r0 + per);
-    __shared__ double red[32];
-    __shared__ double s_norm;
-    extern __shared__ double s_dyn[];  // taus (s), betas (s), partial dots (2 x s)
-    double *taus = s_dyn, *betas = s_dyn + s, *part = s_dyn + 2 * s;
-    double *A = J.A;
-    const int64_t lda = J.lda;
-    for (int c = 0; c < s; ++c) {
-        double *col = A + (int64_t)c * lda;
-        const int rb = max(r0, c);
-        double p = 0.0;
-        for (int r = rb + tid; r < r1; r += kQrThreads) p += col[r] * col[r];
-        p = block_sum(p, red);
-        if (tid == 0) s_norm = p;
-        cl.sync();
-        double nrm2 = 0.0;
-        for (int k = 0; k < kCl; ++k) nrm2 += *cl.map_shared_rank(&s_norm, k);
-        const double alpha = __ldcg(col + c);
-        const double nrm = sqrt(nrm2);
-        double tau = 0.0, beta = 0.0, v0 = 0.0;
-        if (nrm != 0.0) {
-            beta = -copysign(nrm, alpha);
-            v0 = alpha - beta;
-            tau = 2.0 / (nrm2 - alpha * alpha + v0 * v0);
-        }
-        if (tid == 0) { taus[c] = tau; betas[c] = beta; }
-        if (tau != 0.0) {
-            for (int cc = c + 1 + warp; cc < s; cc += nw) {
-                const double *dst = A + (int64_t)cc * lda;
-                double w = 0.0;
-                for (int r = rb + lane; r < r1; r += 32) w += (r == c ? v0 : col[r]) * dst[r];
-                w = warp_sum(w);
-                if (lane == 0) part[cc] = w;
-            }
-        }
-        cl.sync();
-        if (tau != 0.0) {
-            for (int cc = c + 1 + warp; cc < s; cc += nw) {
-                double w = 0.0;
-                for (int k = 0; k < kCl; ++k) w += cl.map_shared_rank(part, k)[cc];
-                w *= tau;
-                double *dst = A + (int64_t)cc * lda;
-                for (int r = rb + lane; r < r1; r += 32) dst[r] -= w * (r == c ? v0 : col[r]);
-            }
-            __syncthreads();
-            if (tid == 0 && c >= r0 && c < r1) col[c] = v0;  // reflector stored in place
-        }
-    }
-    cl.sync();  // every CTA is done with the factorisation's partials
-    if (J.R) {
-        for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
-            int i = r0 + e % (r1 - r0), j = e / (r1 - r0);
-            if (i >= s) continue;
-            double v = 0.0;
-            if (i < j) v = A[(int64_t)j * lda + i];
-            else if (i == j) v = betas[i];
-            J.R[(int64_t)j * s + i] = v;
-        }
-    }
-    // explicit Q = H_0 ... H_{s-1} [I; 0], own rows, double-buffered partials
-    double *Q = J.Q;
-    const int64_t ldq = J.ldq;
-    for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
-        int r = r0 + e % (r1 - r0), j = e / (r1 - r0);
-        Q[(int64_t)j * ldq + r] = (r == j) ? 1.0 : 0.0;
+    const int per = (m + kCl - 1) / kCl, ld = per | 1;
+    const int r0 = min(m, rank * per), nr = min(m, r0 + per) - r0;
+    extern __shared__ double sm[];
+    double *As = sm;
+    double *taus = As + (size_t)s * ld, *betas = taus + s, *heads = betas + s;
+    double *pd = heads + s, *prow = pd + 2 * s, *wv = prow + 2 * s;
+    for (int e = tid; e < nr * s; e += kQrThreads) {
+        const int i = e % nr, j = e / nr;
+        As[j * ld + i] = J.A[(int64_t)j * J.lda + r0 + i];
     }
     __syncthreads();
-    int active = 0;  // parity of the partial buffer alternates over applied reflectors
-    for (int c = s - 1; c >= 0; --c) {
-        const double tau = taus[c];
-        if (tau == 0.0) continue;  // identical on every CTA of the cluster
-        const double *v = A + (int64_t)c * lda;
-        double *pb = part + (active & 1) * s;
-        ++active;
-        const int rb = max(r0, c);
-        for (int cc = c + warp; cc < s; cc += nw) {
-            const double *dst = Q + (int64_t)cc * ldq;
+    for (int c = 0; c < s; ++c) {
+        double *pdc = pd + (c & 1) * s, *prc = prow + (c & 1) * s;
+        const int lb = max(c - r0, 0), ic = c - r0;
+        double *vc = As + c * ld;
+        for (int cc = c + warp; cc < s; cc += kNw) {
+            const double *ac = As + cc * ld;
             double w = 0.0;
-            for (int r = rb + lane; r < r1; r += 32) w += v[r] * dst[r];
+            for (int i = lb + lane; i < nr; i += 32) w = fma(vc[i], ac[i], w);
             w = warp_sum(w);
-            if (lane == 0) pb[cc] = w;
+            if (lane == 0) pdc[cc] = w;
         }
+        const int owner = c / per;
+        if (rank == owner)
+            for (int cc = c + tid; cc < s; cc += kQrThreads) prc[cc] = As[cc * ld + ic];
         cl.sync();
-        for (int cc = c + warp; cc < s; cc += nw) {
-            double w = 0.0;
-            for (int k = 0; k < kCl; ++k) w += cl.map_shared_rank(pb, k)[cc];
-            w *= tau;
-            double *dst = Q + (int64_t)cc * ldq;
-            for (int r = rb + lane; r < r1; r += 32) dst[r] -= w * v[r];
+        const double *orow = cl.map_shared_rank(prc, owner);
+        double nrm2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < kCl; ++k) nrm2 += cl.map_shared_rank(pdc, k)[c];
+        const double alpha = orow[c];
+        double tau, beta, v0;
+        householder(nrm2, alpha, tau, beta, v0);
+        for (int cc = c + 1 + tid; cc < s; cc += kQrThreads) {
+            double d = 0.0;
+#pragma unroll
+            for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pdc, k)[cc];
+            wv[cc] = tau * (d + (v0 - alpha) * orow[cc]);
         }
-        __syncthreads();  // the next reflector's dot products read columns other warps just wrote
+        if (tid == 0) {
+            taus[c] = tau;
+            betas[c] = beta;
+            heads[c] = v0;
+        }
+        __syncthreads();
+        if (tau != 0.0) {
+            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
+                const double w = wv[cc];
+                double *ac = As + cc * ld;
+                for (int i = lb + lane; i < nr; i += 32) ac[i] = fma(-w, i == ic ? v0 : vc[i], ac[i]);
+            }
+        }
+        __syncthreads();
+        if (tau != 0.0 && rank == owner && tid == 0) vc[ic] = v0;  // reflector head stored in place
+    }
+    cl.sync();  // every CTA is done reading the factorisation's partials
+    __syncthreads();
+    if (J.Rt) {  // Rt(i, u) = R(u, i) for the own rows u < s
+        const int nu = max(0, min(nr, s - r0));
+        for (int e = tid; e < nu * s; e += kQrThreads) {
+            const int lu = e / s, i = e % s, u = r0 + lu;
+            double v = 0.0;
+            if (i > u) v = As[i * ld + lu];
+            else if (i == u) v = betas[u];
+            J.Rt[(int64_t)u * s + i] = v;
+        }
+    }
+    if (!J.Q) return;
+    __syncthreads();
+    int act = 0;
+    for (int c = s - 1; c >= 0; --c) {
+        const double tau = taus[c], v0 = heads[c];
+        const int lb = max(c - r0, 0), ic = c - r0;
+        double *vc = As + c * ld;
+        if (tau != 0.0) {  // identical on every CTA of the cluster
+            double *pdc = pd + (act & 1) * s;
+            ++act;
+            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
+                const double *qc = As + cc * ld;
+                double w = 0.0;
+                for (int i = lb + lane; i < nr; i += 32) w = fma(vc[i], qc[i], w);
+                w = warp_sum(w);
+                if (lane == 0) pdc[cc] = w;
+            }
+            cl.sync();
+            for (int cc = c + 1 + tid; cc < s; cc += kQrThreads) {
+                double d = 0.0;
+#pragma unroll
+                for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pdc, k)[cc];
+                wv[cc] = tau * d;
+            }
+            __syncthreads();
+            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
+                const double w = wv[cc];
+                double *qc = As + cc * ld;
+                for (int i = lb + lane; i < nr; i += 32) qc[i] = fma(-w, vc[i], qc[i]);
+            }
+            __syncthreads();
+        }
+        // column c of Q = H_c e_c
+        for (int i = tid; i < nr; i += kQrThreads) {
+            double q;
+            if (i < ic) q = 0.0;
+            else if (i == ic) q = 1.0 - tau * v0 * v0;
+            else q = -tau * v0 * vc[i];
+            vc[i] = q;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nr * s; e += kQrThreads) {
+        const int i = e % nr, j = e / nr;
+        J.Q[(int64_t)j * J.ldq + r0 + i] = As[j * ld + i];
     }
     cl.sync();  // no CTA leaves while another may still read its partials
 }
 
-template <int kCl>
-__global__ void __launch_bounds__(kQrThreads) k_jacobi_svd_cl(const SvdJob *__restrict__ jobs, double tau) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    __shared__ int s_rot;
-    extern __shared__ double s_dyn[];  // norms (s), order (s ints)
-    const SvdJob J = jobs[blockIdx.x / kCl];
-    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / 32;
-    double *A = J.A, *Z = J.Z;
-    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
-        int i = e % s, j = e / s;
-        __stcg(A + (int64_t)j * s + i, __ldcg(J.R + (int64_t)i * s + j));
-        __stcg(Z + (int64_t)j * s + i, (i == j) ? 1.0 : 0.0);
-    }
-    const int np = s + (s & 1);
-    const int gw = rank * nw + warp, ngw = kCl * nw;
-    cl.sync();
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        for (int round = 0; round < np - 1; ++round) {
-            for (int pr = gw; pr < np / 2; pr += ngw) {
-                int a = (pr == 0) ? 0 : 1 + (pr - 1 + round) % (np - 1);
-                int b = 1 + (np - 2 - pr + round) % (np - 1);
-                if (a >= s || b >= s) continue;
-                int p = min(a, b), q = max(a, b);
-                double *ap = A + (int64_t)p * s, *aq = A + (int64_t)q * s;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int r = lane; r < s; r += 32) {
-                    double x = __ldcg(ap + r), y = __ldcg(aq + r);
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
-                double zeta = (be - al) / (2.0 * ga);
-                double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-                for (int r = lane; r < s; r += 32) {
-                    double x = __ldcg(ap + r), y = __ldcg(aq + r);
-                    __stcg(ap + r, c * x - sn * y);
-                    __stcg(aq + r, sn * x + c * y);
-                }
-                double *zp = Z + (int64_t)p * s, *zq = Z + (int64_t)q * s;
-                for (int r = lane; r < s; r += 32) {
-                    double x = __ldcg(zp + r), y = __ldcg(zq + r);
-                    __stcg(zp + r, c * x - sn * y);
-                    __stcg(zq + r, sn * x + c * y);
-                }
-                if (lane == 0) s_rot = 1;
-            }
-            cl.sync();
-        }
-        int any = 0;
-        for (int k = 0; k < kCl; ++k) any |= *cl.map_shared_rank(&s_rot, k);
-        cl.sync();  // every CTA has read the flags before any resets its own
-        if (!any) break;
-    }
-    // every CTA computes all norms and the same order; each writes its share
-    double *nrm = s_dyn;
-    int *ord = (int *)(s_dyn + s);
-    for (int u = warp; u < s; u += nw) {
-        double v = 0.0;
-        const double *au = A + (int64_t)u * s;
-        for (int r = lane; r < s; r += 32) { double x = __ldcg(au + r); v += x * x; }
-        v = warp_sum(v);
-        if (lane == 0) nrm[u] = sqrt(v);
-    }
-    __syncthreads();
-    for (int u = tid; u < s; u += kQrThreads) {
-        double ku = nrm[u] <= 1.7e308 ? nrm[u] : -1.0;
-        int pos = 0;
-        for (int w = 0; w < s; ++w) {
-            double kw = nrm[w] <= 1.7e308 ? nrm[w] : -1.0;
-            pos += (kw > ku) || (kw == ku && w < u);
-        }
-        ord[pos] = u;
-    }
-    __syncthreads();
-    if (rank == 0 && tid == 0) {
-        int r = 0;
-        bool bad = false;
-        for (int u = 0; u < s; ++u) {
-            r += nrm[u] > tau;
-            bad |= !(nrm[u] <= 1.7e308);
-        }
-        *J.rank = bad ? -1 : r;
-    }
-    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
-        int r = e % s, u = e / s, src = min(max(ord[u], 0), s - 1);
-        J.WS[(int64_t)u * s + r] = __ldcg(A + (int64_t)src * s + r);
-        J.Zs[(int64_t)u * s + r] = __ldcg(Z + (int64_t)src * s + r);
-        if (r == 0) J.S[u] = nrm[src];
-    }
+static size_t qr_sm_bytes(int m, int s, int csize) {
+    const int per = (m + csize - 1) / csize, ld = per | 1;
+    return ((size_t)s * ld + 8 * (size_t)s) * sizeof(double);
 }
 
-// Householder QR on a cluster with ONE cluster barrier per column: each CTA
-// reduces, over its own rows r >= c, the squared norm of column c and the raw
-// products d_cc = sum_r A[r][c] A[r][cc]; the CTA that owns row c also
-// publishes that row.  After the barrier every CTA forms the reflector
-// (v = A[:, c] with v[c] = v0) and w_cc = tau (d_cc + (v0 - alpha) A[c][cc]),
-// then updates its own rows.  Buffers alternate by column parity, so a CTA
-// never overwrites values another CTA may still be reading.
+// QR in global memory (A factorised in place; Q and Rt as above), for panels
+// that do not fit in shared memory.  Same barrier scheme as k_qr_sm.
 template <int kCl>
-__global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(kQrThreads) k_qr_gm(const QrJob *__restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const QrJob J = jobs[blockIdx.x / kCl];
     const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = kQrThreads / 32;
     const int per = (m + kCl - 1) / kCl;
     const int r0 = min(m, rank * per), r1 = min(m, r0 + per);
     __shared__ double red[32];
     __shared__ double s_norm[2];
-    // taus (s), betas (s), dots (2 x s), row c of the owner (2 x s)
-    extern __shared__ double s_dyn[];
+    extern __shared__ double s_dyn[];  // taus (s), betas (s), dots (2 x s), row c of the owner (2 x s)
     double *taus = s_dyn, *betas = s_dyn + s, *dots = s_dyn + 2 * s, *prow = s_dyn + 4 * s;
     double *A = J.A;
     const int64_t lda = J.lda;
@@ -521,7 +257,7 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restr
         for (int r = rb + tid; r < r1; r += kQrThreads) p += col[r] * col[r];
         p = block_sum(p, red);
         if (tid == 0) s_norm[par] = p;
-        for (int cc = c + 1 + warp; cc < s; cc += nw) {
+        for (int cc = c + 1 + warp; cc < s; cc += kNw) {
             const double *dst = A + (int64_t)cc * lda;
             double w = 0.0;
             for (int r = rb + lane; r < r1; r += 32) w += col[r] * dst[r];
@@ -536,16 +272,11 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restr
         for (int k = 0; k < kCl; ++k) nrm2 += cl.map_shared_rank(s_norm, k)[par];
         const double *orow = cl.map_shared_rank(pr, owner);
         const double alpha = orow[c];
-        const double nrm = sqrt(nrm2);
-        double tau = 0.0, beta = 0.0, v0 = 0.0;
-        if (nrm != 0.0) {
-            beta = -copysign(nrm, alpha);
-            v0 = alpha - beta;
-            tau = 2.0 / (nrm2 - alpha * alpha + v0 * v0);
-        }
+        double tau, beta, v0;
+        householder(nrm2, alpha, tau, beta, v0);
         if (tid == 0) { taus[c] = tau; betas[c] = beta; }
         if (tau != 0.0) {
-            for (int cc = c + 1 + warp; cc < s; cc += nw) {
+            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
                 double d = 0.0;
                 for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pd, k)[cc];
                 const double w = tau * (d + (v0 - alpha) * orow[cc]);
@@ -558,16 +289,17 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restr
         __syncthreads();
     }
     cl.sync();  // partial buffers are reused below
-    if (J.R) {
+    if (J.Rt) {
         for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
             int i = r0 + e % (r1 - r0), j = e / (r1 - r0);
             if (i >= s) continue;
             double v = 0.0;
             if (i < j) v = A[(int64_t)j * lda + i];
             else if (i == j) v = betas[i];
-            J.R[(int64_t)j * s + i] = v;
+            J.Rt[(int64_t)i * s + j] = v;
         }
     }
+    if (!J.Q) return;
     double *Q = J.Q;
     const int64_t ldq = J.ldq;
     for (int e = tid; e < (r1 - r0) * s; e += kQrThreads) {
@@ -583,7 +315,7 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restr
         double *pb = dots + (active & 1) * s;
         ++active;
         const int rb = max(r0, c);
-        for (int cc = c + warp; cc < s; cc += nw) {
+        for (int cc = c + warp; cc < s; cc += kNw) {
             const double *dst = Q + (int64_t)cc * ldq;
             double w = 0.0;
             for (int r = rb + lane; r < r1; r += 32) w += v[r] * dst[r];
@@ -591,7 +323,7 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restr
             if (lane == 0) pb[cc] = w;
         }
         cl.sync();
-        for (int cc = c + warp; cc < s; cc += nw) {
+        for (int cc = c + warp; cc < s; cc += kNw) {
             double w = 0.0;
             for (int k = 0; k < kCl; ++k) w += cl.map_shared_rank(pb, k)[cc];
             w *= tau;
@@ -603,154 +335,314 @@ __global__ void __launch_bounds__(kQrThreads) k_house_qr_c1(const QrJob *__restr
     cl.sync();
 }
 
-// One-sided Jacobi SVD with a block schedule: the s columns (padded to
-// 2 kCl b with virtual zero columns) form 2 kCl blocks of b columns; every
-// CTA holds two blocks of A and Z in shared memory and rotates all pairs
-// between them (and, in the first block round of a sweep, inside them) with
-// only block barriers; blocks then move through L2 following a round-robin
-// tournament, so each block pair meets once per sweep at the cost of one
-// cluster barrier per block round.
-template <int kCl>
-__global__ void __launch_bounds__(kQrThreads) k_jacobi_blk(const SvdJob *__restrict__ jobs, double tau) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    __shared__ int s_rot;
-    extern __shared__ double s_dyn[];
-    const SvdJob J = jobs[blockIdx.x / kCl];
-    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kQrThreads / 32;
-    const int nblk = 2 * kCl;
-    const int b = (s + nblk - 1) / nblk;
-    double *Ab = s_dyn;          // [2][b][s]
-    double *Zb = s_dyn + 2 * b * s;  // [2][b][s]
-    double *A = J.A, *Z = J.Z;
-    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
-        int i = e % s, j = e / s;
-        __stcg(A + (int64_t)j * s + i, __ldcg(J.R + (int64_t)i * s + j));
-        __stcg(Z + (int64_t)j * s + i, (i == j) ? 1.0 : 0.0);
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi SVD of M = R' (s x s): right rotations make the
+// columns of M mutually orthogonal, M J = W S; S are the column norms and W
+// the unit columns.  Output sorted by S descending (non-finite last).
+struct SvdJob {
+    const double *Rt;  // s x s input R' (ld s)
+    double *work;      // s x s workspace (global-memory variant only)
+    double *W;         // s x s output: unit left singular vectors of R', sorted
+    double *S;         // s output singular values, descending
+    int *rank;         // #{S > tau}, or -1 if any S is not finite
+    int *sweeps;       // number of sweeps run
+    int s;
+};
+
+// Fast approximate reciprocal and reciprocal square root of a double (the
+// PTX approximation instructions); callers refine them where it matters.
+__device__ __forceinline__ double rcp_approx(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+__device__ __forceinline__ double rsqrt_approx(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
+// Rotate columns x and y (length s; the calling warp's lanes stride 32) so
+// that they become orthogonal; returns whether a rotation was applied.
+// Pairs with |x'y| <= tol |x| |y| are left alone.  The rotation angle only
+// steers convergence, so t = tan(angle) is computed from approximations;
+// c = 1/sqrt(1 + t^2) is refined by two Newton steps for the reciprocal
+// square root, y <- y (3 - x y^2) / 2, so that (c, c t) is orthogonal to
+// working precision and the singular values are preserved.
+__device__ __forceinline__ bool jacobi_rotate(double *x, double *y, int s, int lane, double tol2) {
+    double al = 0.0, be = 0.0, ga = 0.0;
+    for (int r = lane; r < s; r += 32) {
+        const double a = x[r], b = y[r];
+        al = fma(a, a, al);
+        be = fma(b, b, be);
+        ga = fma(a, b, ga);
     }
-    cl.sync();
-    auto block_at = [&](int pos, int round) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (nblk - 1); };
-    // rotate column pair (x, y) of the local buffers; virtual (zero) columns are skipped
-    auto rotate = [&](double *ax, double *ay, double *zx, double *zy) {
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < s; r += 32) {
-            double x = ax[r], y = ay[r];
-            al += x * x;
-            be += y * y;
-            ga += x * y;
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) return;
-        double zeta = (be - al) / (2.0 * ga);
-        double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-        for (int r = lane; r < s; r += 32) {
-            double x = ax[r], y = ay[r];
-            ax[r] = cs * x - sn * y;
-            ay[r] = sn * x + cs * y;
-            double u = zx[r], v = zy[r];
-            zx[r] = cs * u - sn * v;
-            zy[r] = sn * u + cs * v;
-        }
-        if (lane == 0) s_rot = 1;
-    };
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (tid == 0) s_rot = 0;
-        for (int round = 0; round < nblk - 1; ++round) {
-            const int bx = block_at(rank, round), by = block_at(nblk - 1 - rank, round);
-            // load the two blocks (virtual columns as zeros)
-            for (int e = tid; e < 2 * b * s; e += kQrThreads) {
-                int slot = e / (b * s), rem = e % (b * s), jj = rem / s, r = rem % s;
-                int gcol = (slot ? by : bx) * b + jj;
-                Ab[e] = gcol < s ? __ldcg(A + (int64_t)gcol * s + r) : 0.0;
-                Zb[e] = gcol < s ? __ldcg(Z + (int64_t)gcol * s + r) : 0.0;
+    al = warp_sum(al);
+    be = warp_sum(be);
+    ga = warp_sum(ga);
+    if (ga == 0.0 || ga * ga <= tol2 * (al * be)) return false;
+    double rg = rcp_approx(2.0 * ga);
+    rg = rg * fma(-2.0 * ga, rg, 2.0);
+    const double zeta = (be - al) * rg, az = fabs(zeta);
+    const double q = fma(zeta, zeta, 1.0);
+    const double t = copysign(az < 1e150 ? rcp_approx(az + q * rsqrt_approx(q)) : 0.5 * rcp_approx(az), zeta);
+    const double u = fma(t, t, 1.0);
+    double c = rsqrt_approx(u);
+    c = c * fma(-0.5 * u * c, c, 1.5);
+    c = c * fma(-0.5 * u * c, c, 1.5);
+    const double sn = c * t;
+    for (int r = lane; r < s; r += 32) {
+        const double a = x[r], b = y[r];
+        x[r] = fma(c, a, -sn * b);
+        y[r] = fma(sn, a, c * b);
+    }
+    return true;
+}
+
+// Convergence threshold of a pair, squared: |x'y| <= 8 sqrt(s) u |x| |y|
+// (u = 2^-53), a few times the rounding error of the dot products, so that
+// rounding alone never keeps a sweep alive.
+__device__ __forceinline__ double jacobi_tol2(int s) {
+    const double tol = 8.0 * sqrt((double)s) * 1.1102230246251565e-16;
+    return tol * tol;
+}
+
+// Sort key of a column norm: non-finite values sort last.
+__device__ __forceinline__ double norm_key(double v) { return v <= 1.7e308 ? v : -1.0; }
+
+// Round-robin tournament over 2C blocks: block held at position `pos` in
+// global round g (position 0 stays, the others rotate), and its inverse.
+__device__ __forceinline__ int block_at(int pos, int g, int nblk) {
+    return pos == 0 ? 0 : 1 + (pos - 1 + g) % (nblk - 1);
+}
+__device__ __forceinline__ int pos_of(int blk, int g, int nblk) {
+    return blk == 0 ? 0 : 1 + ((blk - 1 - g) % (nblk - 1) + (nblk - 1)) % (nblk - 1);
+}
+
+// Rotate all pairs between the two b-column blocks X (global block bx) and Y
+// (by), and, if `inner`, the pairs within each of them.  Virtual columns
+// (global index >= s) are zero and skipped.  Returns whether any rotation
+// was applied by this thread's warp.
+__device__ __forceinline__ bool jacobi_block_pairs(double *X, double *Y, int bx, int by, int b, int s, bool inner,
+                                                   int lane, int warp) {
+    const double tol2 = jacobi_tol2(s);
+    bool rot = false;
+    if (inner) {
+        const int bp = b + (b & 1);
+        for (int ir = 0; ir < bp - 1; ++ir) {
+            for (int pr = warp; pr < bp; pr += kNw) {  // bp/2 pairs per block, two blocks
+                const int slot = pr / (bp / 2), q = pr % (bp / 2);
+                const int a = (q == 0) ? 0 : 1 + (q - 1 + ir) % (bp - 1);
+                const int c2 = 1 + (bp - 2 - q + ir) % (bp - 1);
+                const int blk = slot ? by : bx;
+                if (a >= b || c2 >= b || blk * b + max(a, c2) >= s) continue;
+                double *base = slot ? Y : X;
+                rot |= jacobi_rotate(base + min(a, c2) * s, base + max(a, c2) * s, s, lane, tol2);
             }
             __syncthreads();
-            if (round == 0) {
-                // pairs inside each of the two blocks: round robin over b (padded to even)
-                const int bp = b + (b & 1);
-                for (int ir = 0; ir < bp - 1; ++ir) {
-                    for (int pr = warp; pr < bp; pr += nw) {  // bp/2 pairs per block, two blocks
-                        int slot = pr / (bp / 2), q = pr % (bp / 2);
-                        int a = (q == 0) ? 0 : 1 + (q - 1 + ir) % (bp - 1);
-                        int c2 = 1 + (bp - 2 - q + ir) % (bp - 1);
-                        if (a >= b || c2 >= b) continue;
-                        int gx = (slot ? by : bx) * b + a, gy = (slot ? by : bx) * b + c2;
-                        if (gx >= s || gy >= s) continue;
-                        double *base = Ab + slot * b * s, *zb = Zb + slot * b * s;
-                        rotate(base + min(a, c2) * s, base + max(a, c2) * s, zb + min(a, c2) * s,
-                               zb + max(a, c2) * s);
-                    }
-                    __syncthreads();
+        }
+    }
+    for (int k = 0; k < b; ++k) {
+        for (int i = warp; i < b; i += kNw) {
+            const int jy = (i + k) % b;
+            const int gx = bx * b + i, gy = by * b + jy;
+            if (gx >= s || gy >= s) continue;
+            // the lower global index is the first column of the pair
+            if (gx < gy) rot |= jacobi_rotate(X + i * s, Y + jy * s, s, lane, tol2);
+            else rot |= jacobi_rotate(Y + jy * s, X + i * s, s, lane, tol2);
+        }
+        __syncthreads();
+    }
+    return rot;
+}
+
+// Column norms, descending order over the whole matrix, and the output of the
+// columns held in `cols` (global indices gx * b + j and gy * b + j).
+// `all_nrm` must hold every column's norm on entry.
+__device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols, int gx, int gy, int b, const double *all_nrm,
+                            int lane, int warp) {
+    const int s = J.s;
+    for (int q = warp; q < 2 * b; q += kNw) {
+        const int slot = q / b, j = q % b, u = (slot ? gy : gx) * b + j;
+        if (u >= s) continue;
+        const double ku = norm_key(all_nrm[u]);
+        int pos = 0;
+        for (int w = lane; w < s; w += 32) {
+            const double kw = norm_key(all_nrm[w]);
+            pos += (kw > ku) || (kw == ku && w < u);
+        }
+        pos = __reduce_add_sync(0xFFFFFFFFu, pos);
+        const double nv = all_nrm[u];
+        const bool unit = nv > 0.0 && nv <= 1.7e308;
+        const double *col = cols + q * s;
+        for (int r = lane; r < s; r += 32) J.W[(int64_t)pos * s + r] = unit ? col[r] / nv : col[r];
+        if (lane == 0) J.S[pos] = nv;
+    }
+}
+
+__device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, int sweeps) {
+    *J.sweeps = sweeps;
+    int r = 0;
+    bool bad = false;
+    for (int u = 0; u < J.s; ++u) {
+        r += all_nrm[u] > tau;
+        bad |= !(all_nrm[u] <= 1.7e308);
+    }
+    *J.rank = bad ? -1 : r;
+}
+
+// Block Jacobi with the blocks in shared memory.  Shared memory: two buffers
+// of two b x s blocks, 2b local norms, s gathered norms.
+template <int kCl>
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs, double tau) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ int s_flag[2];
+    extern __shared__ double sm[];
+    const SvdJob J = jobs[blockIdx.x / kCl];
+    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nblk = 2 * kCl;
+    const int b = (s + nblk - 1) / nblk, bs = b * s;
+    auto buf = [&](int k) { return sm + k * 2 * bs; };
+    double *nrm_loc = sm + 4 * bs, *all_nrm = nrm_loc + 2 * b;
+    const int px = rank, py = nblk - 1 - rank;
+    for (int slot = 0; slot < 2; ++slot) {
+        const int blk = block_at(slot ? py : px, 0, nblk);
+        double *dst = buf(0) + slot * bs;
+        for (int e = tid; e < bs; e += kQrThreads) {
+            const int u = blk * b + e / s;
+            dst[e] = u < s ? J.Rt[(int64_t)u * s + e % s] : 0.0;
+        }
+    }
+    __syncthreads();
+    int cur = 0, g = 0, nsweep = 0;
+    bool done = false;
+    for (int sweep = 0; sweep < kMaxSweeps && !done; ++sweep, ++nsweep) {
+        if (tid == 0) s_flag[sweep & 1] = 0;
+        __syncthreads();
+        for (int round = 0; round < nblk - 1; ++round, ++g) {
+            const int bx = block_at(px, g, nblk), by = block_at(py, g, nblk);
+            if (jacobi_block_pairs(buf(cur), buf(cur) + bs, bx, by, b, s, round == 0, lane, warp) && lane == 0)
+                s_flag[sweep & 1] = 1;
+            cl.sync();
+            if (round == nblk - 2) {
+                int any = 0;
+#pragma unroll
+                for (int k = 0; k < kCl; ++k) any |= cl.map_shared_rank(s_flag, k)[sweep & 1];
+                if (!any) {
+                    done = true;
+                    break;
                 }
             }
-            // pairs across the two blocks: b shifts of b disjoint pairs
-            for (int k = 0; k < b; ++k) {
-                for (int i = warp; i < b; i += nw) {
-                    int jy = (i + k) % b;
-                    int gx = bx * b + i, gy = by * b + jy;
-                    if (gx >= s || gy >= s) continue;
-                    // keep the lower global index as the first column of the pair
-                    if (gx < gy) rotate(Ab + i * s, Ab + (b + jy) * s, Zb + i * s, Zb + (b + jy) * s);
-                    else rotate(Ab + (b + jy) * s, Ab + i * s, Zb + (b + jy) * s, Zb + i * s);
-                }
-                __syncthreads();
+            // pull the blocks of round g + 1 from their holders in round g
+            for (int slot = 0; slot < 2; ++slot) {
+                const int blk = block_at(slot ? py : px, g + 1, nblk);
+                const int p = pos_of(blk, g, nblk);
+                const int h = p < kCl ? p : nblk - 1 - p, hs = p < kCl ? 0 : 1;
+                const double *src = cl.map_shared_rank(buf(cur) + hs * bs, h);
+                double *dst = buf(cur ^ 1) + slot * bs;
+                for (int e = tid; e < bs; e += kQrThreads) dst[e] = src[e];
             }
-            // write back the real columns
-            for (int e = tid; e < 2 * b * s; e += kQrThreads) {
-                int slot = e / (b * s), rem = e % (b * s), jj = rem / s, r = rem % s;
-                int gcol = (slot ? by : bx) * b + jj;
-                if (gcol < s) {
-                    __stcg(A + (int64_t)gcol * s + r, Ab[e]);
-                    __stcg(Z + (int64_t)gcol * s + r, Zb[e]);
-                }
+            cur ^= 1;
+            __syncthreads();
+        }
+    }
+    const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
+    for (int q = warp; q < 2 * b; q += kNw) {
+        const double *col = buf(cur) + q * s;
+        double v = 0.0;
+        for (int r = lane; r < s; r += 32) v = fma(col[r], col[r], v);
+        v = warp_sum(v);
+        if (lane == 0) nrm_loc[q] = sqrt(v);
+    }
+    cl.sync();
+    for (int e = tid; e < 2 * b * kCl; e += kQrThreads) {
+        const int h = e / (2 * b), q = e % (2 * b), slot = q / b, j = q % b;
+        const int u = block_at(slot ? nblk - 1 - h : h, g, nblk) * b + j;
+        if (u < s) all_nrm[u] = cl.map_shared_rank(nrm_loc, h)[q];
+    }
+    __syncthreads();
+    jacobi_emit(J, buf(cur), gx, gy, b, all_nrm, lane, warp);
+    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, nsweep);
+    cl.sync();  // no CTA leaves while another may still read its norms
+}
+
+static size_t jacobi_sm_bytes(int s, int csize) {
+    const int b = (s + 2 * csize - 1) / (2 * csize);
+    return ((size_t)4 * b * s + 2 * b + s) * sizeof(double);
+}
+
+// Block Jacobi with the matrix in global memory (L2): the two blocks of a
+// round are staged in shared memory and written back before the cluster
+// barrier.  Shared memory: two b x s blocks, then s norms.
+template <int kCl>
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restrict__ jobs, double tau) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    __shared__ int s_flag[2];
+    extern __shared__ double sm[];
+    const SvdJob J = jobs[blockIdx.x / kCl];
+    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nblk = 2 * kCl;
+    const int b = (s + nblk - 1) / nblk, bs = b * s;
+    double *Ab = sm, *all_nrm = sm + 2 * bs;
+    double *A = J.work;
+    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) __stcg(A + e, J.Rt[e]);
+    cl.sync();
+    const int px = rank, py = nblk - 1 - rank;
+    int g = 0, nsweep = 0;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        ++nsweep;
+        if (tid == 0) s_flag[sweep & 1] = 0;
+        __syncthreads();
+        for (int round = 0; round < nblk - 1; ++round, ++g) {
+            const int bx = block_at(px, g, nblk), by = block_at(py, g, nblk);
+            for (int e = tid; e < 2 * bs; e += kQrThreads) {
+                const int slot = e / bs, u = (slot ? by : bx) * b + (e % bs) / s;
+                Ab[e] = u < s ? __ldcg(A + (int64_t)u * s + e % s) : 0.0;
+            }
+            __syncthreads();
+            if (jacobi_block_pairs(Ab, Ab + bs, bx, by, b, s, round == 0, lane, warp) && lane == 0)
+                s_flag[sweep & 1] = 1;
+            for (int e = tid; e < 2 * bs; e += kQrThreads) {
+                const int slot = e / bs, u = (slot ? by : bx) * b + (e % bs) / s;
+                if (u < s) __stcg(A + (int64_t)u * s + e % s, Ab[e]);
             }
             cl.sync();
         }
         int any = 0;
-        for (int k = 0; k < kCl; ++k) any |= *cl.map_shared_rank(&s_rot, k);
-        cl.sync();
+        for (int k = 0; k < kCl; ++k) any |= cl.map_shared_rank(s_flag, k)[sweep & 1];
         if (!any) break;
     }
-    // every CTA computes all norms and the same order; each writes its share
-    double *nrm = s_dyn;  // block buffers are free now
-    int *ord = (int *)(s_dyn + s);
-    for (int u = warp; u < s; u += nw) {
+    // every CTA computes all norms; each writes its positions' columns
+    for (int u = warp; u < s; u += kNw) {
         double v = 0.0;
-        const double *au = A + (int64_t)u * s;
-        for (int r = lane; r < s; r += 32) { double x = __ldcg(au + r); v += x * x; }
+        for (int r = lane; r < s; r += 32) {
+            const double x = __ldcg(A + (int64_t)u * s + r);
+            v = fma(x, x, v);
+        }
         v = warp_sum(v);
-        if (lane == 0) nrm[u] = sqrt(v);
+        if (lane == 0) all_nrm[u] = sqrt(v);
     }
     __syncthreads();
-    for (int u = tid; u < s; u += kQrThreads) {
-        double ku = nrm[u] <= 1.7e308 ? nrm[u] : -1.0;
-        int pos = 0;
-        for (int w = 0; w < s; ++w) {
-            double kw = nrm[w] <= 1.7e308 ? nrm[w] : -1.0;
-            pos += (kw > ku) || (kw == ku && w < u);
-        }
-        ord[pos] = u;
+    const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
+    for (int e = tid; e < 2 * bs; e += kQrThreads) {
+        const int slot = e / bs, u = (slot ? gy : gx) * b + (e % bs) / s;
+        Ab[e] = u < s ? __ldcg(A + (int64_t)u * s + e % s) : 0.0;
     }
     __syncthreads();
-    if (rank == 0 && tid == 0) {
-        int r = 0;
-        bool bad = false;
-        for (int u = 0; u < s; ++u) {
-            r += nrm[u] > tau;
-            bad |= !(nrm[u] <= 1.7e308);
-        }
-        *J.rank = bad ? -1 : r;
-    }
-    for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) {
-        int r = e % s, u = e / s, src = min(max(ord[u], 0), s - 1);
-        J.WS[(int64_t)u * s + r] = __ldcg(A + (int64_t)src * s + r);
-        J.Zs[(int64_t)u * s + r] = __ldcg(Z + (int64_t)src * s + r);
-        if (r == 0) J.S[u] = nrm[src];
-    }
+    jacobi_emit(J, Ab, gx, gy, b, all_nrm, lane, warp);
+    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, nsweep);
+    cl.sync();  // no CTA leaves while another may still read its flag
 }
+
+static size_t jacobi_gm_bytes(int s, int csize) {
+    const int b = (s + 2 * csize - 1) / (2 * csize);
+    return ((size_t)2 * b * s + s) * sizeof(double);
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers.
 
 template <class K, class... Args>
 static void launch_cluster(K kernel, int csize, int nclusters, size_t smem, cudaStream_t st, Args... args) {
@@ -770,23 +662,42 @@ static void launch_cluster(K kernel, int csize, int nclusters, size_t smem, cuda
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
 }
 
+// Dynamic shared memory a kernel may use: the device's opt-in per-block limit
+// minus the kernel's static shared memory (the attribute is raised once).
+static size_t smem_cap(const void *kernel) {
+    static std::mutex mu;
+    static std::map<const void *, size_t> caps;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = caps.find(kernel);
+    if (it != caps.end()) return it->second;
+    int dev = 0, optin = 0;
+    TLR_CUDA_TRY(cudaGetDevice(&dev));
+    TLR_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    TLR_CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
+    size_t cap = (size_t)optin - fa.sharedSizeBytes;
+    TLR_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
+    caps[kernel] = cap;
+    return cap;
+}
+
 // Whether clusters of 16 CTAs (a non-portable size) can run on this device.
 static bool cluster16_ok() {
     static int state = -1;
     if (state < 0) {
         state = 0;
-        if (cudaFuncSetAttribute(k_house_qr_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess &&
-            cudaFuncSetAttribute(k_house_qr_c1<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess &&
-            cudaFuncSetAttribute(k_jacobi_blk<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess &&
-            cudaFuncSetAttribute(k_jacobi_svd_cl<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                cudaSuccess) {
+        const void *k16[] = {(const void *)k_qr_sm<16>, (const void *)k_qr_gm<16>, (const void *)k_jacobi_sm<16>,
+                             (const void *)k_jacobi_gm<16>};
+        bool ok = true;
+        for (const void *k : k16)
+            ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+        if (ok) {
+            // one cluster of 16 CTAs that each fill an SM's shared memory must fit
+            const size_t need = std::min(smem_cap((const void *)k_qr_sm<16>), smem_cap((const void *)k_jacobi_sm<16>));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16);
             cfg.blockDim = dim3(kQrThreads);
-            cfg.dynamicSmemBytes = 16 * 1024;
+            cfg.dynamicSmemBytes = need;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = 16;
@@ -795,13 +706,125 @@ static bool cluster16_ok() {
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int n1 = 0, n2 = 0;
-            if (cudaOccupancyMaxActiveClusters(&n1, k_house_qr_cl<16>, &cfg) == cudaSuccess &&
-                cudaOccupancyMaxActiveClusters(&n2, k_jacobi_svd_cl<16>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
+            if (cudaOccupancyMaxActiveClusters(&n1, k_qr_sm<16>, &cfg) == cudaSuccess &&
+                cudaOccupancyMaxActiveClusters(&n2, k_jacobi_sm<16>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
                 state = 1;
         }
         cudaGetLastError();  // clear any error of the queries
     }
     return state == 1;
+}
+
+// Cluster sizes by sample size: the panel work per column shrinks with the
+// cluster, the barrier count does not, so small samples use small clusters.
+static int qr_cluster(int s) { return s <= 64 ? 4 : (s <= 128 ? 8 : 16); }
+static int svd_cluster(int s) { return s <= 48 ? 1 : (s <= 96 ? 4 : (s <= 160 ? 8 : 16)); }
+
+using QrKernel = void (*)(const QrJob *);
+using SvdKernel = void (*)(const SvdJob *, double);
+
+static QrKernel qr_sm_kernel(int c) {
+    switch (c) {
+    case 1: return k_qr_sm<1>;
+    case 2: return k_qr_sm<2>;
+    case 4: return k_qr_sm<4>;
+    case 8: return k_qr_sm<8>;
+    default: return k_qr_sm<16>;
+    }
+}
+static SvdKernel svd_sm_kernel(int c) {
+    switch (c) {
+    case 1: return k_jacobi_sm<1>;
+    case 2: return k_jacobi_sm<2>;
+    case 4: return k_jacobi_sm<4>;
+    case 8: return k_jacobi_sm<8>;
+    default: return k_jacobi_sm<16>;
+    }
+}
+
+// One launch per (kernel, cluster size) class, with the class's largest
+// shared-memory need.
+template <class Job, class K>
+struct LaunchClass {
+    K kernel;
+    int csize;
+    size_t smem = 0;
+    std::vector<Job> jobs;
+};
+
+template <class Job, class K, class... Extra>
+static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClass<Job, K>> &cls,
+                           Extra... extra) {
+    for (auto &c : cls) {
+        if (c.jobs.empty()) continue;
+        auto *d = (const Job *)stage_push(ctx, c.jobs.data(), c.jobs.size() * sizeof(Job), st);
+        launch_cluster(c.kernel, c.csize, (int)c.jobs.size(), c.smem, st, d, extra...);
+    }
+}
+
+template <class Job, class K>
+static void add_to_class(std::vector<LaunchClass<Job, K>> &cls, K kernel, int csize, size_t smem, const Job &j) {
+    for (auto &c : cls)
+        if (c.kernel == kernel && c.csize == csize) {
+            c.smem = std::max(c.smem, smem);
+            c.jobs.push_back(j);
+            return;
+        }
+    LaunchClass<Job, K> c{kernel, csize, smem, {j}};
+    cls.push_back(c);
+}
+
+// QR stage for a list of jobs.  `copy[u]` (k x s, may alias nothing) is
+// scratch for jobs that fall back to the in-place global-memory kernel when
+// the input must survive (R-only factorisations).
+static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &jobs, const std::vector<double *> &copy) {
+    const bool big = cluster16_ok();
+    std::vector<LaunchClass<QrJob, QrKernel>> cls;
+    for (size_t u = 0; u < jobs.size(); ++u) {
+        QrJob J = jobs[u];
+        int c = qr_cluster(J.s);
+        if (c == 16 && !big) c = 8;
+        int top = big ? 16 : 8;
+        while (c < top && qr_sm_bytes(J.m, J.s, c) > smem_cap((const void *)qr_sm_kernel(c))) c *= 2;
+        QrKernel k = qr_sm_kernel(c);
+        size_t bytes = qr_sm_bytes(J.m, J.s, c);
+        if (bytes <= smem_cap((const void *)k)) {
+            add_to_class(cls, k, c, bytes, J);
+            continue;
+        }
+        // global-memory fallback: factorises its input in place
+        if (!J.Q) {
+            TLR_CUDA_TRY(cudaMemcpy2DAsync(copy[u], (size_t)J.m * sizeof(double), J.A, (size_t)J.lda * sizeof(double),
+                                           (size_t)J.m * sizeof(double), J.s, cudaMemcpyDeviceToDevice, st));
+            J.A = copy[u];
+            J.lda = J.m;
+        }
+        add_to_class(cls, big ? (QrKernel)k_qr_gm<16> : (QrKernel)k_qr_gm<8>, top, 6 * (size_t)J.s * sizeof(double),
+                     J);
+    }
+    launch_classes(ctx, st, cls);
+}
+
+static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs, double tau) {
+    const bool big = cluster16_ok();
+    const int top = big ? 16 : 8;
+    std::vector<LaunchClass<SvdJob, SvdKernel>> cls;
+    for (const SvdJob &J : jobs) {
+        int c = svd_cluster(J.s);
+        if (c > top) c = top;
+        while (c < top && jacobi_sm_bytes(J.s, c) > smem_cap((const void *)svd_sm_kernel(c))) c = std::max(2 * c, 4);
+        SvdKernel k = svd_sm_kernel(c);
+        size_t bytes = jacobi_sm_bytes(J.s, c);
+        if (bytes <= smem_cap((const void *)k)) {
+            add_to_class(cls, k, c, bytes, J);
+            continue;
+        }
+        SvdKernel kg = big ? (SvdKernel)k_jacobi_gm<16> : (SvdKernel)k_jacobi_gm<8>;
+        bytes = jacobi_gm_bytes(J.s, top);
+        if (bytes > smem_cap((const void *)kg)) throw make_error(TLR_ERR_ARG, "sample size %d too large for this device", J.s);
+        add_to_class(cls, kg, top, bytes, J);
+    }
+    launch_classes(ctx, st, cls, tau);
 }
 
 __global__ void k_gaussian(double *__restrict__ a, int64_t count, uint64_t seed) {
@@ -822,100 +845,11 @@ __global__ void k_gaussian(double *__restrict__ a, int64_t count, uint64_t seed)
 void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
     if (ctx->d_omega) return;
     ctx->omega_rows = kMaxTile;
-    ctx->omega_cols = kMaxSample + kProbes;
+    ctx->omega_cols = kMaxSample;
     int64_t cnt = (int64_t)ctx->omega_rows * ctx->omega_cols;
     TLR_CUDA_TRY(cudaMalloc(&ctx->d_omega, cnt * sizeof(double)));
     launch(k_gaussian, (unsigned)ceil_div(cnt, 256), 256, 0, s, ctx->d_omega, cnt, 0x243F6A8885A308D3ull);
     TLR_CHECK_LAUNCH();
-}
-
-// Launch one stage for a list of jobs: samples below kClusterMinS on one CTA
-// each, larger ones on a cluster of kCl CTAs.
-constexpr int kClusterMinS = 48;
-
-constexpr int kCluster16MinS = 128;
-
-// Launch one stage for a list of jobs by sample size: one CTA each below
-// kClusterMinS, clusters of 8 CTAs up to kCluster16MinS, clusters of 16 above
-// (when the device runs them; else 8).
-template <class Job, class... Extra>
-static void split_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<Job> &jobs,
-                         const std::vector<int> &sizes, void (*one)(const Job *, Extra...),
-                         void (*c8)(const Job *, Extra...), void (*c16)(const Job *, Extra...),
-                         size_t smem_per_s, Extra... extra) {
-    const bool big_ok = cluster16_ok();
-    std::vector<Job> part[3];
-    int smax[3] = {0, 0, 0};
-    for (size_t u = 0; u < jobs.size(); ++u) {
-        int cls = sizes[u] < kClusterMinS ? 0 : ((sizes[u] < kCluster16MinS || !big_ok) ? 1 : 2);
-        part[cls].push_back(jobs[u]);
-        smax[cls] = std::max(smax[cls], sizes[u]);
-    }
-    if (!part[0].empty()) {
-        auto *d = (const Job *)stage_push(ctx, part[0].data(), part[0].size() * sizeof(Job), st);
-        launch(one, (unsigned)part[0].size(), kQrThreads, smem_per_s * smax[0], st, d, extra...);
-        TLR_CHECK_LAUNCH();
-    }
-    if (!part[1].empty()) {
-        auto *d = (const Job *)stage_push(ctx, part[1].data(), part[1].size() * sizeof(Job), st);
-        launch_cluster(c8, 8, (int)part[1].size(), smem_per_s * smax[1], st, d, extra...);
-    }
-    if (!part[2].empty()) {
-        auto *d = (const Job *)stage_push(ctx, part[2].data(), part[2].size() * sizeof(Job), st);
-        launch_cluster(c16, 16, (int)part[2].size(), smem_per_s * smax[2], st, d, extra...);
-    }
-}
-
-// Shared memory of the block Jacobi: two blocks of A and of Z, b = ceil(s / 2C).
-static size_t jacobi_blk_smem(int s, int csize) {
-    int b = (s + 2 * csize - 1) / (2 * csize);
-    return (size_t)4 * b * s * sizeof(double);
-}
-
-// The SVD stage: one CTA per small sample; the block-scheduled cluster kernel
-// where its blocks fit in shared memory; the per-round cluster kernel beyond.
-static void jacobi_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs,
-                          const std::vector<int> &sizes, double tau) {
-    // dynamic shared memory available to the block kernel: the device's opt-in
-    // per-block limit minus the kernel's static shared memory
-    static size_t smem_cap = 0;
-    if (smem_cap == 0) {
-        int dev = 0, optin = 0;
-        TLR_CUDA_TRY(cudaGetDevice(&dev));
-        TLR_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        cudaFuncAttributes fa8, fa16;
-        TLR_CUDA_TRY(cudaFuncGetAttributes(&fa8, k_jacobi_blk<8>));
-        TLR_CUDA_TRY(cudaFuncGetAttributes(&fa16, k_jacobi_blk<16>));
-        size_t cap = (size_t)optin - std::max(fa8.sharedSizeBytes, fa16.sharedSizeBytes);
-        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-        TLR_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_blk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap));
-        smem_cap = cap;
-    }
-    const bool big_ok = cluster16_ok();
-    std::vector<SvdJob> part[5];
-    int smax[5] = {0, 0, 0, 0, 0};
-    for (size_t u = 0; u < jobs.size(); ++u) {
-        int sz = sizes[u], cls;
-        int csize = (sz >= kCluster16MinS && big_ok) ? 16 : 8;
-        if (sz < kClusterMinS) cls = 0;
-        else if (jacobi_blk_smem(sz, csize) <= smem_cap) cls = (csize == 8) ? 1 : 2;
-        else cls = (csize == 8) ? 3 : 4;
-        part[cls].push_back(jobs[u]);
-        smax[cls] = std::max(smax[cls], sz);
-    }
-    const size_t per = sizeof(double) + sizeof(int);
-    for (int cls = 0; cls < 5; ++cls) {
-        if (part[cls].empty()) continue;
-        auto *d = (const SvdJob *)stage_push(ctx, part[cls].data(), part[cls].size() * sizeof(SvdJob), st);
-        int n = (int)part[cls].size();
-        switch (cls) {
-        case 0: launch(k_jacobi_svd, (unsigned)n, kQrThreads, per * smax[0], st, d, tau); TLR_CHECK_LAUNCH(); break;
-        case 1: launch_cluster(k_jacobi_blk<8>, 8, n, jacobi_blk_smem(smax[1], 8), st, d, tau); break;
-        case 2: launch_cluster(k_jacobi_blk<16>, 16, n, jacobi_blk_smem(smax[2], 16), st, d, tau); break;
-        case 3: launch_cluster(k_jacobi_svd_cl<8>, 8, n, per * smax[3], st, d, tau); break;
-        case 4: launch_cluster(k_jacobi_svd_cl<16>, 16, n, per * smax[4], st, d, tau); break;
-        }
-    }
 }
 
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
@@ -934,7 +868,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         TLR_CUDA_TRY(cudaEventRecord(ctx->comp_events[k], st));
         ev.push_back(ctx->comp_events[k]);
     };
-    // 8 marks per round: start, after sampling, QR of Y, projection, QR of B',
+    // 8 marks per round: start, after sampling, QR of Y, projection, QR of B,
     // SVD, host decision, U/V; summed into ctx->comp_ms when the call ends
     struct Flush {
         tlr_ctx *ctx;
@@ -966,7 +900,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
     while (!pending.empty()) {
         const size_t np = pending.size();
         // workspace offsets (doubles)
-        std::vector<int64_t> oY(np), oQ(np), oB(np), oQ2(np), oR(np), oA(np), oZ(np), oS(np), oWS(np), oZs(np);
+        std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np);
         std::vector<int> ps(np);
         int64_t tot = 0;
         auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
@@ -977,15 +911,13 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oY[u] = take((int64_t)J.m * s);
             oQ[u] = take((int64_t)J.m * s);
             oB[u] = take((int64_t)J.k * s);
-            oQ2[u] = take((int64_t)J.k * s);
+            oC[u] = take((int64_t)J.k * s);
             oR[u] = take((int64_t)s * s);
-            oA[u] = take((int64_t)s * s);
-            oZ[u] = take((int64_t)s * s);
+            oW[u] = take((int64_t)s * s);
+            oK[u] = take((int64_t)s * s);
             oS[u] = take(s);
-            oWS[u] = take((int64_t)s * s);
-            oZs[u] = take((int64_t)s * s);
         }
-        DevBuf ws(tot * sizeof(double) + np * sizeof(int) + 256, st);
+        DevBuf ws(tot * sizeof(double) + 2 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
         int *d_rank = (int *)(W + tot);
         cmark();
@@ -1003,13 +935,15 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         cmark();
         // 2. Q = orth(Y)
         std::vector<QrJob> q1(np);
+        std::vector<double *> scratch(np);
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, nullptr, nullptr, J.m, ps[u]};
+            q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, J.m, ps[u]};
+            scratch[u] = W + oC[u];
         }
-        split_launch(ctx, st, q1, ps, k_house_qr, k_house_qr_c1<8>, k_house_qr_c1<16>, 6 * sizeof(double));
+        qr_launch(ctx, st, q1, scratch);
         cmark();
-        // 3. Bt = T' Q, Bt = Q2 R
+        // 3. B = T' Q (kept), R' of B = Q2 R
         std::vector<GemmProb> g2;
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
@@ -1024,22 +958,28 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         std::vector<QrJob> q2(np);
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            q2[u] = QrJob{W + oB[u], J.k, W + oQ2[u], J.k, W + oR[u], nullptr, nullptr, J.k, ps[u]};
+            q2[u] = QrJob{W + oB[u], J.k, nullptr, 0, W + oR[u], J.k, ps[u]};
         }
-        split_launch(ctx, st, q2, ps, k_house_qr, k_house_qr_c1<8>, k_house_qr_c1<16>, 6 * sizeof(double));
+        qr_launch(ctx, st, q2, scratch);
         cmark();
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
-            sv[u] = SvdJob{W + oR[u], W + oA[u], W + oZ[u], W + oWS[u], W + oZs[u], W + oS[u], d_rank + u, ps[u]};
-        jacobi_launch(ctx, st, sv, ps, tau);
+            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + u, ps[u]};
+        svd_launch(ctx, st, sv, tau);
         cmark();
         // decisions on the host
-        std::vector<int> h_rank(np);
-        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+        std::vector<int> h_rank(2 * np);
+        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 2 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
         if (st != ctx->aux) stage_reset_main(ctx);
         cmark();
+        ctx->comp_stats[0] += (long long)np;
+        ctx->comp_stats[1] += 1;
+        for (size_t u = 0; u < np; ++u) {
+            ctx->comp_stats[2] += h_rank[np + u];
+            ctx->comp_stats[3] = std::max(ctx->comp_stats[3], (long long)h_rank[np + u]);
+        }
         std::vector<int> next;
         std::vector<GemmProb> gu, gv;
         for (size_t u = 0; u < np; ++u) {
@@ -1069,14 +1009,15 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             }
             ranks[q] = r;
             if (r == 0) continue;
+            // U = Q W_r, V = B W_r
             GemmProb a{};
             a.A = W + oQ[u]; a.lda = J.m; a.m = J.m; a.k = s;
-            a.B = W + oWS[u]; a.ldb = s; a.n = r;
+            a.B = W + oW[u]; a.ldb = s; a.n = r;
             a.C = J.U; a.ldc = J.ldu;
             gu.push_back(a);
             GemmProb b{};
-            b.A = W + oQ2[u]; b.lda = J.k; b.m = J.k; b.k = s;
-            b.B = W + oZs[u]; b.ldb = s; b.n = r;
+            b.A = W + oB[u]; b.lda = J.k; b.m = J.k; b.k = s;
+            b.B = W + oW[u]; b.ldb = s; b.n = r;
             b.C = J.V; b.ldc = J.ldv;
             gv.push_back(b);
         }
