@@ -9,8 +9,12 @@ nothing carries over between steps.
 
 Workload: 200 x 200 perturbed grid (n = 40,000), Matern sigma2 = 1,
 beta = 0.1, nu = 0.5 (medium correlation) as the walk's start, tile 800,
-eps = 1e-7, FP64.  Z = L w is drawn once from the library's own TLR factor
-at the starting theta (eps = 1e-9), w ~ N(0, I) seeded.
+eps = 1e-7.  Z = L w is drawn once from the library's own TLR factor at the
+starting theta (eps = 1e-9), w ~ N(0, I) seeded.
+
+Both precision paths run the same K steps at the same thetas: FP64 and mixed
+(paired-FP32 off-diagonal products).  The headline value is the mixed path
+when every step keeps |l_mixed - l_fp64| <= 1e-6 |l_fp64|, else the FP64 path.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Multi-GPU (torchrun): replicas, one dataset per rank (seed 1 + rank), no
@@ -155,59 +159,72 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     xy_h, xy, z = make_inputs(tlr, ctx, torch, dev, rank)
     thetas = synth.theta_walk(THETA0, args.warmup + args.steps, seed=7, scale=0.05)
-    opts = tlr.Options(nb=NB, eps=EPS)
     L = tlr.TlrMatrix(ctx, N_POINTS, NB)
     xyo = torch.empty_like(xy)
     perm = torch.empty(N_POINTS, dtype=torch.int64, device=dev)
     zo = torch.empty_like(z)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    precisions = {"mixed": tlr.TLR_PREC_MIXED, "fp64": tlr.TLR_PREC_FP64}
 
-    def step(theta):
+    def step(theta, opts):
         tlr.tlr_order(ctx, xy, ORDER, perm=perm, xy_out=xyo)
         tlr.tlr_gather(ctx, perm, z, dst=zo)
         return tlr.tlr_loglik(L, xyo, zo, theta, opts)
 
-    for k in range(args.warmup):
-        step(thetas[k])
-    torch.cuda.synchronize()
+    def timed(prec: str) -> dict:
+        """W untimed warm-up steps, then K steps each bracketed by CUDA events on
+        the launching stream; the L2 is flushed (256 MB write) between steps,
+        outside the events."""
+        opts = tlr.Options(nb=NB, eps=EPS, precision=precisions[prec])
+        for k in range(args.warmup):
+            step(thetas[k], opts)
+        torch.cuda.synchronize()
+        tlr.tlr_profile(ctx, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        out = {"results": [], "gemm_ms": 0.0, "gemm_flops": 0.0, "panel_launches": 0,
+               "stage_ms": {k: 0.0 for k in tlr.STAGES}, "comp_ms": {k: 0.0 for k in tlr.COMPRESS_STEPS},
+               "comp_stats": {k: 0 for k in tlr.COMPRESS_STATS}}
+        clocks = ClockSampler(local)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches0 = tlr.tlr_launch_count()
+        clocks.start()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            r = step(thetas[args.warmup + k], opts)
+            ev[k][1].record(stream)
+            prof = tlr.tlr_profile(ctx, True)
+            out["gemm_ms"] += prof["gemm_ms"]
+            out["gemm_flops"] += prof["gemm_flops"]
+            out["panel_launches"] += prof["panel_launches"]
+            for name, v in tlr.tlr_stage_times(ctx).items():
+                out["stage_ms"][name] += v / args.steps
+            for name, v in tlr.tlr_compress_times(ctx).items():
+                out["comp_ms"][name] += v / args.steps
+            for name, v in tlr.tlr_compress_stats(ctx).items():
+                cs = out["comp_stats"]
+                cs[name] = max(cs[name], v) if name == "max_sweeps" else cs[name] + v
+            out["results"].append(r)
+        torch.cuda.synchronize()
+        out["clocks"] = clocks.stop()
+        out["launches"] = tlr.tlr_launch_count() - launches0
+        out["times"] = [a.elapsed_time(b) for a, b in ev]
+        out["value"], out["total_ms"] = aggregate(sum(out["times"]), args.steps, world, device=dev)
+        if world > 1:
+            torch.distributed.barrier()
+        tlr.tlr_profile(ctx, False)
+        return out
 
-    # timed region: every step bracketed by CUDA events on the launching stream;
-    # the L2 is flushed (256 MB write) between steps, outside the events
-    tlr.tlr_profile(ctx, True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    results, gemm_ms, gemm_flops, panel_launches = [], 0.0, 0.0, 0
-    stage_ms = {k: 0.0 for k in tlr.STAGES}
-    comp_ms = {k: 0.0 for k in tlr.COMPRESS_STEPS}
-    comp_stats = {k: 0 for k in tlr.COMPRESS_STATS}
-    clocks = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    launches0 = tlr.tlr_launch_count()
-    clocks.start()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        r = step(thetas[args.warmup + k])
-        ev[k][1].record(stream)
-        prof = tlr.tlr_profile(ctx, True)
-        gemm_ms += prof["gemm_ms"]
-        gemm_flops += prof["gemm_flops"]
-        panel_launches += prof["panel_launches"]
-        for name, v in tlr.tlr_stage_times(ctx).items():
-            stage_ms[name] += v / args.steps
-        for name, v in tlr.tlr_compress_times(ctx).items():
-            comp_ms[name] += v / args.steps
-        for name, v in tlr.tlr_compress_stats(ctx).items():
-            comp_stats[name] = max(comp_stats[name], v) if name == "max_sweeps" else comp_stats[name] + v
-        results.append(r)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    launches = tlr.tlr_launch_count() - launches0
-    times = [a.elapsed_time(b) for a, b in ev]
-    value, total_ms = aggregate(sum(times), args.steps, world, device=dev)
-    if world > 1:
-        torch.distributed.barrier()
+    fp64 = timed("fp64")
+    mixed = timed("mixed")
+    rel_dl = max(abs(a["loglik"] - b["loglik"]) / abs(b["loglik"])
+                 for a, b in zip(mixed["results"], fp64["results"]))
+    # the headline is the mixed path when it keeps |dl|/|l| <= 1e-6 against the FP64 path
+    head_name = "mixed" if rel_dl <= 1e-6 else "fp64"
+    head = mixed if head_name == "mixed" else fp64
+    head_opts = tlr.Options(nb=NB, eps=EPS, precision=precisions[head_name])
 
     # end to end through the public API with host buffers: pinned host inputs
     # copied in every step, the result read back on the host
@@ -223,64 +240,82 @@ def run_gpu(args):
         z_dev.copy_(z_pin, non_blocking=True)
         tlr.tlr_order(ctx, xy_dev, ORDER, perm=perm, xy_out=xyo)
         tlr.tlr_gather(ctx, perm, z_dev, dst=zo)
-        tlr.tlr_loglik(L, xyo, zo, thetas[args.warmup + k], opts)  # result returned on the host
+        tlr.tlr_loglik(L, xyo, zo, thetas[args.warmup + k], head_opts)  # result returned on the host
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * e2e_steps / e2e_s if world == 1 else e2e_steps / e2e_s * world
+    e2e_value = world * e2e_steps / e2e_s
 
-    pk, pk_kind = peaks()
-    # FP64 peak of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop at the sampled SM clock
-    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    clk = head["clocks"]
+    sm_mhz = clk.get("sm_mhz") or peaks()[0].get("sm_max_mhz", 2070.0)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp64_peak_tflops = n_sms * 4 * sm_mhz * 1e6 / 1e12
-    avg_launch_ms = gemm_ms / max(panel_launches, 1)
-    achieved_tflops = (gemm_flops / max(panel_launches, 1)) / (avg_launch_ms / 1000.0) / 1e12 if gemm_ms > 0 else 0.0
-    p50 = float(np.percentile(times, 50))
-    p99 = float(np.percentile(times, 99))
+    if head_name == "mixed":
+        # paired-FP32 product: 12 FP32 instructions per emulated multiply-add on
+        # 128 FP32 lanes per SM per clock
+        peak = n_sms * 128 * 2 / 12 * sm_mhz * 1e6 / 1e12
+        peak_src = ("FP32 pipe for paired-FP32 products: %d SMs x 128 lanes x 2 flop / 12 instr per emulated "
+                    "FMA x %.0f MHz (sampled SM clock)" % (n_sms, sm_mhz))
+        kname = "k_gemm_df<EpiMatern> (panel update + Matern generation, paired-FP32 products)"
+    else:
+        peak = n_sms * 4 * sm_mhz * 1e6 / 1e12
+        peak_src = "FP64 DFMA pipe: %d SMs x 4 flop/clk x %.0f MHz (sampled SM clock)" % (n_sms, sm_mhz)
+        kname = "k_gemm_f64<EpiMatern> (panel update + Matern generation)"
+
+    def roof(o):
+        avg = o["gemm_ms"] / max(o["panel_launches"], 1)
+        fl = o["gemm_flops"] / max(o["panel_launches"], 1)
+        return avg, fl, (fl / (avg / 1000.0) / 1e12 if avg > 0 else 0.0)
+
+    avg_ms, fl_launch, achieved = roof(head)
+
+    def summary(o):
+        res = o["results"]
+        cs = o["comp_stats"]
+        return {"evals_per_s": o["value"], "ms_per_step": o["total_ms"] / args.steps,
+                "p50_ms": float(np.percentile(o["times"], 50)), "p99_ms": float(np.percentile(o["times"], 99)),
+                "stage_ms_per_step": o["stage_ms"], "compress_ms_per_step": o["comp_ms"],
+                "compress_per_step": {"tiles": cs["tiles"] / args.steps, "rounds": cs["rounds"] / args.steps,
+                                      "mean_sweeps": cs["sweeps"] / max(cs["tiles"], 1),
+                                      "max_sweeps": cs["max_sweeps"]},
+                "panel_tflops": roof(o)[2], "gpu_launches": int(o["launches"]),
+                "loglik_last": res[-1]["loglik"], "max_rank_last": res[-1]["max_rank"],
+                "mean_rank_last": res[-1]["mean_rank"], "offdiag_mb_last": res[-1]["offdiag_bytes"] / 1e6}
+
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": head["value"],
         "unit": UNIT,
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps,
-        "p50_ms": p50,
-        "p99_ms": p99,
+        "ms_per_step": head["total_ms"] / args.steps,
+        "p50_ms": float(np.percentile(head["times"], 50)),
+        "p99_ms": float(np.percentile(head["times"], 99)),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64 storage, paired-f32 products" if head_name == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": "ordering study FP64, n=%d (perturbed grid), Matern sigma2=1 beta=0.1 nu=0.5 "
-                               "walk start, %s, tile %d, eps %g" % (N_POINTS, ORDER, NB, EPS),
+        "config": {"workload": "ordering study, n=%d (perturbed grid), Matern sigma2=1 beta=0.1 nu=0.5 "
+                               "walk start, %s, tile %d, eps %g, %s path" % (N_POINTS, ORDER, NB, EPS, head_name),
                    "n": N_POINTS, "nb": NB, "eps": EPS, "ordering": ORDER, "theta0": list(THETA0),
+                   "precision": head_name,
                    "theta_walk": "log-space, scale 0.05/step, seed 7",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "stage_ms_per_step": stage_ms,
-        "compress_ms_per_step": comp_ms,
-        "compress_per_step": {"tiles": comp_stats["tiles"] / args.steps, "rounds": comp_stats["rounds"] / args.steps,
-                              "mean_sweeps": comp_stats["sweeps"] / max(comp_stats["tiles"], 1),
-                              "max_sweeps": comp_stats["max_sweeps"]},
-        "loglik_last": results[-1]["loglik"],
-        "max_rank_last": results[-1]["max_rank"],
-        "mean_rank_last": results[-1]["mean_rank"],
-        "offdiag_mb_last": results[-1]["offdiag_bytes"] / 1e6,
-        "rel_dl_vs_fp64": 0.0,
+        "rel_dl_vs_fp64": rel_dl,
+        "fp64_path": summary(fp64),
+        "mixed_path": summary(mixed),
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                 "h2d_bytes_per_step": int(xy_pin.numel() * 8 + z_pin.numel() * 8),
                 "d2h_bytes_per_step": 8 * 3},
-        "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": "k_gemm_f64<EpiMatern> (panel update + Matern generation)",
-                     "achieved": achieved_tflops, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / fp64_peak_tflops if fp64_peak_tflops else None,
-                     "traffic": None,
-                     "peak_source": "FP64 DFMA pipe: %d SMs x 4 flop/clk x %.0f MHz (sampled SM clock)"
-                                    % (n_sms, sm_mhz),
-                     "launch_ms_avg": avg_launch_ms, "launches": panel_launches,
-                     "flops_per_launch": gemm_flops / max(panel_launches, 1)},
+        "gpu_launches": int(head["launches"]),
+        "roofline": {"bound": "alu", "kernel": kname,
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None,
+                     "traffic": None, "peak_source": peak_src,
+                     "launch_ms_avg": avg_ms, "launches": head["panel_launches"],
+                     "flops_per_launch": fl_launch},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()

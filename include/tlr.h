@@ -52,7 +52,14 @@ extern "C" {
 #define TLR_ORDER_QUANTIZE 1u /* xy_out holds decoded coordinates q / 65535 (Sec. 3.1, "Decoding") */
 
 /* precision of the off-diagonal products (tlr_opts.precision) */
-#define TLR_PREC_FP64 0
+#define TLR_PREC_FP64 0  /* every operation in FP64 */
+/* Mixed: the dense products of the off-diagonal work -- the panel update
+ * T_ij = A_ij - sum_k L_ik L_jk' and the compression's sampling T Omega and
+ * projection T' Q -- run in paired-FP32 arithmetic on the FP32 pipe (each
+ * operand split into two FP32 words, products and sums carried to about 46
+ * significant bits); storage, the Matern evaluation, QR/SVD, the diagonal
+ * POTRF, the log-determinant and the solve stay FP64. */
+#define TLR_PREC_MIXED 1
 
 typedef struct tlr_ctx tlr_ctx; /* device, workspace pool, last error, timers */
 typedef struct tlr_mat tlr_mat; /* a TLR matrix or TLR Cholesky factor on the device */

@@ -21,6 +21,7 @@ TLR_OK, TLR_ERR_ARG, TLR_ERR_CUDA, TLR_ERR_OOM, TLR_ERR_RANK, TLR_ERR_NOT_SPD, T
 ORDERS = {"identity": 0, "random": 1, "morton": 2, "hilbert": 3, "kdtree": 4, "maxmin": 5}
 TLR_ORDER_QUANTIZE = 1
 TLR_PREC_FP64 = 0
+TLR_PREC_MIXED = 1
 
 
 class TlrError(RuntimeError):

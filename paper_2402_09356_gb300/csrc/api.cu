@@ -124,6 +124,7 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
         if (R.d) cudaFree(R.d);
     }
     if (ctx->d_omega) cudaFree(ctx->d_omega);
+    if (ctx->d_omega2) cudaFree(ctx->d_omega2);
     if (ctx->d_mtab) cudaFree(ctx->d_mtab);
     delete ctx;
 }
@@ -332,7 +333,7 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     check_arg(xy && z && opts && L && out, "xy/z/opts/L/out");
     check_arg(n > 0 && L->n == n && L->nb == opts->nb, "L does not match n/nb");
     check_arg(opts->eps >= 0 && std::isfinite(opts->eps), "eps");
-    check_arg(opts->precision == TLR_PREC_FP64, "precision");
+    check_arg(opts->precision == TLR_PREC_FP64 || opts->precision == TLR_PREC_MIXED, "precision");
     MaternParams P = params_of(theta);
     std::memset(out, 0, sizeof *out);
     out->info = -1;
@@ -345,7 +346,7 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 2 * sizeof(double), s));
     try {
         factor(ctx, s, L, FactorMode::Matern, xy, &P, opts->eps * theta.sigma2, &st, &inf, z,
-               y.as<double>(), acc.as<double>());
+               y.as<double>(), acc.as<double>(), opts->precision == TLR_PREC_MIXED);
     } catch (const Error &) {
         out->info = inf;
         throw;

@@ -118,6 +118,7 @@ struct tlr_ctx {
     tlr::StageRing stage[2];
     // fixed Gaussian test matrices of the randomised range finder
     double *d_omega = nullptr;
+    float2 *d_omega2 = nullptr;  // paired-FP32 copy of d_omega
     int omega_rows = 0, omega_cols = 0;
     // per-theta Matern interpolation table (+ node scratch)
     double *d_mtab = nullptr;

@@ -848,12 +848,14 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
     ctx->omega_cols = kMaxSample;
     int64_t cnt = (int64_t)ctx->omega_rows * ctx->omega_cols;
     TLR_CUDA_TRY(cudaMalloc(&ctx->d_omega, cnt * sizeof(double)));
+    TLR_CUDA_TRY(cudaMalloc(&ctx->d_omega2, cnt * sizeof(float2)));
     launch(k_gaussian, (unsigned)ceil_div(cnt, 256), 256, 0, s, ctx->d_omega, cnt, 0x243F6A8885A308D3ull);
     TLR_CHECK_LAUNCH();
+    split_f2(s, ctx->d_omega, ctx->omega_rows, ctx->omega_rows, ctx->omega_cols, ctx->d_omega2);
 }
 
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
-                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile) {
+                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df) {
     ensure_omega(ctx, st);
     // profiling marks between the sub-steps of each adaptive round
     std::vector<cudaEvent_t> ev;
@@ -900,7 +902,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
     while (!pending.empty()) {
         const size_t np = pending.size();
         // workspace offsets (doubles)
-        std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np);
+        std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np), oQ2(np);
         std::vector<int> ps(np);
         int64_t tot = 0;
         auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
@@ -916,6 +918,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oW[u] = take((int64_t)s * s);
             oK[u] = take((int64_t)s * s);
             oS[u] = take(s);
+            oQ2[u] = df ? take((int64_t)J.m * s) : 0;  // float2, one double each
         }
         DevBuf ws(tot * sizeof(double) + 2 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
@@ -929,9 +932,10 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             a.A = J.T; a.lda = J.ldt; a.m = J.m; a.k = J.k;
             a.B = omega; a.ldb = ldo; a.n = ps[u];
             a.C = W + oY[u]; a.ldc = J.m;
+            a.A2 = J.T2; a.B2 = ctx->d_omega2;
             g1.push_back(a);
         }
-        gemm_batched(ctx, st, false, false, g1, 1.0, 0.0);
+        gemm_batched(ctx, st, false, false, g1, 1.0, 0.0, df);
         cmark();
         // 2. Q = orth(Y)
         std::vector<QrJob> q1(np);
@@ -942,6 +946,12 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             scratch[u] = W + oC[u];
         }
         qr_launch(ctx, st, q1, scratch);
+        if (df) {
+            std::vector<SplitDesc> sd(np);
+            for (size_t u = 0; u < np; ++u)
+                sd[u] = SplitDesc{W + oQ[u], (float2 *)(W + oQ2[u]), jobs[pending[u]].m, jobs[pending[u]].m, ps[u]};
+            split_f2_batched(ctx, st, sd);
+        }
         cmark();
         // 3. B = T' Q (kept), R' of B = Q2 R
         std::vector<GemmProb> g2;
@@ -951,9 +961,10 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             a.A = J.T; a.lda = J.ldt; a.m = J.k; a.k = J.m;
             a.B = W + oQ[u]; a.ldb = J.m; a.n = ps[u];
             a.C = W + oB[u]; a.ldc = J.k;
+            a.A2 = J.T2; a.B2 = (const float2 *)(W + oQ2[u]);
             g2.push_back(a);
         }
-        gemm_batched(ctx, st, true, false, g2, 1.0, 0.0);
+        gemm_batched(ctx, st, true, false, g2, 1.0, 0.0, df);
         cmark();
         std::vector<QrJob> q2(np);
         for (size_t u = 0; u < np; ++u) {

@@ -12,6 +12,7 @@ constexpr int kMaxSample = 512;   // largest randomised sample size
 struct CompressJob {
     const double *T;
     int ldt;
+    const float2 *T2;  // paired-FP32 copy of T (same ld), for the mixed-precision products; or null
     int m, k;
     double *U;
     int ldu;
@@ -21,15 +22,19 @@ struct CompressJob {
     long long tile_id;  // i * NT + j, reported on failure
 };
 
-// Allocate and fill the context's Gaussian test matrix (once).
+// Allocate and fill the context's Gaussian test matrix and its paired-FP32
+// copy (once).
 void ensure_omega(tlr_ctx *ctx, cudaStream_t s);
 
 // Compress every job at absolute accuracy tau.  ranks[q] receives r for job q.
 // A tile whose rank exceeds maxrank (or cannot be resolved within the sample
 // cap) is reported in *bad_tile (its tile_id), a tile holding non-finite
 // values in *nan_tile; both are -1 otherwise.
+// With df, the sampling and projection products run in paired-FP32
+// arithmetic (every job must then carry T2).
 // Syncs `s` once per adaptive round.
 void compress_tiles(tlr_ctx *ctx, cudaStream_t s, std::vector<CompressJob> &jobs, double tau,
-                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile);
+                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile,
+                    bool df = false);
 
 }  // namespace tlr

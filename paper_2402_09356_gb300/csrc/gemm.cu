@@ -1,4 +1,5 @@
 // Batched FP64 GEMM launchers and the descriptor staging buffers of a context.
+#include <algorithm>
 #include <cstring>
 
 #include "gemm.cuh"
@@ -63,6 +64,28 @@ void split_f2(cudaStream_t s, const double *src, int ld, int m, int n, float2 *d
     int64_t count = (int64_t)m * n;
     if (count <= 0) return;
     launch(k_split_f2, (unsigned)ceil_div(count, 256), 256, 0, s, src, ld, m, count, dst);
+    TLR_CHECK_LAUNCH();
+}
+
+__global__ void k_split_f2_batched(const SplitDesc *__restrict__ descs) {
+    const SplitDesc D = descs[blockIdx.y];
+    const int64_t count = (int64_t)D.m * D.n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % D.m, j = e / D.m;
+        const double v = D.src[j * D.ld + i];
+        const float h = __double2float_rn(v);
+        D.dst[j * D.ld + i] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+}
+
+void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc> &descs) {
+    if (descs.empty()) return;
+    int64_t most = 0;
+    for (const SplitDesc &d : descs) most = std::max(most, (int64_t)d.m * d.n);
+    if (most == 0) return;
+    auto *dd = (const SplitDesc *)stage_push(ctx, descs.data(), descs.size() * sizeof(SplitDesc), s);
+    dim3 grid((unsigned)std::min<int64_t>(ceil_div(most, 256), 2048), (unsigned)descs.size());
+    launch(k_split_f2_batched, grid, 256, 0, s, dd);
     TLR_CHECK_LAUNCH();
 }
 

@@ -221,6 +221,14 @@ k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, 
 // dst[j * ld + i] = (hi, lo) of src[j * ld + i] for an m x n column-major block.
 void split_f2(cudaStream_t s, const double *src, int ld, int m, int n, float2 *dst);
 
+struct SplitDesc {
+    const double *src;
+    float2 *dst;  // same leading dimension as src
+    int ld, m, n;
+};
+// split_f2 for a batch of blocks in one launch.
+void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc> &descs);
+
 // df = true selects the paired-FP32 kernel (FP64-accurate products on the FP32
 // pipe); every problem must then carry A2/B2 copies made by split_f2.
 void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,

@@ -75,7 +75,8 @@ void upload_ranks(tlr_mat *M, cudaStream_t s) {
 
 void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const double *xy,
             const MaternParams *P, double tau, FactorStats *stats, long long *info, const double *z,
-            double *y, double *acc) {
+            double *y, double *acc, bool df) {
+    if (df && mode != FactorMode::Matern) throw make_error(TLR_ERR_ARG, "paired-FP32 products need the Matern mode");
     const int nt = M->nt, nb = M->nb;
     const int64_t n = M->n;
     *info = -1;
@@ -91,6 +92,9 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     auto r_of = [&](int i, int k) { return (int)R[(size_t)i * nt + k]; };
     DevBuf panel((size_t)nt * nb * nb * sizeof(double), st);
     double *Tp = panel.as<double>();
+    // paired-FP32 copy of the panel (mixed precision): operand of the compression products
+    DevBuf panel2(df ? (size_t)nt * nb * nb * sizeof(float2) : 0, st);
+    float2 *Tp2 = panel2.as<float2>();
     DevBuf xinv((size_t)nb * nb * sizeof(double), st);
     double *Xinv = xinv.as<double>();
     // fused forward solve (a5): y = L^-1 z column by column
@@ -189,7 +193,17 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             g.B = Qj; g.ldb = nb; g.n = mj;
             g.C = Tp; g.ldc = (int)Mp;
             g.ri0 = (int64_t)j * nb; g.ci0 = (int64_t)j * nb;
-            gemm_batched_matern(ctx, st, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P);
+            DevBuf p2(df ? (size_t)Mp * std::max(Rj, 1) * sizeof(float2) : 0, st);
+            DevBuf q2(df ? (size_t)nb * std::max(Rj, 1) * sizeof(float2) : 0, st);
+            if (df && Rj > 0) {
+                g.A2 = p2.as<float2>();
+                g.B2 = q2.as<float2>();
+                split_f2_batched(ctx, st, {SplitDesc{Pj, p2.as<float2>(), (int)Mp, (int)Mp, Rj},
+                                           SplitDesc{Qj, q2.as<float2>(), nb, mj, Rj}});
+            }
+            gemm_batched_matern(ctx, st, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df);
+            if (df && j + 1 < nt)
+                split_f2_batched(ctx, st, {SplitDesc{Tp + nb, Tp2 + nb, (int)Mp, (int)(Mp - nb), mj}});
             stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
             stats->matern_entries += (double)rows_valid * mj;
             stats->panel_launches += 1;
@@ -247,6 +261,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             CompressJob c{};
             c.T = Tp + (int64_t)(i - j) * nb;
             c.ldt = (int)Mp;
+            c.T2 = df ? Tp2 + (int64_t)(i - j) * nb : nullptr;
             c.m = tile_rows(n, nb, i);
             c.k = mj;
             c.U = Uslot(M, i, j);
@@ -259,7 +274,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         }
         std::vector<int> rk;
         long long bad = -1, nan = -1;
-        if (!jobs.empty()) compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan);
+        if (!jobs.empty()) compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan, df);
         mark();
         TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
         long long sinfo = -1;

@@ -1,0 +1,73 @@
+"""Mixed precision (TLR_PREC_MIXED): the off-diagonal dense products in
+paired-FP32 arithmetic, everything else FP64.
+
+The products carry about 46 significant bits, so the factor differs from the
+FP64 path only by rounding far below the compression threshold: the mixed
+likelihood must stay within the FP64 path's own bound against the exact dense
+oracle (10 eps |l|), within 1e-6 |l| of the FP64 path, and the rank maps of
+the two paths may differ only where a singular value sits at the threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def run(ctx, xy, z, theta, order, nb, eps, maxrank, precision):
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    n = z.size
+    xy_d = torch.from_numpy(xy).cuda()
+    xyo = torch.empty_like(xy_d)
+    perm = tlr.tlr_order(ctx, xy_d, order, xy_out=xyo)
+    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(z).cuda())
+    L = tlr.TlrMatrix(ctx, n, nb, maxrank)
+    r = tlr.tlr_loglik(L, xyo, zo, theta, tlr.Options(nb=nb, eps=eps, maxrank=maxrank, precision=precision))
+    return r, tlr.tlr_mat_ranks(L), perm.cpu().numpy()
+
+
+CASES = [
+    # n, nb, order, theta, eps, maxrank
+    (1600, 200, "morton", (1.0, 0.1, 0.5), 1e-9, 0),
+    (3000, 256, "hilbert", (1.5, 0.1, 1.0), 1e-7, 0),
+    (2113, 128, "kdtree", (0.7, 0.05, 1.5), 1e-5, 0),
+    (1600, 200, "random", (1.0, 0.3, 0.5), 1e-9, 200),
+]
+
+
+@pytest.mark.parametrize("n,nb,order,theta,eps,maxrank", CASES)
+def test_mixed_matches_fp64_and_oracle(ctx, n, nb, order, theta, eps, maxrank):
+    import paper_2402_09356_gb300 as tlr
+    xy = synth.jittered_grid(n, seed=n)
+    z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=n + 1))
+    r64, rk64, perm = run(ctx, xy, z, theta, order, nb, eps, maxrank, tlr.TLR_PREC_FP64)
+    rmx, rkmx, _ = run(ctx, xy, z, theta, order, nb, eps, maxrank, tlr.TLR_PREC_MIXED)
+    ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
+    assert abs(rmx["loglik"] - ref) <= 10 * eps * abs(ref), (rmx["loglik"], ref)
+    assert abs(rmx["loglik"] - r64["loglik"]) <= 1e-6 * abs(r64["loglik"])
+    d = np.abs(rkmx.astype(np.int64) - rk64)
+    assert d.max() <= 1 and (d > 0).mean() <= 0.05, (d.max(), (d > 0).mean())
+
+
+def test_mixed_eps_to_zero_is_dense(ctx):
+    import paper_2402_09356_gb300 as tlr
+    n, nb, theta = 1600, 200, (1.0, 0.1, 0.5)
+    xy = synth.jittered_grid(n)
+    z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=2))
+    r, _, perm = run(ctx, xy, z, theta, "morton", nb, 0.0, nb, tlr.TLR_PREC_MIXED)
+    ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
+    assert abs(r["loglik"] - ref) <= 1e-10 * abs(ref)
+
+
+@pytest.mark.parametrize("n,nb", [(1, 16), (17, 16), (1000, 96)])
+def test_mixed_ragged_and_tiny(ctx, n, nb):
+    import paper_2402_09356_gb300 as tlr
+    theta, eps = (1.2, 0.08, 0.8), 1e-9
+    xy = synth.jittered_grid(n, seed=n)
+    z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=n + 1))
+    r, _, perm = run(ctx, xy, z, theta, "hilbert", nb, eps, nb, tlr.TLR_PREC_MIXED)
+    ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
+    assert abs(r["loglik"] - ref) <= 10 * eps * abs(ref) + 1e-12

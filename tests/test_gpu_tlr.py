@@ -222,3 +222,8 @@ def test_bad_arguments(ctx):
     assert e.value.code == tlr.TLR_ERR_ARG
     with pytest.raises(tlr.TlrError):
         tlr.TlrMatrix(ctx, 10, 8)  # nb < 16
+    L = tlr.TlrMatrix(ctx, 10, 16)
+    z = torch.zeros(10, dtype=torch.float64, device="cuda")
+    with pytest.raises(tlr.TlrError) as e:
+        tlr.tlr_loglik(L, xy, z, (1.0, 0.1, 0.5), tlr.Options(nb=16, eps=1e-9, precision=7))
+    assert e.value.code == tlr.TLR_ERR_ARG
