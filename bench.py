@@ -275,7 +275,8 @@ def run_gpu(args):
                 "stage_ms_per_step": o["stage_ms"], "compress_ms_per_step": o["comp_ms"],
                 "compress_per_step": {"tiles": cs["tiles"] / args.steps, "rounds": cs["rounds"] / args.steps,
                                       "mean_sweeps": cs["sweeps"] / max(cs["tiles"], 1),
-                                      "max_sweeps": cs["max_sweeps"]},
+                                      "max_sweeps": cs["max_sweeps"],
+                                      "mean_sweeps_fp32": cs["sweeps32"] / max(cs["tiles"], 1)},
                 "panel_tflops": roof(o)[2], "gpu_launches": int(o["launches"]),
                 "loglik_last": res[-1]["loglik"], "max_rank_last": res[-1]["max_rank"],
                 "mean_rank_last": res[-1]["mean_rank"], "offdiag_mb_last": res[-1]["offdiag_bytes"] / 1e6}

@@ -277,9 +277,10 @@ int tlr_stage_times(tlr_ctx *ctx, double *ms);
 int tlr_compress_times(tlr_ctx *ctx, double *ms);
 
 /* Counters of the compressions of the last tlr_loglik / tlr_potrf
- * factorisation, written to out[0..3]: tile compressions run (a tile redone
- * with a larger sample counts again), adaptive rounds, Jacobi sweeps summed
- * over the compressions, and the largest sweep count of one compression.
+ * factorisation, written to out[0..4]: tile compressions run (a tile redone
+ * with a larger sample counts again), adaptive rounds, FP64 Jacobi sweeps
+ * summed over the compressions, the largest FP64 sweep count of one
+ * compression, and FP32 (preconditioning) Jacobi sweeps summed.
  * Collected whether or not profiling is on.  Errors: TLR_ERR_ARG. */
 int tlr_compress_stats(tlr_ctx *ctx, int64_t *out);
 

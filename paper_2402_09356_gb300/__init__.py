@@ -398,11 +398,11 @@ def tlr_compress_times(ctx: Context) -> dict:
     return {k: a[i] for i, k in enumerate(COMPRESS_STEPS)}
 
 
-COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps")
+COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps", "sweeps32")
 
 
 def tlr_compress_stats(ctx: Context) -> dict:
-    a = (ctypes.c_int64 * 4)()
+    a = (ctypes.c_int64 * 5)()
     ctx.check(load_library().tlr_compress_stats(ctx.h, a))
     return {k: int(a[i]) for i, k in enumerate(COMPRESS_STATS)}
 

@@ -132,7 +132,7 @@ struct tlr_ctx {
     // GEMM, QR of B', SVD, host decision (incl. sync), U/V GEMMs
     std::vector<cudaEvent_t> comp_events;
     double comp_ms[7] = {0, 0, 0, 0, 0, 0, 0};
-    long long comp_stats[4] = {0, 0, 0, 0};  // tiles, rounds, Jacobi sweeps (sum, max)
+    long long comp_stats[5] = {0, 0, 0, 0, 0};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum)
 };
 
 struct tlr_mat {

@@ -35,6 +35,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include <cooperative_groups.h>
 
@@ -52,7 +53,8 @@ constexpr int kQrThreads = 256;
 constexpr int kNw = kQrThreads / 32;
 constexpr int kMaxSweeps = 40;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     return v;
@@ -93,6 +95,74 @@ struct QrJob {
 };
 
 // ---------------------------------------------------------------------------
+// Work split of one panel step over a CTA's threads.  GB300 issues FP64 at
+// 1/64 of the FP32 rate, so the FP64 instruction count is what matters: each
+// thread owns whole columns (lanes <-> columns, no shuffle reductions), and
+// when the columns fill fewer than all warps the rows are split into G
+// interleaved groups over the spare warps (their partial dot products are
+// summed through shared memory).  Thread t handles row group t / width and
+// columns first + t % width + k * width.
+struct PanelSplit {
+    int G, width;
+    __device__ __forceinline__ explicit PanelSplit(int ncols) {
+        const int cw = (ncols + 31) / 32;
+        if (cw >= kNw || cw == 0) {
+            G = 1;
+            width = kQrThreads;
+        } else {
+            G = kNw / cw;
+            width = 32 * cw;
+        }
+    }
+};
+
+// Dot products d_cc = sum over local rows i >= lb of v[i] A(i, cc) for the
+// columns cc in [first, s), written to out[cc].  red: kQrThreads doubles.
+__device__ __forceinline__ void panel_dots(const double *As, int ld, const double *v, int first, int s, int lb, int nr,
+                                           double *red, double *out) {
+    const int tid = threadIdx.x;
+    const PanelSplit ps(s - first);
+    const int g = tid / ps.width;
+    if (ps.G == 1) {
+        for (int cc = first + tid; cc < s; cc += ps.width) {
+            const double *ac = As + cc * ld;
+            double d = 0.0;
+            for (int i = lb; i < nr; ++i) d = fma(v[i], ac[i], d);
+            out[cc] = d;
+        }
+        return;
+    }
+    const int cc = first + tid % ps.width;
+    if (tid < ps.G * ps.width && cc < s) {
+        const double *ac = As + cc * ld;
+        double d = 0.0;
+        for (int i = lb + g; i < nr; i += ps.G) d = fma(v[i], ac[i], d);
+        red[tid] = d;
+    }
+    __syncthreads();
+    if (tid < ps.width && cc < s) {
+        double d = 0.0;
+        for (int q = 0; q < ps.G; ++q) d += red[q * ps.width + tid];
+        out[cc] = d;
+    }
+}
+
+// A(i, cc) -= w[cc] v(i) for local rows i >= lb and columns cc in [first, s),
+// where v(i) = v[i] except v(ic) = vhead when ic is a local row.
+__device__ __forceinline__ void panel_update(double *As, int ld, const double *v, int ic, double vhead,
+                                             const double *w, int first, int s, int lb, int nr) {
+    const int tid = threadIdx.x;
+    const PanelSplit ps(s - first);
+    if (tid >= ps.G * ps.width) return;
+    const int g = tid / ps.width;
+    for (int cc = first + tid % ps.width; cc < s; cc += ps.width) {
+        const double wc = w[cc];
+        double *ac = As + cc * ld;
+        for (int i = lb + g; i < nr; i += ps.G) ac[i] = fma(-wc, i == ic ? vhead : v[i], ac[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // QR with the panel in shared memory.  CTA `rank` of the cluster owns rows
 // [r0, r0 + nr) of all s columns, column-major with an odd leading dimension.
 // Column c: every CTA forms the dot products of column c with columns c..s-1
@@ -104,19 +174,19 @@ struct QrJob {
 // Q = H_0 ... H_{s-1} [I; 0] is then accumulated backwards in place: before
 // H_c is applied, columns > c already hold their final values below row c,
 // and column c becomes H_c e_c (LAPACK's dorg2r ordering).
-// Shared memory: s * ld + 8 s doubles.
+// Shared memory: s * ld + 8 s + kQrThreads doubles.
 template <int kCl>
 __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const QrJob J = jobs[blockIdx.x / kCl];
-    const int m = J.m, s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = J.m, s = J.s, tid = threadIdx.x;
     const int per = (m + kCl - 1) / kCl, ld = per | 1;
     const int r0 = min(m, rank * per), nr = min(m, r0 + per) - r0;
     extern __shared__ double sm[];
     double *As = sm;
     double *taus = As + (size_t)s * ld, *betas = taus + s, *heads = betas + s;
-    double *pd = heads + s, *prow = pd + 2 * s, *wv = prow + 2 * s;
+    double *pd = heads + s, *prow = pd + 2 * s, *wv = prow + 2 * s, *red = wv + s;
     for (int e = tid; e < nr * s; e += kQrThreads) {
         const int i = e % nr, j = e / nr;
         As[j * ld + i] = J.A[(int64_t)j * J.lda + r0 + i];
@@ -126,13 +196,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         double *pdc = pd + (c & 1) * s, *prc = prow + (c & 1) * s;
         const int lb = max(c - r0, 0), ic = c - r0;
         double *vc = As + c * ld;
-        for (int cc = c + warp; cc < s; cc += kNw) {
-            const double *ac = As + cc * ld;
-            double w = 0.0;
-            for (int i = lb + lane; i < nr; i += 32) w = fma(vc[i], ac[i], w);
-            w = warp_sum(w);
-            if (lane == 0) pdc[cc] = w;
-        }
+        panel_dots(As, ld, vc, c, s, lb, nr, red, pdc);
         const int owner = c / per;
         if (rank == owner)
             for (int cc = c + tid; cc < s; cc += kQrThreads) prc[cc] = As[cc * ld + ic];
@@ -156,18 +220,11 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
             heads[c] = v0;
         }
         __syncthreads();
-        if (tau != 0.0) {
-            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
-                const double w = wv[cc];
-                double *ac = As + cc * ld;
-                for (int i = lb + lane; i < nr; i += 32) ac[i] = fma(-w, i == ic ? v0 : vc[i], ac[i]);
-            }
-        }
+        if (tau != 0.0) panel_update(As, ld, vc, ic, v0, wv, c + 1, s, lb, nr);
         __syncthreads();
         if (tau != 0.0 && rank == owner && tid == 0) vc[ic] = v0;  // reflector head stored in place
     }
     cl.sync();  // every CTA is done reading the factorisation's partials
-    __syncthreads();
     if (J.Rt) {  // Rt(i, u) = R(u, i) for the own rows u < s
         const int nu = max(0, min(nr, s - r0));
         for (int e = tid; e < nu * s; e += kQrThreads) {
@@ -188,13 +245,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         if (tau != 0.0) {  // identical on every CTA of the cluster
             double *pdc = pd + (act & 1) * s;
             ++act;
-            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
-                const double *qc = As + cc * ld;
-                double w = 0.0;
-                for (int i = lb + lane; i < nr; i += 32) w = fma(vc[i], qc[i], w);
-                w = warp_sum(w);
-                if (lane == 0) pdc[cc] = w;
-            }
+            panel_dots(As, ld, vc, c + 1, s, lb, nr, red, pdc);
             cl.sync();
             for (int cc = c + 1 + tid; cc < s; cc += kQrThreads) {
                 double d = 0.0;
@@ -203,11 +254,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
                 wv[cc] = tau * d;
             }
             __syncthreads();
-            for (int cc = c + 1 + warp; cc < s; cc += kNw) {
-                const double w = wv[cc];
-                double *qc = As + cc * ld;
-                for (int i = lb + lane; i < nr; i += 32) qc[i] = fma(-w, vc[i], qc[i]);
-            }
+            panel_update(As, ld, vc, -1, 0.0, wv, c + 1, s, lb, nr);
             __syncthreads();
         }
         // column c of Q = H_c e_c
@@ -229,7 +276,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
 
 static size_t qr_sm_bytes(int m, int s, int csize) {
     const int per = (m + csize - 1) / csize, ld = per | 1;
-    return ((size_t)s * ld + 8 * (size_t)s) * sizeof(double);
+    return ((size_t)s * ld + 8 * (size_t)s + kQrThreads) * sizeof(double);
 }
 
 // QR in global memory (A factorised in place; Q and Rt as above), for panels
@@ -345,7 +392,7 @@ struct SvdJob {
     double *W;         // s x s output: unit left singular vectors of R', sorted
     double *S;         // s output singular values, descending
     int *rank;         // #{S > tau}, or -1 if any S is not finite
-    int *sweeps;       // number of sweeps run
+    int *sweeps;       // sweeps run: [0] FP64, [1] FP32
     int s;
 };
 
@@ -362,17 +409,19 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
     return y;
 }
 
-// Rotate columns x and y (length s; the calling warp's lanes stride 32) so
-// that they become orthogonal; returns whether a rotation was applied.
-// Pairs with |x'y| <= tol |x| |y| are left alone.  The rotation angle only
-// steers convergence, so t = tan(angle) is computed from approximations;
-// c = 1/sqrt(1 + t^2) is refined by two Newton steps for the reciprocal
-// square root, y <- y (3 - x y^2) / 2, so that (c, c t) is orthogonal to
-// working precision and the singular values are preserved.
-__device__ __forceinline__ bool jacobi_rotate(double *x, double *y, int s, int lane, double tol2) {
-    double al = 0.0, be = 0.0, ga = 0.0;
-    for (int r = lane; r < s; r += 32) {
-        const double a = x[r], b = y[r];
+// Rotate columns x and y so that their first sdot entries become orthogonal;
+// the rotation is applied to all srot entries (srot > sdot carries the
+// accumulated rotations along).  Returns whether a rotation was applied.
+// Pairs with |x'y| <= tol |x| |y| (tol2 = tol^2) are left alone.
+// FP64: the rotation angle only steers convergence, so t = tan(angle) comes
+// from approximations; c = 1/sqrt(1 + t^2) is refined by two Newton steps for
+// the reciprocal square root, y <- y (3 - x y^2) / 2, so that (c, c t) is
+// orthogonal to working precision and the singular values are preserved.
+template <class T>
+__device__ __forceinline__ bool jacobi_rotate(T *x, T *y, int sdot, int srot, int lane, T tol2) {
+    T al = 0, be = 0, ga = 0;
+    for (int r = lane; r < sdot; r += 32) {
+        const T a = x[r], b = y[r];
         al = fma(a, a, al);
         be = fma(b, b, be);
         ga = fma(a, b, ga);
@@ -380,19 +429,29 @@ __device__ __forceinline__ bool jacobi_rotate(double *x, double *y, int s, int l
     al = warp_sum(al);
     be = warp_sum(be);
     ga = warp_sum(ga);
-    if (ga == 0.0 || ga * ga <= tol2 * (al * be)) return false;
-    double rg = rcp_approx(2.0 * ga);
-    rg = rg * fma(-2.0 * ga, rg, 2.0);
-    const double zeta = (be - al) * rg, az = fabs(zeta);
-    const double q = fma(zeta, zeta, 1.0);
-    const double t = copysign(az < 1e150 ? rcp_approx(az + q * rsqrt_approx(q)) : 0.5 * rcp_approx(az), zeta);
-    const double u = fma(t, t, 1.0);
-    double c = rsqrt_approx(u);
-    c = c * fma(-0.5 * u * c, c, 1.5);
-    c = c * fma(-0.5 * u * c, c, 1.5);
-    const double sn = c * t;
-    for (int r = lane; r < s; r += 32) {
-        const double a = x[r], b = y[r];
+    if (ga == T(0) || ga * ga <= tol2 * (al * be)) return false;
+    T c, sn;
+    if constexpr (std::is_same<T, double>::value) {
+        double rg = rcp_approx(2.0 * ga);
+        rg = rg * fma(-2.0 * ga, rg, 2.0);
+        const double zeta = (be - al) * rg, az = fabs(zeta);
+        const double q = fma(zeta, zeta, 1.0);
+        const double t =
+            copysign(az < 1e150 ? rcp_approx(az + q * rsqrt_approx(q)) : 0.5 * rcp_approx(az), zeta);
+        const double u = fma(t, t, 1.0);
+        c = rsqrt_approx(u);
+        c = c * fma(-0.5 * u * c, c, 1.5);
+        c = c * fma(-0.5 * u * c, c, 1.5);
+        sn = c * t;
+    } else {
+        const float zeta = (be - al) / (2.0f * ga);
+        const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+        if (t == 0.0f) return false;  // below FP32 resolution
+        c = rsqrtf(fmaf(t, t, 1.0f));
+        sn = c * t;
+    }
+    for (int r = lane; r < srot; r += 32) {
+        const T a = x[r], b = y[r];
         x[r] = fma(c, a, -sn * b);
         y[r] = fma(sn, a, c * b);
     }
@@ -400,11 +459,13 @@ __device__ __forceinline__ bool jacobi_rotate(double *x, double *y, int s, int l
 }
 
 // Convergence threshold of a pair, squared: |x'y| <= 8 sqrt(s) u |x| |y|
-// (u = 2^-53), a few times the rounding error of the dot products, so that
-// rounding alone never keeps a sweep alive.
-__device__ __forceinline__ double jacobi_tol2(int s) {
-    const double tol = 8.0 * sqrt((double)s) * 1.1102230246251565e-16;
-    return tol * tol;
+// (u the unit roundoff of T), a few times the rounding error of the dot
+// products, so that rounding alone never keeps a sweep alive.
+template <class T>
+__device__ __forceinline__ T jacobi_tol2(int s) {
+    const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-8;
+    const double tol = 8.0 * sqrt((double)s) * u;
+    return (T)(tol * tol);
 }
 
 // Sort key of a column norm: non-finite values sort last.
@@ -420,12 +481,12 @@ __device__ __forceinline__ int pos_of(int blk, int g, int nblk) {
 }
 
 // Rotate all pairs between the two b-column blocks X (global block bx) and Y
-// (by), and, if `inner`, the pairs within each of them.  Virtual columns
-// (global index >= s) are zero and skipped.  Returns whether any rotation
-// was applied by this thread's warp.
-__device__ __forceinline__ bool jacobi_block_pairs(double *X, double *Y, int bx, int by, int b, int s, bool inner,
-                                                   int lane, int warp) {
-    const double tol2 = jacobi_tol2(s);
+// (by), and, if `inner`, the pairs within each of them.  Columns are srot
+// apart within a block; virtual columns (global index >= s) are zero and
+// skipped.  Returns whether any rotation was applied by this thread's warp.
+template <class T>
+__device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, int bx, int by, int b, int s, int srot, bool inner,
+                                                   int lane, int warp, T tol2) {
     bool rot = false;
     if (inner) {
         const int bp = b + (b & 1);
@@ -436,8 +497,8 @@ __device__ __forceinline__ bool jacobi_block_pairs(double *X, double *Y, int bx,
                 const int c2 = 1 + (bp - 2 - q + ir) % (bp - 1);
                 const int blk = slot ? by : bx;
                 if (a >= b || c2 >= b || blk * b + max(a, c2) >= s) continue;
-                double *base = slot ? Y : X;
-                rot |= jacobi_rotate(base + min(a, c2) * s, base + max(a, c2) * s, s, lane, tol2);
+                T *base = slot ? Y : X;
+                rot |= jacobi_rotate(base + min(a, c2) * srot, base + max(a, c2) * srot, s, srot, lane, tol2);
             }
             __syncthreads();
         }
@@ -448,19 +509,69 @@ __device__ __forceinline__ bool jacobi_block_pairs(double *X, double *Y, int bx,
             const int gx = bx * b + i, gy = by * b + jy;
             if (gx >= s || gy >= s) continue;
             // the lower global index is the first column of the pair
-            if (gx < gy) rot |= jacobi_rotate(X + i * s, Y + jy * s, s, lane, tol2);
-            else rot |= jacobi_rotate(Y + jy * s, X + i * s, s, lane, tol2);
+            if (gx < gy) rot |= jacobi_rotate(X + i * srot, Y + jy * srot, s, srot, lane, tol2);
+            else rot |= jacobi_rotate(Y + jy * srot, X + i * srot, s, srot, lane, tol2);
         }
         __syncthreads();
     }
     return rot;
 }
 
+// Sweeps of the shared-memory block Jacobi: each CTA holds two blocks of b
+// columns (srot elements each) in buf(cur); after each block round the CTAs
+// pull their next blocks over DSMEM into buf(cur ^ 1).  Runs until a sweep
+// rotates nothing or max_sweeps; g (global round) and cur are updated so
+// that buf(cur) holds the blocks of positions (rank, 2C - 1 - rank) at round
+// g on return.  Returns the number of sweeps run.
+template <int kCl, class T>
+__device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, T *buf1, int b, int s, int srot, int max_sweeps, int &g,
+                             int &cur, int *s_flag) {
+    constexpr int nblk = 2 * kCl;
+    const int rank = (int)cl.block_rank(), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int px = rank, py = nblk - 1 - rank, bs = b * srot;
+    const T tol2 = jacobi_tol2<T>(s);
+    auto buf = [&](int k) { return k ? buf1 : buf0; };
+    int nsweep = 0;
+    bool done = false;
+    for (int sweep = 0; sweep < max_sweeps && !done; ++sweep, ++nsweep) {
+        if (tid == 0) s_flag[sweep & 1] = 0;
+        __syncthreads();
+        for (int round = 0; round < nblk - 1; ++round, ++g) {
+            const int bx = block_at(px, g, nblk), by = block_at(py, g, nblk);
+            if (jacobi_block_pairs<T>(buf(cur), buf(cur) + bs, bx, by, b, s, srot, round == 0, lane, warp, tol2) &&
+                lane == 0)
+                s_flag[sweep & 1] = 1;
+            cl.sync();
+            if (round == nblk - 2) {
+                int any = 0;
+#pragma unroll
+                for (int k = 0; k < kCl; ++k) any |= cl.map_shared_rank(s_flag, k)[sweep & 1];
+                if (!any) {
+                    done = true;
+                    break;
+                }
+            }
+            // pull the blocks of round g + 1 from their holders in round g
+            for (int slot = 0; slot < 2; ++slot) {
+                const int blk = block_at(slot ? py : px, g + 1, nblk);
+                const int p = pos_of(blk, g, nblk);
+                const int h = p < kCl ? p : nblk - 1 - p, hs = p < kCl ? 0 : 1;
+                const T *src = cl.map_shared_rank(buf(cur) + hs * bs, h);
+                T *dst = buf(cur ^ 1) + slot * bs;
+                for (int e = tid; e < bs; e += kQrThreads) dst[e] = src[e];
+            }
+            cur ^= 1;
+            __syncthreads();
+        }
+    }
+    return nsweep;
+}
+
 // Column norms, descending order over the whole matrix, and the output of the
 // columns held in `cols` (global indices gx * b + j and gy * b + j).
 // `all_nrm` must hold every column's norm on entry.
-__device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols, int gx, int gy, int b, const double *all_nrm,
-                            int lane, int warp) {
+__device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols, int gx, int gy, int b,
+                                            const double *all_nrm, int lane, int warp) {
     const int s = J.s;
     for (int q = warp; q < 2 * b; q += kNw) {
         const int slot = q / b, j = q % b, u = (slot ? gy : gx) * b + j;
@@ -480,8 +591,9 @@ __device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols,
     }
 }
 
-__device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, int sweeps) {
-    *J.sweeps = sweeps;
+__device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, int sweeps, int sweeps32) {
+    J.sweeps[0] = sweeps;
+    J.sweeps[1] = sweeps32;
     int r = 0;
     bool bad = false;
     for (int u = 0; u < J.s; ++u) {
@@ -491,8 +603,22 @@ __device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, 
     *J.rank = bad ? -1 : r;
 }
 
-// Block Jacobi with the blocks in shared memory.  Shared memory: two buffers
-// of two b x s blocks, 2b local norms, s gathered norms.
+constexpr int kMaxSweeps32 = 12;
+
+// Block Jacobi with the blocks in shared memory, in two precisions.
+//  A. FP32 sweeps on fl32(M), M = R', carrying the accumulated rotations J
+//     (each column holds s entries of M then s of J), until FP32 convergence.
+//  B. M1 = M J in FP64 (M read from R', J from shared memory) into `work`.
+//  C. FP64 sweeps on M1 until convergence; S, W from M1's columns.
+// J is orthogonal to FP32 accuracy, so M1 = (M J_o)(I + E) with J_o
+// orthogonal and |E| ~ 1e-7: a right multiplicative perturbation, under
+// which every singular value of M1 is that of M times (1 + O(|E|)) and the
+// dominant left singular subspace of M1 projects M with the error
+// sigma_{r+1}(M) (1 + O(|E|)) (relative perturbation theory; Eisenstat and
+// Ipsen 1995).  The FP32 sweeps do the bulk of the rotations on a pipe 64
+// times faster than FP64; the FP64 phase then converges in a few sweeps.
+// Shared memory: two buffers of two b x s blocks (FP64 layout; the FP32
+// phase stores b x 2s floats in the same bytes), 2b local norms, s norms.
 template <int kCl>
 __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs, double tau) {
     cg::cluster_group cl = cg::this_cluster();
@@ -503,53 +629,71 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nblk = 2 * kCl;
     const int b = (s + nblk - 1) / nblk, bs = b * s;
-    auto buf = [&](int k) { return sm + k * 2 * bs; };
     double *nrm_loc = sm + 4 * bs, *all_nrm = nrm_loc + 2 * b;
     const int px = rank, py = nblk - 1 - rank;
+    // A. FP32 phase
+    float *f0 = reinterpret_cast<float *>(sm), *f1 = reinterpret_cast<float *>(sm + 2 * bs);
+    const int s2 = 2 * s, bsf = b * s2;
     for (int slot = 0; slot < 2; ++slot) {
         const int blk = block_at(slot ? py : px, 0, nblk);
-        double *dst = buf(0) + slot * bs;
-        for (int e = tid; e < bs; e += kQrThreads) {
-            const int u = blk * b + e / s;
-            dst[e] = u < s ? J.Rt[(int64_t)u * s + e % s] : 0.0;
+        float *dst = f0 + slot * bsf;
+        for (int e = tid; e < bsf; e += kQrThreads) {
+            const int u = blk * b + e / s2, r = e % s2;
+            float v = 0.0f;
+            if (u < s) v = r < s ? (float)J.Rt[(int64_t)u * s + r] : (r - s == u ? 1.0f : 0.0f);
+            dst[e] = v;
         }
     }
     __syncthreads();
-    int cur = 0, g = 0, nsweep = 0;
-    bool done = false;
-    for (int sweep = 0; sweep < kMaxSweeps && !done; ++sweep, ++nsweep) {
-        if (tid == 0) s_flag[sweep & 1] = 0;
-        __syncthreads();
-        for (int round = 0; round < nblk - 1; ++round, ++g) {
-            const int bx = block_at(px, g, nblk), by = block_at(py, g, nblk);
-            if (jacobi_block_pairs(buf(cur), buf(cur) + bs, bx, by, b, s, round == 0, lane, warp) && lane == 0)
-                s_flag[sweep & 1] = 1;
-            cl.sync();
-            if (round == nblk - 2) {
-                int any = 0;
+    int g = 0, cur = 0;
+    const int sw32 = jacobi_sweeps<kCl, float>(cl, f0, f1, b, s, s2, kMaxSweeps32, g, cur, s_flag);
+    // B. M1 = M J for the held columns, 8 at a time; rows i = tid, tid + 256
+    {
+        const float *F = cur ? f1 : f0;
+        const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
+        for (int q0 = 0; q0 < 2 * b; q0 += 8) {
+            double acc[8][2];
 #pragma unroll
-                for (int k = 0; k < kCl; ++k) any |= cl.map_shared_rank(s_flag, k)[sweep & 1];
-                if (!any) {
-                    done = true;
-                    break;
+            for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = 0.0;
+            for (int k = 0; k < s; ++k) {
+                const double m0 = tid < s ? J.Rt[(int64_t)k * s + tid] : 0.0;
+                const double m1 = tid + kQrThreads < s ? J.Rt[(int64_t)k * s + tid + kQrThreads] : 0.0;
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const int q = q0 + a;
+                    const double jk = q < 2 * b ? (double)F[q * s2 + s + k] : 0.0;
+                    acc[a][0] = fma(m0, jk, acc[a][0]);
+                    acc[a][1] = fma(m1, jk, acc[a][1]);
                 }
             }
-            // pull the blocks of round g + 1 from their holders in round g
-            for (int slot = 0; slot < 2; ++slot) {
-                const int blk = block_at(slot ? py : px, g + 1, nblk);
-                const int p = pos_of(blk, g, nblk);
-                const int h = p < kCl ? p : nblk - 1 - p, hs = p < kCl ? 0 : 1;
-                const double *src = cl.map_shared_rank(buf(cur) + hs * bs, h);
-                double *dst = buf(cur ^ 1) + slot * bs;
-                for (int e = tid; e < bs; e += kQrThreads) dst[e] = src[e];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int q = q0 + a;
+                if (q >= 2 * b) break;
+                const int u = (q < b ? gx : gy) * b + q % b;
+                if (u >= s) continue;
+                if (tid < s) J.work[(int64_t)u * s + tid] = acc[a][0];
+                if (tid + kQrThreads < s) J.work[(int64_t)u * s + tid + kQrThreads] = acc[a][1];
             }
-            cur ^= 1;
-            __syncthreads();
         }
     }
+    cl.sync();  // M1 complete; no CTA reads another's FP32 blocks any more
+    // C. FP64 phase on M1, starting from the same block positions
+    for (int slot = 0; slot < 2; ++slot) {
+        const int blk = block_at(slot ? py : px, g, nblk);
+        double *dst = sm + slot * bs;
+        for (int e = tid; e < bs; e += kQrThreads) {
+            const int u = blk * b + e / s;
+            dst[e] = u < s ? J.work[(int64_t)u * s + e % s] : 0.0;
+        }
+    }
+    __syncthreads();
+    cur = 0;
+    const int sw64 = jacobi_sweeps<kCl, double>(cl, sm, sm + 2 * bs, b, s, s, kMaxSweeps, g, cur, s_flag);
+    double *D = cur ? sm + 2 * bs : sm;
     const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
     for (int q = warp; q < 2 * b; q += kNw) {
-        const double *col = buf(cur) + q * s;
+        const double *col = D + q * s;
         double v = 0.0;
         for (int r = lane; r < s; r += 32) v = fma(col[r], col[r], v);
         v = warp_sum(v);
@@ -562,8 +706,8 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
         if (u < s) all_nrm[u] = cl.map_shared_rank(nrm_loc, h)[q];
     }
     __syncthreads();
-    jacobi_emit(J, buf(cur), gx, gy, b, all_nrm, lane, warp);
-    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, nsweep);
+    jacobi_emit(J, D, gx, gy, b, all_nrm, lane, warp);
+    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, sw64, sw32);
     cl.sync();  // no CTA leaves while another may still read its norms
 }
 
@@ -602,7 +746,9 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
                 Ab[e] = u < s ? __ldcg(A + (int64_t)u * s + e % s) : 0.0;
             }
             __syncthreads();
-            if (jacobi_block_pairs(Ab, Ab + bs, bx, by, b, s, round == 0, lane, warp) && lane == 0)
+            if (jacobi_block_pairs<double>(Ab, Ab + bs, bx, by, b, s, s, round == 0, lane, warp,
+                                           jacobi_tol2<double>(s)) &&
+                lane == 0)
                 s_flag[sweep & 1] = 1;
             for (int e = tid; e < 2 * bs; e += kQrThreads) {
                 const int slot = e / bs, u = (slot ? by : bx) * b + (e % bs) / s;
@@ -632,7 +778,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
     }
     __syncthreads();
     jacobi_emit(J, Ab, gx, gy, b, all_nrm, lane, warp);
-    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, nsweep);
+    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, nsweep, 0);
     cl.sync();  // no CTA leaves while another may still read its flag
 }
 
@@ -920,7 +1066,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oS[u] = take(s);
             oQ2[u] = df ? take((int64_t)J.m * s) : 0;  // float2, one double each
         }
-        DevBuf ws(tot * sizeof(double) + 2 * np * sizeof(int) + 256, st);
+        DevBuf ws(tot * sizeof(double) + 3 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
         int *d_rank = (int *)(W + tot);
         cmark();
@@ -976,20 +1122,21 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
-            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + u, ps[u]};
+            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 2 * u, ps[u]};
         svd_launch(ctx, st, sv, tau);
         cmark();
         // decisions on the host
-        std::vector<int> h_rank(2 * np);
-        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 2 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
+        std::vector<int> h_rank(3 * np);
+        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 3 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
         if (st != ctx->aux) stage_reset_main(ctx);
         cmark();
         ctx->comp_stats[0] += (long long)np;
         ctx->comp_stats[1] += 1;
         for (size_t u = 0; u < np; ++u) {
-            ctx->comp_stats[2] += h_rank[np + u];
-            ctx->comp_stats[3] = std::max(ctx->comp_stats[3], (long long)h_rank[np + u]);
+            ctx->comp_stats[2] += h_rank[np + 2 * u];
+            ctx->comp_stats[3] = std::max(ctx->comp_stats[3], (long long)h_rank[np + 2 * u]);
+            ctx->comp_stats[4] += h_rank[np + 2 * u + 1];
         }
         std::vector<int> next;
         std::vector<GemmProb> gu, gv;
