@@ -90,6 +90,9 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
         TLR_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(DevStatus)));
         TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_status, sizeof(DevStatus), cudaHostAllocDefault));
         TLR_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        for (cudaStream_t &c : ctx->cls_stream) TLR_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->cls_fork, cudaEventDisableTiming));
+        for (cudaEvent_t &e : ctx->cls_join) TLR_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreate(&ctx->ev_a));
         TLR_CUDA_TRY(cudaEventCreate(&ctx->ev_b));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -116,6 +119,11 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    for (cudaStream_t c : ctx->cls_stream)
+        if (c) cudaStreamDestroy(c);
+    if (ctx->cls_fork) cudaEventDestroy(ctx->cls_fork);
+    for (cudaEvent_t e : ctx->cls_join)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : {ctx->ev_a, ctx->ev_b, ctx->ev_fork, ctx->ev_join})
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);

@@ -113,6 +113,11 @@ struct tlr_ctx {
     tlr::DevStatus *d_status = nullptr;   // device status word
     tlr::DevStatus *h_status = nullptr;   // pinned host mirror
     cudaStream_t aux = nullptr;           // second stream for concurrent tile work
+    // compression: one stream per launch class (cluster size), forked from and
+    // joined to the calling stream
+    static constexpr int kClassStreams = 4, kClassEvents = 8;
+    cudaStream_t cls_stream[kClassStreams] = {};
+    cudaEvent_t cls_fork = nullptr, cls_join[kClassEvents] = {};
     cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_fork = nullptr, ev_join = nullptr;
     // descriptor staging: ring 0 for the caller's stream, ring 1 for `aux`
     tlr::StageRing stage[2];

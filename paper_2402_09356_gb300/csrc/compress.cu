@@ -889,7 +889,9 @@ static SvdKernel svd_sm_kernel(int c) {
 }
 
 // One launch per (kernel, cluster size) class, with the class's largest
-// shared-memory need.
+// shared-memory need.  The classes run concurrently, each on its own stream
+// (forked from and joined back to the calling stream), largest clusters
+// first: a column's compression then costs its slowest class, not the sum.
 template <class Job, class K>
 struct LaunchClass {
     K kernel;
@@ -901,11 +903,28 @@ struct LaunchClass {
 template <class Job, class K, class... Extra>
 static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClass<Job, K>> &cls,
                            Extra... extra) {
-    for (auto &c : cls) {
-        if (c.jobs.empty()) continue;
-        auto *d = (const Job *)stage_push(ctx, c.jobs.data(), c.jobs.size() * sizeof(Job), st);
-        launch_cluster(c.kernel, c.csize, (int)c.jobs.size(), c.smem, st, d, extra...);
+    std::vector<LaunchClass<Job, K> *> use;
+    for (auto &c : cls)
+        if (!c.jobs.empty()) use.push_back(&c);
+    std::stable_sort(use.begin(), use.end(), [](const LaunchClass<Job, K> *a, const LaunchClass<Job, K> *b) {
+        return a->csize > b->csize;
+    });
+    // descriptors go up on the calling stream, before the fork
+    std::vector<const Job *> dj;
+    for (auto *c : use) dj.push_back((const Job *)stage_push(ctx, c->jobs.data(), c->jobs.size() * sizeof(Job), st));
+    if (use.size() == 1) {
+        launch_cluster(use[0]->kernel, use[0]->csize, (int)use[0]->jobs.size(), use[0]->smem, st, dj[0], extra...);
+        return;
     }
+    if ((int)use.size() > tlr_ctx::kClassEvents) throw make_error(TLR_ERR_ARG, "too many launch classes");
+    TLR_CUDA_TRY(cudaEventRecord(ctx->cls_fork, st));
+    for (size_t k = 0; k < use.size(); ++k) {
+        cudaStream_t cs = ctx->cls_stream[k % tlr_ctx::kClassStreams];
+        TLR_CUDA_TRY(cudaStreamWaitEvent(cs, ctx->cls_fork, 0));
+        launch_cluster(use[k]->kernel, use[k]->csize, (int)use[k]->jobs.size(), use[k]->smem, cs, dj[k], extra...);
+        TLR_CUDA_TRY(cudaEventRecord(ctx->cls_join[k], cs));
+    }
+    for (size_t k = 0; k < use.size(); ++k) TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->cls_join[k], 0));
 }
 
 template <class Job, class K>
