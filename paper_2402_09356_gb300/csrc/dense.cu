@@ -13,6 +13,7 @@
 namespace tlr {
 
 constexpr int kBlk = 32;
+constexpr int kStrip = 64;  // column strips of the trailing update
 
 // Cholesky of the w x w diagonal block at (p0, p0) of A (lower part).
 __global__ void k_potrf_block(double *__restrict__ A, int lda, int m, int p0, DevStatus *st,
@@ -98,13 +99,13 @@ void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long l
         double *P = A + (int64_t)p0 * lda + p0 + w;
         double *A22 = A + (int64_t)(p0 + w) * lda + p0 + w;
         std::vector<GemmProb> probs;
-        for (int cb = 0; cb < rest; cb += kGemmBN) {
+        for (int cb = 0; cb < rest; cb += kStrip) {
             GemmProb g{};
             g.A = P + cb;
             g.B = P + cb;
             g.C = A22 + (int64_t)cb * lda + cb;
             g.m = rest - cb;
-            g.n = std::min(kGemmBN, rest - cb);
+            g.n = std::min(kStrip, rest - cb);
             g.k = w;
             g.lda = lda;
             g.ldb = lda;

@@ -23,14 +23,14 @@ void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s) {
     return d;
 }
 
-template <class Epi>
-static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
-                   double alpha, const Epi &epi, bool df) {
+template <int BM, int BN, class Epi>
+static void launch_shape(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                         double alpha, const Epi &epi, bool df) {
     if (probs.empty()) return;
     std::vector<int> off(probs.size() + 1, 0);
     for (size_t b = 0; b < probs.size(); ++b) {
         const GemmProb &p = probs[b];
-        int tiles = (p.m > 0 && p.n > 0) ? (int)(ceil_div(p.m, kGemmBM) * ceil_div(p.n, kGemmBN)) : 0;
+        int tiles = (p.m > 0 && p.n > 0) ? (int)(ceil_div(p.m, BM) * ceil_div(p.n, BN)) : 0;
         off[b + 1] = off[b] + tiles;
     }
     int total = off.back();
@@ -38,16 +38,29 @@ static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const st
     auto *dp = (const GemmProb *)stage_push(ctx, probs.data(), probs.size() * sizeof(GemmProb), s);
     auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
     int np = (int)probs.size();
+    // the transposition pairs the library uses: NN, TN, NT (no TT)
+    if (ta && tb) throw make_error(TLR_ERR_ARG, "GEMM with both operands transposed is not provided");
     if (df) {
-        if (!ta && !tb) launch(k_gemm_df<false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-        else if (!ta && tb) launch(k_gemm_df<false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-        else if (ta && !tb) launch(k_gemm_df<true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-        else launch(k_gemm_df<true, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    } else if (!ta && !tb) launch(k_gemm_f64<false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    else if (!ta && tb) launch(k_gemm_f64<false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    else if (ta && !tb) launch(k_gemm_f64<true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    else launch(k_gemm_f64<true, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        if (!ta && !tb) launch(k_gemm_df<BM, BN, false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        else if (!ta) launch(k_gemm_df<BM, BN, false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        else launch(k_gemm_df<BM, BN, true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    } else if (!ta && !tb) launch(k_gemm_f64<BM, BN, false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else if (!ta) launch(k_gemm_f64<BM, BN, false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else launch(k_gemm_f64<BM, BN, true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
     TLR_CHECK_LAUNCH();
+}
+
+// Split a batch by output shape: problems with at most 32 rows and/or 32
+// columns go to the thin tile shapes, whose padding stays small.
+template <class Epi>
+static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                        double alpha, const Epi &epi, bool df) {
+    std::vector<GemmProb> cls[4];  // 64x64, 64x32, 32x64, 32x32
+    for (const GemmProb &p : probs) cls[(p.m <= 32 ? 2 : 0) + (p.n <= 32 ? 1 : 0)].push_back(p);
+    launch_shape<64, 64>(ctx, s, ta, tb, cls[0], alpha, epi, df);
+    launch_shape<64, 32>(ctx, s, ta, tb, cls[1], alpha, epi, df);
+    launch_shape<32, 64>(ctx, s, ta, tb, cls[2], alpha, epi, df);
+    launch_shape<32, 32>(ctx, s, ta, tb, cls[3], alpha, epi, df);
 }
 
 __global__ void k_split_f2(const double *__restrict__ src, int ld, int m, int64_t count,
@@ -96,11 +109,26 @@ void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vec
 
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
                          double alpha, const double *xy, int64_t n, const MaternParams &P, bool df) {
+    if (!tb) throw make_error(TLR_ERR_ARG, "the Matern panel product takes B transposed");
     EpiMatern e;
     e.xy = xy;
     e.n = n;
     e.P = P;
-    launch_gemm(ctx, s, false, tb, probs, alpha, e, df);
+    std::vector<GemmProb> big;
+    for (const GemmProb &p : probs) big.push_back(p);
+    // the panel update is one large product: 64 x 64 tiles
+    if (big.empty()) return;
+    std::vector<int> off(big.size() + 1, 0);
+    for (size_t b = 0; b < big.size(); ++b)
+        off[b + 1] = off[b] + ((big[b].m > 0 && big[b].n > 0) ? (int)(ceil_div(big[b].m, 64) * ceil_div(big[b].n, 64)) : 0);
+    int total = off.back();
+    if (total == 0) return;
+    auto *dp = (const GemmProb *)stage_push(ctx, big.data(), big.size() * sizeof(GemmProb), s);
+    auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
+    int np = (int)big.size();
+    if (df) launch(k_gemm_df<64, 64, false, true, EpiMatern>, total, kGemmThreads, 0, s, dp, dt, np, alpha, e);
+    else launch(k_gemm_f64<64, 64, false, true, EpiMatern>, total, kGemmThreads, 0, s, dp, dt, np, alpha, e);
+    TLR_CHECK_LAUNCH();
 }
 
 }  // namespace tlr

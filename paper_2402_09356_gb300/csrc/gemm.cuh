@@ -1,12 +1,13 @@
 // Batched FP64 GEMM with per-problem sizes and a pluggable epilogue.
 //
 // C_b = epilogue(alpha * op(A_b) op(B_b), C_b) for every problem b of a batch;
-// one launch covers all problems (blockIdx.x runs over the concatenated
-// 64 x 64 output tiles; a binary search over the per-problem tile offsets
-// finds the problem).  Matrices are column major.  Each thread accumulates a
-// 4 x 4 block over K in steps of 16 staged through shared memory.  GB300's
-// FP64 pipe issues 2 DFMA/clk/SM, so this register blocking already keeps the
-// kernel bound by the FP64 units, not by shared memory or HBM.
+// one launch covers all problems of one tile shape (blockIdx.x runs over the
+// concatenated output tiles; a binary search over the per-problem tile
+// offsets finds the problem).  Matrices are column major.  Each thread
+// accumulates a register block over K in steps of 16 staged through shared
+// memory.  GB300's FP64 pipe issues 2 DFMA/clk/SM, so this register blocking
+// already keeps the kernel bound by the FP64 units, not by shared memory or
+// HBM.
 #pragma once
 
 #include "common.cuh"
@@ -25,7 +26,7 @@ struct GemmProb {
     const float2 *B2;
 };
 
-constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 16, kGemmThreads = 256;
+constexpr int kGemmBK = 16, kGemmThreads = 256;
 
 // C = alpha * AB + beta * C   (C is not read when beta == 0)
 struct EpiLinear {
@@ -49,49 +50,62 @@ struct EpiMatern {
     }
 };
 
-template <bool TA, bool TB, class Epi>
-__global__ void __launch_bounds__(kGemmThreads)
-k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob,
-           double alpha, Epi epi) {
-    __shared__ double As[kGemmBK][kGemmBM + 1];
-    __shared__ double Bs[kGemmBK][kGemmBN + 1];
-    const int tid = threadIdx.x;
-    // locate the problem
+// Locate the problem of output tile blockIdx.x (binary search over the
+// per-problem tile offsets) and the tile's first row and column.
+template <int BM, int BN>
+__device__ __forceinline__ bool gemm_tile(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off,
+                                          int nprob, GemmProb &p, int &m0, int &n0) {
     int lo = 0, hi = nprob - 1, t = blockIdx.x;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    const GemmProb p = probs[lo];
-    int local = t - tile_off[lo];
-    int tm = (p.m + kGemmBM - 1) / kGemmBM;
-    if (tm == 0) return;
-    const int m0 = (local % tm) * kGemmBM, n0 = (local / tm) * kGemmBN;
-    const int r0 = (tid & 15) * 4, c0 = (tid >> 4) * 4;
-    double acc[4][4];
+    p = probs[lo];
+    const int local = t - tile_off[lo];
+    const int tm = (p.m + BM - 1) / BM;
+    if (tm == 0) return false;
+    m0 = (local % tm) * BM;
+    n0 = (local / tm) * BN;
+    return true;
+}
+
+// One BM x BN output tile per CTA of 256 threads (a 16 x 16 thread grid,
+// BM/16 x BN/16 outputs per thread), K in steps of 16 through shared memory.
+// Tiles of 64 x 64 serve large products; 32-row or 32-column tiles serve the
+// many thin products of the low-rank updates (ranks of a few tens), whose
+// padding would otherwise dominate.
+template <int BM, int BN, bool TA, bool TB, class Epi>
+__global__ void __launch_bounds__(kGemmThreads)
+k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob,
+           double alpha, Epi epi) {
+    constexpr int TM = BM / 16, TN = BN / 16;
+    __shared__ double As[kGemmBK][BM + 1];
+    __shared__ double Bs[kGemmBK][BN + 1];
+    const int tid = threadIdx.x;
+    GemmProb p;
+    int m0, n0;
+    if (!gemm_tile<BM, BN>(probs, tile_off, nprob, p, m0, n0)) return;
+    const int r0 = (tid & 15) * TM, c0 = (tid >> 4) * TN;
+    double acc[TM][TN];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < TN; ++b) acc[a][b] = 0.0;
 
     for (int k0 = 0; k0 < p.k; k0 += kGemmBK) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int r, kk;
-            if (!TA) { r = tid & 63; kk = (tid >> 6) + 4 * q; }
-            else     { kk = tid & 15; r = (tid >> 4) + 16 * q; }
-            int gr = m0 + r, gk = k0 + kk;
+        for (int e = tid; e < BM * kGemmBK; e += kGemmThreads) {
+            const int r = TA ? e / kGemmBK : e % BM, kk = TA ? e % kGemmBK : e / BM;
+            const int gr = m0 + r, gk = k0 + kk;
             double v = 0.0;
             if (gr < p.m && gk < p.k)
                 v = TA ? p.A[(int64_t)gr * p.lda + gk] : p.A[(int64_t)gk * p.lda + gr];
             As[kk][r] = v;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int c, kk;
-            if (!TB) { kk = tid & 15; c = (tid >> 4) + 16 * q; }
-            else     { c = tid & 63; kk = (tid >> 6) + 4 * q; }
-            int gc = n0 + c, gk = k0 + kk;
+        for (int e = tid; e < BN * kGemmBK; e += kGemmThreads) {
+            const int c = TB ? e % BN : e / kGemmBK, kk = TB ? e / BN : e % kGemmBK;
+            const int gc = n0 + c, gk = k0 + kk;
             double v = 0.0;
             if (gc < p.n && gk < p.k)
                 v = TB ? p.B[(int64_t)gk * p.ldb + gc] : p.B[(int64_t)gc * p.ldb + gk];
@@ -100,22 +114,24 @@ k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off,
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kGemmBK; ++kk) {
-            double a[4], b[4];
+            double a[TM], b[TN];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { a[q] = As[kk][r0 + q]; b[q] = Bs[kk][c0 + q]; }
+            for (int q = 0; q < TM; ++q) a[q] = As[kk][r0 + q];
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int q = 0; q < TN; ++q) b[q] = Bs[kk][c0 + q];
 #pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+            for (int x = 0; x < TM; ++x)
+#pragma unroll
+                for (int y = 0; y < TN; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
+    for (int y = 0; y < TN; ++y) {
         int c = n0 + c0 + y;
         if (c >= p.n) continue;
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < TM; ++x) {
             int r = m0 + r0 + x;
             if (r >= p.m) continue;
             double *cp = p.C + (int64_t)c * p.ldc + r;
@@ -127,10 +143,11 @@ k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off,
 // The same product with paired-FP32 ("double-float") arithmetic on the FP32
 // pipe, which GB300 issues 64 times faster than FP64.  Each operand x is read
 // as hi = fl32(x), lo = fl32(x - hi) (|x - hi - lo| <= 2^-48 |x|) from the
-// copies A2, B2 that split_f2 made once per operand.  A product is a_hi b_hi + (its exact rounding error,
-// by FMA) + a_hi b_lo + a_lo b_hi; the high parts are accumulated with TwoSum
-// (Knuth; Dekker 1971) and all low-order terms in a second FP32 accumulator,
-// so a K-term dot product carries about 46 bits, i.e. ~1e-13 relative error.
+// copies A2, B2 that split_f2 made once per operand.  A product is
+// a_hi b_hi + (its exact rounding error, by FMA) + a_hi b_lo + a_lo b_hi; the
+// high parts are accumulated with TwoSum (Knuth; Dekker 1971) and all
+// low-order terms in a second FP32 accumulator, so a K-term dot product
+// carries about 46 bits, i.e. ~1e-13 relative error.
 __device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float &ch, float &cl) {
     float p = __fmul_rn(ah, bh);
     float e = __fmaf_rn(ah, bh, -p);
@@ -143,47 +160,37 @@ __device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, f
     cl = __fadd_rn(cl, __fadd_rn(err, e));
 }
 
-template <bool TA, bool TB, class Epi>
+template <int BM, int BN, bool TA, bool TB, class Epi>
 __global__ void __launch_bounds__(kGemmThreads)
 k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob, double alpha,
           Epi epi) {
-    __shared__ float2 As[kGemmBK][kGemmBM + 1];
-    __shared__ float2 Bs[kGemmBK][kGemmBN + 1];
+    constexpr int TM = BM / 16, TN = BN / 16;
+    __shared__ float2 As[kGemmBK][BM + 1];
+    __shared__ float2 Bs[kGemmBK][BN + 1];
     const int tid = threadIdx.x;
-    int lo = 0, hi = nprob - 1, t = blockIdx.x;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const GemmProb p = probs[lo];
-    int local = t - tile_off[lo];
-    int tm = (p.m + kGemmBM - 1) / kGemmBM;
-    if (tm == 0) return;
-    const int m0 = (local % tm) * kGemmBM, n0 = (local / tm) * kGemmBN;
-    const int r0 = (tid & 15) * 4, c0 = (tid >> 4) * 4;
-    float ch[4][4], cl[4][4];
+    GemmProb p;
+    int m0, n0;
+    if (!gemm_tile<BM, BN>(probs, tile_off, nprob, p, m0, n0)) return;
+    const int r0 = (tid & 15) * TM, c0 = (tid >> 4) * TN;
+    float ch[TM][TN], cl[TM][TN];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) { ch[a][b] = 0.f; cl[a][b] = 0.f; }
+        for (int b = 0; b < TN; ++b) { ch[a][b] = 0.f; cl[a][b] = 0.f; }
     for (int k0 = 0; k0 < p.k; k0 += kGemmBK) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int r, kk;
-            if (!TA) { r = tid & 63; kk = (tid >> 6) + 4 * q; }
-            else     { kk = tid & 15; r = (tid >> 4) + 16 * q; }
-            int gr = m0 + r, gk = k0 + kk;
+        for (int e = tid; e < BM * kGemmBK; e += kGemmThreads) {
+            const int r = TA ? e / kGemmBK : e % BM, kk = TA ? e % kGemmBK : e / BM;
+            const int gr = m0 + r, gk = k0 + kk;
             float2 v = make_float2(0.f, 0.f);
             if (gr < p.m && gk < p.k)
                 v = TA ? p.A2[(int64_t)gr * p.lda + gk] : p.A2[(int64_t)gk * p.lda + gr];
             As[kk][r] = v;
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int c, kk;
-            if (!TB) { kk = tid & 15; c = (tid >> 4) + 16 * q; }
-            else     { c = tid & 63; kk = (tid >> 6) + 4 * q; }
-            int gc = n0 + c, gk = k0 + kk;
+        for (int e = tid; e < BN * kGemmBK; e += kGemmThreads) {
+            const int c = TB ? e % BN : e / kGemmBK, kk = TB ? e / BN : e % kGemmBK;
+            const int gc = n0 + c, gk = k0 + kk;
             float2 v = make_float2(0.f, 0.f);
             if (gc < p.n && gk < p.k)
                 v = TB ? p.B2[(int64_t)gk * p.ldb + gc] : p.B2[(int64_t)gc * p.ldb + gk];
@@ -192,22 +199,24 @@ k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, 
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < kGemmBK; ++kk) {
-            float2 a[4], b[4];
+            float2 a[TM], b[TN];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { a[q] = As[kk][r0 + q]; b[q] = Bs[kk][c0 + q]; }
+            for (int q = 0; q < TM; ++q) a[q] = As[kk][r0 + q];
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+            for (int q = 0; q < TN; ++q) b[q] = Bs[kk][c0 + q];
 #pragma unroll
-                for (int y = 0; y < 4; ++y) df_fma(a[x].x, a[x].y, b[y].x, b[y].y, ch[x][y], cl[x][y]);
+            for (int x = 0; x < TM; ++x)
+#pragma unroll
+                for (int y = 0; y < TN; ++y) df_fma(a[x].x, a[x].y, b[y].x, b[y].y, ch[x][y], cl[x][y]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
+    for (int y = 0; y < TN; ++y) {
         int c = n0 + c0 + y;
         if (c >= p.n) continue;
 #pragma unroll
-        for (int x = 0; x < 4; ++x) {
+        for (int x = 0; x < TM; ++x) {
             int r = m0 + r0 + x;
             if (r >= p.m) continue;
             double *cp = p.C + (int64_t)c * p.ldc + r;
