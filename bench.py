@@ -183,6 +183,7 @@ def run_gpu(args):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         out = {"results": [], "gemm_ms": 0.0, "gemm_flops": 0.0, "panel_launches": 0,
                "stage_ms": {k: 0.0 for k in tlr.STAGES}, "comp_ms": {k: 0.0 for k in tlr.COMPRESS_STEPS},
+               "detail_ms": {k: 0.0 for k in tlr.DETAILS},
                "comp_stats": {k: 0 for k in tlr.COMPRESS_STATS}}
         clocks = ClockSampler(local)
         if world > 1:
@@ -203,6 +204,8 @@ def run_gpu(args):
                 out["stage_ms"][name] += v / args.steps
             for name, v in tlr.tlr_compress_times(ctx).items():
                 out["comp_ms"][name] += v / args.steps
+            for name, v in tlr.tlr_detail_times(ctx).items():
+                out["detail_ms"][name] += v / args.steps
             for name, v in tlr.tlr_compress_stats(ctx).items():
                 cs = out["comp_stats"]
                 cs[name] = max(cs[name], v) if name == "max_sweeps" else cs[name] + v
@@ -273,6 +276,7 @@ def run_gpu(args):
         return {"evals_per_s": o["value"], "ms_per_step": o["total_ms"] / args.steps,
                 "p50_ms": float(np.percentile(o["times"], 50)), "p99_ms": float(np.percentile(o["times"], 99)),
                 "stage_ms_per_step": o["stage_ms"], "compress_ms_per_step": o["comp_ms"],
+                "detail_ms_per_step": o["detail_ms"],
                 "compress_per_step": {"tiles": cs["tiles"] / args.steps, "rounds": cs["rounds"] / args.steps,
                                       "mean_sweeps": cs["sweeps"] / max(cs["tiles"], 1),
                                       "max_sweeps": cs["max_sweeps"],

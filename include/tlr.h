@@ -269,6 +269,15 @@ int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops,
  * of their V factors.  Errors: TLR_ERR_ARG. */
 int tlr_stage_times(tlr_ctx *ctx, double *ms);
 
+/* Finer device times (ms) of the last profiled tlr_loglik factorisation,
+ * summed over columns, written to ms[0..count-1]: operand gather, W = V'V,
+ * P = U W, forward-solve update, paired-FP32 operand copies, panel update,
+ * diagonal copy, compression, wait for the side stream, V <- L^-1 V, solve
+ * and log-determinant terms, Gram matrix V' V of the finished column, then on
+ * the side stream: POTRF, L^-1.
+ * Returns the number of values written (at most 14), or TLR_ERR_ARG (< 0). */
+int tlr_detail_times(tlr_ctx *ctx, double *ms, int count);
+
 /* Device time (ms) of the compression sub-steps of the last profiled
  * factorisation, written to ms[0..6]: sampling GEMM (T Omega), QR of the
  * sample, projection GEMM (T' Q), QR of the projection, SVD of the small

@@ -96,6 +96,7 @@ _SIGS = {
     "tlr_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_compress_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_compress_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "tlr_detail_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "tlr_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(tlr_theta),
@@ -396,6 +397,18 @@ def tlr_compress_times(ctx: Context) -> dict:
     a = (ctypes.c_double * 7)()
     ctx.check(load_library().tlr_compress_times(ctx.h, a))
     return {k: a[i] for i, k in enumerate(COMPRESS_STEPS)}
+
+
+DETAILS = ("build_copy", "build_w", "build_p", "build_solve", "split", "panel", "diag_copy", "compress",
+           "join_wait", "trsm", "solve", "gram", "potrf", "inverse")
+
+
+def tlr_detail_times(ctx: Context) -> dict:
+    a = (ctypes.c_double * len(DETAILS))()
+    n = load_library().tlr_detail_times(ctx.h, a, len(DETAILS))
+    if n < 0:
+        ctx.check(n)
+    return {k: a[i] for i, k in enumerate(DETAILS[:n])}
 
 
 COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps", "sweeps32")

@@ -398,6 +398,7 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     ctx->last_matern_entries = st.matern_entries;
     ctx->last_panel_launches = st.panel_launches;
     for (int k = 0; k < kStages; ++k) ctx->last_stage_ms[k] = st.stage_ms[k];
+    for (int k = 0; k < kDetail; ++k) ctx->last_detail_ms[k] = st.detail_ms[k];
 }
 
 int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
@@ -420,6 +421,12 @@ int tlr_stage_times(tlr_ctx *ctx, double *ms) {
     if (!ctx || !ms) return TLR_ERR_ARG;
     for (int k = 0; k < kStages; ++k) ms[k] = ctx->last_stage_ms[k];
     return TLR_OK;
+}
+
+int tlr_detail_times(tlr_ctx *ctx, double *ms, int count) {
+    if (!ctx || !ms || count < 0) return TLR_ERR_ARG;
+    for (int k = 0; k < count && k < kDetail; ++k) ms[k] = ctx->last_detail_ms[k];
+    return std::min(count, (int)kDetail);
 }
 
 int tlr_compress_times(tlr_ctx *ctx, double *ms) {

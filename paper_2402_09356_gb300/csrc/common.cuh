@@ -133,6 +133,7 @@ struct tlr_ctx {
     double last_gemm_ms = 0.0, last_gemm_flops = 0.0, last_matern_entries = 0.0;
     int last_panel_launches = 0;
     double last_stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double last_detail_ms[16] = {};
     // compression sub-steps (when profiling): sample GEMM, QR of Y, projection
     // GEMM, QR of B', SVD, host decision (incl. sync), U/V GEMMs
     std::vector<cudaEvent_t> comp_events;

@@ -115,10 +115,31 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         TLR_CUDA_TRY(cudaEventRecord(e, st));
         marks.push_back(e);
     };
+    // detail marks (profiling): each attributes the time since the previous
+    // mark on its stream to one of the kDetail buckets
+    struct DMark {
+        cudaEvent_t e;
+        int idx;
+    };
+    std::vector<DMark> dm_main, dm_aux;
+    // per finished column k: the Gram matrix G_k = V_k' V_k of its packed V
+    // factors V_k = [V_ik]_{i>k} (order of i, zero-rank tiles left out), the
+    // column offset of each tile in V_k, and V_k' y_k for the fused solve
+    std::vector<DevBuf> gram(nt), vty(nt);
+    std::vector<int> gram_n(nt, 0);
+    std::vector<std::vector<int>> gram_off(nt);
+    auto dmark = [&](std::vector<DMark> &v, cudaStream_t s, int idx) {
+        if (!ctx->profile) return;
+        profile_events(ctx, prof_used + 1);
+        cudaEvent_t e = ctx->prof_events[prof_used++];
+        TLR_CUDA_TRY(cudaEventRecord(e, s));
+        v.push_back(DMark{e, idx});
+    };
     for (int j = 0; j < nt; ++j) {
         const int mj = tile_rows(n, nb, j);
         const int64_t Mp = (int64_t)(nt - j) * nb;  // panel leading dimension
         mark();
+        dmark(dm_main, st, -1);
         // --- Q_j = [U_j0 | ... ] and offsets
         std::vector<int> off(j + 1, 0);
         for (int k = 0; k < j; ++k) off[k + 1] = off[k] + r_of(j, k);
@@ -133,56 +154,45 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                     cq.push_back(CopyDesc{Uslot(M, j, k), nb, Qj + (int64_t)off[k] * nb, nb, mj, r_of(j, k)});
             copy_batched(ctx, st, cq);
             TLR_CUDA_TRY(cudaMemsetAsync(Pj, 0, (size_t)Mp * Rj * sizeof(double), st));
-            // W_ik = V_ik' V_jk, then P block (i, k) = U_ik W_ik
-            std::vector<int64_t> woff;
-            int64_t wtot = 0;
-            struct Pair { int i, k; int64_t w; };
-            std::vector<Pair> pairs;
-            for (int i = j; i < nt; ++i)
-                for (int k = 0; k < j; ++k)
-                    if (r_of(i, k) > 0 && r_of(j, k) > 0) {
-                        pairs.push_back(Pair{i, k, wtot});
-                        wtot += (int64_t)r_of(i, k) * r_of(j, k);
-                    }
-            DevBuf wbuf((size_t)std::max<int64_t>(wtot, 1) * sizeof(double), st);
-            double *Wb = wbuf.as<double>();
-            std::vector<GemmProb> gw, gp;
-            for (const Pair &pp : pairs) {
-                int rik = r_of(pp.i, pp.k), rjk = r_of(j, pp.k), mk = tile_rows(n, nb, pp.k);
-                GemmProb a{};
-                a.A = Vslot(M, pp.i, pp.k); a.lda = nb; a.m = rik; a.k = mk;
-                a.B = Vslot(M, j, pp.k); a.ldb = nb; a.n = rjk;
-                a.C = Wb + pp.w; a.ldc = rik;
-                gw.push_back(a);
-                GemmProb b{};
-                b.A = Uslot(M, pp.i, pp.k); b.lda = nb; b.m = tile_rows(n, nb, pp.i); b.k = rik;
-                b.B = Wb + pp.w; b.ldb = rik; b.n = rjk;
-                b.C = Pj + (int64_t)off[pp.k] * Mp + (int64_t)(pp.i - j) * nb; b.ldc = (int)Mp;
-                gp.push_back(b);
-                stats->flops += 2.0 * mk * rik * rjk + 2.0 * b.m * rik * rjk;
+            dmark(dm_main, st, kDetBuildCopy);
+            // P block (i, k) = U_ik W_ik with W_ik = V_ik' V_jk, a block of the
+            // Gram matrix G_k of column k's V factors (formed once per column)
+            std::vector<GemmProb> gp;
+            for (int k = 0; k < j; ++k) {
+                const int rjk = r_of(j, k);
+                if (rjk <= 0) continue;
+                const int S = gram_n[k];
+                const double *G = gram[k].as<double>();
+                for (int i = j; i < nt; ++i) {
+                    const int rik = r_of(i, k);
+                    if (rik <= 0) continue;
+                    GemmProb b{};
+                    b.A = Uslot(M, i, k); b.lda = nb; b.m = tile_rows(n, nb, i); b.k = rik;
+                    b.B = G + (int64_t)gram_off[k][j] * S + gram_off[k][i]; b.ldb = S; b.n = rjk;
+                    b.C = Pj + (int64_t)off[k] * Mp + (int64_t)(i - j) * nb; b.ldc = (int)Mp;
+                    gp.push_back(b);
+                    stats->flops += 2.0 * b.m * rik * rjk;
+                }
             }
-            gemm_batched(ctx, st, true, false, gw, 1.0, 0.0);
             gemm_batched(ctx, st, false, false, gp, 1.0, 0.0);
+            dmark(dm_main, st, kDetBuildP);
         }
         if (solve && Rj > 0) {
-            // y_j -= Q_j c, c_k = V_jk' y_k (the y_k, k < j, are final)
+            // y_j -= Q_j c, c_k = V_jk' y_k: a slice of column k's V' y_k
             DevBuf cb((size_t)Rj * sizeof(double), st);
-            std::vector<GemmProb> gc;
+            std::vector<CopyDesc> cc;
             for (int k = 0; k < j; ++k) {
                 int r = r_of(j, k);
                 if (r <= 0) continue;
-                GemmProb a{};
-                a.A = Vslot(M, j, k); a.lda = nb; a.m = r; a.k = tile_rows(n, nb, k);
-                a.B = y + (int64_t)k * nb; a.ldb = nb; a.n = 1;
-                a.C = cb.as<double>() + off[k]; a.ldc = r;
-                gc.push_back(a);
+                cc.push_back(CopyDesc{vty[k].as<double>() + gram_off[k][j], r, cb.as<double>() + off[k], r, r, 1});
             }
-            gemm_batched(ctx, st, true, false, gc, 1.0, 0.0);
+            copy_batched(ctx, st, cc);
             GemmProb g{};
             g.A = Qj; g.lda = nb; g.m = mj; g.k = Rj;
             g.B = cb.as<double>(); g.ldb = Rj; g.n = 1;
             g.C = y + (int64_t)j * nb; g.ldc = nb;
             gemm_batched(ctx, st, false, false, std::vector<GemmProb>{g}, -1.0, 1.0);
+            dmark(dm_main, st, kDetBuildSolve);
         }
         mark();
         // --- panel: T_{:,j} = A_{:,j} - P_j Q_j'
@@ -200,10 +210,14 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 g.B2 = q2.as<float2>();
                 split_f2_batched(ctx, st, {SplitDesc{Pj, p2.as<float2>(), (int)Mp, (int)Mp, Rj},
                                            SplitDesc{Qj, q2.as<float2>(), nb, mj, Rj}});
+                dmark(dm_main, st, kDetSplit);
             }
             gemm_batched_matern(ctx, st, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df);
-            if (df && j + 1 < nt)
+            dmark(dm_main, st, kDetPanel);
+            if (df && j + 1 < nt) {
                 split_f2_batched(ctx, st, {SplitDesc{Tp + nb, Tp2 + nb, (int)Mp, (int)(Mp - nb), mj}});
+                dmark(dm_main, st, kDetSplit);
+            }
             stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
             stats->matern_entries += (double)rows_valid * mj;
             stats->panel_launches += 1;
@@ -244,9 +258,12 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
             aux_marks.push_back(ctx->prof_events[prof_used++]);
         }
+        dmark(dm_aux, ctx->aux, -1);
         potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
+        dmark(dm_aux, ctx->aux, kDetPotrf);
         set_identity(ctx->aux, Xinv, nb, mj);
         trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
+        dmark(dm_aux, ctx->aux, kDetInverse);
         if (ctx->profile) {
             profile_events(ctx, prof_used + 1);
             TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
@@ -274,9 +291,12 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         }
         std::vector<int> rk;
         long long bad = -1, nan = -1;
+        dmark(dm_main, st, kDetDiagCopy);
         if (!jobs.empty()) compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan, df);
         mark();
+        dmark(dm_main, st, kDetCompress);
         TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
+        dmark(dm_main, st, kDetJoin);
         long long sinfo = -1;
         int sc = status_fetch(ctx, st, &sinfo);  // syncs st, after the side stream's work
         if (sc) { *info = sinfo; throw make_error(sc, "TLR Cholesky: non-positive pivot at row %lld", sinfo); }
@@ -296,16 +316,21 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             stats->flops += 8.0 * m * k * (rk[q] + 8);  // sampling + projection GEMMs (approx.)
         }
         // --- V_ij <- L_jj^-1 V_ij as one batched GEMM into a scratch panel, then copied back
+        DevBuf vtmp;  // the packed V factors of column j, alive through the solve step
+        const double *vty_src = nullptr;
+        int vty_pending = 0;
         {
             std::vector<GemmProb> gt;
             std::vector<CopyDesc> cb;
             int64_t off_c = 0;
             for (int i = j + 1; i < nt; ++i) off_c += r_of(i, j);
-            DevBuf vtmp((size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(double), st);
+            vtmp.alloc((size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(double), st);
             off_c = 0;
+            gram_off[j].assign(nt, -1);
             for (int i = j + 1; i < nt; ++i) {
                 int r = r_of(i, j);
                 if (r <= 0) continue;
+                gram_off[j][i] = (int)off_c;
                 GemmProb g{};
                 g.A = Xinv; g.lda = nb; g.m = mj; g.k = mj;
                 g.B = Vslot(M, i, j); g.ldb = nb; g.n = r;
@@ -317,6 +342,31 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             }
             gemm_batched(ctx, st, false, false, gt, 1.0, 0.0);
             copy_batched(ctx, st, cb);
+            dmark(dm_main, st, kDetTrsm);
+            // G_j = V_j' V_j for the later columns' updates
+            const int S = (int)off_c;
+            gram_n[j] = S;
+            if (S > 0 && j + 1 < nt) {
+                gram[j].alloc((size_t)S * S * sizeof(double), st);
+                GemmProb g{};
+                g.A = vtmp.as<double>(); g.lda = nb; g.m = S; g.k = mj;
+                g.B = vtmp.as<double>(); g.ldb = nb; g.n = S;
+                g.C = gram[j].as<double>(); g.ldc = S;
+                DevBuf v2(df ? (size_t)nb * S * sizeof(float2) : 0, st);
+                if (df) {
+                    split_f2_batched(ctx, st, {SplitDesc{vtmp.as<double>(), v2.as<float2>(), nb, mj, S}});
+                    g.A2 = g.B2 = v2.as<float2>();
+                }
+                gemm_batched(ctx, st, true, false, std::vector<GemmProb>{g}, 1.0, 0.0, df);
+                stats->flops += 2.0 * S * S * mj;
+                dmark(dm_main, st, kDetGram);
+            }
+            if (solve && S > 0 && j + 1 < nt) {
+                // V_j' y_j once y_j is final (after the solve step below)
+                vty[j].alloc((size_t)S * sizeof(double), st);
+                vty_src = vtmp.as<double>();
+                vty_pending = S;
+            }
         }
         if (solve) {
             double *yj = y + (int64_t)j * nb;
@@ -328,8 +378,27 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             TLR_CUDA_TRY(cudaMemcpyAsync(yj, ytmp.as<double>(), mj * sizeof(double), cudaMemcpyDeviceToDevice, st));
             diag_logsum(st, Dj, nb, mj, acc, ctx->d_status);
             sumsq(st, yj, mj, acc + 1);
+            if (vty_pending > 0) {
+                GemmProb v{};
+                v.A = vty_src; v.lda = nb; v.m = vty_pending; v.k = mj;
+                v.B = yj; v.ldb = nb; v.n = 1;
+                v.C = vty[j].as<double>(); v.ldc = vty_pending;
+                gemm_batched(ctx, st, true, false, std::vector<GemmProb>{v}, 1.0, 0.0);
+            }
+            dmark(dm_main, st, kDetSolve);
         }
         mark();
+    }
+    if (ctx->profile) {
+        for (std::vector<DMark> *v : {&dm_main, &dm_aux})
+            if (!v->empty()) TLR_CUDA_TRY(cudaEventSynchronize(v->back().e));
+        for (std::vector<DMark> *v : {&dm_main, &dm_aux})
+            for (size_t k = 1; k < v->size(); ++k) {
+                if ((*v)[k].idx < 0) continue;
+                float ms = 0.f;
+                TLR_CUDA_TRY(cudaEventElapsedTime(&ms, (*v)[k - 1].e, (*v)[k].e));
+                stats->detail_ms[(*v)[k].idx] += ms;
+            }
     }
     upload_ranks(M, st);
     if (ctx->profile) {

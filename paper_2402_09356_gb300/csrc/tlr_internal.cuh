@@ -19,6 +19,25 @@ void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &des
 
 constexpr int kStages = 5;
 
+// finer profiling buckets of the factorisation (device ms, summed over columns)
+enum DetailBucket {
+    kDetBuildCopy,   // Q_j gather, P_j clear
+    kDetBuildW,      // unused (W_ik now comes from the Gram matrices)
+    kDetBuildP,      // P block (i, k) = U_ik W_ik
+    kDetBuildSolve,  // fused forward-solve update of y_j
+    kDetSplit,       // paired-FP32 operand copies
+    kDetPanel,       // panel update GEMM with Matern generation
+    kDetDiagCopy,    // diagonal tile copy and fork to the side stream
+    kDetCompress,    // off-diagonal compression
+    kDetJoin,        // waiting for the side stream (POTRF + inverse)
+    kDetTrsm,        // V_ij <- L_jj^-1 V_ij
+    kDetSolve,       // y_j <- L_jj^-1 y_j, log-determinant and |y|^2 terms, V_j' y_j
+    kDetGram,        // G_j = V_j' V_j
+    kDetPotrf,       // side stream: dense POTRF of the diagonal tile
+    kDetInverse,     // side stream: L_jj^-1
+    kDetail
+};
+
 enum class FactorMode {
     Matern,  // tiles generated from the Matern kernel inside the panel update (likelihood path)
     Tlr      // tiles taken from the compressed input held in the matrix (tlr_potrf)
@@ -33,6 +52,7 @@ struct FactorStats {
     // device time per stage (when ctx->profile): low-rank operand build, panel
     // update GEMM, diagonal POTRF, compression, TRSM of V
     float stage_ms[kStages] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float detail_ms[kDetail] = {};
 };
 
 void profile_events(tlr_ctx *ctx, int count);
