@@ -409,35 +409,40 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
     return y;
 }
 
+// Squared norm of the first sdot entries of x (lanes stride 32; warp-uniform result).
+template <class T>
+__device__ __forceinline__ T col_norm2(const T *x, int sdot, int lane) {
+    T a = 0;
+    for (int r = lane; r < sdot; r += 32) a = fma(x[r], x[r], a);
+    return warp_sum(a);
+}
+
 // Rotate columns x and y so that their first sdot entries become orthogonal;
 // the rotation is applied to all srot entries (srot > sdot carries the
-// accumulated rotations along).  Returns whether a rotation was applied.
-// Pairs with |x'y| <= tol |x| |y| (tol2 = tol^2) are left alone.
+// accumulated rotations along).  nx, ny hold the squared norms of the two
+// columns (first sdot entries) and are updated, so that a pair costs one dot
+// product instead of three (the update is c^2 (a -+ 2 t g + t^2 b), exact for
+// any t; a norm is recomputed when that formula cancels more than three
+// digits).  Returns whether a rotation was applied.  Pairs with
+// |x'y| <= tol |x| |y| (tol2 = tol^2) are left alone.
 // FP64: the rotation angle only steers convergence, so t = tan(angle) comes
 // from approximations; c = 1/sqrt(1 + t^2) is refined by two Newton steps for
 // the reciprocal square root, y <- y (3 - x y^2) / 2, so that (c, c t) is
 // orthogonal to working precision and the singular values are preserved.
 template <class T>
-__device__ __forceinline__ bool jacobi_rotate(T *x, T *y, int sdot, int srot, int lane, T tol2) {
-    T al = 0, be = 0, ga = 0;
-    for (int r = lane; r < sdot; r += 32) {
-        const T a = x[r], b = y[r];
-        al = fma(a, a, al);
-        be = fma(b, b, be);
-        ga = fma(a, b, ga);
-    }
-    al = warp_sum(al);
-    be = warp_sum(be);
+__device__ __forceinline__ bool jacobi_rotate(T *x, T *y, T *nx, T *ny, int sdot, int srot, int lane, T tol2) {
+    const T al = *nx, be = *ny;
+    T ga = 0;
+    for (int r = lane; r < sdot; r += 32) ga = fma(x[r], y[r], ga);
     ga = warp_sum(ga);
     if (ga == T(0) || ga * ga <= tol2 * (al * be)) return false;
-    T c, sn;
+    T c, sn, t;
     if constexpr (std::is_same<T, double>::value) {
         double rg = rcp_approx(2.0 * ga);
         rg = rg * fma(-2.0 * ga, rg, 2.0);
         const double zeta = (be - al) * rg, az = fabs(zeta);
         const double q = fma(zeta, zeta, 1.0);
-        const double t =
-            copysign(az < 1e150 ? rcp_approx(az + q * rsqrt_approx(q)) : 0.5 * rcp_approx(az), zeta);
+        t = copysign(az < 1e150 ? rcp_approx(az + q * rsqrt_approx(q)) : 0.5 * rcp_approx(az), zeta);
         const double u = fma(t, t, 1.0);
         c = rsqrt_approx(u);
         c = c * fma(-0.5 * u * c, c, 1.5);
@@ -445,7 +450,7 @@ __device__ __forceinline__ bool jacobi_rotate(T *x, T *y, int sdot, int srot, in
         sn = c * t;
     } else {
         const float zeta = (be - al) / (2.0f * ga);
-        const float t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+        t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
         if (t == 0.0f) return false;  // below FP32 resolution
         c = rsqrtf(fmaf(t, t, 1.0f));
         sn = c * t;
@@ -454,6 +459,14 @@ __device__ __forceinline__ bool jacobi_rotate(T *x, T *y, int sdot, int srot, in
         const T a = x[r], b = y[r];
         x[r] = fma(c, a, -sn * b);
         y[r] = fma(sn, a, c * b);
+    }
+    const T c2 = c * c, tg = T(2) * t * ga, tt = t * t;
+    T al2 = c2 * (al - tg + tt * be), be2 = c2 * (be + tg + tt * al);
+    if (!(al2 > T(1e-3) * c2 * (al + tt * be))) al2 = col_norm2(x, sdot, lane);
+    if (!(be2 > T(1e-3) * c2 * (be + tt * al))) be2 = col_norm2(y, sdot, lane);
+    if (lane == 0) {
+        *nx = al2;
+        *ny = be2;
     }
     return true;
 }
@@ -482,11 +495,12 @@ __device__ __forceinline__ int pos_of(int blk, int g, int nblk) {
 
 // Rotate all pairs between the two b-column blocks X (global block bx) and Y
 // (by), and, if `inner`, the pairs within each of them.  Columns are srot
-// apart within a block; virtual columns (global index >= s) are zero and
-// skipped.  Returns whether any rotation was applied by this thread's warp.
+// apart within a block; NX, NY hold their squared norms.  Virtual columns
+// (global index >= s) are zero and skipped.  Returns whether any rotation was
+// applied by this thread's warp.
 template <class T>
-__device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, int bx, int by, int b, int s, int srot, bool inner,
-                                                   int lane, int warp, T tol2) {
+__device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, T *NX, T *NY, int bx, int by, int b, int s, int srot,
+                                                   bool inner, int lane, int warp, T tol2) {
     bool rot = false;
     if (inner) {
         const int bp = b + (b & 1);
@@ -498,7 +512,9 @@ __device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, int bx, int by, i
                 const int blk = slot ? by : bx;
                 if (a >= b || c2 >= b || blk * b + max(a, c2) >= s) continue;
                 T *base = slot ? Y : X;
-                rot |= jacobi_rotate(base + min(a, c2) * srot, base + max(a, c2) * srot, s, srot, lane, tol2);
+                T *nrm = slot ? NY : NX;
+                const int lo = min(a, c2), hi = max(a, c2);
+                rot |= jacobi_rotate(base + lo * srot, base + hi * srot, nrm + lo, nrm + hi, s, srot, lane, tol2);
             }
             __syncthreads();
         }
@@ -509,36 +525,50 @@ __device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, int bx, int by, i
             const int gx = bx * b + i, gy = by * b + jy;
             if (gx >= s || gy >= s) continue;
             // the lower global index is the first column of the pair
-            if (gx < gy) rot |= jacobi_rotate(X + i * srot, Y + jy * srot, s, srot, lane, tol2);
-            else rot |= jacobi_rotate(Y + jy * srot, X + i * srot, s, srot, lane, tol2);
+            if (gx < gy) rot |= jacobi_rotate(X + i * srot, Y + jy * srot, NX + i, NY + jy, s, srot, lane, tol2);
+            else rot |= jacobi_rotate(Y + jy * srot, X + i * srot, NY + jy, NX + i, s, srot, lane, tol2);
         }
         __syncthreads();
     }
     return rot;
 }
 
+// Squared norms of the 2b columns of a buffer (first s entries of each).
+template <class T>
+__device__ __forceinline__ void block_norms(const T *cols, T *nrm, int b, int s, int srot, int lane, int warp) {
+    for (int q = warp; q < 2 * b; q += kNw) {
+        const T v = col_norm2(cols + q * srot, s, lane);
+        if (lane == 0) nrm[q] = v;
+    }
+    __syncthreads();
+}
+
 // Sweeps of the shared-memory block Jacobi: each CTA holds two blocks of b
-// columns (srot elements each) in buf(cur); after each block round the CTAs
-// pull their next blocks over DSMEM into buf(cur ^ 1).  Runs until a sweep
+// columns (srot elements each) and their squared norms in buffer cur
+// (buf0 + cur * stride: slot 0, slot 1, then 2b norms); after each block
+// round the CTAs pull their next blocks over DSMEM into the other buffer.
+// Norms are recomputed at the start of every sweep.  Runs until a sweep
 // rotates nothing or max_sweeps; g (global round) and cur are updated so
-// that buf(cur) holds the blocks of positions (rank, 2C - 1 - rank) at round
-// g on return.  Returns the number of sweeps run.
+// that buffer cur holds the blocks of positions (rank, 2C - 1 - rank) at
+// round g on return.  Returns the number of sweeps run.
 template <int kCl, class T>
-__device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, T *buf1, int b, int s, int srot, int max_sweeps, int &g,
-                             int &cur, int *s_flag) {
+__device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, int stride, int b, int s, int srot, int max_sweeps,
+                             int &g, int &cur, int *s_flag) {
     constexpr int nblk = 2 * kCl;
     const int rank = (int)cl.block_rank(), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int px = rank, py = nblk - 1 - rank, bs = b * srot;
     const T tol2 = jacobi_tol2<T>(s);
-    auto buf = [&](int k) { return k ? buf1 : buf0; };
+    auto buf = [&](int k) { return buf0 + k * stride; };
     int nsweep = 0;
     bool done = false;
     for (int sweep = 0; sweep < max_sweeps && !done; ++sweep, ++nsweep) {
         if (tid == 0) s_flag[sweep & 1] = 0;
-        __syncthreads();
+        block_norms(buf(cur), buf(cur) + 2 * bs, b, s, srot, lane, warp);
         for (int round = 0; round < nblk - 1; ++round, ++g) {
             const int bx = block_at(px, g, nblk), by = block_at(py, g, nblk);
-            if (jacobi_block_pairs<T>(buf(cur), buf(cur) + bs, bx, by, b, s, srot, round == 0, lane, warp, tol2) &&
+            T *B = buf(cur);
+            if (jacobi_block_pairs<T>(B, B + bs, B + 2 * bs, B + 2 * bs + b, bx, by, b, s, srot, round == 0, lane,
+                                      warp, tol2) &&
                 lane == 0)
                 s_flag[sweep & 1] = 1;
             cl.sync();
@@ -551,14 +581,15 @@ __device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, T *buf1, int b, int
                     break;
                 }
             }
-            // pull the blocks of round g + 1 from their holders in round g
+            // pull the blocks (and norms) of round g + 1 from their holders in round g
             for (int slot = 0; slot < 2; ++slot) {
                 const int blk = block_at(slot ? py : px, g + 1, nblk);
                 const int p = pos_of(blk, g, nblk);
                 const int h = p < kCl ? p : nblk - 1 - p, hs = p < kCl ? 0 : 1;
-                const T *src = cl.map_shared_rank(buf(cur) + hs * bs, h);
-                T *dst = buf(cur ^ 1) + slot * bs;
-                for (int e = tid; e < bs; e += kQrThreads) dst[e] = src[e];
+                const T *src = cl.map_shared_rank(buf(cur), h);
+                T *dst = buf(cur ^ 1);
+                for (int e = tid; e < bs; e += kQrThreads) dst[slot * bs + e] = src[hs * bs + e];
+                for (int e = tid; e < b; e += kQrThreads) dst[2 * bs + slot * b + e] = src[2 * bs + hs * b + e];
             }
             cur ^= 1;
             __syncthreads();
@@ -617,8 +648,9 @@ constexpr int kMaxSweeps32 = 12;
 // sigma_{r+1}(M) (1 + O(|E|)) (relative perturbation theory; Eisenstat and
 // Ipsen 1995).  The FP32 sweeps do the bulk of the rotations on a pipe 64
 // times faster than FP64; the FP64 phase then converges in a few sweeps.
-// Shared memory: two buffers of two b x s blocks (FP64 layout; the FP32
-// phase stores b x 2s floats in the same bytes), 2b local norms, s norms.
+// Shared memory: two buffers of two b x s blocks and 2b squared norms (FP64
+// layout; the FP32 phase stores b x 2s floats per block in the same bytes),
+// 2b local norms, s gathered norms.
 template <int kCl>
 __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs, double tau) {
     cg::cluster_group cl = cg::this_cluster();
@@ -629,11 +661,12 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nblk = 2 * kCl;
     const int b = (s + nblk - 1) / nblk, bs = b * s;
-    double *nrm_loc = sm + 4 * bs, *all_nrm = nrm_loc + 2 * b;
+    const int stride = 2 * bs + 2 * b;  // one buffer: two blocks, 2b norms (FP64 layout)
+    double *nrm_loc = sm + 2 * stride, *all_nrm = nrm_loc + 2 * b;
     const int px = rank, py = nblk - 1 - rank;
-    // A. FP32 phase
-    float *f0 = reinterpret_cast<float *>(sm), *f1 = reinterpret_cast<float *>(sm + 2 * bs);
-    const int s2 = 2 * s, bsf = b * s2;
+    // A. FP32 phase (the same buffers hold b x 2s floats per block)
+    float *f0 = reinterpret_cast<float *>(sm);
+    const int s2 = 2 * s, bsf = b * s2, stride_f = 2 * bsf + 2 * b;
     for (int slot = 0; slot < 2; ++slot) {
         const int blk = block_at(slot ? py : px, 0, nblk);
         float *dst = f0 + slot * bsf;
@@ -646,10 +679,10 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     }
     __syncthreads();
     int g = 0, cur = 0;
-    const int sw32 = jacobi_sweeps<kCl, float>(cl, f0, f1, b, s, s2, kMaxSweeps32, g, cur, s_flag);
+    const int sw32 = jacobi_sweeps<kCl, float>(cl, f0, stride_f, b, s, s2, kMaxSweeps32, g, cur, s_flag);
     // B. M1 = M J for the held columns, 8 at a time; rows i = tid, tid + 256
     {
-        const float *F = cur ? f1 : f0;
+        const float *F = f0 + cur * stride_f;
         const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
         for (int q0 = 0; q0 < 2 * b; q0 += 8) {
             double acc[8][2];
@@ -689,8 +722,8 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     }
     __syncthreads();
     cur = 0;
-    const int sw64 = jacobi_sweeps<kCl, double>(cl, sm, sm + 2 * bs, b, s, s, kMaxSweeps, g, cur, s_flag);
-    double *D = cur ? sm + 2 * bs : sm;
+    const int sw64 = jacobi_sweeps<kCl, double>(cl, sm, stride, b, s, s, kMaxSweeps, g, cur, s_flag);
+    double *D = sm + cur * stride;
     const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
     for (int q = warp; q < 2 * b; q += kNw) {
         const double *col = D + q * s;
@@ -713,12 +746,12 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
 
 static size_t jacobi_sm_bytes(int s, int csize) {
     const int b = (s + 2 * csize - 1) / (2 * csize);
-    return ((size_t)4 * b * s + 2 * b + s) * sizeof(double);
+    return ((size_t)4 * b * s + 6 * b + s) * sizeof(double);
 }
 
 // Block Jacobi with the matrix in global memory (L2): the two blocks of a
 // round are staged in shared memory and written back before the cluster
-// barrier.  Shared memory: two b x s blocks, then s norms.
+// barrier.  Shared memory: two b x s blocks, their 2b squared norms, s norms.
 template <int kCl>
 __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restrict__ jobs, double tau) {
     cg::cluster_group cl = cg::this_cluster();
@@ -729,7 +762,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
     const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nblk = 2 * kCl;
     const int b = (s + nblk - 1) / nblk, bs = b * s;
-    double *Ab = sm, *all_nrm = sm + 2 * bs;
+    double *Ab = sm, *Nb = sm + 2 * bs, *all_nrm = Nb + 2 * b;
     double *A = J.work;
     for (int e = rank * kQrThreads + tid; e < s * s; e += kCl * kQrThreads) __stcg(A + e, J.Rt[e]);
     cl.sync();
@@ -746,7 +779,8 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
                 Ab[e] = u < s ? __ldcg(A + (int64_t)u * s + e % s) : 0.0;
             }
             __syncthreads();
-            if (jacobi_block_pairs<double>(Ab, Ab + bs, bx, by, b, s, s, round == 0, lane, warp,
+            block_norms(Ab, Nb, b, s, s, lane, warp);
+            if (jacobi_block_pairs<double>(Ab, Ab + bs, Nb, Nb + b, bx, by, b, s, s, round == 0, lane, warp,
                                            jacobi_tol2<double>(s)) &&
                 lane == 0)
                 s_flag[sweep & 1] = 1;
@@ -784,7 +818,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
 
 static size_t jacobi_gm_bytes(int s, int csize) {
     const int b = (s + 2 * csize - 1) / (2 * csize);
-    return ((size_t)2 * b * s + s) * sizeof(double);
+    return ((size_t)2 * b * s + 2 * b + s) * sizeof(double);
 }
 
 // ---------------------------------------------------------------------------
