@@ -1054,7 +1054,9 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
 }
 
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
-                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df) {
+                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df,
+                    const std::function<void()> &overlap) {
+    bool overlapped = false;
     ensure_omega(ctx, st);
     // profiling marks between the sub-steps of each adaptive round
     std::vector<cudaEvent_t> ev;
@@ -1181,6 +1183,10 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         // decisions on the host
         std::vector<int> h_rank(3 * np);
         TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 3 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (overlap && !overlapped) {
+            overlapped = true;
+            overlap();
+        }
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
         if (st != ctx->aux) stage_reset_main(ctx);
         cmark();
@@ -1238,6 +1244,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         // the workspace is released stream-ordered after these GEMMs
         pending.swap(next);
     }
+    if (overlap && !overlapped) overlap();  // nothing was compressed
 }
 
 }  // namespace tlr

@@ -1,6 +1,7 @@
 // Batched FP64 GEMM launchers and the descriptor staging buffers of a context.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "gemm.cuh"
 
@@ -50,12 +51,44 @@ static void launch_shape(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const s
     TLR_CHECK_LAUNCH();
 }
 
+static void launch_gemv(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                        double alpha, const EpiLinear &epi) {
+    if (probs.empty()) return;
+    std::vector<int> off(probs.size() + 1, 0);
+    for (size_t b = 0; b < probs.size(); ++b)
+        off[b + 1] = off[b] + (probs[b].m > 0 ? (int)ceil_div(probs[b].m, kGemvRows) : 0);
+    int total = off.back();
+    if (total == 0) return;
+    auto *dp = (const GemmProb *)stage_push(ctx, probs.data(), probs.size() * sizeof(GemmProb), s);
+    auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
+    int np = (int)probs.size();
+    if (ta && tb) launch(k_gemv<true, true>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else if (ta) launch(k_gemv<true, false>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else if (tb) launch(k_gemv<false, true>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    else launch(k_gemv<false, false>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+    TLR_CHECK_LAUNCH();
+}
+
 // Split a batch by output shape: problems with at most 32 rows and/or 32
-// columns go to the thin tile shapes, whose padding stays small.
+// columns go to the thin tile shapes, whose padding stays small; FP64
+// matrix-vector products (n = 1) go to the GEMV kernel.
 template <class Epi>
 static void launch_gemm(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
                         double alpha, const Epi &epi, bool df) {
     std::vector<GemmProb> cls[4];  // 64x64, 64x32, 32x64, 32x32
+    if constexpr (std::is_same<Epi, EpiLinear>::value) {
+        if (!df) {
+            std::vector<GemmProb> vec, rest;
+            for (const GemmProb &p : probs) (p.n == 1 ? vec : rest).push_back(p);
+            launch_gemv(ctx, s, ta, tb, vec, alpha, epi);
+            for (const GemmProb &p : rest) cls[(p.m <= 32 ? 2 : 0) + (p.n <= 32 ? 1 : 0)].push_back(p);
+            launch_shape<64, 64>(ctx, s, ta, tb, cls[0], alpha, epi, df);
+            launch_shape<64, 32>(ctx, s, ta, tb, cls[1], alpha, epi, df);
+            launch_shape<32, 64>(ctx, s, ta, tb, cls[2], alpha, epi, df);
+            launch_shape<32, 32>(ctx, s, ta, tb, cls[3], alpha, epi, df);
+            return;
+        }
+    }
     for (const GemmProb &p : probs) cls[(p.m <= 32 ? 2 : 0) + (p.n <= 32 ? 1 : 0)].push_back(p);
     launch_shape<64, 64>(ctx, s, ta, tb, cls[0], alpha, epi, df);
     launch_shape<64, 32>(ctx, s, ta, tb, cls[1], alpha, epi, df);
@@ -80,24 +113,27 @@ void split_f2(cudaStream_t s, const double *src, int ld, int m, int n, float2 *d
     TLR_CHECK_LAUNCH();
 }
 
+// blockIdx.y: descriptor; blockIdx.x strides over its columns, threads over rows.
 __global__ void k_split_f2_batched(const SplitDesc *__restrict__ descs) {
     const SplitDesc D = descs[blockIdx.y];
-    const int64_t count = (int64_t)D.m * D.n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % D.m, j = e / D.m;
-        const double v = D.src[j * D.ld + i];
-        const float h = __double2float_rn(v);
-        D.dst[j * D.ld + i] = make_float2(h, __double2float_rn(v - (double)h));
+    for (int j = blockIdx.x; j < D.n; j += gridDim.x) {
+        const double *src = D.src + (int64_t)j * D.ld;
+        float2 *dst = D.dst + (int64_t)j * D.ld;
+        for (int i = threadIdx.x; i < D.m; i += blockDim.x) {
+            const double v = src[i];
+            const float h = __double2float_rn(v);
+            dst[i] = make_float2(h, __double2float_rn(v - (double)h));
+        }
     }
 }
 
 void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc> &descs) {
     if (descs.empty()) return;
-    int64_t most = 0;
-    for (const SplitDesc &d : descs) most = std::max(most, (int64_t)d.m * d.n);
+    int most = 0;
+    for (const SplitDesc &d : descs) most = std::max(most, (d.m > 0) ? d.n : 0);
     if (most == 0) return;
     auto *dd = (const SplitDesc *)stage_push(ctx, descs.data(), descs.size() * sizeof(SplitDesc), s);
-    dim3 grid((unsigned)std::min<int64_t>(ceil_div(most, 256), 2048), (unsigned)descs.size());
+    dim3 grid((unsigned)std::min(most, 1024), (unsigned)descs.size());
     launch(k_split_f2_batched, grid, 256, 0, s, dd);
     TLR_CHECK_LAUNCH();
 }

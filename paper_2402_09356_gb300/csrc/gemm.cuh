@@ -225,6 +225,46 @@ k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, 
     }
 }
 
+// Matrix-vector products (n = 1) with the linear epilogue:
+//   TA:  one warp per output, lanes over k (the row of A' is contiguous);
+//   !TA: one thread per output row, k in sequence (coalesced across threads).
+// blockIdx.x runs over the concatenated per-problem tiles of kGemvRows outputs.
+constexpr int kGemvRows = 256;
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(kGemmThreads)
+k_gemv(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob, double alpha, EpiLinear epi) {
+    int lo = 0, hi = nprob - 1, t = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const GemmProb p = probs[lo];
+    const int r0 = (t - tile_off[lo]) * kGemvRows;
+    auto bk = [&](int k) { return TB ? p.B[(int64_t)k * p.ldb] : p.B[k]; };
+    if (TA) {
+        const int lane = threadIdx.x & 31;
+        for (int r = r0 + (threadIdx.x >> 5); r < min(p.m, r0 + kGemvRows); r += kGemmThreads / 32) {
+            const double *a = p.A + (int64_t)r * p.lda;
+            double d = 0.0;
+            for (int k = lane; k < p.k; k += 32) d = fma(a[k], bk(k), d);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
+            if (lane == 0) p.C[r] = epi(p, r, 0, alpha * d, p.C + r);
+        }
+    } else {
+        const int r = r0 + threadIdx.x;
+        if (r >= p.m) return;
+        double d0 = 0.0, d1 = 0.0;
+        int k = 0;
+        for (; k + 1 < p.k; k += 2) {
+            d0 = fma(p.A[(int64_t)k * p.lda + r], bk(k), d0);
+            d1 = fma(p.A[(int64_t)(k + 1) * p.lda + r], bk(k + 1), d1);
+        }
+        if (k < p.k) d0 = fma(p.A[(int64_t)k * p.lda + r], bk(k), d0);
+        p.C[r] = epi(p, r, 0, alpha * (d0 + d1), p.C + r);
+    }
+}
+
 // Host launcher: uploads the descriptors through the context's staging
 // buffers and launches one kernel for the whole batch.
 // dst[j * ld + i] = (hi, lo) of src[j * ld + i] for an m x n column-major block.

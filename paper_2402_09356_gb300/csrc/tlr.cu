@@ -26,11 +26,13 @@
 
 namespace tlr {
 
+// blockIdx.y: descriptor; blockIdx.x strides over its columns, threads over rows.
 __global__ void k_copy_batched(const CopyDesc *__restrict__ d) {
-    const CopyDesc c = d[blockIdx.x];
-    for (int64_t e = threadIdx.x; e < (int64_t)c.m * c.n; e += blockDim.x) {
-        int r = (int)(e % c.m), col = (int)(e / c.m);
-        c.dst[(int64_t)col * c.ldd + r] = c.src ? c.src[(int64_t)col * c.lds + r] : 0.0;
+    const CopyDesc c = d[blockIdx.y];
+    for (int col = blockIdx.x; col < c.n; col += gridDim.x) {
+        const double *src = c.src ? c.src + (int64_t)col * c.lds : nullptr;
+        double *dst = c.dst + (int64_t)col * c.ldd;
+        for (int r = threadIdx.x; r < c.m; r += blockDim.x) dst[r] = src ? src[r] : 0.0;
     }
 }
 
@@ -49,8 +51,10 @@ void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &des
     for (const CopyDesc &c : descs)
         if (c.m > 0 && c.n > 0) act.push_back(c);
     if (act.empty()) return;
+    int most = 0;
+    for (const CopyDesc &c : act) most = std::max(most, c.n);
     auto *dd = (const CopyDesc *)stage_push(ctx, act.data(), act.size() * sizeof(CopyDesc), s);
-    launch(k_copy_batched, (unsigned)act.size(), 256, 0, s, dd);
+    launch(k_copy_batched, dim3((unsigned)std::min(most, 128), (unsigned)act.size()), 256, 0, s, dd);
     TLR_CHECK_LAUNCH();
 }
 
@@ -253,23 +257,28 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         copy_batched(ctx, st, {CopyDesc{Tp, (int)Mp, Dj, nb, mj, mj}});
         TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
         TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-        if (ctx->profile) {
-            profile_events(ctx, prof_used + 1);
-            TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
-            aux_marks.push_back(ctx->prof_events[prof_used++]);
-        }
-        dmark(dm_aux, ctx->aux, -1);
-        potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
-        dmark(dm_aux, ctx->aux, kDetPotrf);
-        set_identity(ctx->aux, Xinv, nb, mj);
-        trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
-        dmark(dm_aux, ctx->aux, kDetInverse);
-        if (ctx->profile) {
-            profile_events(ctx, prof_used + 1);
-            TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
-            aux_marks.push_back(ctx->prof_events[prof_used++]);
-        }
-        TLR_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
+        // the side stream's launches go first: its chain of small dependent
+        // kernels then starts before the compression fills the GPU
+        auto enqueue_aux = [&]() {
+            if (ctx->profile) {
+                profile_events(ctx, prof_used + 1);
+                TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
+                aux_marks.push_back(ctx->prof_events[prof_used++]);
+            }
+            dmark(dm_aux, ctx->aux, -1);
+            potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
+            dmark(dm_aux, ctx->aux, kDetPotrf);
+            set_identity(ctx->aux, Xinv, nb, mj);
+            trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
+            dmark(dm_aux, ctx->aux, kDetInverse);
+            if (ctx->profile) {
+                profile_events(ctx, prof_used + 1);
+                TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
+                aux_marks.push_back(ctx->prof_events[prof_used++]);
+            }
+            TLR_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
+        };
+        enqueue_aux();
         stats->flops += (double)mj * mj * mj / 3.0 + (double)mj * mj * mj / 3.0;
         mark();
         // --- compress T_ij, i > j (main stream, concurrently with the above)
@@ -340,7 +349,20 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 off_c += r;
                 stats->flops += 2.0 * mj * mj * r;
             }
-            gemm_batched(ctx, st, false, false, gt, 1.0, 0.0);
+            DevBuf x2(df && !gt.empty() ? (size_t)nb * nb * sizeof(float2) : 0, st);
+            DevBuf v2(df && !gt.empty() ? (size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(float2) : 0, st);
+            if (df && !gt.empty()) {
+                // paired-FP32 operands: X, and the V factors packed like the output
+                std::vector<SplitDesc> sd{SplitDesc{Xinv, x2.as<float2>(), nb, mj, mj}};
+                for (GemmProb &g : gt) {
+                    const int64_t o = g.C - vtmp.as<double>();
+                    sd.push_back(SplitDesc{g.B, v2.as<float2>() + o, nb, mj, g.n});
+                    g.A2 = x2.as<float2>();
+                    g.B2 = v2.as<float2>() + o;
+                }
+                split_f2_batched(ctx, st, sd);
+            }
+            gemm_batched(ctx, st, false, false, gt, 1.0, 0.0, df);
             copy_batched(ctx, st, cb);
             dmark(dm_main, st, kDetTrsm);
             // G_j = V_j' V_j for the later columns' updates
