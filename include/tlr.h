@@ -270,12 +270,14 @@ int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops,
 int tlr_stage_times(tlr_ctx *ctx, double *ms);
 
 /* Finer device times (ms) of the last profiled tlr_loglik factorisation,
- * summed over columns, written to ms[0..count-1]: operand gather, W = V'V,
- * P = U W, forward-solve update, paired-FP32 operand copies, panel update,
- * diagonal copy, compression, wait for the side stream, V <- L^-1 V, solve
- * and log-determinant terms, Gram matrix V' V of the finished column, then on
- * the side stream: POTRF, L^-1.
- * Returns the number of values written (at most 14), or TLR_ERR_ARG (< 0). */
+ * summed over columns, written to ms[0..count-1].  Main stream: operands of a
+ * main-stream panel update, look-ahead correction by the previous column,
+ * wait for the look-ahead stream, forward-solve update, paired-FP32 copy of
+ * the panel, main-stream panel GEMM, diagonal copy, compression, wait for the
+ * side stream, V <- L^-1 V, solve and log-determinant terms, Gram matrix V'V
+ * of the finished column.  Side stream: POTRF, L^-1.  Look-ahead stream:
+ * operands and panel GEMM of the next column's update.
+ * Returns the number of values written (at most 16), or TLR_ERR_ARG (< 0). */
 int tlr_detail_times(tlr_ctx *ctx, double *ms, int count);
 
 /* Device time (ms) of the compression sub-steps of the last profiled

@@ -399,8 +399,8 @@ def tlr_compress_times(ctx: Context) -> dict:
     return {k: a[i] for i, k in enumerate(COMPRESS_STEPS)}
 
 
-DETAILS = ("build_copy", "build_w", "build_p", "build_solve", "split", "panel", "diag_copy", "compress",
-           "join_wait", "trsm", "solve", "gram", "potrf", "inverse")
+DETAILS = ("build", "correct", "ahead_wait", "solve_update", "split", "panel", "diag_copy", "compress", "join_wait",
+           "trsm", "solve", "gram", "potrf", "inverse", "ahead_build", "ahead_panel")
 
 
 def tlr_detail_times(ctx: Context) -> dict:

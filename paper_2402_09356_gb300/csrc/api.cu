@@ -89,8 +89,16 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
         TLR_CUDA_TRY(cudaMalloc(&ctx->d_status, sizeof(DevStatus)));
         TLR_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(DevStatus)));
         TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_status, sizeof(DevStatus), cudaHostAllocDefault));
-        TLR_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
-        for (cudaStream_t &c : ctx->cls_stream) TLR_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+        // the critical-path streams (diagonal POTRF, compression classes) get the
+        // highest priority, so that the look-ahead panel GEMM fills in behind them
+        int prio_lo = 0, prio_hi = 0;
+        TLR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_hi));
+        TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->la, cudaStreamNonBlocking, prio_lo));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_la_fork, cudaEventDisableTiming));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_la_join, cudaEventDisableTiming));
+        for (cudaStream_t &c : ctx->cls_stream)
+            TLR_CUDA_TRY(cudaStreamCreateWithPriority(&c, cudaStreamNonBlocking, prio_hi));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->cls_fork, cudaEventDisableTiming));
         for (cudaEvent_t &e : ctx->cls_join) TLR_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreate(&ctx->ev_a));
@@ -119,6 +127,9 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->la) cudaStreamDestroy(ctx->la);
+    for (cudaEvent_t e : {ctx->ev_la_fork, ctx->ev_la_join})
+        if (e) cudaEventDestroy(e);
     for (cudaStream_t c : ctx->cls_stream)
         if (c) cudaStreamDestroy(c);
     if (ctx->cls_fork) cudaEventDestroy(ctx->cls_fork);

@@ -112,15 +112,17 @@ struct tlr_ctx {
     std::string err;
     tlr::DevStatus *d_status = nullptr;   // device status word
     tlr::DevStatus *h_status = nullptr;   // pinned host mirror
-    cudaStream_t aux = nullptr;           // second stream for concurrent tile work
+    cudaStream_t aux = nullptr;           // second stream for concurrent tile work (high priority)
+    cudaStream_t la = nullptr;            // look-ahead stream: the next column's panel update
+    cudaEvent_t ev_la_fork = nullptr, ev_la_join = nullptr;
     // compression: one stream per launch class (cluster size), forked from and
     // joined to the calling stream
     static constexpr int kClassStreams = 4, kClassEvents = 8;
     cudaStream_t cls_stream[kClassStreams] = {};
     cudaEvent_t cls_fork = nullptr, cls_join[kClassEvents] = {};
     cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_fork = nullptr, ev_join = nullptr;
-    // descriptor staging: ring 0 for the caller's stream, ring 1 for `aux`
-    tlr::StageRing stage[2];
+    // descriptor staging: ring 0 for the caller's stream, 1 for `aux`, 2 for `la`
+    tlr::StageRing stage[3];
     // fixed Gaussian test matrices of the randomised range finder
     double *d_omega = nullptr;
     float2 *d_omega2 = nullptr;  // paired-FP32 copy of d_omega

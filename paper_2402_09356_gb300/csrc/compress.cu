@@ -923,9 +923,10 @@ static SvdKernel svd_sm_kernel(int c) {
 }
 
 // One launch per (kernel, cluster size) class, with the class's largest
-// shared-memory need.  The classes run concurrently, each on its own stream
-// (forked from and joined back to the calling stream), largest clusters
-// first: a column's compression then costs its slowest class, not the sum.
+// shared-memory need.  The classes run concurrently, each on its own
+// high-priority stream (forked from and joined back to the calling stream),
+// largest clusters first: a column's compression then costs its slowest
+// class, not the sum.
 template <class Job, class K>
 struct LaunchClass {
     K kernel;
@@ -946,10 +947,7 @@ static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClas
     // descriptors go up on the calling stream, before the fork
     std::vector<const Job *> dj;
     for (auto *c : use) dj.push_back((const Job *)stage_push(ctx, c->jobs.data(), c->jobs.size() * sizeof(Job), st));
-    if (use.size() == 1) {
-        launch_cluster(use[0]->kernel, use[0]->csize, (int)use[0]->jobs.size(), use[0]->smem, st, dj[0], extra...);
-        return;
-    }
+    if (use.empty()) return;
     if ((int)use.size() > tlr_ctx::kClassEvents) throw make_error(TLR_ERR_ARG, "too many launch classes");
     TLR_CUDA_TRY(cudaEventRecord(ctx->cls_fork, st));
     for (size_t k = 0; k < use.size(); ++k) {

@@ -8,7 +8,7 @@
 namespace tlr {
 
 void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s) {
-    StageRing &R = ctx->stage[(s == ctx->aux) ? 1 : 0];
+    StageRing &R = ctx->stage[(s == ctx->aux) ? 1 : (s == ctx->la ? 2 : 0)];
     size_t need = (bytes + 255) & ~(size_t)255;
     if (need > R.cap) throw make_error(TLR_ERR_ARG, "descriptor batch too large (%zu bytes)", bytes);
     if (R.off + need > R.cap) {

@@ -16,6 +16,7 @@
 // codes recompress after every single low-rank update instead).
 #include <algorithm>
 #include <cmath>
+#include <exception>
 
 #include "common.cuh"
 #include "compress.cuh"
@@ -94,8 +95,15 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     R.assign((size_t)nt * nt, 0);
     for (int t = 0; t < nt; ++t) R[(size_t)t * nt + t] = tile_rows(n, nb, t);
     auto r_of = [&](int i, int k) { return (int)R[(size_t)i * nt + k]; };
-    DevBuf panel((size_t)nt * nb * nb * sizeof(double), st);
-    double *Tp = panel.as<double>();
+    // Look-ahead (likelihood path): the update of column j+1 by the columns
+    // k < j runs on a third stream while column j is compressed (which keeps
+    // most SMs idle); only the update by column j itself stays on the
+    // critical path.  Two panel buffers alternate between the columns.
+    const bool ahead = (mode == FactorMode::Matern) && nt > 1;
+    DevBuf panel_buf[2];
+    panel_buf[0].alloc((size_t)nt * nb * nb * sizeof(double), st);
+    if (ahead) panel_buf[1].alloc((size_t)nt * nb * nb * sizeof(double), st);
+    int cur = 0;
     // paired-FP32 copy of the panel (mixed precision): operand of the compression products
     DevBuf panel2(df ? (size_t)nt * nb * nb * sizeof(float2) : 0, st);
     float2 *Tp2 = panel2.as<float2>();
@@ -106,9 +114,10 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     DevBuf ytmp(solve ? (size_t)nb * sizeof(double) : 0, st);
     if (solve && y != z) TLR_CUDA_TRY(cudaMemcpyAsync(y, z, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::vector<cudaEvent_t> aux_marks;  // potrf + inverse on the side stream (profiling)
-    // the side stream must not start before the buffers above exist
+    // the side streams must not start before the buffers above exist
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
     TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->la, ctx->ev_fork, 0));
 
     // stage boundary events (profiling): 6 marks per column
     std::vector<cudaEvent_t> marks;
@@ -125,13 +134,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         cudaEvent_t e;
         int idx;
     };
-    std::vector<DMark> dm_main, dm_aux;
-    // per finished column k: the Gram matrix G_k = V_k' V_k of its packed V
-    // factors V_k = [V_ik]_{i>k} (order of i, zero-rank tiles left out), the
-    // column offset of each tile in V_k, and V_k' y_k for the fused solve
-    std::vector<DevBuf> gram(nt), vty(nt);
-    std::vector<int> gram_n(nt, 0);
-    std::vector<std::vector<int>> gram_off(nt);
+    std::vector<DMark> dm_main, dm_aux, dm_la;
     auto dmark = [&](std::vector<DMark> &v, cudaStream_t s, int idx) {
         if (!ctx->profile) return;
         profile_events(ctx, prof_used + 1);
@@ -139,117 +142,211 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         TLR_CUDA_TRY(cudaEventRecord(e, s));
         v.push_back(DMark{e, idx});
     };
-    for (int j = 0; j < nt; ++j) {
-        const int mj = tile_rows(n, nb, j);
-        const int64_t Mp = (int64_t)(nt - j) * nb;  // panel leading dimension
-        mark();
-        dmark(dm_main, st, -1);
-        // --- Q_j = [U_j0 | ... ] and offsets
-        std::vector<int> off(j + 1, 0);
-        for (int k = 0; k < j; ++k) off[k + 1] = off[k] + r_of(j, k);
-        const int Rj = off[j];
-        DevBuf qbuf((size_t)nb * std::max(Rj, 1) * sizeof(double), st);
-        DevBuf pbuf((size_t)Mp * std::max(Rj, 1) * sizeof(double), st);
-        double *Qj = qbuf.as<double>(), *Pj = pbuf.as<double>();
-        if (Rj > 0) {
+    // per finished column k: the Gram matrix G_k = V_k' V_k of its packed V
+    // factors V_k = [V_ik]_{i>k} (order of i, zero-rank tiles left out), the
+    // column offset of each tile in V_k, and V_k' y_k for the fused solve
+    std::vector<DevBuf> gram(nt), vty(nt);
+    std::vector<int> gram_n(nt, 0);
+    std::vector<std::vector<int>> gram_off(nt);
+    // On an error the buffers above are released stream-ordered on st while
+    // the side and look-ahead streams may still use them: wait for those first.
+    struct SideStreamGuard {
+        tlr_ctx *ctx;
+        ~SideStreamGuard() {
+            if (std::uncaught_exceptions()) {
+                cudaStreamSynchronize(ctx->la);
+                cudaStreamSynchronize(ctx->aux);
+            }
+        }
+    } side_guard{ctx};
+
+    // Update of column c's panel T (the tiles i >= c stacked, leading
+    // dimension (nt - c) nb) by the factor columns k0 <= k < k1:
+    //   T = A - P Q'  (generate: the Matern epilogue evaluates A)  or  T -= P Q',
+    // with Q = [U_ck]_k and the P block (i, k) = U_ik W_ik, W_ik = V_ik' V_ck a
+    // block of G_k.  The whole panel is one GEMM; all work on stream s.
+    auto panel_update = [&](int c, int k0, int k1, double *T, cudaStream_t s, bool generate,
+                            std::vector<DMark> &dm, int det_build, int det_gemm) {
+        const int mc = tile_rows(n, nb, c);
+        const int64_t Mp = (int64_t)(nt - c) * nb;
+        std::vector<int> off(std::max(k1 - k0, 0) + 1, 0);
+        for (int k = k0; k < k1; ++k) off[k - k0 + 1] = off[k - k0] + r_of(c, k);
+        const int Rc = off.back();
+        DevBuf qbuf((size_t)nb * std::max(Rc, 1) * sizeof(double), s);
+        DevBuf pbuf((size_t)Mp * std::max(Rc, 1) * sizeof(double), s);
+        double *Qc = qbuf.as<double>(), *Pc = pbuf.as<double>();
+        if (Rc > 0) {
             std::vector<CopyDesc> cq;
-            for (int k = 0; k < j; ++k)
-                if (r_of(j, k) > 0)
-                    cq.push_back(CopyDesc{Uslot(M, j, k), nb, Qj + (int64_t)off[k] * nb, nb, mj, r_of(j, k)});
-            copy_batched(ctx, st, cq);
-            TLR_CUDA_TRY(cudaMemsetAsync(Pj, 0, (size_t)Mp * Rj * sizeof(double), st));
-            dmark(dm_main, st, kDetBuildCopy);
-            // P block (i, k) = U_ik W_ik with W_ik = V_ik' V_jk, a block of the
-            // Gram matrix G_k of column k's V factors (formed once per column)
+            for (int k = k0; k < k1; ++k)
+                if (r_of(c, k) > 0)
+                    cq.push_back(CopyDesc{Uslot(M, c, k), nb, Qc + (int64_t)off[k - k0] * nb, nb, mc, r_of(c, k)});
+            copy_batched(ctx, s, cq);
+            TLR_CUDA_TRY(cudaMemsetAsync(Pc, 0, (size_t)Mp * Rc * sizeof(double), s));
             std::vector<GemmProb> gp;
-            for (int k = 0; k < j; ++k) {
-                const int rjk = r_of(j, k);
-                if (rjk <= 0) continue;
+            for (int k = k0; k < k1; ++k) {
+                const int rck = r_of(c, k);
+                if (rck <= 0) continue;
                 const int S = gram_n[k];
                 const double *G = gram[k].as<double>();
-                for (int i = j; i < nt; ++i) {
+                for (int i = c; i < nt; ++i) {
                     const int rik = r_of(i, k);
                     if (rik <= 0) continue;
                     GemmProb b{};
                     b.A = Uslot(M, i, k); b.lda = nb; b.m = tile_rows(n, nb, i); b.k = rik;
-                    b.B = G + (int64_t)gram_off[k][j] * S + gram_off[k][i]; b.ldb = S; b.n = rjk;
-                    b.C = Pj + (int64_t)off[k] * Mp + (int64_t)(i - j) * nb; b.ldc = (int)Mp;
+                    b.B = G + (int64_t)gram_off[k][c] * S + gram_off[k][i]; b.ldb = S; b.n = rck;
+                    b.C = Pc + (int64_t)off[k - k0] * Mp + (int64_t)(i - c) * nb; b.ldc = (int)Mp;
                     gp.push_back(b);
-                    stats->flops += 2.0 * b.m * rik * rjk;
+                    stats->flops += 2.0 * b.m * rik * rck;
                 }
             }
-            gemm_batched(ctx, st, false, false, gp, 1.0, 0.0);
-            dmark(dm_main, st, kDetBuildP);
+            gemm_batched(ctx, s, false, false, gp, 1.0, 0.0);
         }
-        if (solve && Rj > 0) {
-            // y_j -= Q_j c, c_k = V_jk' y_k: a slice of column k's V' y_k
-            DevBuf cb((size_t)Rj * sizeof(double), st);
-            std::vector<CopyDesc> cc;
-            for (int k = 0; k < j; ++k) {
-                int r = r_of(j, k);
-                if (r <= 0) continue;
-                cc.push_back(CopyDesc{vty[k].as<double>() + gram_off[k][j], r, cb.as<double>() + off[k], r, r, 1});
+        const int64_t rows_valid = n - (int64_t)c * nb;
+        GemmProb g{};
+        g.A = Pc; g.lda = (int)Mp; g.m = (int)Mp; g.k = Rc;
+        g.B = Qc; g.ldb = nb; g.n = mc;
+        g.C = T; g.ldc = (int)Mp;
+        g.ri0 = (int64_t)c * nb; g.ci0 = (int64_t)c * nb;
+        DevBuf p2(df && Rc > 0 ? (size_t)Mp * Rc * sizeof(float2) : 0, s);
+        DevBuf q2(df && Rc > 0 ? (size_t)nb * Rc * sizeof(float2) : 0, s);
+        if (df && Rc > 0) {
+            g.A2 = p2.as<float2>();
+            g.B2 = q2.as<float2>();
+            split_f2_batched(ctx, s, {SplitDesc{Pc, p2.as<float2>(), (int)Mp, (int)Mp, Rc},
+                                      SplitDesc{Qc, q2.as<float2>(), nb, mc, Rc}});
+        }
+        dmark(dm, s, det_build);
+        if (generate) {
+            gemm_batched_matern(ctx, s, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df);
+            stats->matern_entries += (double)rows_valid * mc;
+            stats->panel_launches += 1;
+        } else if (Rc > 0) {
+            gemm_batched(ctx, s, false, true, std::vector<GemmProb>{g}, -1.0, 1.0, df);
+        }
+        dmark(dm, s, det_gemm);
+        stats->gemm_flops += 2.0 * (double)rows_valid * mc * Rc;
+        stats->flops += 2.0 * (double)rows_valid * mc * Rc;
+    };
+
+    // Look-ahead correction of column c's panel by column k = c - 1 alone:
+    //   T_ic -= U_ik Z_i,  Z_i = W_ik U_ck',  W_ik = V_ik' V_ck  (a block of G_k),
+    // grouped so that the inner dimension of the large product is r_ik.
+    auto panel_correct = [&](int c, double *T, cudaStream_t s) {
+        const int k = c - 1;
+        const int rck = r_of(c, k);
+        if (rck <= 0) return;
+        const int mc = tile_rows(n, nb, c);
+        const int64_t Mp = (int64_t)(nt - c) * nb;
+        const int S = gram_n[k];
+        const double *G = gram[k].as<double>();
+        int64_t ztot = 0;
+        std::vector<int64_t> zoff(nt, -1);
+        for (int i = c; i < nt; ++i)
+            if (r_of(i, k) > 0) {
+                zoff[i] = ztot;
+                ztot += r_of(i, k);
             }
-            copy_batched(ctx, st, cc);
-            GemmProb g{};
-            g.A = Qj; g.lda = nb; g.m = mj; g.k = Rj;
-            g.B = cb.as<double>(); g.ldb = Rj; g.n = 1;
-            g.C = y + (int64_t)j * nb; g.ldc = nb;
-            gemm_batched(ctx, st, false, false, std::vector<GemmProb>{g}, -1.0, 1.0);
-            dmark(dm_main, st, kDetBuildSolve);
+        if (ztot == 0) return;
+        DevBuf zb((size_t)ztot * nb * sizeof(double), s);
+        std::vector<GemmProb> gz, gu;
+        for (int i = c; i < nt; ++i) {
+            const int rik = r_of(i, k);
+            if (rik <= 0) continue;
+            GemmProb a{};
+            a.A = G + (int64_t)gram_off[k][c] * S + gram_off[k][i]; a.lda = S; a.m = rik; a.k = rck;
+            a.B = Uslot(M, c, k); a.ldb = nb; a.n = mc;
+            a.C = zb.as<double>() + zoff[i] * nb; a.ldc = rik;
+            gz.push_back(a);
+            GemmProb b{};
+            b.A = Uslot(M, i, k); b.lda = nb; b.m = tile_rows(n, nb, i); b.k = rik;
+            b.B = zb.as<double>() + zoff[i] * nb; b.ldb = rik; b.n = mc;
+            b.C = T + (int64_t)(i - c) * nb; b.ldc = (int)Mp;
+            gu.push_back(b);
+            stats->flops += 2.0 * rik * rck * mc + 2.0 * b.m * rik * mc;
+            stats->gemm_flops += 2.0 * b.m * rik * mc;
+        }
+        gemm_batched(ctx, s, false, true, gz, 1.0, 0.0);
+        DevBuf u2(df ? (size_t)ztot * nb * sizeof(float2) : 0, s);
+        DevBuf z2(df ? (size_t)ztot * nb * sizeof(float2) : 0, s);
+        if (df) {
+            std::vector<SplitDesc> sd;
+            for (GemmProb &b : gu) {
+                const int64_t o = b.B - zb.as<double>();
+                sd.push_back(SplitDesc{b.A, u2.as<float2>() + o, nb, b.m, b.k});
+                sd.push_back(SplitDesc{b.B, z2.as<float2>() + o, b.k, b.k, mc});
+                b.A2 = u2.as<float2>() + o;
+                b.B2 = z2.as<float2>() + o;
+            }
+            split_f2_batched(ctx, s, sd);
+        }
+        gemm_batched(ctx, s, false, false, gu, -1.0, 1.0, df);
+    };
+
+    // y_c -= sum_{k<c} U_ck c_k, c_k = V_ck' y_k: a slice of column k's V_k' y_k
+    auto solve_update = [&](int c) {
+        const int mc = tile_rows(n, nb, c);
+        std::vector<int> off(c + 1, 0);
+        for (int k = 0; k < c; ++k) off[k + 1] = off[k] + r_of(c, k);
+        const int Rc = off[c];
+        if (Rc <= 0) return;
+        DevBuf qb((size_t)nb * Rc * sizeof(double), st), cb((size_t)Rc * sizeof(double), st);
+        std::vector<CopyDesc> cq, cc;
+        for (int k = 0; k < c; ++k) {
+            const int r = r_of(c, k);
+            if (r <= 0) continue;
+            cq.push_back(CopyDesc{Uslot(M, c, k), nb, qb.as<double>() + (int64_t)off[k] * nb, nb, mc, r});
+            cc.push_back(CopyDesc{vty[k].as<double>() + gram_off[k][c], r, cb.as<double>() + off[k], r, r, 1});
+        }
+        copy_batched(ctx, st, cq);
+        copy_batched(ctx, st, cc);
+        GemmProb g{};
+        g.A = qb.as<double>(); g.lda = nb; g.m = mc; g.k = Rc;
+        g.B = cb.as<double>(); g.ldb = Rc; g.n = 1;
+        g.C = y + (int64_t)c * nb; g.ldc = nb;
+        gemm_batched(ctx, st, false, false, std::vector<GemmProb>{g}, -1.0, 1.0);
+    };
+
+    for (int j = 0; j < nt; ++j) {
+        const int mj = tile_rows(n, nb, j);
+        const int64_t Mp = (int64_t)(nt - j) * nb;  // panel leading dimension
+        double *Tp = panel_buf[cur].as<double>();
+        mark();
+        dmark(dm_main, st, -1);
+        // --- panel: T_{:,j} = A_{:,j} - sum_{k<j} L_{:,k} L_jk'
+        if (!ahead || j == 0) {
+            if (mode == FactorMode::Tlr) {
+                // densify the compressed input column: T_jj = D_jj, T_ij = U_ij V_ij'
+                TLR_CUDA_TRY(cudaMemsetAsync(Tp, 0, (size_t)Mp * nb * sizeof(double), st));
+                copy_batched(ctx, st, {CopyDesc{M->D + (int64_t)j * nb * nb, nb, Tp, (int)Mp, mj, mj}});
+                std::vector<GemmProb> gd;
+                for (int i = j + 1; i < nt; ++i) {
+                    int rin = prev[(size_t)i * nt + j];
+                    if (rin <= 0) continue;
+                    GemmProb a{};
+                    a.A = Uslot(M, i, j); a.lda = nb; a.m = tile_rows(n, nb, i); a.k = rin;
+                    a.B = Vslot(M, i, j); a.ldb = nb; a.n = mj;
+                    a.C = Tp + (int64_t)(i - j) * nb; a.ldc = (int)Mp;
+                    gd.push_back(a);
+                }
+                gemm_batched(ctx, st, false, true, gd, 1.0, 0.0);
+            }
+            panel_update(j, 0, j, Tp, st, mode == FactorMode::Matern, dm_main, kDetBuild, kDetPanel);
+        } else {
+            // the update by the columns k < j - 1 ran on the look-ahead stream
+            TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_la_join, 0));
+            dmark(dm_main, st, kDetAheadWait);
+            panel_correct(j, Tp, st);
+            dmark(dm_main, st, kDetCorrect);
+        }
+        if (solve && j > 0) {
+            solve_update(j);
+            dmark(dm_main, st, kDetSolveUpd);
         }
         mark();
-        // --- panel: T_{:,j} = A_{:,j} - P_j Q_j'
-        const int64_t rows_valid = n - (int64_t)j * nb;
-        if (mode == FactorMode::Matern) {
-            GemmProb g{};
-            g.A = Pj; g.lda = (int)Mp; g.m = (int)Mp; g.k = Rj;
-            g.B = Qj; g.ldb = nb; g.n = mj;
-            g.C = Tp; g.ldc = (int)Mp;
-            g.ri0 = (int64_t)j * nb; g.ci0 = (int64_t)j * nb;
-            DevBuf p2(df ? (size_t)Mp * std::max(Rj, 1) * sizeof(float2) : 0, st);
-            DevBuf q2(df ? (size_t)nb * std::max(Rj, 1) * sizeof(float2) : 0, st);
-            if (df && Rj > 0) {
-                g.A2 = p2.as<float2>();
-                g.B2 = q2.as<float2>();
-                split_f2_batched(ctx, st, {SplitDesc{Pj, p2.as<float2>(), (int)Mp, (int)Mp, Rj},
-                                           SplitDesc{Qj, q2.as<float2>(), nb, mj, Rj}});
-                dmark(dm_main, st, kDetSplit);
-            }
-            gemm_batched_matern(ctx, st, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df);
-            dmark(dm_main, st, kDetPanel);
-            if (df && j + 1 < nt) {
-                split_f2_batched(ctx, st, {SplitDesc{Tp + nb, Tp2 + nb, (int)Mp, (int)(Mp - nb), mj}});
-                dmark(dm_main, st, kDetSplit);
-            }
-            stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
-            stats->matern_entries += (double)rows_valid * mj;
-            stats->panel_launches += 1;
-        } else {
-            // densify the compressed input column: T_jj = D_jj, T_ij = U_ij V_ij'
-            TLR_CUDA_TRY(cudaMemsetAsync(Tp, 0, (size_t)Mp * nb * sizeof(double), st));
-            copy_batched(ctx, st, {CopyDesc{M->D + (int64_t)j * nb * nb, nb, Tp, (int)Mp, mj, mj}});
-            std::vector<GemmProb> gd;
-            for (int i = j + 1; i < nt; ++i) {
-                int rin = prev[(size_t)i * nt + j];
-                if (rin <= 0) continue;
-                GemmProb a{};
-                a.A = Uslot(M, i, j); a.lda = nb; a.m = tile_rows(n, nb, i); a.k = rin;
-                a.B = Vslot(M, i, j); a.ldb = nb; a.n = mj;
-                a.C = Tp + (int64_t)(i - j) * nb; a.ldc = (int)Mp;
-                gd.push_back(a);
-            }
-            gemm_batched(ctx, st, false, true, gd, 1.0, 0.0);
-            if (Rj > 0) {
-                GemmProb g{};
-                g.A = Pj; g.lda = (int)Mp; g.m = (int)Mp; g.k = Rj;
-                g.B = Qj; g.ldb = nb; g.n = mj;
-                g.C = Tp; g.ldc = (int)Mp;
-                gemm_batched(ctx, st, false, true, std::vector<GemmProb>{g}, -1.0, 1.0);
-            }
-            stats->gemm_flops += 2.0 * (double)rows_valid * mj * Rj;
+        if (df && j + 1 < nt) {
+            split_f2_batched(ctx, st, {SplitDesc{Tp + nb, Tp2 + nb, (int)Mp, (int)(Mp - nb), mj}});
+            dmark(dm_main, st, kDetSplit);
         }
-        stats->flops += 2.0 * (double)rows_valid * mj * Rj;
         mark();
         // --- L_jj = chol(T_jj) into D_j and X = L_jj^-1, on the side stream:
         // they are independent of the compression of the column's other tiles
@@ -257,29 +354,34 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         copy_batched(ctx, st, {CopyDesc{Tp, (int)Mp, Dj, nb, mj, mj}});
         TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
         TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-        // the side stream's launches go first: its chain of small dependent
-        // kernels then starts before the compression fills the GPU
-        auto enqueue_aux = [&]() {
-            if (ctx->profile) {
-                profile_events(ctx, prof_used + 1);
-                TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
-                aux_marks.push_back(ctx->prof_events[prof_used++]);
-            }
-            dmark(dm_aux, ctx->aux, -1);
-            potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
-            dmark(dm_aux, ctx->aux, kDetPotrf);
-            set_identity(ctx->aux, Xinv, nb, mj);
-            trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
-            dmark(dm_aux, ctx->aux, kDetInverse);
-            if (ctx->profile) {
-                profile_events(ctx, prof_used + 1);
-                TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
-                aux_marks.push_back(ctx->prof_events[prof_used++]);
-            }
-            TLR_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
-        };
-        enqueue_aux();
+        if (ctx->profile) {
+            profile_events(ctx, prof_used + 1);
+            TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
+            aux_marks.push_back(ctx->prof_events[prof_used++]);
+        }
+        dmark(dm_aux, ctx->aux, -1);
+        potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
+        dmark(dm_aux, ctx->aux, kDetPotrf);
+        set_identity(ctx->aux, Xinv, nb, mj);
+        trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
+        dmark(dm_aux, ctx->aux, kDetInverse);
+        if (ctx->profile) {
+            profile_events(ctx, prof_used + 1);
+            TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
+            aux_marks.push_back(ctx->prof_events[prof_used++]);
+        }
+        TLR_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->aux));
         stats->flops += (double)mj * mj * mj / 3.0 + (double)mj * mj * mj / 3.0;
+        // --- look-ahead: column j+1's update by the columns k < j, concurrently
+        // with this column's compression (G_k, k < j, are final)
+        if (ahead && j + 1 < nt) {
+            TLR_CUDA_TRY(cudaEventRecord(ctx->ev_la_fork, st));
+            TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->la, ctx->ev_la_fork, 0));
+            dmark(dm_la, ctx->la, -1);
+            panel_update(j + 1, 0, j, panel_buf[cur ^ 1].as<double>(), ctx->la, true, dm_la, kDetAheadBuild,
+                         kDetAheadPanel);
+            TLR_CUDA_TRY(cudaEventRecord(ctx->ev_la_join, ctx->la));
+        }
         mark();
         // --- compress T_ij, i > j (main stream, concurrently with the above)
         std::vector<CompressJob> jobs;
@@ -410,11 +512,12 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             dmark(dm_main, st, kDetSolve);
         }
         mark();
+        if (ahead) cur ^= 1;
     }
     if (ctx->profile) {
-        for (std::vector<DMark> *v : {&dm_main, &dm_aux})
+        for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la})
             if (!v->empty()) TLR_CUDA_TRY(cudaEventSynchronize(v->back().e));
-        for (std::vector<DMark> *v : {&dm_main, &dm_aux})
+        for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la})
             for (size_t k = 1; k < v->size(); ++k) {
                 if ((*v)[k].idx < 0) continue;
                 float ms = 0.f;
@@ -438,7 +541,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             TLR_CUDA_TRY(cudaEventElapsedTime(&ms, aux_marks[c], aux_marks[c + 1]));
             stats->stage_ms[2] += ms;
         }
-        stats->gemm_ms += stats->stage_ms[1];
+        stats->gemm_ms += stats->detail_ms[kDetPanel] + stats->detail_ms[kDetAheadPanel];
     }
 }
 

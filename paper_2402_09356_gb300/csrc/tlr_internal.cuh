@@ -21,12 +21,12 @@ constexpr int kStages = 5;
 
 // finer profiling buckets of the factorisation (device ms, summed over columns)
 enum DetailBucket {
-    kDetBuildCopy,   // Q_j gather, P_j clear
-    kDetBuildW,      // unused (W_ik now comes from the Gram matrices)
-    kDetBuildP,      // P block (i, k) = U_ik W_ik
-    kDetBuildSolve,  // fused forward-solve update of y_j
-    kDetSplit,       // paired-FP32 operand copies
-    kDetPanel,       // panel update GEMM with Matern generation
+    kDetBuild,       // P_j, Q_j operands of a main-stream panel update
+    kDetCorrect,     // look-ahead: correction of the panel by the previous column
+    kDetAheadWait,   // main stream waiting for the look-ahead stream
+    kDetSolveUpd,    // fused forward-solve update of y_j
+    kDetSplit,       // paired-FP32 copy of the panel for the compression
+    kDetPanel,       // panel update GEMM on the main stream
     kDetDiagCopy,    // diagonal tile copy and fork to the side stream
     kDetCompress,    // off-diagonal compression
     kDetJoin,        // waiting for the side stream (POTRF + inverse)
@@ -35,6 +35,8 @@ enum DetailBucket {
     kDetGram,        // G_j = V_j' V_j
     kDetPotrf,       // side stream: dense POTRF of the diagonal tile
     kDetInverse,     // side stream: L_jj^-1
+    kDetAheadBuild,  // look-ahead stream: P, Q operands of the next column's update
+    kDetAheadPanel,  // look-ahead stream: the next column's panel GEMM (Matern epilogue)
     kDetail
 };
 
