@@ -42,12 +42,12 @@ static void launch_shape(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const s
     // the transposition pairs the library uses: NN, TN, NT (no TT)
     if (ta && tb) throw make_error(TLR_ERR_ARG, "GEMM with both operands transposed is not provided");
     if (df) {
-        if (!ta && !tb) launch(k_gemm_df<BM, BN, false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-        else if (!ta) launch(k_gemm_df<BM, BN, false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-        else launch(k_gemm_df<BM, BN, true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    } else if (!ta && !tb) launch(k_gemm_f64<BM, BN, false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    else if (!ta) launch(k_gemm_f64<BM, BN, false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
-    else launch(k_gemm_f64<BM, BN, true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, alpha, epi);
+        if (!ta && !tb) launch(k_gemm_df<BM, BN, false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, total, alpha, epi);
+        else if (!ta) launch(k_gemm_df<BM, BN, false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, total, alpha, epi);
+        else launch(k_gemm_df<BM, BN, true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, total, alpha, epi);
+    } else if (!ta && !tb) launch(k_gemm_f64<BM, BN, false, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, total, alpha, epi);
+    else if (!ta) launch(k_gemm_f64<BM, BN, false, true, Epi>, total, kGemmThreads, 0, s, dp, dt, np, total, alpha, epi);
+    else launch(k_gemm_f64<BM, BN, true, false, Epi>, total, kGemmThreads, 0, s, dp, dt, np, total, alpha, epi);
     TLR_CHECK_LAUNCH();
 }
 
@@ -144,7 +144,7 @@ void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vec
 }
 
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
-                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df) {
+                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df, int max_ctas) {
     if (!tb) throw make_error(TLR_ERR_ARG, "the Matern panel product takes B transposed");
     EpiMatern e;
     e.xy = xy;
@@ -162,8 +162,27 @@ void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vecto
     auto *dp = (const GemmProb *)stage_push(ctx, big.data(), big.size() * sizeof(GemmProb), s);
     auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
     int np = (int)big.size();
-    if (df) launch(k_gemm_df<64, 64, false, true, EpiMatern>, total, kGemmThreads, 0, s, dp, dt, np, alpha, e);
-    else launch(k_gemm_f64<64, 64, false, true, EpiMatern>, total, kGemmThreads, 0, s, dp, dt, np, alpha, e);
+    const int grid = max_ctas > 0 ? std::min(total, max_ctas) : total;
+    // a capped grid also reserves more than half of an SM's shared memory per
+    // CTA (unused), so that each of its CTAs holds an SM of its own and the
+    // other SMs stay free for the critical-path kernels
+    size_t smem = 0;
+    if (max_ctas > 0) {
+        static size_t reserve = 0;
+        if (reserve == 0) {
+            int dev = 0, per_sm = 0;
+            TLR_CUDA_TRY(cudaGetDevice(&dev));
+            TLR_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            size_t r = (size_t)per_sm / 2 + 1024;
+            for (const void *k : {(const void *)k_gemm_df<64, 64, false, true, EpiMatern>,
+                                  (const void *)k_gemm_f64<64, 64, false, true, EpiMatern>})
+                TLR_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r));
+            reserve = r;
+        }
+        smem = reserve;
+    }
+    if (df) launch(k_gemm_df<64, 64, false, true, EpiMatern>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
+    else launch(k_gemm_f64<64, 64, false, true, EpiMatern>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
     TLR_CHECK_LAUNCH();
 }
 

@@ -50,12 +50,12 @@ struct EpiMatern {
     }
 };
 
-// Locate the problem of output tile blockIdx.x (binary search over the
-// per-problem tile offsets) and the tile's first row and column.
+// Locate the problem of output tile t (binary search over the per-problem
+// tile offsets) and the tile's first row and column.
 template <int BM, int BN>
 __device__ __forceinline__ bool gemm_tile(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off,
-                                          int nprob, GemmProb &p, int &m0, int &n0) {
-    int lo = 0, hi = nprob - 1, t = blockIdx.x;
+                                          int nprob, int t, GemmProb &p, int &m0, int &n0) {
+    int lo = 0, hi = nprob - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
@@ -69,22 +69,25 @@ __device__ __forceinline__ bool gemm_tile(const GemmProb *__restrict__ probs, co
     return true;
 }
 
-// One BM x BN output tile per CTA of 256 threads (a 16 x 16 thread grid,
-// BM/16 x BN/16 outputs per thread), K in steps of 16 through shared memory.
+// BM x BN output tiles, CTA b taking tiles b, b + gridDim.x, ... (a grid
+// smaller than the tile count keeps the product to that many CTAs), 256
+// threads per CTA (a 16 x 16 thread grid, BM/16 x BN/16 outputs per thread),
+// K in steps of 16 through shared memory.
 // Tiles of 64 x 64 serve large products; 32-row or 32-column tiles serve the
 // many thin products of the low-rank updates (ranks of a few tens), whose
 // padding would otherwise dominate.
 template <int BM, int BN, bool TA, bool TB, class Epi>
 __global__ void __launch_bounds__(kGemmThreads)
-k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob,
+k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob, int ntiles,
            double alpha, Epi epi) {
     constexpr int TM = BM / 16, TN = BN / 16;
     __shared__ double As[kGemmBK][BM + 1];
     __shared__ double Bs[kGemmBK][BN + 1];
     const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     GemmProb p;
     int m0, n0;
-    if (!gemm_tile<BM, BN>(probs, tile_off, nprob, p, m0, n0)) return;
+    if (!gemm_tile<BM, BN>(probs, tile_off, nprob, t, p, m0, n0)) continue;
     const int r0 = (tid & 15) * TM, c0 = (tid >> 4) * TN;
     double acc[TM][TN];
 #pragma unroll
@@ -138,6 +141,8 @@ k_gemm_f64(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off,
             *cp = epi(p, r, c, alpha * acc[x][y], cp);
         }
     }
+    __syncthreads();  // the next tile reuses the shared tiles
+    }
 }
 
 // The same product with paired-FP32 ("double-float") arithmetic on the FP32
@@ -162,15 +167,16 @@ __device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, f
 
 template <int BM, int BN, bool TA, bool TB, class Epi>
 __global__ void __launch_bounds__(kGemmThreads)
-k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob, double alpha,
-          Epi epi) {
+k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, int nprob, int ntiles,
+          double alpha, Epi epi) {
     constexpr int TM = BM / 16, TN = BN / 16;
     __shared__ float2 As[kGemmBK][BM + 1];
     __shared__ float2 Bs[kGemmBK][BN + 1];
     const int tid = threadIdx.x;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     GemmProb p;
     int m0, n0;
-    if (!gemm_tile<BM, BN>(probs, tile_off, nprob, p, m0, n0)) return;
+    if (!gemm_tile<BM, BN>(probs, tile_off, nprob, t, p, m0, n0)) continue;
     const int r0 = (tid & 15) * TM, c0 = (tid >> 4) * TN;
     float ch[TM][TN], cl[TM][TN];
 #pragma unroll
@@ -222,6 +228,8 @@ k_gemm_df(const GemmProb *__restrict__ probs, const int *__restrict__ tile_off, 
             double *cp = p.C + (int64_t)c * p.ldc + r;
             *cp = epi(p, r, c, alpha * ((double)ch[x][y] + (double)cl[x][y]), cp);
         }
+    }
+    __syncthreads();  // the next tile reuses the shared tiles
     }
 }
 
@@ -282,7 +290,10 @@ void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc>
 // pipe); every problem must then carry A2/B2 copies made by split_f2.
 void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
                   double alpha, double beta, bool df = false);
+// max_ctas > 0 caps the grid (the CTAs then loop over the tiles), so that a
+// product running beside critical-path work leaves SMs free.
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
-                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df = false);
+                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df = false,
+                         int max_ctas = 0);
 
 }  // namespace tlr

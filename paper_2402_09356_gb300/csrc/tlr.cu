@@ -100,6 +100,10 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     // most SMs idle); only the update by column j itself stays on the
     // critical path.  Two panel buffers alternate between the columns.
     const bool ahead = (mode == FactorMode::Matern) && nt > 1;
+    // The look-ahead panel GEMM runs uncapped at the lowest stream priority:
+    // capping it to a subset of the SMs (max_ctas > 0) starves the
+    // compression's bursts of wide launches and measured slower.
+    const int ahead_ctas = 0;
     DevBuf panel_buf[2];
     panel_buf[0].alloc((size_t)nt * nb * nb * sizeof(double), st);
     if (ahead) panel_buf[1].alloc((size_t)nt * nb * nb * sizeof(double), st);
@@ -166,7 +170,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     // with Q = [U_ck]_k and the P block (i, k) = U_ik W_ik, W_ik = V_ik' V_ck a
     // block of G_k.  The whole panel is one GEMM; all work on stream s.
     auto panel_update = [&](int c, int k0, int k1, double *T, cudaStream_t s, bool generate,
-                            std::vector<DMark> &dm, int det_build, int det_gemm) {
+                            std::vector<DMark> &dm, int det_build, int det_gemm, int max_ctas) {
         const int mc = tile_rows(n, nb, c);
         const int64_t Mp = (int64_t)(nt - c) * nb;
         std::vector<int> off(std::max(k1 - k0, 0) + 1, 0);
@@ -217,7 +221,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         }
         dmark(dm, s, det_build);
         if (generate) {
-            gemm_batched_matern(ctx, s, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df);
+            gemm_batched_matern(ctx, s, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df, max_ctas);
             stats->matern_entries += (double)rows_valid * mc;
             stats->panel_launches += 1;
         } else if (Rc > 0) {
@@ -330,7 +334,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 }
                 gemm_batched(ctx, st, false, true, gd, 1.0, 0.0);
             }
-            panel_update(j, 0, j, Tp, st, mode == FactorMode::Matern, dm_main, kDetBuild, kDetPanel);
+            panel_update(j, 0, j, Tp, st, mode == FactorMode::Matern, dm_main, kDetBuild, kDetPanel, 0);
         } else {
             // the update by the columns k < j - 1 ran on the look-ahead stream
             TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_la_join, 0));
@@ -379,7 +383,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->la, ctx->ev_la_fork, 0));
             dmark(dm_la, ctx->la, -1);
             panel_update(j + 1, 0, j, panel_buf[cur ^ 1].as<double>(), ctx->la, true, dm_la, kDetAheadBuild,
-                         kDetAheadPanel);
+                         kDetAheadPanel, ahead_ctas);
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_la_join, ctx->la));
         }
         mark();
