@@ -220,12 +220,16 @@ def run_gpu(args):
         tlr.tlr_profile(ctx, False)
         return out
 
-    fp64 = timed("fp64")
-    mixed = timed("mixed")
-    rel_dl = max(abs(a["loglik"] - b["loglik"]) / abs(b["loglik"])
-                 for a, b in zip(mixed["results"], fp64["results"]))
-    # the headline is the mixed path when it keeps |dl|/|l| <= 1e-6 against the FP64 path
-    head_name = "mixed" if rel_dl <= 1e-6 else "fp64"
+    fp64 = timed("fp64") if args.paths in ("both", "fp64") else None
+    mixed = timed("mixed") if args.paths in ("both", "mixed") else None
+    if fp64 is not None and mixed is not None:
+        rel_dl = max(abs(a["loglik"] - b["loglik"]) / abs(b["loglik"])
+                     for a, b in zip(mixed["results"], fp64["results"]))
+        # the headline is the mixed path when it keeps |dl|/|l| <= 1e-6 against the FP64 path
+        head_name = "mixed" if rel_dl <= 1e-6 else "fp64"
+    else:
+        rel_dl = None  # one path only (profiling runs)
+        head_name = "mixed" if mixed is not None else "fp64"
     head = mixed if head_name == "mixed" else fp64
     head_opts = tlr.Options(nb=NB, eps=EPS, precision=precisions[head_name])
 
@@ -308,8 +312,8 @@ def run_gpu(args):
                    "l2": "flushed between timed steps (256 MB write outside the events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "rel_dl_vs_fp64": rel_dl,
-        "fp64_path": summary(fp64),
-        "mixed_path": summary(mixed),
+        "fp64_path": summary(fp64) if fp64 is not None else None,
+        "mixed_path": summary(mixed) if mixed is not None else None,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                 "h2d_bytes_per_step": int(xy_pin.numel() * 8 + z_pin.numel() * 8),
@@ -395,6 +399,8 @@ def main():
     ap.add_argument("--nb", type=int, default=NB)
     ap.add_argument("--eps", type=float, default=EPS)
     ap.add_argument("--order", default=ORDER)
+    ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
+                    help="precision paths to time (both for the headline; one for profiling runs)")
     args = ap.parse_args()
     N_POINTS, NB, EPS, ORDER = args.n, args.nb, args.eps, args.order
     if args.impl == "reference":
