@@ -295,6 +295,15 @@ int tlr_compress_times(tlr_ctx *ctx, double *ms);
  * Collected whether or not profiling is on.  Errors: TLR_ERR_ARG. */
 int tlr_compress_stats(tlr_ctx *ctx, int64_t *out);
 
+/* The cluster Jacobi SVD on 16-CTA clusters (the high-rank tiles next to the
+ * diagonal) during the last profiled factorisation, written to out[0..3]:
+ * device time (ms, CUDA events on its stream, summed over launches), FP64
+ * floating-point operations as executed (one FP64 product M J of 2 s^3, the
+ * column norms at every FP64 sweep, one dot product per pair checked, one
+ * two-column rotation per pair rotated), number of launches, and number of
+ * clusters (tiles) over those launches.  Errors: TLR_ERR_ARG. */
+int tlr_kernel_stats(tlr_ctx *ctx, double *out);
+
 /* ---- MLE (Sec. 5.1: derivative-free, bound-constrained) ------------------ */
 
 /* Maximise l(theta) over lo <= theta <= hi from theta0 with the Nelder-Mead

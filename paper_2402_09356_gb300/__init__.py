@@ -96,6 +96,7 @@ _SIGS = {
     "tlr_stage_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_compress_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_compress_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "tlr_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "tlr_detail_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "tlr_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
@@ -409,6 +410,14 @@ def tlr_detail_times(ctx: Context) -> dict:
     if n < 0:
         ctx.check(n)
     return {k: a[i] for i, k in enumerate(DETAILS[:n])}
+
+
+def tlr_kernel_stats(ctx: Context) -> dict:
+    """The 16-CTA cluster Jacobi of the last profiled factorisation."""
+    a = (ctypes.c_double * 4)()
+    ctx.check(load_library().tlr_kernel_stats(ctx.h, a))
+    return {"jacobi16_ms": a[0], "jacobi16_flops": a[1], "jacobi16_launches": int(a[2]),
+            "jacobi16_clusters": int(a[3])}
 
 
 COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps", "sweeps32")

@@ -138,6 +138,7 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     for (cudaEvent_t e : {ctx->ev_a, ctx->ev_b, ctx->ev_fork, ctx->ev_join})
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->cls_time_events) cudaEventDestroy(e);
     for (StageRing &R : ctx->stage) {
         if (R.h) cudaFreeHost(R.h);
         if (R.d) cudaFree(R.d);
@@ -443,6 +444,15 @@ int tlr_detail_times(tlr_ctx *ctx, double *ms, int count) {
 int tlr_compress_times(tlr_ctx *ctx, double *ms) {
     if (!ctx || !ms) return TLR_ERR_ARG;
     for (int k = 0; k < 7; ++k) ms[k] = ctx->comp_ms[k];
+    return TLR_OK;
+}
+
+int tlr_kernel_stats(tlr_ctx *ctx, double *out) {
+    if (!ctx || !out) return TLR_ERR_ARG;
+    out[0] = ctx->k16_ms;
+    out[1] = ctx->k16_flops;
+    out[2] = (double)ctx->k16_launches;
+    out[3] = (double)ctx->k16_clusters;
     return TLR_OK;
 }
 

@@ -141,6 +141,10 @@ struct tlr_ctx {
     std::vector<cudaEvent_t> comp_events;
     double comp_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     long long comp_stats[5] = {0, 0, 0, 0, 0};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum)
+    // the 16-CTA cluster Jacobi (profiling): device ms, FP64 flops, launches, clusters
+    std::vector<cudaEvent_t> cls_time_events;
+    double k16_ms = 0.0, k16_flops = 0.0;
+    long long k16_launches = 0, k16_clusters = 0;
 };
 
 struct tlr_mat {

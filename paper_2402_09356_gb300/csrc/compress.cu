@@ -392,7 +392,7 @@ struct SvdJob {
     double *W;         // s x s output: unit left singular vectors of R', sorted
     double *S;         // s output singular values, descending
     int *rank;         // #{S > tau}, or -1 if any S is not finite
-    int *sweeps;       // sweeps run: [0] FP64, [1] FP32
+    int *sweeps;       // [0] FP64 sweeps, [1] FP32 sweeps, [2] FP64 pairs checked, [3] FP64 pairs rotated
     int s;
 };
 
@@ -500,7 +500,7 @@ __device__ __forceinline__ int pos_of(int blk, int g, int nblk) {
 // applied by this thread's warp.
 template <class T>
 __device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, T *NX, T *NY, int bx, int by, int b, int s, int srot,
-                                                   bool inner, int lane, int warp, T tol2) {
+                                                   bool inner, int lane, int warp, T tol2, int &nchk, int &nrot) {
     bool rot = false;
     if (inner) {
         const int bp = b + (b & 1);
@@ -514,7 +514,10 @@ __device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, T *NX, T *NY, int
                 T *base = slot ? Y : X;
                 T *nrm = slot ? NY : NX;
                 const int lo = min(a, c2), hi = max(a, c2);
-                rot |= jacobi_rotate(base + lo * srot, base + hi * srot, nrm + lo, nrm + hi, s, srot, lane, tol2);
+                const bool r = jacobi_rotate(base + lo * srot, base + hi * srot, nrm + lo, nrm + hi, s, srot, lane, tol2);
+                rot |= r;
+                ++nchk;
+                nrot += r;
             }
             __syncthreads();
         }
@@ -525,8 +528,11 @@ __device__ __forceinline__ bool jacobi_block_pairs(T *X, T *Y, T *NX, T *NY, int
             const int gx = bx * b + i, gy = by * b + jy;
             if (gx >= s || gy >= s) continue;
             // the lower global index is the first column of the pair
-            if (gx < gy) rot |= jacobi_rotate(X + i * srot, Y + jy * srot, NX + i, NY + jy, s, srot, lane, tol2);
-            else rot |= jacobi_rotate(Y + jy * srot, X + i * srot, NY + jy, NX + i, s, srot, lane, tol2);
+            const bool r = gx < gy ? jacobi_rotate(X + i * srot, Y + jy * srot, NX + i, NY + jy, s, srot, lane, tol2)
+                                   : jacobi_rotate(Y + jy * srot, X + i * srot, NY + jy, NX + i, s, srot, lane, tol2);
+            rot |= r;
+            ++nchk;
+            nrot += r;
         }
         __syncthreads();
     }
@@ -553,7 +559,8 @@ __device__ __forceinline__ void block_norms(const T *cols, T *nrm, int b, int s,
 // round g on return.  Returns the number of sweeps run.
 template <int kCl, class T>
 __device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, int stride, int b, int s, int srot, int max_sweeps,
-                             int &g, int &cur, int *s_flag) {
+                             int &g, int &cur, int *s_flag, int *tally = nullptr) {
+    int nchk = 0, nrot = 0;  // pairs checked and rotated by this warp (warp-uniform)
     constexpr int nblk = 2 * kCl;
     const int rank = (int)cl.block_rank(), tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int px = rank, py = nblk - 1 - rank, bs = b * srot;
@@ -568,7 +575,7 @@ __device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, int stride, int b, 
             const int bx = block_at(px, g, nblk), by = block_at(py, g, nblk);
             T *B = buf(cur);
             if (jacobi_block_pairs<T>(B, B + bs, B + 2 * bs, B + 2 * bs + b, bx, by, b, s, srot, round == 0, lane,
-                                      warp, tol2) &&
+                                      warp, tol2, nchk, nrot) &&
                 lane == 0)
                 s_flag[sweep & 1] = 1;
             cl.sync();
@@ -594,6 +601,10 @@ __device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, int stride, int b, 
             cur ^= 1;
             __syncthreads();
         }
+    }
+    if (tally && lane == 0) {
+        atomicAdd(tally, nchk);
+        atomicAdd(tally + 1, nrot);
     }
     return nsweep;
 }
@@ -625,6 +636,7 @@ __device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols,
 __device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, int sweeps, int sweeps32) {
     J.sweeps[0] = sweeps;
     J.sweeps[1] = sweeps32;
+    J.sweeps[2] = J.sweeps[3] = 0;
     int r = 0;
     bool bad = false;
     for (int u = 0; u < J.s; ++u) {
@@ -656,12 +668,14 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     __shared__ int s_flag[2];
+    __shared__ int s_tally[2];  // FP64 phase: pairs checked, pairs rotated (this CTA)
     extern __shared__ double sm[];
     const SvdJob J = jobs[blockIdx.x / kCl];
     const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nblk = 2 * kCl;
     const int b = (s + nblk - 1) / nblk, bs = b * s;
     const int stride = 2 * bs + 2 * b;  // one buffer: two blocks, 2b norms (FP64 layout)
+    if (tid == 0) s_tally[0] = s_tally[1] = 0;
     double *nrm_loc = sm + 2 * stride, *all_nrm = nrm_loc + 2 * b;
     const int px = rank, py = nblk - 1 - rank;
     // A. FP32 phase (the same buffers hold b x 2s floats per block)
@@ -722,7 +736,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     }
     __syncthreads();
     cur = 0;
-    const int sw64 = jacobi_sweeps<kCl, double>(cl, sm, stride, b, s, s, kMaxSweeps, g, cur, s_flag);
+    const int sw64 = jacobi_sweeps<kCl, double>(cl, sm, stride, b, s, s, kMaxSweeps, g, cur, s_flag, s_tally);
     double *D = sm + cur * stride;
     const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
     for (int q = warp; q < 2 * b; q += kNw) {
@@ -740,8 +754,17 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     }
     __syncthreads();
     jacobi_emit(J, D, gx, gy, b, all_nrm, lane, warp);
-    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, sw64, sw32);
-    cl.sync();  // no CTA leaves while another may still read its norms
+    if (rank == 0 && tid == 0) {
+        jacobi_rank(J, all_nrm, tau, sw64, sw32);
+        int chk = 0, rot = 0;
+        for (int k = 0; k < kCl; ++k) {
+            chk += cl.map_shared_rank(s_tally, k)[0];
+            rot += cl.map_shared_rank(s_tally, k)[1];
+        }
+        J.sweeps[2] = chk;
+        J.sweeps[3] = rot;
+    }
+    cl.sync();  // no CTA leaves while another may still read its norms or tallies
 }
 
 static size_t jacobi_sm_bytes(int s, int csize) {
@@ -780,8 +803,9 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
             }
             __syncthreads();
             block_norms(Ab, Nb, b, s, s, lane, warp);
+            int nchk = 0, nrot = 0;
             if (jacobi_block_pairs<double>(Ab, Ab + bs, Nb, Nb + b, bx, by, b, s, s, round == 0, lane, warp,
-                                           jacobi_tol2<double>(s)) &&
+                                           jacobi_tol2<double>(s), nchk, nrot) &&
                 lane == 0)
                 s_flag[sweep & 1] = 1;
             for (int e = tid; e < 2 * bs; e += kQrThreads) {
@@ -935,9 +959,24 @@ struct LaunchClass {
     std::vector<Job> jobs;
 };
 
+// Events around the launch of one class (profiling).
+struct ClassTiming {
+    int csize = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+static cudaEvent_t pooled_event(tlr_ctx *ctx, size_t &used) {
+    while (ctx->cls_time_events.size() <= used) {
+        cudaEvent_t e;
+        TLR_CUDA_TRY(cudaEventCreate(&e));
+        ctx->cls_time_events.push_back(e);
+    }
+    return ctx->cls_time_events[used++];
+}
+
 template <class Job, class K, class... Extra>
 static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClass<Job, K>> &cls,
-                           Extra... extra) {
+                           ClassTiming *timing, Extra... extra) {
     std::vector<LaunchClass<Job, K> *> use;
     for (auto &c : cls)
         if (!c.jobs.empty()) use.push_back(&c);
@@ -953,8 +992,16 @@ static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClas
     for (size_t k = 0; k < use.size(); ++k) {
         cudaStream_t cs = ctx->cls_stream[k % tlr_ctx::kClassStreams];
         TLR_CUDA_TRY(cudaStreamWaitEvent(cs, ctx->cls_fork, 0));
+        const bool timed = timing && timing->csize == use[k]->csize;
+        if (timed) TLR_CUDA_TRY(cudaEventRecord(timing->e0, cs));
         launch_cluster(use[k]->kernel, use[k]->csize, (int)use[k]->jobs.size(), use[k]->smem, cs, dj[k], extra...);
+        if (timed) TLR_CUDA_TRY(cudaEventRecord(timing->e1, cs));
         TLR_CUDA_TRY(cudaEventRecord(ctx->cls_join[k], cs));
+    }
+    if (timing) {  // a class that did not run leaves the events unrecorded
+        bool ran = false;
+        for (auto *c : use) ran |= (c->csize == timing->csize);
+        if (!ran) timing->csize = 0;
     }
     for (size_t k = 0; k < use.size(); ++k) TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->cls_join[k], 0));
 }
@@ -999,14 +1046,19 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
         add_to_class(cls, big ? (QrKernel)k_qr_gm<16> : (QrKernel)k_qr_gm<8>, top, 6 * (size_t)J.s * sizeof(double),
                      J);
     }
-    launch_classes(ctx, st, cls);
+    launch_classes(ctx, st, cls, (ClassTiming *)nullptr);
 }
 
-static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs, double tau) {
+// The SVD stage.  csize_of[u] receives the cluster size job u ran on (0 for
+// the global-memory variant); `timing` (optional) times one cluster size.
+static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs, double tau,
+                       std::vector<int> &csize_of, ClassTiming *timing) {
+    csize_of.assign(jobs.size(), 0);
     const bool big = cluster16_ok();
     const int top = big ? 16 : 8;
     std::vector<LaunchClass<SvdJob, SvdKernel>> cls;
-    for (const SvdJob &J : jobs) {
+    for (size_t u = 0; u < jobs.size(); ++u) {
+        const SvdJob &J = jobs[u];
         int c = svd_cluster(J.s);
         if (c > top) c = top;
         while (c < top && jacobi_sm_bytes(J.s, c) > smem_cap((const void *)svd_sm_kernel(c))) c = std::max(2 * c, 4);
@@ -1014,6 +1066,7 @@ static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> 
         size_t bytes = jacobi_sm_bytes(J.s, c);
         if (bytes <= smem_cap((const void *)k)) {
             add_to_class(cls, k, c, bytes, J);
+            csize_of[u] = c;
             continue;
         }
         SvdKernel kg = big ? (SvdKernel)k_jacobi_gm<16> : (SvdKernel)k_jacobi_gm<8>;
@@ -1021,7 +1074,7 @@ static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> 
         if (bytes > smem_cap((const void *)kg)) throw make_error(TLR_ERR_ARG, "sample size %d too large for this device", J.s);
         add_to_class(cls, kg, top, bytes, J);
     }
-    launch_classes(ctx, st, cls, tau);
+    launch_classes(ctx, st, cls, timing, tau);
 }
 
 __global__ void k_gaussian(double *__restrict__ a, int64_t count, uint64_t seed) {
@@ -1119,7 +1172,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oS[u] = take(s);
             oQ2[u] = df ? take((int64_t)J.m * s) : 0;  // float2, one double each
         }
-        DevBuf ws(tot * sizeof(double) + 3 * np * sizeof(int) + 256, st);
+        DevBuf ws(tot * sizeof(double) + 5 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
         int *d_rank = (int *)(W + tot);
         cmark();
@@ -1175,12 +1228,20 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
-            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 2 * u, ps[u]};
-        svd_launch(ctx, st, sv, tau);
+            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u]};
+        std::vector<int> svd_csize;
+        ClassTiming t16;
+        size_t ev_used = 0;
+        if (ctx->profile) {
+            t16.csize = 16;
+            t16.e0 = pooled_event(ctx, ev_used);
+            t16.e1 = pooled_event(ctx, ev_used);
+        }
+        svd_launch(ctx, st, sv, tau, svd_csize, ctx->profile ? &t16 : nullptr);
         cmark();
         // decisions on the host
-        std::vector<int> h_rank(3 * np);
-        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 3 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
+        std::vector<int> h_rank(5 * np);
+        TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 5 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
         if (overlap && !overlapped) {
             overlapped = true;
             overlap();
@@ -1191,9 +1252,31 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         ctx->comp_stats[0] += (long long)np;
         ctx->comp_stats[1] += 1;
         for (size_t u = 0; u < np; ++u) {
-            ctx->comp_stats[2] += h_rank[np + 2 * u];
-            ctx->comp_stats[3] = std::max(ctx->comp_stats[3], (long long)h_rank[np + 2 * u]);
-            ctx->comp_stats[4] += h_rank[np + 2 * u + 1];
+            const int *sw = h_rank.data() + np + 4 * u;
+            ctx->comp_stats[2] += sw[0];
+            ctx->comp_stats[3] = std::max(ctx->comp_stats[3], (long long)sw[0]);
+            ctx->comp_stats[4] += sw[1];
+        }
+        if (ctx->profile && t16.csize == 16) {
+            // FP64 work of the 16-CTA Jacobi launch, counted as executed:
+            // M1 = M J (2 s^3), the norms at each FP64 sweep and at the end
+            // (2 s^2 each), one dot product per pair checked (2 s), one
+            // rotation of two columns per pair rotated (6 s)
+            float ms = 0.f;
+            TLR_CUDA_TRY(cudaEventElapsedTime(&ms, t16.e0, t16.e1));
+            double fl = 0.0;
+            int jobs16 = 0;
+            for (size_t u = 0; u < np; ++u) {
+                if (svd_csize[u] != 16) continue;
+                const int *sw = h_rank.data() + np + 4 * u;
+                const double s = ps[u];
+                fl += 2.0 * s * s * s + 2.0 * s * s * (sw[0] + 1) + 2.0 * s * sw[2] + 6.0 * s * sw[3];
+                ++jobs16;
+            }
+            ctx->k16_ms += ms;
+            ctx->k16_flops += fl;
+            ctx->k16_launches += 1;
+            ctx->k16_clusters += jobs16;
         }
         std::vector<int> next;
         std::vector<GemmProb> gu, gv;

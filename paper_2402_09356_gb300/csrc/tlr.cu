@@ -92,6 +92,8 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     int prof_used = 0;
     for (double &v : ctx->comp_ms) v = 0.0;
     for (long long &v : ctx->comp_stats) v = 0;
+    ctx->k16_ms = ctx->k16_flops = 0.0;
+    ctx->k16_launches = ctx->k16_clusters = 0;
     R.assign((size_t)nt * nt, 0);
     for (int t = 0; t < nt; ++t) R[(size_t)t * nt + t] = tile_rows(n, nb, t);
     auto r_of = [&](int i, int k) { return (int)R[(size_t)i * nt + k]; };
