@@ -647,6 +647,7 @@ __device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, 
 }
 
 constexpr int kMaxSweeps32 = 12;
+constexpr int kRefineSteps = 3;  // FP64 Gram refinement steps after the FP32 sweeps
 
 // Block Jacobi with the blocks in shared memory, in two precisions.
 //  A. FP32 sweeps on fl32(M), M = R', carrying the accumulated rotations J
@@ -663,7 +664,11 @@ constexpr int kMaxSweeps32 = 12;
 // Shared memory: two buffers of two b x s blocks and 2b squared norms (FP64
 // layout; the FP32 phase stores b x 2s floats per block in the same bytes),
 // 2b local norms, s gathered norms.
-template <int kCl>
+// kMode: kJacFull runs A, B, C and writes W, S, rank; kJacPrecond runs A and
+// B only (M1 left in `work` for the FP64 Gram refinement); kJacFinish runs C
+// only, on the M1 found in `work`.
+enum { kJacFull = 0, kJacPrecond = 1, kJacFinish = 2 };
+template <int kCl, int kMode>
 __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs, double tau) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -678,6 +683,8 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     if (tid == 0) s_tally[0] = s_tally[1] = 0;
     double *nrm_loc = sm + 2 * stride, *all_nrm = nrm_loc + 2 * b;
     const int px = rank, py = nblk - 1 - rank;
+    int g = 0, cur = 0, sw32 = 0;
+    if (kMode != kJacFinish) {
     // A. FP32 phase (the same buffers hold b x 2s floats per block)
     float *f0 = reinterpret_cast<float *>(sm);
     const int s2 = 2 * s, bsf = b * s2, stride_f = 2 * bsf + 2 * b;
@@ -692,8 +699,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
         }
     }
     __syncthreads();
-    int g = 0, cur = 0;
-    const int sw32 = jacobi_sweeps<kCl, float>(cl, f0, stride_f, b, s, s2, kMaxSweeps32, g, cur, s_flag);
+    sw32 = jacobi_sweeps<kCl, float>(cl, f0, stride_f, b, s, s2, kMaxSweeps32, g, cur, s_flag);
     // B. M1 = M J for the held columns, 8 at a time; rows i = tid, tid + 256
     {
         const float *F = f0 + cur * stride_f;
@@ -725,6 +731,15 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
         }
     }
     cl.sync();  // M1 complete; no CTA reads another's FP32 blocks any more
+    if (kMode == kJacPrecond) {
+        if (rank == 0 && tid == 0) {
+            J.sweeps[0] = 0;
+            J.sweeps[1] = sw32;
+            J.sweeps[2] = J.sweeps[3] = 0;
+        }
+        return;
+    }
+    }  // kMode != kJacFinish
     // C. FP64 phase on M1, starting from the same block positions
     for (int slot = 0; slot < 2; ++slot) {
         const int blk = block_at(slot ? py : px, g, nblk);
@@ -765,6 +780,98 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
         J.sweeps[3] = rot;
     }
     cl.sync();  // no CTA leaves while another may still read its norms or tallies
+}
+
+// FP64 Gram refinement of M1 (the columns of which are orthogonal to FP32
+// accuracy after the preconditioning sweeps).  With G = M1'M1, every pair
+// (i < j) gets its one-sided Jacobi angle t_ij from (G_ii, G_jj, G_ij), and
+// all pairs are applied at once: M1 <- M1 (I + A), A_ij = t_ij, A_ji = -t_ij.
+// For simple singular values this is a Newton-type step that squares the
+// pairwise cosines |G_ij| / sqrt(G_ii G_jj) (~1e-6 -> ~1e-10 -> below the
+// FP64 threshold in three steps); I + A is orthogonal to second order, a
+// right multiplicative perturbation that moves the singular values by O(|A|^2)
+// relative.  Pairs of two columns below 0.1 tau are skipped: their mutual
+// orthogonality decides neither the rank nor the kept singular vectors.
+// off[0] receives the largest cosine over the other pairs (as ordered bits).
+struct RefineJob {
+    const double *G;   // s x s Gram matrix (ld s)
+    double *IA;        // s x s output I + A (ld s)
+    unsigned long long *off;
+    double tail2;      // (0.1 tau)^2
+    int s;
+};
+
+__global__ void k_refine_angles(const RefineJob *__restrict__ jobs) {
+    const RefineJob J = jobs[blockIdx.y];
+    const int s = J.s;
+    double worst = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < s * s; e += gridDim.x * blockDim.x) {
+        const int i = e % s, j = e / s;
+        double v = (i == j) ? 1.0 : 0.0;
+        if (i != j) {
+            const int a = min(i, j), b = max(i, j);
+            const double al = J.G[(int64_t)a * s + a], be = J.G[(int64_t)b * s + b], ga = J.G[(int64_t)b * s + a];
+            if (!(al < J.tail2 && be < J.tail2) && ga != 0.0) {
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                v = (i == a) ? t : -t;
+                const double c = fabs(ga) / sqrt(al * be);
+                worst = c == c ? fmax(worst, c) : INFINITY;
+            }
+        }
+        J.IA[e] = v;
+    }
+    for (int o = 16; o; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xFFFFFFFFu, worst, o));
+    if ((threadIdx.x & 31) == 0 && worst > 0.0) atomicMax(J.off, (unsigned long long)__double_as_longlong(worst));
+}
+
+// Singular values and vectors of the refined M1 (one CTA per job): column
+// norms, descending order (non-finite last), W = unit columns, S, and the
+// rank #{S > tau}: -1 for non-finite values, -2 when the refinement had not
+// converged (the caller then finishes with FP64 Jacobi sweeps).
+struct EmitJob {
+    const double *X;   // s x s refined M1 (ld s)
+    double *W;
+    double *S;
+    int *rank;
+    const unsigned long long *off;
+    int s;
+};
+
+__global__ void __launch_bounds__(kQrThreads) k_svd_emit(const EmitJob *__restrict__ jobs, double tau) {
+    extern __shared__ double nrm[];
+    const EmitJob J = jobs[blockIdx.x];
+    const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int u = warp; u < s; u += kNw) {
+        const double v = col_norm2(J.X + (int64_t)u * s, s, lane);
+        if (lane == 0) nrm[u] = sqrt(v);
+    }
+    __syncthreads();
+    for (int u = warp; u < s; u += kNw) {
+        const double ku = norm_key(nrm[u]);
+        int pos = 0;
+        for (int w = lane; w < s; w += 32) {
+            const double kw = norm_key(nrm[w]);
+            pos += (kw > ku) || (kw == ku && w < u);
+        }
+        pos = __reduce_add_sync(0xFFFFFFFFu, pos);
+        const double nv = nrm[u];
+        const bool unit = nv > 0.0 && nv <= 1.7e308;
+        const double *col = J.X + (int64_t)u * s;
+        for (int r = lane; r < s; r += 32) J.W[(int64_t)pos * s + r] = unit ? col[r] / nv : col[r];
+        if (lane == 0) J.S[pos] = nv;
+    }
+    if (tid == 0) {
+        int r = 0;
+        bool bad = false;
+        for (int u = 0; u < s; ++u) {
+            r += nrm[u] > tau;
+            bad |= !(nrm[u] <= 1.7e308);
+        }
+        const double off = __longlong_as_double((long long)*J.off);
+        const double tol = 8.0 * sqrt((double)s) * 1.1102230246251565e-16;
+        *J.rank = bad ? -1 : (off > tol ? -2 : r);
+    }
 }
 
 static size_t jacobi_sm_bytes(int s, int csize) {
@@ -890,14 +997,15 @@ static bool cluster16_ok() {
     static int state = -1;
     if (state < 0) {
         state = 0;
-        const void *k16[] = {(const void *)k_qr_sm<16>, (const void *)k_qr_gm<16>, (const void *)k_jacobi_sm<16>,
+        const void *k16[] = {(const void *)k_qr_sm<16>, (const void *)k_qr_gm<16>, (const void *)k_jacobi_sm<16, kJacFull>,
+                             (const void *)k_jacobi_sm<16, kJacPrecond>, (const void *)k_jacobi_sm<16, kJacFinish>,
                              (const void *)k_jacobi_gm<16>};
         bool ok = true;
         for (const void *k : k16)
             ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
         if (ok) {
             // one cluster of 16 CTAs that each fill an SM's shared memory must fit
-            const size_t need = std::min(smem_cap((const void *)k_qr_sm<16>), smem_cap((const void *)k_jacobi_sm<16>));
+            const size_t need = std::min(smem_cap((const void *)k_qr_sm<16>), smem_cap((const void *)k_jacobi_sm<16, kJacFull>));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16);
             cfg.blockDim = dim3(kQrThreads);
@@ -911,7 +1019,7 @@ static bool cluster16_ok() {
             cfg.numAttrs = 1;
             int n1 = 0, n2 = 0;
             if (cudaOccupancyMaxActiveClusters(&n1, k_qr_sm<16>, &cfg) == cudaSuccess &&
-                cudaOccupancyMaxActiveClusters(&n2, k_jacobi_sm<16>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
+                cudaOccupancyMaxActiveClusters(&n2, k_jacobi_sm<16, kJacFull>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
                 state = 1;
         }
         cudaGetLastError();  // clear any error of the queries
@@ -936,14 +1044,19 @@ static QrKernel qr_sm_kernel(int c) {
     default: return k_qr_sm<16>;
     }
 }
-static SvdKernel svd_sm_kernel(int c) {
+template <int kMode>
+static SvdKernel svd_sm_kernel_m(int c) {
     switch (c) {
-    case 1: return k_jacobi_sm<1>;
-    case 2: return k_jacobi_sm<2>;
-    case 4: return k_jacobi_sm<4>;
-    case 8: return k_jacobi_sm<8>;
-    default: return k_jacobi_sm<16>;
+    case 1: return k_jacobi_sm<1, kMode>;
+    case 2: return k_jacobi_sm<2, kMode>;
+    case 4: return k_jacobi_sm<4, kMode>;
+    case 8: return k_jacobi_sm<8, kMode>;
+    default: return k_jacobi_sm<16, kMode>;
     }
+}
+static SvdKernel svd_sm_kernel(int c, int mode) {
+    return mode == kJacPrecond ? svd_sm_kernel_m<kJacPrecond>(c)
+                               : (mode == kJacFinish ? svd_sm_kernel_m<kJacFinish>(c) : svd_sm_kernel_m<kJacFull>(c));
 }
 
 // One launch per (kernel, cluster size) class, with the class's largest
@@ -1052,7 +1165,7 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
 // The SVD stage.  csize_of[u] receives the cluster size job u ran on (0 for
 // the global-memory variant); `timing` (optional) times one cluster size.
 static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs, double tau,
-                       std::vector<int> &csize_of, ClassTiming *timing) {
+                       std::vector<int> &csize_of, ClassTiming *timing, int mode) {
     csize_of.assign(jobs.size(), 0);
     const bool big = cluster16_ok();
     const int top = big ? 16 : 8;
@@ -1061,8 +1174,8 @@ static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> 
         const SvdJob &J = jobs[u];
         int c = svd_cluster(J.s);
         if (c > top) c = top;
-        while (c < top && jacobi_sm_bytes(J.s, c) > smem_cap((const void *)svd_sm_kernel(c))) c = std::max(2 * c, 4);
-        SvdKernel k = svd_sm_kernel(c);
+        while (c < top && jacobi_sm_bytes(J.s, c) > smem_cap((const void *)svd_sm_kernel(c, mode))) c = std::max(2 * c, 4);
+        SvdKernel k = svd_sm_kernel(c, mode);
         size_t bytes = jacobi_sm_bytes(J.s, c);
         if (bytes <= smem_cap((const void *)k)) {
             add_to_class(cls, k, c, bytes, J);
@@ -1154,7 +1267,8 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
     while (!pending.empty()) {
         const size_t np = pending.size();
         // workspace offsets (doubles)
-        std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np), oQ2(np);
+        std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np), oQ2(np), oX2(np), oG(np),
+            oIA(np);
         std::vector<int> ps(np);
         int64_t tot = 0;
         auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
@@ -1171,10 +1285,14 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oK[u] = take((int64_t)s * s);
             oS[u] = take(s);
             oQ2[u] = df ? take((int64_t)J.m * s) : 0;  // float2, one double each
+            oX2[u] = take((int64_t)s * s);
+            oG[u] = take((int64_t)s * s);
+            oIA[u] = take((int64_t)s * s);
         }
-        DevBuf ws(tot * sizeof(double) + 5 * np * sizeof(int) + 256, st);
+        DevBuf ws(tot * sizeof(double) + np * sizeof(unsigned long long) + 5 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
-        int *d_rank = (int *)(W + tot);
+        unsigned long long *d_off = (unsigned long long *)(W + tot);
+        int *d_rank = (int *)(d_off + np);
         cmark();
         // 1. Y = T Omega_s
         std::vector<GemmProb> g1;
@@ -1237,7 +1355,59 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             t16.e0 = pooled_event(ctx, ev_used);
             t16.e1 = pooled_event(ctx, ev_used);
         }
-        svd_launch(ctx, st, sv, tau, svd_csize, ctx->profile ? &t16 : nullptr);
+        svd_launch(ctx, st, sv, tau, svd_csize, ctx->profile ? &t16 : nullptr, kJacPrecond);
+        // FP64 Gram refinement (batched over the tiles), then W, S and the rank
+        std::vector<double *> xfin(np, nullptr);
+        {
+            std::vector<size_t> rj;
+            int smax = 0;
+            for (size_t u = 0; u < np; ++u)
+                if (svd_csize[u] > 0) {
+                    rj.push_back(u);
+                    smax = std::max(smax, ps[u]);
+                }
+            if (!rj.empty()) {
+                std::vector<double *> X(np), Xn(np);
+                for (size_t u : rj) {
+                    X[u] = W + oK[u];
+                    Xn[u] = W + oX2[u];
+                }
+                for (int it = 0; it < kRefineSteps; ++it) {
+                    std::vector<GemmProb> gg, gx;
+                    std::vector<RefineJob> rjobs;
+                    for (size_t u : rj) {
+                        const int sz = ps[u];
+                        GemmProb a{};
+                        a.A = X[u]; a.lda = sz; a.m = sz; a.k = sz;
+                        a.B = X[u]; a.ldb = sz; a.n = sz;
+                        a.C = W + oG[u]; a.ldc = sz;
+                        gg.push_back(a);
+                        rjobs.push_back(RefineJob{W + oG[u], W + oIA[u], d_off + u, 0.01 * tau * tau, sz});
+                        GemmProb b{};
+                        b.A = X[u]; b.lda = sz; b.m = sz; b.k = sz;
+                        b.B = W + oIA[u]; b.ldb = sz; b.n = sz;
+                        b.C = Xn[u]; b.ldc = sz;
+                        gx.push_back(b);
+                    }
+                    gemm_batched(ctx, st, true, false, gg, 1.0, 0.0);
+                    TLR_CUDA_TRY(cudaMemsetAsync(d_off, 0, np * sizeof(unsigned long long), st));
+                    auto *dr = (const RefineJob *)stage_push(ctx, rjobs.data(), rjobs.size() * sizeof(RefineJob), st);
+                    launch(k_refine_angles, dim3((unsigned)std::min<int64_t>(ceil_div(smax * smax, 256), 64),
+                                                 (unsigned)rjobs.size()), 256, 0, st, dr);
+                    TLR_CHECK_LAUNCH();
+                    gemm_batched(ctx, st, false, false, gx, 1.0, 0.0);
+                    for (size_t u : rj) std::swap(X[u], Xn[u]);
+                }
+                std::vector<EmitJob> ej;
+                for (size_t u : rj) {
+                    ej.push_back(EmitJob{X[u], W + oW[u], W + oS[u], d_rank + u, d_off + u, ps[u]});
+                    xfin[u] = X[u];
+                }
+                auto *de = (const EmitJob *)stage_push(ctx, ej.data(), ej.size() * sizeof(EmitJob), st);
+                launch(k_svd_emit, (unsigned)ej.size(), kQrThreads, (size_t)smax * sizeof(double), st, de, tau);
+                TLR_CHECK_LAUNCH();
+            }
+        }
         cmark();
         // decisions on the host
         std::vector<int> h_rank(5 * np);
@@ -1248,6 +1418,19 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         }
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
         if (st != ctx->aux) stage_reset_main(ctx);
+        {
+            // tiles whose Gram refinement did not converge: FP64 Jacobi sweeps on the refined M1
+            std::vector<SvdJob> fin;
+            for (size_t u = 0; u < np; ++u)
+                if (h_rank[u] == -2)
+                    fin.push_back(SvdJob{W + oR[u], xfin[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u]});
+            if (!fin.empty()) {
+                std::vector<int> cs_fin;
+                svd_launch(ctx, st, fin, tau, cs_fin, nullptr, kJacFinish);
+                TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 5 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
+                TLR_CUDA_TRY(cudaStreamSynchronize(st));
+            }
+        }
         cmark();
         ctx->comp_stats[0] += (long long)np;
         ctx->comp_stats[1] += 1;
