@@ -95,6 +95,9 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
         TLR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
         TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_hi));
         TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->la, cudaStreamNonBlocking, prio_lo));
+        TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->hp, cudaStreamNonBlocking, prio_hi));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_hp_fork, cudaEventDisableTiming));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_hp_join, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_la_fork, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_la_join, cudaEventDisableTiming));
         for (cudaStream_t &c : ctx->cls_stream)
@@ -128,7 +131,8 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->la) cudaStreamDestroy(ctx->la);
-    for (cudaEvent_t e : {ctx->ev_la_fork, ctx->ev_la_join})
+    if (ctx->hp) cudaStreamDestroy(ctx->hp);
+    for (cudaEvent_t e : {ctx->ev_la_fork, ctx->ev_la_join, ctx->ev_hp_fork, ctx->ev_hp_join})
         if (e) cudaEventDestroy(e);
     for (cudaStream_t c : ctx->cls_stream)
         if (c) cudaStreamDestroy(c);

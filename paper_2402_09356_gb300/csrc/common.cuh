@@ -115,14 +115,16 @@ struct tlr_ctx {
     cudaStream_t aux = nullptr;           // second stream for concurrent tile work (high priority)
     cudaStream_t la = nullptr;            // look-ahead stream: the next column's panel update
     cudaEvent_t ev_la_fork = nullptr, ev_la_join = nullptr;
+    cudaStream_t hp = nullptr;            // high-priority stream of the factorisation's compression
+    cudaEvent_t ev_hp_fork = nullptr, ev_hp_join = nullptr;
     // compression: one stream per launch class (cluster size), forked from and
     // joined to the calling stream
     static constexpr int kClassStreams = 4, kClassEvents = 8;
     cudaStream_t cls_stream[kClassStreams] = {};
     cudaEvent_t cls_fork = nullptr, cls_join[kClassEvents] = {};
     cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_fork = nullptr, ev_join = nullptr;
-    // descriptor staging: ring 0 for the caller's stream, 1 for `aux`, 2 for `la`
-    tlr::StageRing stage[3];
+    // descriptor staging: ring 0 for the caller's stream, 1 for `aux`, 2 for `la`, 3 for `hp`
+    tlr::StageRing stage[4];
     // fixed Gaussian test matrices of the randomised range finder
     double *d_omega = nullptr;
     float2 *d_omega2 = nullptr;  // paired-FP32 copy of d_omega
@@ -162,7 +164,11 @@ struct tlr_mat {
 
 namespace tlr {
 
-inline void stage_reset_main(tlr_ctx *ctx) { ctx->stage[0].off = 0; }
+inline int stage_ring(const tlr_ctx *ctx, cudaStream_t s) {
+    return s == ctx->aux ? 1 : (s == ctx->la ? 2 : (s == ctx->hp ? 3 : 0));
+}
+// Marks the ring of stream s empty; only valid right after a sync of s.
+inline void stage_reset(tlr_ctx *ctx, cudaStream_t s) { ctx->stage[stage_ring(ctx, s)].off = 0; }
 
 inline int64_t off_index(int i, int j) { return (int64_t)i * (i - 1) / 2 + j; }
 inline int tile_rows(int64_t n, int nb, int t) {
@@ -170,12 +176,10 @@ inline int tile_rows(int64_t n, int nb, int t) {
     return (int)(r < nb ? r : nb);
 }
 
-// Copies `bytes` of host data into the staging ring of stream `s` (ring 1 for
-// ctx->aux, ring 0 otherwise) and returns the device address of the copy
-// (stream ordered on `s`).
+// Copies `bytes` of host data into the staging ring of stream `s` (one ring
+// per internal stream, ring 0 for the caller's) and returns the device address
+// of the copy (stream ordered on `s`).
 void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s);
-// Marks ring 0 empty; only valid right after a sync of the stream that uses it.
-inline void stage_reset_main(tlr_ctx *ctx);
 
 // Status word helpers (host side).
 void status_reset(tlr_ctx *ctx, cudaStream_t s);

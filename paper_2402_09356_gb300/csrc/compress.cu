@@ -1417,7 +1417,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             overlap();
         }
         TLR_CUDA_TRY(cudaStreamSynchronize(st));
-        if (st != ctx->aux) stage_reset_main(ctx);
+        stage_reset(ctx, st);
         {
             // tiles whose Gram refinement did not converge: FP64 Jacobi sweeps on the refined M1
             std::vector<SvdJob> fin;

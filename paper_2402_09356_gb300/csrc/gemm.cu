@@ -1,6 +1,7 @@
 // Batched FP64 GEMM launchers and the descriptor staging buffers of a context.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "gemm.cuh"
@@ -8,7 +9,7 @@
 namespace tlr {
 
 void *stage_push(tlr_ctx *ctx, const void *data, size_t bytes, cudaStream_t s) {
-    StageRing &R = ctx->stage[(s == ctx->aux) ? 1 : (s == ctx->la ? 2 : 0)];
+    StageRing &R = ctx->stage[stage_ring(ctx, s)];
     size_t need = (bytes + 255) & ~(size_t)255;
     if (need > R.cap) throw make_error(TLR_ERR_ARG, "descriptor batch too large (%zu bytes)", bytes);
     if (R.off + need > R.cap) {
@@ -144,7 +145,8 @@ void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vec
 }
 
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
-                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df, int max_ctas) {
+                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df, int max_ctas,
+                         int ctas_per_sm) {
     if (!tb) throw make_error(TLR_ERR_ARG, "the Matern panel product takes B transposed");
     EpiMatern e;
     e.xy = xy;
@@ -163,23 +165,27 @@ void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vecto
     auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
     int np = (int)big.size();
     const int grid = max_ctas > 0 ? std::min(total, max_ctas) : total;
-    // a capped grid also reserves more than half of an SM's shared memory per
-    // CTA (unused), so that each of its CTAs holds an SM of its own and the
-    // other SMs stay free for the critical-path kernels
+    // A capped grid reserves more than half of an SM's shared memory per CTA
+    // (unused), so that each of its CTAs holds an SM of its own; ctas_per_sm
+    // = k reserves more than 1/(k+1) of it, so that at most k CTAs of this
+    // product share an SM and the rest of every SM stays open to the
+    // critical-path kernels on the high-priority streams.
     size_t smem = 0;
-    if (max_ctas > 0) {
-        static size_t reserve = 0;
-        if (reserve == 0) {
-            int dev = 0, per_sm = 0;
-            TLR_CUDA_TRY(cudaGetDevice(&dev));
-            TLR_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-            size_t r = (size_t)per_sm / 2 + 1024;
+    const int per = max_ctas > 0 ? 1 : ctas_per_sm;
+    if (per > 0) {
+        static std::mutex mu;
+        static size_t set_to = 0;
+        int dev = 0, per_sm = 0;
+        TLR_CUDA_TRY(cudaGetDevice(&dev));
+        TLR_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        smem = (size_t)per_sm / (per + 1) + 1024;
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem > set_to) {
             for (const void *k : {(const void *)k_gemm_df<64, 64, false, true, EpiMatern>,
                                   (const void *)k_gemm_f64<64, 64, false, true, EpiMatern>})
-                TLR_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r));
-            reserve = r;
+                TLR_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            set_to = smem;
         }
-        smem = reserve;
     }
     if (df) launch(k_gemm_df<64, 64, false, true, EpiMatern>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
     else launch(k_gemm_f64<64, 64, false, true, EpiMatern>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);

@@ -290,10 +290,11 @@ void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc>
 // pipe); every problem must then carry A2/B2 copies made by split_f2.
 void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
                   double alpha, double beta, bool df = false);
-// max_ctas > 0 caps the grid (the CTAs then loop over the tiles), so that a
-// product running beside critical-path work leaves SMs free.
+// For a product running beside critical-path work: max_ctas > 0 caps the
+// grid (the CTAs then loop over the tiles, one per SM); ctas_per_sm > 0
+// allows at most that many of its CTAs on one SM.
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
                          double alpha, const double *xy, int64_t n, const MaternParams &P, bool df = false,
-                         int max_ctas = 0);
+                         int max_ctas = 0, int ctas_per_sm = 0);
 
 }  // namespace tlr

@@ -27,6 +27,8 @@
 
 namespace tlr {
 
+constexpr int kAheadCtasPerSm = 2;
+
 // blockIdx.y: descriptor; blockIdx.x strides over its columns, threads over rows.
 __global__ void k_copy_batched(const CopyDesc *__restrict__ d) {
     const CopyDesc c = d[blockIdx.y];
@@ -102,10 +104,11 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     // most SMs idle); only the update by column j itself stays on the
     // critical path.  Two panel buffers alternate between the columns.
     const bool ahead = (mode == FactorMode::Matern) && nt > 1;
-    // The look-ahead panel GEMM runs uncapped at the lowest stream priority:
-    // capping it to a subset of the SMs (max_ctas > 0) starves the
-    // compression's bursts of wide launches and measured slower.
-    const int ahead_ctas = 0;
+    // The look-ahead panel GEMM runs at the lowest stream priority with at most
+    // two of its CTAs per SM, so that every SM keeps room for the compression
+    // (on a high-priority stream) and the diagonal POTRF.  (Giving it a fixed
+    // subset of whole SMs starved the compression's wide launches instead.)
+    const int ahead_ctas = kAheadCtasPerSm;
     DevBuf panel_buf[2];
     panel_buf[0].alloc((size_t)nt * nb * nb * sizeof(double), st);
     if (ahead) panel_buf[1].alloc((size_t)nt * nb * nb * sizeof(double), st);
@@ -162,6 +165,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             if (std::uncaught_exceptions()) {
                 cudaStreamSynchronize(ctx->la);
                 cudaStreamSynchronize(ctx->aux);
+                cudaStreamSynchronize(ctx->hp);
             }
         }
     } side_guard{ctx};
@@ -172,7 +176,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     // with Q = [U_ck]_k and the P block (i, k) = U_ik W_ik, W_ik = V_ik' V_ck a
     // block of G_k.  The whole panel is one GEMM; all work on stream s.
     auto panel_update = [&](int c, int k0, int k1, double *T, cudaStream_t s, bool generate,
-                            std::vector<DMark> &dm, int det_build, int det_gemm, int max_ctas) {
+                            std::vector<DMark> &dm, int det_build, int det_gemm, int ctas_per_sm) {
         const int mc = tile_rows(n, nb, c);
         const int64_t Mp = (int64_t)(nt - c) * nb;
         std::vector<int> off(std::max(k1 - k0, 0) + 1, 0);
@@ -223,7 +227,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         }
         dmark(dm, s, det_build);
         if (generate) {
-            gemm_batched_matern(ctx, s, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df, max_ctas);
+            gemm_batched_matern(ctx, s, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df, 0, ctas_per_sm);
             stats->matern_entries += (double)rows_valid * mc;
             stats->panel_launches += 1;
         } else if (Rc > 0) {
@@ -409,7 +413,14 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         std::vector<int> rk;
         long long bad = -1, nan = -1;
         dmark(dm_main, st, kDetDiagCopy);
-        if (!jobs.empty()) compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan, df);
+        if (!jobs.empty()) {
+            // on the high-priority stream, ahead of the look-ahead GEMM
+            TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_fork, st));
+            TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->hp, ctx->ev_hp_fork, 0));
+            compress_tiles(ctx, ctx->hp, jobs, tau, M->maxrank, rk, &bad, &nan, df);
+            TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_join, ctx->hp));
+            TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_hp_join, 0));
+        }
         mark();
         dmark(dm_main, st, kDetCompress);
         TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
