@@ -27,7 +27,7 @@
 
 namespace tlr {
 
-constexpr int kAheadCtasPerSm = 2;
+constexpr int kAheadCtasPerSm = 1;
 
 // blockIdx.y: descriptor; blockIdx.x strides over its columns, threads over rows.
 __global__ void k_copy_batched(const CopyDesc *__restrict__ d) {
@@ -105,9 +105,11 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     // critical path.  Two panel buffers alternate between the columns.
     const bool ahead = (mode == FactorMode::Matern) && nt > 1;
     // The look-ahead panel GEMM runs at the lowest stream priority with at most
-    // two of its CTAs per SM, so that every SM keeps room for the compression
-    // (on a high-priority stream) and the diagonal POTRF.  (Giving it a fixed
-    // subset of whole SMs starved the compression's wide launches instead.)
+    // one of its CTAs per SM, so that every SM keeps room (threads and shared
+    // memory) for the compression (on a high-priority stream) and the
+    // diagonal POTRF.  Two per SM left too little shared memory for the
+    // compression's cluster kernels; a fixed subset of whole SMs starved the
+    // compression's wide launches.
     const int ahead_ctas = kAheadCtasPerSm;
     DevBuf panel_buf[2];
     panel_buf[0].alloc((size_t)nt * nb * nb * sizeof(double), st);
