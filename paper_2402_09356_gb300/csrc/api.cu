@@ -149,6 +149,7 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     }
     if (ctx->d_omega) cudaFree(ctx->d_omega);
     if (ctx->d_omega2) cudaFree(ctx->d_omega2);
+    if (ctx->d_potrf_scratch) cudaFree(ctx->d_potrf_scratch);
     if (ctx->d_mtab) cudaFree(ctx->d_mtab);
     delete ctx;
 }

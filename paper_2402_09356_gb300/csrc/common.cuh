@@ -66,6 +66,26 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
     g_launch_count.fetch_add(1, std::memory_order_relaxed);
 }
 
+// Launch on thread-block clusters of `csize` CTAs (counted like launch()).
+template <typename... KArgs, typename... Args>
+inline void launch_clustered(void (*kernel)(KArgs...), int csize, int nclusters, int threads, size_t smem,
+                             cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nclusters * csize));
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TLR_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, args...));
+    g_launch_count.fetch_add(1, std::memory_order_relaxed);
+}
+
 // Stream-ordered device buffer from the CUDA memory pool.
 class DevBuf {
 public:
@@ -145,6 +165,7 @@ struct tlr_ctx {
     long long comp_stats[5] = {0, 0, 0, 0, 0};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum)
     // the 16-CTA cluster Jacobi (profiling): device ms, FP64 flops, launches, clusters
     std::vector<cudaEvent_t> cls_time_events;
+    double *d_potrf_scratch = nullptr;  // diagonal-block inverses of the cluster POTRF
     double k16_ms = 0.0, k16_flops = 0.0;
     long long k16_launches = 0, k16_clusters = 0;
 };

@@ -6,11 +6,15 @@
 // Blocks of 32 rows/columns are factored or solved by one CTA in shared
 // memory; everything else is a batched GEMM update so that it spreads over
 // the whole GPU (one SM's FP64 pipe alone would take milliseconds per tile).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "dense.cuh"
 #include "gemm.cuh"
 
 namespace tlr {
+
+namespace cg = cooperative_groups;
 
 constexpr int kBlk = 32;
 constexpr int kStrip = 64;  // column strips of the trailing update
@@ -118,6 +122,215 @@ void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long l
     TLR_CHECK_LAUNCH();
 }
 
+// ---------------------------------------------------------------------------
+// Cholesky and inverse of one diagonal tile in a single launch.
+//
+// One cluster of kCl CTAs; the tile (m <= 1024, column major) stays in global
+// memory, which for one tile is L2-resident, and every load goes to L2
+// (__ldcg: another CTA may have written the line in an earlier phase).  A
+// cluster barrier (release/acquire at cluster scope) separates dependent
+// phases.  With 32-wide blocks, block step k of the right-looking Cholesky:
+//   1. CTA 0 factors the diagonal block L_kk and inverts it (shared memory),
+//      the inverse kept in `dinv` for step 2 and for L^-1;
+//   2. every thread of the cluster takes one row r below the block:
+//      A[r, k-block] <- A[r, k-block] L_kk^-T;
+//   3. the trailing lower triangle A_IJ -= P_I P_J' by 32 x 32 output tiles
+//      spread round-robin over the CTAs.
+// Then X = L^-1 by right-looking substitution on X = I: block step k applies
+// X[k, :] <- L_kk^-1 X[k, :] (columns over all threads), then
+// X[I, :] -= L_Ik X[k, :] for the rows below (tiles over the CTAs).
+// FP64 throughout.  A non-positive pivot sets NOT_SPD (info = row_base + row)
+// and every CTA leaves at the next barrier.
+constexpr int kPotrfThreads = 256;
+
+// C (32 x 32, rows r0.., cols c0.. of a column-major matrix) -= A B' or A B:
+// a, b are 32 x 32 operand blocks already in shared memory as [row][k].
+__device__ __forceinline__ void tile_update32(double *C, int ldc, const double (*a)[kBlk + 1],
+                                              const double (*b)[kBlk + 1], int rows, int cols, bool lower_only) {
+    const int tid = threadIdx.x, tr = (tid & 15) * 2, tc = (tid >> 4) * 2;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll 8
+    for (int k = 0; k < kBlk; ++k) {
+        const double a0 = a[tr][k], a1 = a[tr + 1][k], b0 = b[tc][k], b1 = b[tc + 1][k];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const int r = tr + x, c = tc + y;
+            if (r < rows && c < cols && (!lower_only || c <= r)) {
+                double *p = C + (int64_t)c * ldc + r;
+                *p = __ldcg(p) - acc[x][y];
+            }
+        }
+}
+
+// `scratch`: 32 x 1024 doubles for the diagonal block inverses, then one
+// word through which CTA 0 tells the cluster to stop (the context's status
+// word may be set by kernels on other streams at any time, so the CTAs do not
+// each read it to decide).
+template <int kCl>
+__global__ void __launch_bounds__(kPotrfThreads)
+k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevStatus *st, long long row_base) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), tid = threadIdx.x;
+    const int gtid = rank * kPotrfThreads + tid, gthreads = kCl * kPotrfThreads;
+    __shared__ double sa[kBlk][kBlk + 1], sb[kBlk][kBlk + 1], sl[kBlk][kBlk + 1];
+    __shared__ int s_bad;
+    const int nbk = (m + kBlk - 1) / kBlk;
+    double *dinv = scratch;
+    long long *stop = reinterpret_cast<long long *>(scratch + (int64_t)kBlk * kBlk * kBlk);
+    if (rank == 0 && tid == 0) __stcg(stop, __ldcg(&st->code) ? 1LL : 0LL);
+    cl.sync();
+    if (__ldcg(stop)) return;
+    for (int kb = 0; kb < nbk; ++kb) {
+        const int p = kb * kBlk, w = min(kBlk, m - p);
+        double *Li = dinv + (int64_t)kb * kBlk * kBlk;  // L_kk^-1, [row][col] row major, 32 x 32
+        // 1. diagonal block
+        if (rank == 0) {
+            for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+                const int r = e % kBlk, c = e / kBlk;
+                sa[r][c] = (r < w && c < w && c <= r) ? __ldcg(A + (int64_t)(p + c) * lda + p + r) : 0.0;
+            }
+            if (tid == 0) s_bad = -1;
+            __syncthreads();
+            if (tid < kBlk) {
+                const int r = tid;
+                for (int c = 0; c < w; ++c) {
+                    if (r == c) {
+                        const double d = sa[c][c];
+                        if (!(d > 0.0)) s_bad = c;
+                        else sa[c][c] = sqrt(d);
+                    }
+                    __syncwarp();
+                    if (s_bad >= 0) break;
+                    if (r > c && r < w) sa[r][c] /= sa[c][c];
+                    __syncwarp();
+                    if (r > c && r < w) {
+                        const double lrc = sa[r][c];
+                        for (int cc = c + 1; cc <= r; ++cc) sa[r][cc] -= lrc * sa[cc][c];
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            if (s_bad >= 0) {
+                if (tid == 0) {
+                    set_status(st, TLR_ERR_NOT_SPD, row_base + p + s_bad);
+                    __stcg(stop, 1LL);
+                }
+            } else {
+                // inverse of the lower triangular block: column c of L^-1 by thread c
+                if (tid < kBlk) {
+                    const int c = tid;
+                    for (int r = 0; r < kBlk; ++r) {
+                        double v = 0.0;
+                        if (c < w && r < w && r >= c) {
+                            v = (r == c) ? 1.0 : 0.0;
+                            for (int k = c; k < r; ++k) v -= sa[r][k] * sl[k][c];
+                            v /= sa[r][r];
+                        }
+                        sl[r][c] = v;
+                    }
+                }
+                __syncthreads();
+                for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+                    const int r = e % kBlk, c = e / kBlk;
+                    if (r < w && c < w) A[(int64_t)(p + c) * lda + p + r] = (c <= r) ? sa[r][c] : 0.0;
+                    Li[r * kBlk + c] = sl[r][c];
+                }
+            }
+        }
+        cl.sync();
+        if (__ldcg(stop)) return;  // written by CTA 0 only, before the barrier
+        // 2. panel rows below the block: x <- a L_kk^-T, x_c = sum_{k<=c} a_k Linv[c][k]
+        for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) sl[e / kBlk][e % kBlk] = __ldcg(Li + e);
+        __syncthreads();
+        for (int r = p + w + gtid; r < m; r += gthreads) {
+            double a[kBlk];
+#pragma unroll
+            for (int k = 0; k < kBlk; ++k) a[k] = k < w ? __ldcg(A + (int64_t)(p + k) * lda + r) : 0.0;
+#pragma unroll
+            for (int c = 0; c < kBlk; ++c) {
+                if (c >= w) break;
+                double x = 0.0;
+#pragma unroll
+                for (int k = 0; k <= c; ++k) x = fma(a[k], sl[c][k], x);
+                A[(int64_t)(p + c) * lda + r] = x;
+            }
+        }
+        cl.sync();
+        // 3. trailing update of the lower triangle, tiles (bi >= bj > kb)
+        const int nt = nbk - kb - 1;
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int t = rank; t < ntiles; t += kCl) {
+            int bi = 0, rem = t;  // t -> (bi, bj), bi = kb+1+i, bj = kb+1+j, j <= i
+            while (rem > bi) { rem -= bi + 1; ++bi; }
+            const int I = kb + 1 + bi, Jb = kb + 1 + rem;
+            const int ri = I * kBlk, cj = Jb * kBlk;
+            const int rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
+            __syncthreads();
+            for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+                const int r = e % kBlk, k = e / kBlk;
+                sa[r][k] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
+                sb[r][k] = (r < cols && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + cj + r) : 0.0;
+            }
+            __syncthreads();
+            tile_update32(A + (int64_t)cj * lda + ri, lda, sa, sb, rows, cols, I == Jb);
+        }
+        cl.sync();
+    }
+    // zero the strict upper triangle; X = I
+    for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
+        const int r = (int)(e % m), c = (int)(e / m);
+        if (r < c) A[(int64_t)c * lda + r] = 0.0;
+        X[(int64_t)c * ldx + r] = (r == c) ? 1.0 : 0.0;
+    }
+    cl.sync();
+    for (int kb = 0; kb < nbk; ++kb) {
+        const int p = kb * kBlk, w = min(kBlk, m - p), ncols = p + w;
+        const double *Li = dinv + (int64_t)kb * kBlk * kBlk;
+        for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) sl[e / kBlk][e % kBlk] = __ldcg(Li + e);
+        __syncthreads();
+        // a. X[k-block, c] <- L_kk^-1 X[k-block, c] for the columns c < p + w
+        for (int c = gtid; c < ncols; c += gthreads) {
+            double x[kBlk];
+#pragma unroll
+            for (int k = 0; k < kBlk; ++k) x[k] = k < w ? __ldcg(X + (int64_t)c * ldx + p + k) : 0.0;
+#pragma unroll
+            for (int r = 0; r < kBlk; ++r) {
+                if (r >= w) break;
+                double v = 0.0;
+#pragma unroll
+                for (int k = 0; k <= r; ++k) v = fma(sl[r][k], x[k], v);
+                X[(int64_t)c * ldx + p + r] = v;
+            }
+        }
+        cl.sync();
+        // b. X[I, J] -= L[I, k] X[k, J] for row blocks I > k and column blocks J <= k
+        const int nI = nbk - kb - 1, nJ = kb + 1, ntiles = nI * nJ;
+        for (int t = rank; t < ntiles; t += kCl) {
+            const int I = kb + 1 + t % nI, Jb = t / nI;
+            const int ri = I * kBlk, cj = Jb * kBlk;
+            const int rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
+            __syncthreads();
+            for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+                const int r = e % kBlk, k = e / kBlk;
+                sa[r][k] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
+                // b operand as [col][k]: X[p + k, cj + col]
+                sb[r][k] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
+            }
+            __syncthreads();
+            tile_update32(X + (int64_t)cj * ldx + ri, ldx, sa, sb, rows, cols, false);
+        }
+        cl.sync();
+    }
+}
+
 // Solve L X = B for the 32-row block at p0 of every right-hand side column.
 // Columns of all problems are concatenated; col_off gives each problem's start.
 __global__ void k_trsm_left_block(const double *__restrict__ Lm, int ldl, int m, int p0,
@@ -192,6 +405,39 @@ void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int
         }
         gemm_batched(ctx, s, false, false, probs, -1.0, 1.0);
     }
+}
+
+void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *X, int ldx, long long row_base) {
+    if (m <= 0) return;
+    if (m > kBlk * kBlk) throw make_error(TLR_ERR_ARG, "tile too large for the cluster POTRF (%d)", m);
+    if (!ctx->d_potrf_scratch)
+        TLR_CUDA_TRY(cudaMalloc(&ctx->d_potrf_scratch, ((size_t)kBlk * kBlk * kBlk + 8) * sizeof(double)));
+    static int csize = 0;  // 16 CTAs where the device runs such clusters, else 8
+    if (csize == 0) {
+        csize = 8;
+        if (cudaFuncSetAttribute(k_potrf_inv<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16);
+            cfg.blockDim = dim3(kPotrfThreads);
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 16;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_potrf_inv<16>, &cfg) == cudaSuccess && nclusters > 0)
+                csize = 16;
+        }
+        cudaGetLastError();  // clear any error of the queries
+    }
+    if (csize == 16)
+        launch_clustered(k_potrf_inv<16>, 16, 1, kPotrfThreads, 0, s, A, lda, m, X, ldx, ctx->d_potrf_scratch,
+                         ctx->d_status, row_base);
+    else
+        launch_clustered(k_potrf_inv<8>, 8, 1, kPotrfThreads, 0, s, A, lda, m, X, ldx, ctx->d_potrf_scratch,
+                         ctx->d_status, row_base);
 }
 
 // acc[0] += sum_r log A[r, r]  (one block, fixed reduction order)

@@ -18,6 +18,12 @@ struct RhsDesc {
 // context status to TLR_ERR_NOT_SPD with info = row_base + local row.
 void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long long row_base);
 
+// A = L L' in place (lower; strict upper zeroed) and X = L^-1 (m x m, lower,
+// ld ldx) in one launch on one thread-block cluster; m <= 1024.  A
+// non-positive pivot sets NOT_SPD (info = row_base + local row); X is then
+// not written.
+void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *X, int ldx, long long row_base);
+
 // B <- L^-1 B for every right-hand side matrix (L lower triangular m x m).
 void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int m,
                      const std::vector<RhsDesc> &rhs);

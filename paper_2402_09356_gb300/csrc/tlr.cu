@@ -372,11 +372,8 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             aux_marks.push_back(ctx->prof_events[prof_used++]);
         }
         dmark(dm_aux, ctx->aux, -1);
-        potrf_dense(ctx, ctx->aux, Dj, nb, mj, (long long)j * nb);
+        potrf_inv(ctx, ctx->aux, Dj, nb, mj, Xinv, nb, (long long)j * nb);  // one cluster launch
         dmark(dm_aux, ctx->aux, kDetPotrf);
-        set_identity(ctx->aux, Xinv, nb, mj);
-        trsm_left_lower(ctx, ctx->aux, Dj, nb, mj, {RhsDesc{Xinv, mj, nb}});
-        dmark(dm_aux, ctx->aux, kDetInverse);
         if (ctx->profile) {
             profile_events(ctx, prof_used + 1);
             TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));

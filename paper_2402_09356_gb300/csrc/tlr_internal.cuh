@@ -33,8 +33,8 @@ enum DetailBucket {
     kDetTrsm,        // V_ij <- L_jj^-1 V_ij
     kDetSolve,       // y_j <- L_jj^-1 y_j, log-determinant and |y|^2 terms, V_j' y_j
     kDetGram,        // G_j = V_j' V_j
-    kDetPotrf,       // side stream: dense POTRF of the diagonal tile
-    kDetInverse,     // side stream: L_jj^-1
+    kDetPotrf,       // side stream: dense POTRF of the diagonal tile and L_jj^-1 (one launch)
+    kDetInverse,     // unused (the inverse is part of the POTRF launch)
     kDetAheadBuild,  // look-ahead stream: P, Q operands of the next column's update
     kDetAheadPanel,  // look-ahead stream: the next column's panel GEMM (Matern epilogue)
     kDetail
