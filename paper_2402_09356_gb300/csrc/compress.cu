@@ -116,28 +116,88 @@ struct PanelSplit {
     }
 };
 
+// Element arithmetic of the shared-memory QR: FP64, or paired FP32 (each
+// element held as hi + lo, two FP32 words in the bytes of one double; dot
+// products accumulate with the TwoSum scheme of df_fma, updates a - w v form
+// the exact product of the high words by FMA and renormalise), which runs on
+// the FP32 pipe at about 46-bit accuracy.  Per-column scalars stay FP64.
+template <bool kDf>
+struct QrArith;
+template <>
+struct QrArith<false> {
+    using T = double;
+    struct Acc {
+        double d = 0.0;
+    };
+    static __device__ __forceinline__ T from(double x) { return x; }
+    static __device__ __forceinline__ double to(T x) { return x; }
+    static __device__ __forceinline__ void acc(Acc &a, T x, T y) { a.d = fma(x, y, a.d); }
+    static __device__ __forceinline__ double val(const Acc &a) { return a.d; }
+    // a - w v, with w prepared by prep()
+    struct W {
+        double w;
+    };
+    static __device__ __forceinline__ W prep(double w) { return W{w}; }
+    static __device__ __forceinline__ T axmy(T a, const W &w, T v) { return fma(-w.w, v, a); }
+};
+template <>
+struct QrArith<true> {
+    using T = float2;
+    struct Acc {
+        float h = 0.f, l = 0.f;
+    };
+    static __device__ __forceinline__ T from(double x) {
+        const float h = __double2float_rn(x);
+        return make_float2(h, __double2float_rn(x - (double)h));
+    }
+    static __device__ __forceinline__ double to(T x) { return (double)x.x + (double)x.y; }
+    static __device__ __forceinline__ void acc(Acc &a, T x, T y) { df_fma(x.x, x.y, y.x, y.y, a.h, a.l); }
+    static __device__ __forceinline__ double val(const Acc &a) { return (double)a.h + (double)a.l; }
+    struct W {
+        float h, l;
+    };
+    static __device__ __forceinline__ W prep(double w) {
+        const float h = __double2float_rn(w);
+        return W{h, __double2float_rn(w - (double)h)};
+    }
+    static __device__ __forceinline__ T axmy(T a, const W &w, T v) {
+        const float ph = __fmul_rn(w.h, v.x);
+        float pl = __fmaf_rn(w.h, v.x, -ph);
+        pl = __fmaf_rn(w.h, v.y, pl);
+        pl = __fmaf_rn(w.l, v.x, pl);
+        // TwoSum of a.x and -ph
+        const float sh = __fsub_rn(a.x, ph);
+        const float bp = __fsub_rn(sh, a.x);
+        const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sh, bp)), __fsub_rn(-ph, bp));
+        const float sl = __fadd_rn(__fsub_rn(a.y, pl), err);
+        const float hi = __fadd_rn(sh, sl);
+        return make_float2(hi, __fsub_rn(sl, __fsub_rn(hi, sh)));
+    }
+};
+
 // Dot products d_cc = sum over local rows i >= lb of v[i] A(i, cc) for the
 // columns cc in [first, s), written to out[cc].  red: kQrThreads doubles.
-__device__ __forceinline__ void panel_dots(const double *As, int ld, const double *v, int first, int s, int lb, int nr,
+template <class Ar, class T>
+__device__ __forceinline__ void panel_dots(const T *As, int ld, const T *v, int first, int s, int lb, int nr,
                                            double *red, double *out) {
     const int tid = threadIdx.x;
     const PanelSplit ps(s - first);
     const int g = tid / ps.width;
     if (ps.G == 1) {
         for (int cc = first + tid; cc < s; cc += ps.width) {
-            const double *ac = As + cc * ld;
-            double d = 0.0;
-            for (int i = lb; i < nr; ++i) d = fma(v[i], ac[i], d);
-            out[cc] = d;
+            const T *ac = As + cc * ld;
+            typename Ar::Acc d;
+            for (int i = lb; i < nr; ++i) Ar::acc(d, v[i], ac[i]);
+            out[cc] = Ar::val(d);
         }
         return;
     }
     const int cc = first + tid % ps.width;
     if (tid < ps.G * ps.width && cc < s) {
-        const double *ac = As + cc * ld;
-        double d = 0.0;
-        for (int i = lb + g; i < nr; i += ps.G) d = fma(v[i], ac[i], d);
-        red[tid] = d;
+        const T *ac = As + cc * ld;
+        typename Ar::Acc d;
+        for (int i = lb + g; i < nr; i += ps.G) Ar::acc(d, v[i], ac[i]);
+        red[tid] = Ar::val(d);
     }
     __syncthreads();
     if (tid < ps.width && cc < s) {
@@ -149,16 +209,17 @@ __device__ __forceinline__ void panel_dots(const double *As, int ld, const doubl
 
 // A(i, cc) -= w[cc] v(i) for local rows i >= lb and columns cc in [first, s),
 // where v(i) = v[i] except v(ic) = vhead when ic is a local row.
-__device__ __forceinline__ void panel_update(double *As, int ld, const double *v, int ic, double vhead,
-                                             const double *w, int first, int s, int lb, int nr) {
+template <class Ar, class T>
+__device__ __forceinline__ void panel_update(T *As, int ld, const T *v, int ic, T vhead, const double *w, int first,
+                                             int s, int lb, int nr) {
     const int tid = threadIdx.x;
     const PanelSplit ps(s - first);
     if (tid >= ps.G * ps.width) return;
     const int g = tid / ps.width;
     for (int cc = first + tid % ps.width; cc < s; cc += ps.width) {
-        const double wc = w[cc];
-        double *ac = As + cc * ld;
-        for (int i = lb + g; i < nr; i += ps.G) ac[i] = fma(-wc, i == ic ? vhead : v[i], ac[i]);
+        const typename Ar::W wc = Ar::prep(w[cc]);
+        T *ac = As + cc * ld;
+        for (int i = lb + g; i < nr; i += ps.G) ac[i] = Ar::axmy(ac[i], wc, i == ic ? vhead : v[i]);
     }
 }
 
@@ -175,8 +236,11 @@ __device__ __forceinline__ void panel_update(double *As, int ld, const double *v
 // H_c is applied, columns > c already hold their final values below row c,
 // and column c becomes H_c e_c (LAPACK's dorg2r ordering).
 // Shared memory: s * ld + 8 s + kQrThreads doubles.
-template <int kCl>
+template <int kCl, bool kDf>
 __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ jobs) {
+    using Ar = QrArith<kDf>;
+    using T = typename Ar::T;
+    static_assert(sizeof(T) == sizeof(double), "the panel element takes the bytes of one double");
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const QrJob J = jobs[blockIdx.x / kCl];
@@ -184,22 +248,22 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
     const int per = (m + kCl - 1) / kCl, ld = per | 1;
     const int r0 = min(m, rank * per), nr = min(m, r0 + per) - r0;
     extern __shared__ double sm[];
-    double *As = sm;
-    double *taus = As + (size_t)s * ld, *betas = taus + s, *heads = betas + s;
+    T *As = reinterpret_cast<T *>(sm);
+    double *taus = sm + (size_t)s * ld, *betas = taus + s, *heads = betas + s;
     double *pd = heads + s, *prow = pd + 2 * s, *wv = prow + 2 * s, *red = wv + s;
     for (int e = tid; e < nr * s; e += kQrThreads) {
         const int i = e % nr, j = e / nr;
-        As[j * ld + i] = J.A[(int64_t)j * J.lda + r0 + i];
+        As[j * ld + i] = Ar::from(J.A[(int64_t)j * J.lda + r0 + i]);
     }
     __syncthreads();
     for (int c = 0; c < s; ++c) {
         double *pdc = pd + (c & 1) * s, *prc = prow + (c & 1) * s;
         const int lb = max(c - r0, 0), ic = c - r0;
-        double *vc = As + c * ld;
-        panel_dots(As, ld, vc, c, s, lb, nr, red, pdc);
+        T *vc = As + c * ld;
+        panel_dots<Ar>(As, ld, vc, c, s, lb, nr, red, pdc);
         const int owner = c / per;
         if (rank == owner)
-            for (int cc = c + tid; cc < s; cc += kQrThreads) prc[cc] = As[cc * ld + ic];
+            for (int cc = c + tid; cc < s; cc += kQrThreads) prc[cc] = Ar::to(As[cc * ld + ic]);
         cl.sync();
         const double *orow = cl.map_shared_rank(prc, owner);
         double nrm2 = 0.0;
@@ -220,9 +284,9 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
             heads[c] = v0;
         }
         __syncthreads();
-        if (tau != 0.0) panel_update(As, ld, vc, ic, v0, wv, c + 1, s, lb, nr);
+        if (tau != 0.0) panel_update<Ar>(As, ld, vc, ic, Ar::from(v0), wv, c + 1, s, lb, nr);
         __syncthreads();
-        if (tau != 0.0 && rank == owner && tid == 0) vc[ic] = v0;  // reflector head stored in place
+        if (tau != 0.0 && rank == owner && tid == 0) vc[ic] = Ar::from(v0);  // reflector head stored in place
     }
     cl.sync();  // every CTA is done reading the factorisation's partials
     if (J.Rt) {  // Rt(i, u) = R(u, i) for the own rows u < s
@@ -230,7 +294,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         for (int e = tid; e < nu * s; e += kQrThreads) {
             const int lu = e / s, i = e % s, u = r0 + lu;
             double v = 0.0;
-            if (i > u) v = As[i * ld + lu];
+            if (i > u) v = Ar::to(As[i * ld + lu]);
             else if (i == u) v = betas[u];
             J.Rt[(int64_t)u * s + i] = v;
         }
@@ -241,11 +305,11 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
     for (int c = s - 1; c >= 0; --c) {
         const double tau = taus[c], v0 = heads[c];
         const int lb = max(c - r0, 0), ic = c - r0;
-        double *vc = As + c * ld;
+        T *vc = As + c * ld;
         if (tau != 0.0) {  // identical on every CTA of the cluster
             double *pdc = pd + (act & 1) * s;
             ++act;
-            panel_dots(As, ld, vc, c + 1, s, lb, nr, red, pdc);
+            panel_dots<Ar>(As, ld, vc, c + 1, s, lb, nr, red, pdc);
             cl.sync();
             for (int cc = c + 1 + tid; cc < s; cc += kQrThreads) {
                 double d = 0.0;
@@ -254,22 +318,23 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
                 wv[cc] = tau * d;
             }
             __syncthreads();
-            panel_update(As, ld, vc, -1, 0.0, wv, c + 1, s, lb, nr);
+            panel_update<Ar>(As, ld, vc, -1, Ar::from(0.0), wv, c + 1, s, lb, nr);
             __syncthreads();
         }
         // column c of Q = H_c e_c
+        const typename Ar::W tv = Ar::prep(tau * v0);
         for (int i = tid; i < nr; i += kQrThreads) {
-            double q;
-            if (i < ic) q = 0.0;
-            else if (i == ic) q = 1.0 - tau * v0 * v0;
-            else q = -tau * v0 * vc[i];
+            T q;
+            if (i < ic) q = Ar::from(0.0);
+            else if (i == ic) q = Ar::from(1.0 - tau * v0 * v0);
+            else q = Ar::axmy(Ar::from(0.0), tv, vc[i]);
             vc[i] = q;
         }
         __syncthreads();
     }
     for (int e = tid; e < nr * s; e += kQrThreads) {
         const int i = e % nr, j = e / nr;
-        J.Q[(int64_t)j * J.ldq + r0 + i] = As[j * ld + i];
+        J.Q[(int64_t)j * J.ldq + r0 + i] = Ar::to(As[j * ld + i]);
     }
     cl.sync();  // no CTA leaves while another may still read its partials
 }
@@ -997,7 +1062,7 @@ static bool cluster16_ok() {
     static int state = -1;
     if (state < 0) {
         state = 0;
-        const void *k16[] = {(const void *)k_qr_sm<16>, (const void *)k_qr_gm<16>, (const void *)k_jacobi_sm<16, kJacFull>,
+        const void *k16[] = {(const void *)k_qr_sm<16, false>, (const void *)k_qr_sm<16, true>, (const void *)k_qr_gm<16>, (const void *)k_jacobi_sm<16, kJacFull>,
                              (const void *)k_jacobi_sm<16, kJacPrecond>, (const void *)k_jacobi_sm<16, kJacFinish>,
                              (const void *)k_jacobi_gm<16>};
         bool ok = true;
@@ -1005,7 +1070,7 @@ static bool cluster16_ok() {
             ok = ok && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
         if (ok) {
             // one cluster of 16 CTAs that each fill an SM's shared memory must fit
-            const size_t need = std::min(smem_cap((const void *)k_qr_sm<16>), smem_cap((const void *)k_jacobi_sm<16, kJacFull>));
+            const size_t need = std::min(smem_cap((const void *)k_qr_sm<16, false>), smem_cap((const void *)k_jacobi_sm<16, kJacFull>));
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16);
             cfg.blockDim = dim3(kQrThreads);
@@ -1018,7 +1083,7 @@ static bool cluster16_ok() {
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int n1 = 0, n2 = 0;
-            if (cudaOccupancyMaxActiveClusters(&n1, k_qr_sm<16>, &cfg) == cudaSuccess &&
+            if (cudaOccupancyMaxActiveClusters(&n1, k_qr_sm<16, false>, &cfg) == cudaSuccess &&
                 cudaOccupancyMaxActiveClusters(&n2, k_jacobi_sm<16, kJacFull>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
                 state = 1;
         }
@@ -1035,15 +1100,17 @@ static int svd_cluster(int s) { return s <= 48 ? 1 : (s <= 96 ? 4 : (s <= 160 ? 
 using QrKernel = void (*)(const QrJob *);
 using SvdKernel = void (*)(const SvdJob *, double);
 
-static QrKernel qr_sm_kernel(int c) {
+template <bool kDf>
+static QrKernel qr_sm_kernel_t(int c) {
     switch (c) {
-    case 1: return k_qr_sm<1>;
-    case 2: return k_qr_sm<2>;
-    case 4: return k_qr_sm<4>;
-    case 8: return k_qr_sm<8>;
-    default: return k_qr_sm<16>;
+    case 1: return k_qr_sm<1, kDf>;
+    case 2: return k_qr_sm<2, kDf>;
+    case 4: return k_qr_sm<4, kDf>;
+    case 8: return k_qr_sm<8, kDf>;
+    default: return k_qr_sm<16, kDf>;
     }
 }
+static QrKernel qr_sm_kernel(int c, bool df) { return df ? qr_sm_kernel_t<true>(c) : qr_sm_kernel_t<false>(c); }
 template <int kMode>
 static SvdKernel svd_sm_kernel_m(int c) {
     switch (c) {
@@ -1134,7 +1201,8 @@ static void add_to_class(std::vector<LaunchClass<Job, K>> &cls, K kernel, int cs
 // QR stage for a list of jobs.  `copy[u]` (k x s, may alias nothing) is
 // scratch for jobs that fall back to the in-place global-memory kernel when
 // the input must survive (R-only factorisations).
-static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &jobs, const std::vector<double *> &copy) {
+static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &jobs, const std::vector<double *> &copy,
+                      bool df) {
     const bool big = cluster16_ok();
     std::vector<LaunchClass<QrJob, QrKernel>> cls;
     for (size_t u = 0; u < jobs.size(); ++u) {
@@ -1142,8 +1210,8 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
         int c = qr_cluster(J.s);
         if (c == 16 && !big) c = 8;
         int top = big ? 16 : 8;
-        while (c < top && qr_sm_bytes(J.m, J.s, c) > smem_cap((const void *)qr_sm_kernel(c))) c *= 2;
-        QrKernel k = qr_sm_kernel(c);
+        while (c < top && qr_sm_bytes(J.m, J.s, c) > smem_cap((const void *)qr_sm_kernel(c, df))) c *= 2;
+        QrKernel k = qr_sm_kernel(c, df);
         size_t bytes = qr_sm_bytes(J.m, J.s, c);
         if (bytes <= smem_cap((const void *)k)) {
             add_to_class(cls, k, c, bytes, J);
@@ -1315,7 +1383,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             q1[u] = QrJob{W + oY[u], J.m, W + oQ[u], J.m, nullptr, J.m, ps[u]};
             scratch[u] = W + oC[u];
         }
-        qr_launch(ctx, st, q1, scratch);
+        qr_launch(ctx, st, q1, scratch, df);
         if (df) {
             std::vector<SplitDesc> sd(np);
             for (size_t u = 0; u < np; ++u)
@@ -1341,7 +1409,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             const CompressJob &J = jobs[pending[u]];
             q2[u] = QrJob{W + oB[u], J.k, nullptr, 0, W + oR[u], J.k, ps[u]};
         }
-        qr_launch(ctx, st, q2, scratch);
+        qr_launch(ctx, st, q2, scratch, df);
         cmark();
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
@@ -1389,13 +1457,13 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
                         b.C = Xn[u]; b.ldc = sz;
                         gx.push_back(b);
                     }
-                    gemm_batched(ctx, st, true, false, gg, 1.0, 0.0);
+                    gemm_batched_small(ctx, st, true, false, gg, 1.0, 0.0);
                     TLR_CUDA_TRY(cudaMemsetAsync(d_off, 0, np * sizeof(unsigned long long), st));
                     auto *dr = (const RefineJob *)stage_push(ctx, rjobs.data(), rjobs.size() * sizeof(RefineJob), st);
                     launch(k_refine_angles, dim3((unsigned)std::min<int64_t>(ceil_div(smax * smax, 256), 64),
                                                  (unsigned)rjobs.size()), 256, 0, st, dr);
                     TLR_CHECK_LAUNCH();
-                    gemm_batched(ctx, st, false, false, gx, 1.0, 0.0);
+                    gemm_batched_small(ctx, st, false, false, gx, 1.0, 0.0);
                     for (size_t u : rj) std::swap(X[u], Xn[u]);
                 }
                 std::vector<EmitJob> ej;

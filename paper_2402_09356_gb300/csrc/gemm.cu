@@ -139,6 +139,11 @@ void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc>
     TLR_CHECK_LAUNCH();
 }
 
+void gemm_batched_small(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                        double alpha, double beta) {
+    launch_shape<32, 32>(ctx, s, ta, tb, probs, alpha, EpiLinear{beta}, false);
+}
+
 void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
                   double alpha, double beta, bool df) {
     launch_gemm(ctx, s, ta, tb, probs, alpha, EpiLinear{beta}, df);

@@ -286,6 +286,11 @@ struct SplitDesc {
 // split_f2 for a batch of blocks in one launch.
 void split_f2_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<SplitDesc> &descs);
 
+// FP64, 32 x 32 output tiles for every problem: four times the CTAs of the
+// 64 x 64 shape, for small square products on the critical path.
+void gemm_batched_small(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
+                        double alpha, double beta);
+
 // df = true selects the paired-FP32 kernel (FP64-accurate products on the FP32
 // pipe); every problem must then carry A2/B2 copies made by split_f2.
 void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector<GemmProb> &probs,
