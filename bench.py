@@ -379,10 +379,12 @@ def cpu_baseline_sample(n_sample: int = 6400, theta=THETA0):
     t2 = time.perf_counter()
     f = N_POINTS / n_sample
     est = (t1 - t0) * f ** 2 + (t2 - t1) * f ** 3
+    side = math.ceil(math.sqrt(n_sample))
     return {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "dense FP64 oracle at n=6400 (80x80 grid): Matern fill %.2fs x (40000/6400)^2, "
-                      "Cholesky+solve %.2fs x (40000/6400)^3 -> %.1fs per n=40k evaluation"
-                      % (t1 - t0, t2 - t1, est)}
+            "sample": "dense FP64 oracle at n=%d (perturbed %dx%d grid, first n points): Matern fill %.2fs x "
+                      "(%d/%d)^2, Cholesky+solve %.2fs x (%d/%d)^3 -> %.1fs per n=%d evaluation"
+                      % (n_sample, side, side, t1 - t0, N_POINTS, n_sample, t2 - t1, N_POINTS, n_sample, est,
+                         N_POINTS)}
 
 
 def run_reference(args):
@@ -406,7 +408,7 @@ def run_reference(args):
             "config": {"workload": "dense FP64 oracle likelihood, n=3200 samples scaled to n=40,000",
                        "n": N_POINTS, "theta0": list(THETA0)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": vals[-1]["sample"].replace("6400", "3200")},
+                             "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
