@@ -1059,9 +1059,9 @@ static size_t smem_cap(const void *kernel) {
 
 // Whether clusters of 16 CTAs (a non-portable size) can run on this device.
 static bool cluster16_ok() {
-    static int state = -1;
-    if (state < 0) {
-        state = 0;
+    static std::once_flag once;
+    static int state = 0;
+    std::call_once(once, [] {
         const void *k16[] = {(const void *)k_qr_sm<16, false>, (const void *)k_qr_sm<16, true>, (const void *)k_qr_gm<16>, (const void *)k_jacobi_sm<16, kJacFull>,
                              (const void *)k_jacobi_sm<16, kJacPrecond>, (const void *)k_jacobi_sm<16, kJacFinish>,
                              (const void *)k_jacobi_gm<16>};
@@ -1088,7 +1088,7 @@ static bool cluster16_ok() {
                 state = 1;
         }
         cudaGetLastError();  // clear any error of the queries
-    }
+    });
     return state == 1;
 }
 

@@ -6,6 +6,8 @@
 // Blocks of 32 rows/columns are factored or solved by one CTA in shared
 // memory; everything else is a batched GEMM update so that it spreads over
 // the whole GPU (one SM's FP64 pipe alone would take milliseconds per tile).
+#include <mutex>
+
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -412,9 +414,9 @@ void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *
     if (m > kBlk * kBlk) throw make_error(TLR_ERR_ARG, "tile too large for the cluster POTRF (%d)", m);
     if (!ctx->d_potrf_scratch)
         TLR_CUDA_TRY(cudaMalloc(&ctx->d_potrf_scratch, ((size_t)kBlk * kBlk * kBlk + 8) * sizeof(double)));
-    static int csize = 0;  // 16 CTAs where the device runs such clusters, else 8
-    if (csize == 0) {
-        csize = 8;
+    static std::once_flag once;
+    static int csize = 8;  // 16 CTAs where the device runs such clusters, else 8
+    std::call_once(once, [] {
         if (cudaFuncSetAttribute(k_potrf_inv<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16);
@@ -431,7 +433,7 @@ void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *
                 csize = 16;
         }
         cudaGetLastError();  // clear any error of the queries
-    }
+    });
     if (csize == 16)
         launch_clustered(k_potrf_inv<16>, 16, 1, kPotrfThreads, 0, s, A, lda, m, X, ldx, ctx->d_potrf_scratch,
                          ctx->d_status, row_base);
