@@ -414,6 +414,212 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- many datasets: batched evaluation (256 datasets) and serving -----------
+
+BATCH_BUCKETS = ((2000, 5000), (5000, 10000), (10000, 20001))
+BATCH_TILE_CANDIDATES = (256, 384, 512, 800)
+
+
+def batched_datasets(count: int, seed: int = 2024):
+    """Sizes n ~ U[2000, 20000] and starting thetas sigma2 ~ U[0.5, 2], beta ~
+    U[0.02, 0.3], nu ~ U[0.5, 2.5] of the batched workload (seeded)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(2000, 20001, count)
+    thetas = np.stack([rng.uniform(0.5, 2.0, count), rng.uniform(0.02, 0.3, count),
+                       rng.uniform(0.5, 2.5, count)], axis=1)
+    return sizes, thetas
+
+
+def run_batched(args):
+    """Batched workload: `--datasets` independent datasets (jittered grids,
+    first n points of a ceil(sqrt n)^2 grid, Z ~ N(0, I) seeded), Morton order,
+    eps 1e-7.  Tile size per n bucket picked by the pool's autotuner on one
+    dataset of the bucket.  One step = every dataset evaluated once (one
+    tlr_pool_loglik call), thetas moving along a per-dataset log-space walk."""
+    import numpy as np
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    import synth
+    count = args.datasets
+    sizes, th0 = batched_datasets(count)
+    pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
+    t_setup = time.perf_counter()
+    bucket_of = [next(b for b, (lo, hi) in enumerate(BATCH_BUCKETS) if lo <= n < hi) for n in sizes]
+    ids = [None] * count
+    tuned = {}
+    for b, (lo, hi) in enumerate(BATCH_BUCKETS):
+        members = [i for i in range(count) if bucket_of[i] == b]
+        if not members:
+            continue
+        mid = (lo + hi) / 2
+        rep = min(members, key=lambda i: abs(sizes[i] - mid))
+        n = int(sizes[rep])
+        ids[rep] = tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=10 + rep), synth.standard_normal(n, seed=5000 + rep),
+                                    "morton")
+        best, ms = tlr.tlr_pool_tune(pool, ids[rep], tuple(th0[rep]), list(BATCH_TILE_CANDIDATES), eps=EPS,
+                                     precision=tlr.TLR_PREC_MIXED)
+        tuned[b] = {"n": n, "best_nb": best, "ms": ms}
+    for i in range(count):
+        if ids[i] is None:
+            n = int(sizes[i])
+            ids[i] = tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=10 + i), synth.standard_normal(n, seed=5000 + i),
+                                      "morton", nb=tuned[bucket_of[i]]["best_nb"])
+    setup_s = time.perf_counter() - t_setup
+    walks = [synth.theta_walk(tuple(th0[i]), args.warmup + args.steps, seed=900 + i, scale=0.05) for i in range(count)]
+    out = {}
+    clocks_all = {}
+    for name, prec in (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED)):
+        for k in range(args.warmup):
+            tlr.tlr_pool_loglik(pool, ids, [tuple(w[k]) for w in walks], eps=EPS, precision=prec)
+        clocks = ClockSampler(0)
+        torch.cuda.synchronize()
+        launches0 = tlr.tlr_launch_count()
+        clocks.start()
+        times, results, fails = [], [], 0
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            res, st = tlr.tlr_pool_loglik(pool, ids, [tuple(w[args.warmup + k]) for w in walks], eps=EPS,
+                                          precision=prec)
+            times.append(time.perf_counter() - t0)
+            fails += sum(1 for x in st if x != 0)
+            results.append([r["loglik"] if x == 0 else None for r, x in zip(res, st)])
+        torch.cuda.synchronize()
+        clocks_all[name] = clocks.stop()
+        total = sum(times)
+        out[name] = {"evals_per_s": count * args.steps / total, "s_per_step": total / args.steps,
+                     "failed": fails, "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
+    rel = [abs(a - b) / abs(b) for ra, rb in zip(out["mixed"]["results"], out["fp64"]["results"])
+           for a, b in zip(ra, rb) if a is not None and b is not None]
+    st = tlr.tlr_pool_stats(pool)
+    head = "mixed" if rel and max(rel) <= 1e-6 else "fp64"
+    line = {"metric": "batched TLR l(theta) evals/s, %d datasets n~U[2000,20000]" % count,
+            "value": out[head]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * out[head]["s_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 storage, paired-f32 products" if head == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "batched: %d datasets, n ~ U[2000, 20000] jittered grids, theta ~ U(sigma2 "
+                                   "[0.5,2], beta [0.02,0.3], nu [0.5,2.5]), Morton, eps %g, %d workers"
+                                   % (count, EPS, args.workers),
+                       "precision": head, "workers": args.workers, "maxrank": args.maxrank,
+                       "tile_autotune": {str(BATCH_BUCKETS[b]): v for b, v in tuned.items()},
+                       "timing": "host wall clock around each blocking tlr_pool_loglik (all datasets)",
+                       "l2": "inputs (all datasets' factors) larger than L2"},
+            "fp64_path": {k: v for k, v in out["fp64"].items() if k != "results"},
+            "mixed_path": {k: v for k, v in out["mixed"].items() if k != "results"},
+            "rel_dl_mixed_vs_fp64_max": max(rel) if rel else None,
+            "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
+            "gpu_launches": out[head]["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    pool.close()
+
+
+SERVE_SIZES = (5000, 10000, 20000, 40000, 80000)
+
+
+def run_serving(args):
+    """Serving workload: 32 resident datasets with n cycling through 5k, 10k,
+    20k, 40k, 80k (jittered grids, Z ~ N(0, I) seeded, Hilbert order, tile
+    800), a Poisson stream of `--requests` l(theta) requests at `--rate` per
+    second on uniformly drawn datasets, theta following each dataset's own
+    simplex-like walk in log(sigma2, beta, nu) around (1, 0.1, 1.0), and two
+    MLE jobs (n = 5k and 10k) submitted beside the stream.  Latency = host
+    time from submission to completion."""
+    import threading
+    import numpy as np
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    import synth
+    nd = 32
+    sizes = [SERVE_SIZES[i % len(SERVE_SIZES)] for i in range(nd)]
+    pool = tlr.Pool(0, workers=args.workers, nb=NB, maxrank=args.maxrank)
+    t_setup = time.perf_counter()
+    ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=300 + i), synth.standard_normal(n, seed=600 + i),
+                            "hilbert") for i, n in enumerate(sizes)]
+    setup_s = time.perf_counter() - t_setup
+    rng = np.random.default_rng(77)
+    R = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, R))
+    targets = rng.integers(0, nd, R)
+    steps_of = [0] * nd
+    per_data = np.bincount(targets, minlength=nd)
+    walks = [synth.theta_walk((1.0, 0.1, 1.0), int(per_data[d]) + 1, seed=1200 + d, scale=0.15) for d in range(nd)]
+    mle_ids = [ids[0], ids[1]]
+    out = {}
+    for name, prec in (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED)):
+        # warm-up: one request per dataset size
+        for i in range(len(SERVE_SIZES)):
+            tlr.tlr_pool_wait(pool, tlr.tlr_pool_submit(pool, ids[i], (1.0, 0.1, 1.0), EPS, prec))
+        steps_of = [0] * nd
+        tickets = [None] * R
+        mle_out = {}
+
+        def mle(j, did):
+            t0 = time.perf_counter()
+            th, ll, it = tlr.tlr_pool_mle(pool, did, (0.8, 0.08, 1.2), (0.05, 0.005, 0.2), (5.0, 1.0, 3.0),
+                                          eps=EPS, precision=prec, tol=1e-6, max_iter=args.mle_iters)
+            mle_out[j] = {"n": sizes[mle_ids.index(did)], "theta": th, "loglik": ll, "evals": it,
+                          "wall_s": time.perf_counter() - t0}
+
+        clocks = ClockSampler(0)
+        torch.cuda.synchronize()
+        launches0 = tlr.tlr_launch_count()
+        clocks.start()
+        t_start = time.perf_counter()
+        mle_threads = [threading.Thread(target=mle, args=(j, d)) for j, d in enumerate(mle_ids)]
+        for t in mle_threads:
+            t.start()
+        for q in range(R):
+            delay = t_start + arrivals[q] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            d = int(targets[q])
+            th = tuple(walks[d][steps_of[d]])
+            steps_of[d] += 1
+            tickets[q] = tlr.tlr_pool_submit(pool, ids[d], th, EPS, prec)
+        lat, queue, run, fails = [], [], [], 0
+        by_n = {n: [] for n in SERVE_SIZES}
+        for q in range(R):
+            try:
+                _, tm = tlr.tlr_pool_wait(pool, tickets[q])
+            except tlr.TlrError:
+                fails += 1
+                continue
+            lat.append(tm["latency_ms"])
+            queue.append(tm["queue_ms"])
+            run.append(tm["run_ms"])
+            by_n[sizes[int(targets[q])]].append(tm["latency_ms"])
+        t_stream = time.perf_counter() - t_start
+        for t in mle_threads:
+            t.join()
+        t_all = time.perf_counter() - t_start
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        mle_evals = sum(v["evals"] for v in mle_out.values())
+        pct = lambda a, p: float(np.percentile(a, p)) if a else None
+        out[name] = {"evals_per_s": (R - fails + mle_evals) / t_all, "stream_evals_per_s": (R - fails) / t_stream,
+                     "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "queue_p50_ms": pct(queue, 50),
+                     "run_p50_ms": pct(run, 50), "failed": fails, "wall_s": t_all,
+                     "by_n": {str(n): {"count": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99)}
+                              for n, v in by_n.items()},
+                     "mle": mle_out, "clocks": clk, "gpu_launches": int(tlr.tlr_launch_count() - launches0),
+                     "pool": tlr.tlr_pool_stats(pool)}
+    line = {"metric": "served TLR l(theta) evals/s and p50/p99 latency, 32 resident datasets",
+            "value": out["mixed"]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": R, "warmup": 5,
+            "ms_per_step": 1000.0 / out["mixed"]["evals_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 storage, paired-f32 products", "data": "synthetic",
+            "p50_ms": out["mixed"]["p50_ms"], "p99_ms": out["mixed"]["p99_ms"],
+            "config": {"workload": "serving: 32 resident datasets n in {5k,10k,20k,40k,80k}, nu=1.0 walk start, "
+                                   "Hilbert, tile %d, eps %g, Poisson %g req/s x %d requests + 2 MLE jobs, "
+                                   "%d workers" % (NB, EPS, args.rate, R, args.workers),
+                       "workers": args.workers, "maxrank": args.maxrank, "rate": args.rate, "requests": R,
+                       "latency": "host clock, submission to completion"},
+            "fp64_path": out["fp64"], "mixed_path": out["mixed"], "setup_s": setup_s,
+            "clocks": out["mixed"]["clocks"], "gpu_launches": out["mixed"]["gpu_launches"]}
+    print(json.dumps(line), flush=True)
+    pool.close()
+
+
 def main():
     global N_POINTS, NB, EPS, ORDER
     ap = argparse.ArgumentParser()
@@ -428,6 +634,15 @@ def main():
     ap.add_argument("--order", default=ORDER)
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="precision paths to time (both for the headline; one for profiling runs)")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serving"],
+                    help="headline: one n = 40,000 evaluation per step; batched: many datasets per step; "
+                         "serving: a Poisson request stream over resident datasets")
+    ap.add_argument("--workers", type=int, default=8, help="pool workers (batched / serving)")
+    ap.add_argument("--datasets", type=int, default=256, help="datasets of the batched workload")
+    ap.add_argument("--maxrank", type=int, default=0, help="rank slots per tile (batched / serving; 0 = nb/2)")
+    ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream")
+    ap.add_argument("--rate", type=float, default=500.0, help="arrival rate of the serving stream (1/s)")
+    ap.add_argument("--mle-iters", type=int, default=30, help="evaluations per MLE job (serving)")
     args = ap.parse_args()
     N_POINTS, NB, EPS, ORDER = args.n, args.nb, args.eps, args.order
     if args.impl == "reference":
@@ -435,7 +650,12 @@ def main():
         return
     from paper_2402_09356_gb300 import build as lib_build
     lib_build.build()
-    run_gpu(args)
+    if args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
+    else:
+        run_gpu(args)
 
 
 if __name__ == "__main__":

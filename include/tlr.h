@@ -19,7 +19,7 @@
  *  - Locations are SoA float64: xy[0..n) = x, xy[n..2n) = y.
  *  - Matrix tiles are column major.  The tile size is nb; NT = ceil(n / nb);
  *    tile t covers rows [t nb, min(n, (t+1) nb)) and has m_t rows.
- *  - A context is used by one host thread at a time.
+ *  - A context is used by one host thread at a time (a pool, below, by any).
  */
 #ifndef TLR_H
 #define TLR_H
@@ -316,6 +316,143 @@ int tlr_kernel_stats(tlr_ctx *ctx, double *out);
 int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tlr_opts *opts,
             tlr_theta theta0, tlr_theta lo, tlr_theta hi, double tol, int max_iter,
             tlr_mat *L, tlr_theta *theta_hat, double *ll_hat, int *iters, void *stream);
+
+/* ---- many datasets: batched evaluation and serving -------------------------
+ *
+ * The paper evaluates each replicate separately (Sec. 5.1); a pool evaluates
+ * many independent likelihoods at once.  It keeps datasets resident on one
+ * device -- ordered locations, ordered observations, the permutation, and the
+ * rank map of each dataset's last factor -- and runs l(theta) requests on
+ * `workers` concurrent workers, each a host thread with its own context and
+ * streams, so that the kernels of different requests overlap on the device.
+ *
+ * Admission (continuous batching).  Requests queue in arrival order.  A
+ * request starts as soon as a worker is free, no earlier request of its
+ * dataset is running, and the device memory it needs fits the pool's HBM
+ * budget: its dataset's TLR factor storage (kept resident between requests;
+ * idle factors of other datasets are evicted least recently used first when
+ * room is needed) plus the evaluation's workspace.  A request waiting for
+ * memory to allocate a factor is not overtaken by later requests that would
+ * allocate one too.
+ *
+ * Determinism.  The requests of one dataset run one at a time in submission
+ * order, and each starts from the rank map its dataset's previous request
+ * left (the sample sizes of the compression, Sec. 2).  The k-th result of a
+ * dataset is therefore bit-for-bit the one a single context gets from k
+ * tlr_loglik calls on one tlr_mat in that order, whatever else runs beside it.
+ *
+ * Thread safety: every tlr_pool_* call may be made from any host thread.
+ * Errors of a pool call leave a message in tlr_pool_last_error(), kept per
+ * calling thread. */
+typedef struct tlr_pool tlr_pool;
+
+typedef struct {
+    int32_t workers;    /* concurrent evaluations, 1..64 */
+    int32_t nb;         /* tile size of datasets added with nb <= 0 (16..1024) */
+    int32_t maxrank;    /* off-diagonal rank slots per tile; <= 0 selects nb / 2 */
+    uint32_t flags;     /* reserved, 0 */
+    int64_t hbm_budget; /* device bytes the pool may hold (resident data, factors,
+                           workspace); <= 0 selects 90% of the free memory */
+} tlr_pool_opts;
+
+/* Create a pool on CUDA device `device`.
+ * Errors: TLR_ERR_ARG, TLR_ERR_CUDA, TLR_ERR_OOM. */
+int tlr_pool_create(int device, const tlr_pool_opts *opts, tlr_pool **out);
+
+/* Finish every queued request, stop the workers and free the pool's memory.
+ * Results not yet collected by tlr_pool_wait are discarded.  NULL is ignored. */
+void tlr_pool_destroy(tlr_pool *p);
+
+/* Message of the last failing tlr_pool_* call of the calling thread. */
+const char *tlr_pool_last_error(void);
+
+/* Register a dataset of n locations xy (SoA, 2n values) and observations z
+ * (n values); both host or device pointers, copied.  The locations are
+ * ordered on the device with `order` (TLR_ORDER_*, `seed` for RANDOM) and
+ * the observations permuted alike; the dataset's tile size is nb (<= 0: the
+ * pool's).  *id receives its handle.
+ * Errors: TLR_ERR_ARG; TLR_ERR_OOM if its resident bytes, plus the factor and
+ * workspace of the largest registered dataset, would exceed the budget. */
+int tlr_pool_add(tlr_pool *p, const double *xy, const double *z, int64_t n, int order, uint64_t seed,
+                 int nb, int *id);
+
+/* Wait for the dataset's queued requests, then unregister it and free its
+ * memory.  Errors: TLR_ERR_ARG (unknown id). */
+int tlr_pool_remove(tlr_pool *p, int id);
+
+/* Device pointers of a dataset's resident data (any output may be NULL): n,
+ * tile size, ordered locations (2n), ordered observations (n), permutation
+ * (n, position -> input index), and the largest rank of its last factor (0
+ * before the first evaluation).  Pointers stay valid until the dataset is
+ * removed; read them only while no request of the dataset runs.
+ * Errors: TLR_ERR_ARG. */
+int tlr_pool_dataset(tlr_pool *p, int id, int64_t *n, int *nb, const double **xy, const double **z,
+                     const int64_t **perm, int32_t *last_max_rank);
+
+/* Queue one l(theta) evaluation (Eq. 1.2) of dataset `id` at accuracy eps
+ * (tlr_opts.eps) and precision TLR_PREC_*; returns at once with *ticket.
+ * Errors: TLR_ERR_ARG (unknown id, bad eps/precision). */
+int tlr_pool_submit(tlr_pool *p, int id, tlr_theta theta, double eps, int precision, int64_t *ticket);
+
+/* Block until request `ticket` has finished; its result goes to *out (may be
+ * NULL) and, if times_ms is not NULL, times_ms[0..2] = time queued, time
+ * running, and latency from submission to completion (host clock, ms).  The
+ * ticket is consumed.  Returns the request's own status (a failed
+ * evaluation's message is then in tlr_pool_last_error()), or TLR_ERR_ARG for
+ * an unknown ticket. */
+int tlr_pool_wait(tlr_pool *p, int64_t ticket, tlr_result *out, double *times_ms);
+
+/* Batched evaluation: submit count requests (ids[i], theta[i]) and wait for
+ * all of them.  out[i] and status[i] (either may be NULL) receive each
+ * result; returns TLR_OK if all succeeded, else the first failing status in
+ * index order. */
+int tlr_pool_loglik(tlr_pool *p, int count, const int *ids, const tlr_theta *theta, double eps,
+                    int precision, tlr_result *out, int *status);
+
+/* tlr_mle (the same search and stopping rules) for a resident dataset, run
+ * on the calling thread with every evaluation submitted to the pool, where it
+ * mixes with the other requests.  Outputs on host. */
+int tlr_pool_mle(tlr_pool *p, int id, double eps, int precision, tlr_theta theta0, tlr_theta lo,
+                 tlr_theta hi, double tol, int max_iter, tlr_theta *theta_hat, double *ll_hat, int *iters);
+
+/* Tile-size autotuning for one dataset: for each candidate tile size
+ * cands[0..ncand) that fits the budget, two evaluations at theta (the first
+ * sets the rank map, the second is timed on the device); the dataset keeps
+ * the fastest tile size, written to *best, with ms[i] the timed evaluation
+ * (-1 if skipped).  The dataset's rank map restarts empty.  Waits for the
+ * dataset's queued requests first.  Errors: TLR_ERR_ARG, or the first error
+ * of an evaluation. */
+int tlr_pool_tune(tlr_pool *p, int id, tlr_theta theta, double eps, int precision, const int32_t *cands,
+                  int ncand, int32_t *best, double *ms);
+
+/* Device bytes the admission model charges for a dataset of n locations at
+ * tile size nb and rank slots maxrank (<= 0: nb / 2), written to out[0..2]:
+ * resident data (32 n: locations, observations, permutation), TLR factor
+ * storage (NT nb^2 diagonal + 2 nb maxrank per off-diagonal tile, doubles,
+ * plus the NT^2 int32 rank map), and the estimated workspace of one
+ * evaluation before the dataset's first rank map is known.  Host only.
+ * Errors: TLR_ERR_ARG. */
+int tlr_pool_footprint(int64_t n, int nb, int maxrank, int64_t *out);
+
+/* Counters, written to out[0..count) (returns the number written, at most
+ * 12): budget, bytes in use, peak bytes in use, resident dataset bytes,
+ * resident factor bytes, resident factors, evictions, requests completed,
+ * requests queued, requests running, most requests running at once, factor
+ * allocations.  Byte figures follow the admission model (factor storage
+ * exact, workspace estimated). */
+int tlr_pool_stats(tlr_pool *p, int64_t *out, int count);
+
+/* The admission policy of the pool run as a discrete-event simulation on the
+ * host (no device used): `workers` slots, `ndata` datasets with base, factor
+ * and workspace bytes, and nreq requests (dataset req_data[i], arriving at
+ * req_arrival[i], nondecreasing, and running for req_cost[i] once started).
+ * Writes each request's start and finish time, the peak bytes in use and the
+ * number of evictions.  Errors: TLR_ERR_ARG; TLR_ERR_OOM if some dataset
+ * could not be registered under the budget. */
+int tlr_sched_simulate(int64_t budget, int workers, int ndata, const int64_t *base_bytes,
+                       const int64_t *factor_bytes, const int64_t *work_bytes, int nreq,
+                       const int32_t *req_data, const double *req_arrival, const double *req_cost,
+                       double *start, double *finish, int64_t *peak_bytes, int64_t *evictions);
 
 #ifdef __cplusplus
 }

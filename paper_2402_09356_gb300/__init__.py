@@ -50,6 +50,11 @@ class tlr_result(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class tlr_pool_opts(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("nb", ctypes.c_int32), ("maxrank", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("hbm_budget", ctypes.c_int64)]
+
+
 _lib = None
 
 _SIGS = {
@@ -102,6 +107,33 @@ _SIGS = {
                                ctypes.POINTER(tlr_opts), tlr_theta, tlr_theta, tlr_theta, ctypes.c_double,
                                ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(tlr_theta),
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
+    "tlr_pool_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(tlr_pool_opts), ctypes.POINTER(ctypes.c_void_p)]),
+    "tlr_pool_destroy": (None, [ctypes.c_void_p]),
+    "tlr_pool_last_error": (ctypes.c_char_p, []),
+    "tlr_pool_add": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "tlr_pool_remove": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "tlr_pool_dataset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "tlr_pool_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, tlr_theta, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "tlr_pool_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(tlr_result),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "tlr_pool_loglik": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_pool_mle": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int, tlr_theta,
+                                    tlr_theta, tlr_theta, ctypes.c_double, ctypes.c_int, ctypes.POINTER(tlr_theta),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "tlr_pool_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, tlr_theta, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "tlr_pool_footprint": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "tlr_pool_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tlr_sched_simulate": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
 }
 
 
@@ -442,3 +474,186 @@ def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1
 
 def loglik_log2pi(n: int) -> float:
     return -0.5 * n * math.log(2 * math.pi)
+
+
+# ---- many datasets: batched evaluation and serving ----------------------------
+
+POOL_STATS = ("budget", "used", "peak", "resident_data_bytes", "resident_factor_bytes", "resident_factors",
+              "evictions", "completed", "queued", "running", "max_running", "allocations")
+
+
+def _pool_check(rc: int):
+    if rc != TLR_OK:
+        raise TlrError(rc, load_library().tlr_pool_last_error().decode())
+
+
+def _host_or_device_ptr(a):
+    """Address of a contiguous float64 numpy array or torch tensor (host or CUDA)."""
+    import numpy as np
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TlrError(TLR_ERR_ARG, "arrays must be contiguous float64")
+        return ctypes.c_void_p(a.ctypes.data)
+    import torch
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise TlrError(TLR_ERR_ARG, "tensors must be contiguous float64")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+class Pool:
+    """Owns a tlr_pool: resident datasets evaluated by concurrent workers."""
+
+    def __init__(self, device: int = 0, workers: int = 4, nb: int = 800, maxrank: int = 0, hbm_budget: int = 0):
+        lib = load_library()
+        o = tlr_pool_opts(int(workers), int(nb), int(maxrank), 0, int(hbm_budget))
+        h = ctypes.c_void_p()
+        _pool_check(lib.tlr_pool_create(int(device), ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self.device = device
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().tlr_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tlr_pool_create(device: int = 0, workers: int = 4, nb: int = 800, maxrank: int = 0, hbm_budget: int = 0) -> Pool:
+    return Pool(device, workers, nb, maxrank, hbm_budget)
+
+
+def tlr_pool_destroy(pool: Pool):
+    pool.close()
+
+
+def tlr_pool_add(pool: Pool, xy, z, order="morton", seed: int = 3, nb: int = 0) -> int:
+    """Register a dataset (xy SoA 2n and z n, float64 numpy or torch, host or CUDA); returns its id."""
+    n = z.shape[0] if hasattr(z, "shape") else len(z)
+    if (xy.numel() if hasattr(xy, "numel") else xy.size) != 2 * n:
+        raise TlrError(TLR_ERR_ARG, "xy must hold 2n values")
+    if isinstance(order, str):
+        order = ORDERS[order]
+    i = ctypes.c_int(-1)
+    _pool_check(load_library().tlr_pool_add(pool.h, _host_or_device_ptr(xy), _host_or_device_ptr(z), int(n),
+                                            int(order), ctypes.c_uint64(seed & (2**64 - 1)), int(nb),
+                                            ctypes.byref(i)))
+    return i.value
+
+
+def tlr_pool_remove(pool: Pool, id: int):
+    _pool_check(load_library().tlr_pool_remove(pool.h, int(id)))
+
+
+def tlr_pool_dataset(pool: Pool, id: int) -> dict:
+    """The dataset's resident data as CUDA tensors (views of the pool's memory; read while it is idle)."""
+    import torch
+    n, nb, mr = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int32()
+    xy, z, perm = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _pool_check(load_library().tlr_pool_dataset(pool.h, int(id), ctypes.byref(n), ctypes.byref(nb),
+                                                ctypes.byref(xy), ctypes.byref(z), ctypes.byref(perm),
+                                                ctypes.byref(mr)))
+    dev = torch.device("cuda", pool.device)
+
+    def copy(addr, count, typestr):
+        # a zero-copy view through the CUDA array interface, then an owned copy
+        buf = _CudaArray(addr, count, typestr)
+        return torch.as_tensor(buf, device=dev).clone()
+
+    N = n.value
+    return {"n": N, "nb": nb.value, "last_max_rank": mr.value,
+            "xy": copy(xy.value, 2 * N, "<f8"), "z": copy(z.value, N, "<f8"), "perm": copy(perm.value, N, "<i8")}
+
+
+class _CudaArray:
+    def __init__(self, addr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (addr, True),
+                                         "version": 2, "strides": None}
+
+
+def tlr_pool_submit(pool: Pool, id: int, theta, eps: float = 1e-7, precision: int = TLR_PREC_FP64) -> int:
+    t = ctypes.c_int64()
+    _pool_check(load_library().tlr_pool_submit(pool.h, int(id), _theta(theta), float(eps), int(precision),
+                                               ctypes.byref(t)))
+    return t.value
+
+
+def tlr_pool_wait(pool: Pool, ticket: int):
+    """Block for a request; returns (result dict, times_ms dict).  Raises TlrError if it failed."""
+    res = tlr_result()
+    tm = (ctypes.c_double * 3)()
+    rc = load_library().tlr_pool_wait(pool.h, int(ticket), ctypes.byref(res), tm)
+    if rc != TLR_OK:
+        raise TlrError(rc, load_library().tlr_pool_last_error().decode(), res.info)
+    return res.as_dict(), {"queue_ms": tm[0], "run_ms": tm[1], "latency_ms": tm[2]}
+
+
+def tlr_pool_loglik(pool: Pool, ids, thetas, eps: float = 1e-7, precision: int = TLR_PREC_FP64):
+    """Batched evaluation; returns (list of result dicts, list of status codes)."""
+    cnt = len(ids)
+    ida = (ctypes.c_int * cnt)(*[int(i) for i in ids])
+    tha = (tlr_theta * cnt)(*[_theta(t) for t in thetas])
+    out = (tlr_result * cnt)()
+    st = (ctypes.c_int * cnt)()
+    load_library().tlr_pool_loglik(pool.h, cnt, ida, tha, float(eps), int(precision), out, st)
+    return [out[i].as_dict() for i in range(cnt)], [st[i] for i in range(cnt)]
+
+
+def tlr_pool_mle(pool: Pool, id: int, theta0, lo, hi, eps: float = 1e-7, precision: int = TLR_PREC_FP64,
+                 tol: float = 1e-9, max_iter: int = 200):
+    th, ll, it = tlr_theta(), ctypes.c_double(), ctypes.c_int()
+    _pool_check(load_library().tlr_pool_mle(pool.h, int(id), float(eps), int(precision), _theta(theta0),
+                                            _theta(lo), _theta(hi), float(tol), int(max_iter), ctypes.byref(th),
+                                            ctypes.byref(ll), ctypes.byref(it)))
+    return (th.sigma2, th.beta, th.nu), ll.value, it.value
+
+
+def tlr_pool_tune(pool: Pool, id: int, theta, cands, eps: float = 1e-7, precision: int = TLR_PREC_FP64):
+    """Tile-size autotuning of one dataset; returns (best nb, {nb: ms})."""
+    k = len(cands)
+    ca = (ctypes.c_int32 * k)(*[int(c) for c in cands])
+    ms = (ctypes.c_double * k)()
+    best = ctypes.c_int32()
+    _pool_check(load_library().tlr_pool_tune(pool.h, int(id), _theta(theta), float(eps), int(precision), ca, k,
+                                             ctypes.byref(best), ms))
+    return best.value, {int(cands[i]): ms[i] for i in range(k)}
+
+
+def tlr_pool_footprint(n: int, nb: int, maxrank: int = 0) -> dict:
+    """Bytes the pool's admission charges for a dataset: resident data, factor storage, first workspace estimate."""
+    a = (ctypes.c_int64 * 3)()
+    _pool_check(load_library().tlr_pool_footprint(int(n), int(nb), int(maxrank), a))
+    return {"base": a[0], "factor": a[1], "work": a[2]}
+
+
+def tlr_pool_stats(pool: Pool) -> dict:
+    a = (ctypes.c_int64 * len(POOL_STATS))()
+    k = load_library().tlr_pool_stats(pool.h, a, len(POOL_STATS))
+    if k < 0:
+        _pool_check(k)
+    return {POOL_STATS[i]: a[i] for i in range(k)}
+
+
+def tlr_sched_simulate(budget: int, workers: int, base, factor, work, req_data, req_arrival, req_cost):
+    """Host-only simulation of the pool's admission policy; returns (start, finish, peak, evictions)."""
+    import numpy as np
+    base = np.ascontiguousarray(base, dtype=np.int64)
+    factor = np.ascontiguousarray(factor, dtype=np.int64)
+    work = np.ascontiguousarray(work, dtype=np.int64)
+    rd = np.ascontiguousarray(req_data, dtype=np.int32)
+    ra = np.ascontiguousarray(req_arrival, dtype=np.float64)
+    rc_ = np.ascontiguousarray(req_cost, dtype=np.float64)
+    start = np.zeros(len(rd))
+    finish = np.zeros(len(rd))
+    peak, ev = ctypes.c_int64(), ctypes.c_int64()
+    vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+    rc = load_library().tlr_sched_simulate(int(budget), int(workers), len(base), vp(base), vp(factor), vp(work),
+                                           len(rd), vp(rd), vp(ra), vp(rc_), vp(start), vp(finish),
+                                           ctypes.byref(peak), ctypes.byref(ev))
+    _pool_check(rc)
+    return start, finish, peak.value, ev.value

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 
 #include "common.cuh"
 #include "compress.cuh"
@@ -63,6 +64,91 @@ static MaternParams params_of(tlr_theta th) {
         throw make_error(TLR_ERR_ARG, "theta must be positive and finite (sigma2=%g beta=%g nu=%g)",
                          th.sigma2, th.beta, th.nu);
     return P;
+}
+
+bool mle_bounds_ok(tlr_theta lo, tlr_theta hi) {
+    return lo.sigma2 > 0 && lo.beta > 0 && lo.nu > 0 && hi.sigma2 >= lo.sigma2 && hi.beta >= lo.beta &&
+           hi.nu >= lo.nu && std::isfinite(hi.sigma2) && std::isfinite(hi.beta) && std::isfinite(hi.nu);
+}
+
+void mle_nelder_mead(const std::function<double(tlr_theta)> &negll, tlr_theta theta0, tlr_theta lo,
+                     tlr_theta hi, double tol, int max_iter, tlr_theta *theta_hat, double *ll_hat, int *iters) {
+    const double llo[3] = {std::log(lo.sigma2), std::log(lo.beta), std::log(lo.nu)};
+    const double lhi[3] = {std::log(hi.sigma2), std::log(hi.beta), std::log(hi.nu)};
+    int evals = 0;
+    auto clampv = [&](double *v) {
+        for (int d = 0; d < 3; ++d) v[d] = std::min(lhi[d], std::max(llo[d], v[d]));
+    };
+    // the search runs in log(theta)
+    auto f = [&](const double *v) -> double {
+        ++evals;
+        return negll(tlr_theta{std::exp(v[0]), std::exp(v[1]), std::exp(v[2])});
+    };
+    double x[4][3], fx[4];
+    double v0[3] = {std::log(theta0.sigma2), std::log(theta0.beta), std::log(theta0.nu)};
+    clampv(v0);
+    for (int p = 0; p < 4; ++p) {
+        for (int d = 0; d < 3; ++d) x[p][d] = v0[d];
+        if (p > 0) x[p][p - 1] += 0.1;
+        clampv(x[p]);
+        fx[p] = f(x[p]);
+    }
+    // Nelder-Mead (reflection 1, expansion 2, contraction 1/2, shrink 1/2)
+    while (evals < max_iter) {
+        int idx[4] = {0, 1, 2, 3};
+        std::sort(idx, idx + 4, [&](int a, int b) { return fx[a] < fx[b]; });
+        double xs[4][3], fs[4];
+        for (int p = 0; p < 4; ++p) {
+            fs[p] = fx[idx[p]];
+            for (int d = 0; d < 3; ++d) xs[p][d] = x[idx[p]][d];
+        }
+        std::memcpy(x, xs, sizeof x);
+        std::memcpy(fx, fs, sizeof fx);
+        if (std::isfinite(fx[3]) && std::fabs(fx[3] - fx[0]) <= tol * (1.0 + std::fabs(fx[0]))) break;
+        double diam = 0.0;  // simplex size in log(theta)
+        for (int p = 1; p < 4; ++p)
+            for (int d = 0; d < 3; ++d) diam = std::max(diam, std::fabs(x[p][d] - x[0][d]));
+        if (diam < 1e-8) break;
+        double c[3] = {0, 0, 0};
+        for (int p = 0; p < 3; ++p)
+            for (int d = 0; d < 3; ++d) c[d] += x[p][d] / 3.0;
+        double xr[3], xe[3], xc[3];
+        for (int d = 0; d < 3; ++d) xr[d] = c[d] + (c[d] - x[3][d]);
+        clampv(xr);
+        double fr = f(xr);
+        if (fr < fx[0]) {
+            for (int d = 0; d < 3; ++d) xe[d] = c[d] + 2.0 * (c[d] - x[3][d]);
+            clampv(xe);
+            double fe = f(xe);
+            if (fe < fr) { std::memcpy(x[3], xe, sizeof xe); fx[3] = fe; }
+            else { std::memcpy(x[3], xr, sizeof xr); fx[3] = fr; }
+        } else if (fr < fx[2]) {
+            std::memcpy(x[3], xr, sizeof xr);
+            fx[3] = fr;
+        } else {
+            bool outside = fr < fx[3];
+            for (int d = 0; d < 3; ++d)
+                xc[d] = outside ? c[d] + 0.5 * (xr[d] - c[d]) : c[d] + 0.5 * (x[3][d] - c[d]);
+            clampv(xc);
+            double fc = f(xc);
+            if (fc < (outside ? fr : fx[3])) {
+                std::memcpy(x[3], xc, sizeof xc);
+                fx[3] = fc;
+            } else {
+                for (int p = 1; p < 4; ++p) {
+                    for (int d = 0; d < 3; ++d) x[p][d] = x[0][d] + 0.5 * (x[p][d] - x[0][d]);
+                    fx[p] = f(x[p]);
+                }
+            }
+        }
+    }
+    int best = 0;
+    for (int p = 1; p < 4; ++p)
+        if (fx[p] < fx[best]) best = p;
+    if (!std::isfinite(fx[best])) throw make_error(TLR_ERR_NOT_SPD, "no feasible likelihood evaluation");
+    *theta_hat = tlr_theta{std::exp(x[best][0]), std::exp(x[best][1]), std::exp(x[best][2])};
+    *ll_hat = -fx[best];
+    *iters = evals;
 }
 
 }  // namespace tlr
@@ -472,20 +558,11 @@ int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tl
             tlr_theta *theta_hat, double *ll_hat, int *iters, void *stream) {
     return guarded(ctx, [&] {
         check_arg(theta_hat && ll_hat && iters && max_iter > 0 && tol > 0, "mle outputs");
-        check_arg(lo.sigma2 > 0 && lo.beta > 0 && lo.nu > 0 && hi.sigma2 >= lo.sigma2 && hi.beta >= lo.beta &&
-                      hi.nu >= lo.nu, "bounds");
+        check_arg(mle_bounds_ok(lo, hi), "bounds");
         cudaStream_t s = (cudaStream_t)stream;
-        const double llo[3] = {std::log(lo.sigma2), std::log(lo.beta), std::log(lo.nu)};
-        const double lhi[3] = {std::log(hi.sigma2), std::log(hi.beta), std::log(hi.nu)};
-        int evals = 0;
-        auto clampv = [&](double *v) {
-            for (int d = 0; d < 3; ++d) v[d] = std::min(lhi[d], std::max(llo[d], v[d]));
-        };
-        // f = -l(theta) in log coordinates; failed evaluations are +inf
-        auto f = [&](const double *v) -> double {
-            tlr_theta th{std::exp(v[0]), std::exp(v[1]), std::exp(v[2])};
+        // f = -l(theta); failed evaluations are +inf
+        auto f = [&](tlr_theta th) -> double {
             tlr_result r;
-            ++evals;
             try {
                 loglik_impl(ctx, xy, z, n, th, opts, L, &r, s);
             } catch (const Error &e) {
@@ -497,71 +574,7 @@ int tlr_mle(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, const tl
             }
             return -r.loglik;
         };
-        double x[4][3], fx[4];
-        double v0[3] = {std::log(theta0.sigma2), std::log(theta0.beta), std::log(theta0.nu)};
-        clampv(v0);
-        for (int p = 0; p < 4; ++p) {
-            for (int d = 0; d < 3; ++d) x[p][d] = v0[d];
-            if (p > 0) x[p][p - 1] += 0.1;
-            clampv(x[p]);
-            fx[p] = f(x[p]);
-        }
-        // Nelder-Mead (reflection 1, expansion 2, contraction 1/2, shrink 1/2)
-        while (evals < max_iter) {
-            int idx[4] = {0, 1, 2, 3};
-            std::sort(idx, idx + 4, [&](int a, int b) { return fx[a] < fx[b]; });
-            double xs[4][3], fs[4];
-            for (int p = 0; p < 4; ++p) {
-                fs[p] = fx[idx[p]];
-                for (int d = 0; d < 3; ++d) xs[p][d] = x[idx[p]][d];
-            }
-            std::memcpy(x, xs, sizeof x);
-            std::memcpy(fx, fs, sizeof fx);
-            if (std::isfinite(fx[3]) && std::fabs(fx[3] - fx[0]) <= tol * (1.0 + std::fabs(fx[0]))) break;
-            double diam = 0.0;  // simplex size in log(theta)
-            for (int p = 1; p < 4; ++p)
-                for (int d = 0; d < 3; ++d) diam = std::max(diam, std::fabs(x[p][d] - x[0][d]));
-            if (diam < 1e-8) break;
-            double c[3] = {0, 0, 0};
-            for (int p = 0; p < 3; ++p)
-                for (int d = 0; d < 3; ++d) c[d] += x[p][d] / 3.0;
-            double xr[3], xe[3], xc[3];
-            for (int d = 0; d < 3; ++d) xr[d] = c[d] + (c[d] - x[3][d]);
-            clampv(xr);
-            double fr = f(xr);
-            if (fr < fx[0]) {
-                for (int d = 0; d < 3; ++d) xe[d] = c[d] + 2.0 * (c[d] - x[3][d]);
-                clampv(xe);
-                double fe = f(xe);
-                if (fe < fr) { std::memcpy(x[3], xe, sizeof xe); fx[3] = fe; }
-                else { std::memcpy(x[3], xr, sizeof xr); fx[3] = fr; }
-            } else if (fr < fx[2]) {
-                std::memcpy(x[3], xr, sizeof xr);
-                fx[3] = fr;
-            } else {
-                bool outside = fr < fx[3];
-                for (int d = 0; d < 3; ++d)
-                    xc[d] = outside ? c[d] + 0.5 * (xr[d] - c[d]) : c[d] + 0.5 * (x[3][d] - c[d]);
-                clampv(xc);
-                double fc = f(xc);
-                if (fc < (outside ? fr : fx[3])) {
-                    std::memcpy(x[3], xc, sizeof xc);
-                    fx[3] = fc;
-                } else {
-                    for (int p = 1; p < 4; ++p) {
-                        for (int d = 0; d < 3; ++d) x[p][d] = x[0][d] + 0.5 * (x[p][d] - x[0][d]);
-                        fx[p] = f(x[p]);
-                    }
-                }
-            }
-        }
-        int best = 0;
-        for (int p = 1; p < 4; ++p)
-            if (fx[p] < fx[best]) best = p;
-        if (!std::isfinite(fx[best])) throw make_error(TLR_ERR_NOT_SPD, "no feasible likelihood evaluation");
-        *theta_hat = tlr_theta{std::exp(x[best][0]), std::exp(x[best][1]), std::exp(x[best][2])};
-        *ll_hat = -fx[best];
-        *iters = evals;
+        mle_nelder_mead(f, theta0, lo, hi, tol, max_iter, theta_hat, ll_hat, iters);
     });
 }
 

@@ -1,6 +1,8 @@
 // Internal interfaces between the TLR driver (tlr.cu) and the C ABI (api.cu).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 #include "matern.cuh"
 
@@ -85,5 +87,16 @@ void gather(const int64_t *perm, const double *src, int64_t n, double *dst, cuda
 // covariance (matern.cu)
 void generate_tiles(const double *xy, int64_t n, int nb, const MaternParams &P, double *tiles, cudaStream_t s);
 void matern_vec(const double *d, int64_t m, const MaternParams &P, double *out, cudaStream_t s);
+
+// Bounds of a maximum-likelihood search: positive, finite, lo <= hi.
+bool mle_bounds_ok(tlr_theta lo, tlr_theta hi);
+
+// Derivative-free maximum-likelihood search (Sec. 5.1): Nelder-Mead in
+// log(theta) over the box [lo, hi] (bounds by clamping) on negll(theta) =
+// -l(theta), +inf for a failed evaluation.  Stops when the simplex spread in
+// -l falls below tol * (1 + |l|), its size in log(theta) below 1e-8, or after
+// max_iter evaluations.  Throws NOT_SPD if no evaluation was finite.
+void mle_nelder_mead(const std::function<double(tlr_theta)> &negll, tlr_theta theta0, tlr_theta lo,
+                     tlr_theta hi, double tol, int max_iter, tlr_theta *theta_hat, double *ll_hat, int *iters);
 
 }  // namespace tlr

@@ -50,9 +50,10 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "tlr.h"
 int main(void) {
-  printf("%zu %zu %zu\\n", sizeof(tlr_theta), sizeof(tlr_opts), sizeof(tlr_result));
+  printf("%zu %zu %zu %zu\\n", sizeof(tlr_theta), sizeof(tlr_opts), sizeof(tlr_result), sizeof(tlr_pool_opts));
   printf("%zu %zu %zu %zu\\n", offsetof(tlr_opts, eps), offsetof(tlr_opts, precision),
          offsetof(tlr_result, info), offsetof(tlr_result, ms_total));
+  printf("%zu\\n", offsetof(tlr_pool_opts, hbm_budget));
   return 0;
 }
 """)
@@ -60,9 +61,10 @@ int main(void) {
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     sizes = [int(v) for v in out]
-    assert sizes[:3] == [ctypes.sizeof(tlr.tlr_theta), ctypes.sizeof(tlr.tlr_opts), ctypes.sizeof(tlr.tlr_result)]
-    assert sizes[3:] == [tlr.tlr_opts.eps.offset, tlr.tlr_opts.precision.offset, tlr.tlr_result.info.offset,
-                         tlr.tlr_result.ms_total.offset]
+    assert sizes[:4] == [ctypes.sizeof(tlr.tlr_theta), ctypes.sizeof(tlr.tlr_opts), ctypes.sizeof(tlr.tlr_result),
+                         ctypes.sizeof(tlr.tlr_pool_opts)]
+    assert sizes[4:] == [tlr.tlr_opts.eps.offset, tlr.tlr_opts.precision.offset, tlr.tlr_result.info.offset,
+                         tlr.tlr_result.ms_total.offset, tlr.tlr_pool_opts.hbm_budget.offset]
 
 
 def test_context_creation_fails_cleanly_without_gpu(lib):
