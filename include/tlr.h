@@ -349,7 +349,8 @@ typedef struct tlr_pool tlr_pool;
 typedef struct {
     int32_t workers;    /* concurrent evaluations, 1..64 */
     int32_t nb;         /* tile size of datasets added with nb <= 0 (16..1024) */
-    int32_t maxrank;    /* off-diagonal rank slots per tile; <= 0 selects nb / 2 */
+    int32_t maxrank;    /* off-diagonal rank slots per tile, capped at each dataset's
+                           tile size; <= 0 selects half the tile size */
     uint32_t flags;     /* reserved, 0 */
     int64_t hbm_budget; /* device bytes the pool may hold (resident data, factors,
                            workspace); <= 0 selects 90% of the free memory */

@@ -572,7 +572,7 @@ def tlr_pool_dataset(pool: Pool, id: int) -> dict:
 
 class _CudaArray:
     def __init__(self, addr: int, count: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (addr, True),
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (addr, False),
                                          "version": 2, "strides": None}
 
 

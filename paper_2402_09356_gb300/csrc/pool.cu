@@ -282,7 +282,6 @@ int tlr_pool_create(int device, const tlr_pool_opts *opts, tlr_pool **out) {
     *out = nullptr;
     if (opts->workers < 1 || opts->workers > 64) return pool_fail(TLR_ERR_ARG, "workers must be 1..64");
     if (opts->nb < 16 || opts->nb > kMaxTile) return pool_fail(TLR_ERR_ARG, "nb must be 16..1024");
-    if (opts->maxrank > opts->nb) return pool_fail(TLR_ERR_ARG, "maxrank > nb");
     if (opts->flags != 0) return pool_fail(TLR_ERR_ARG, "flags");
     auto *p = new tlr_pool();
     p->device = device;

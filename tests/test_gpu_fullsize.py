@@ -1,0 +1,117 @@
+"""Parity at the full benchmark size (n = 40,000, tile 800, eps = 1e-7, the
+bench's launch configuration), where the dense oracle likelihood is too slow:
+
+* sampled tiles of L L' against the oracle's covariance tiles.  In the
+  left-looking factorisation tile (i, j) of L L' equals Sigma_ij minus the one
+  truncation made when T_ij = Sigma_ij - sum_k L_ik L_jk' was compressed
+  (Sec. 2: singular values <= eps sigma2 dropped), so its spectral-norm error
+  is at most eps sigma2 (small slack for the randomised range finder and
+  rounding); diagonal tiles are exact up to the covariance entries' own
+  1e-12 relative accuracy (spectral norm <= nb 1e-12 sigma2) and rounding.
+* the log-determinant equals 2 sum log diag(L_jj) read back from the factor.
+* exact l is invariant under any permutation of the locations (Sec. 3): the
+  Hilbert and Morton results agree within twice the 10 eps |l| bound each
+  meets, and the mixed path stays within 1e-6 |l| of the FP64 path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+N, NB, EPS, THETA = 40000, 800, 1e-7, (1.0, 0.1, 0.5)
+SAMPLED = [(0, 0), (1, 0), (2, 1), (25, 24), (30, 10), (49, 0), (49, 48)]
+
+
+def factor(ctx, order, precision):
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    xy = synth.jittered_grid(N, seed=1)
+    w = synth.standard_normal(N, seed=2)
+    xy_d = torch.from_numpy(xy).cuda()
+    xyo = torch.empty_like(xy_d)
+    perm = tlr.tlr_order(ctx, xy_d, order, xy_out=xyo)
+    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(w).cuda())
+    L = tlr.TlrMatrix(ctx, N, NB)
+    r = tlr.tlr_loglik(L, xyo, zo, THETA, tlr.Options(nb=NB, eps=EPS, precision=precision))
+    return L, r, xyo.cpu().numpy()
+
+
+class Tiles:
+    """Factor tiles read back to the host: L_jj dense, L_ij = U_ij V_ij'."""
+
+    def __init__(self, L):
+        import paper_2402_09356_gb300 as tlr
+        self.L, self.tlr, self.cache = L, tlr, {}
+
+    def get(self, i, j):
+        if (i, j) not in self.cache:
+            t = self.tlr.tlr_mat_tile(self.L, i, j)
+            self.cache[(i, j)] = t.cpu().numpy() if i == j else (t[0].cpu().numpy(), t[1].cpu().numpy())
+        return self.cache[(i, j)]
+
+    def llt(self, i, j):
+        """Tile (i, j), i >= j, of L L'."""
+        acc = 0.0
+        for k in range(j):
+            Ui, Vi = self.get(i, k)
+            Uj, Vj = self.get(j, k)
+            acc = acc + Ui @ ((Vi.T @ Vj) @ Uj.T)
+        Ljj = self.get(j, j)
+        if i == j:
+            return acc + Ljj @ Ljj.T
+        Ui, Vi = self.get(i, j)
+        return acc + Ui @ (Vi.T @ Ljj.T)
+
+
+def block_xy(xy, t):
+    n = xy.size // 2
+    a, b = t * NB, min(n, (t + 1) * NB)
+    return np.concatenate([xy[:n][a:b], xy[n:][a:b]])
+
+
+@pytest.fixture(scope="module")
+def hilbert64(ctx):
+    import paper_2402_09356_gb300 as tlr
+    L, r, xyo = factor(ctx, "hilbert", tlr.TLR_PREC_FP64)
+    yield L, r, xyo
+    L.close()
+
+
+def test_fullsize_sampled_tiles_of_llt(ctx, hilbert64):
+    L, r, xyo = hilbert64
+    tiles = Tiles(L)
+    for i, j in SAMPLED:
+        S = oracle.cov_block(block_xy(xyo, i), block_xy(xyo, j), THETA)
+        err = np.linalg.norm(tiles.llt(i, j) - S, 2)
+        if i == j:
+            assert err <= 2.5 * NB * 1e-12 * THETA[0], (i, j, err)
+        else:
+            assert err <= 1.5 * EPS * THETA[0], (i, j, err)
+
+
+def test_fullsize_logdet_from_diagonal(ctx, hilbert64):
+    L, r, _ = hilbert64
+    tiles = Tiles(L)
+    nt = (N + NB - 1) // NB
+    s = sum(np.log(np.diag(tiles.get(t, t))).sum() for t in range(nt))
+    assert abs(2 * s - r["logdet"]) <= 1e-11 * abs(r["logdet"])
+
+
+def test_fullsize_ordering_invariance_and_mixed(ctx, hilbert64):
+    import paper_2402_09356_gb300 as tlr
+    _, r64, _ = hilbert64
+    Lm, rm, _ = factor(ctx, "morton", tlr.TLR_PREC_FP64)
+    Lm.close()
+    Lx, rx, xyo = factor(ctx, "hilbert", tlr.TLR_PREC_MIXED)
+    ref = abs(r64["loglik"])
+    assert abs(rm["loglik"] - r64["loglik"]) <= 20 * EPS * ref, (rm["loglik"], r64["loglik"])
+    assert abs(rx["loglik"] - r64["loglik"]) <= 1e-6 * ref, (rx["loglik"], r64["loglik"])
+    # the mixed factor meets the same tile bound
+    tiles = Tiles(Lx)
+    for i, j in SAMPLED[1:4]:
+        S = oracle.cov_block(block_xy(xyo, i), block_xy(xyo, j), THETA)
+        assert np.linalg.norm(tiles.llt(i, j) - S, 2) <= 1.5 * EPS * THETA[0]
+    Lx.close()

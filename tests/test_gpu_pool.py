@@ -16,6 +16,9 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
+# rank slots: the whole tile (maxrank = nb), so that no request of these small
+# cases stops at a rank cap
+FULL = 1024
 KEYS = ("loglik", "logdet", "quad", "max_rank", "mean_rank", "offdiag_bytes")
 
 
@@ -25,10 +28,12 @@ def make(n, seed, theta):
     return xy, z
 
 
-def alone(ctx, pool, did, seq, maxrank=0):
-    """The dataset's request sequence on one context and one tlr_mat."""
+def alone(ctx, pool, did, seq):
+    """The dataset's request sequence on one context and one tlr_mat (rank
+    slots = the tile size, as in the pools below)."""
     import paper_2402_09356_gb300 as tlr
     d = tlr.tlr_pool_dataset(pool, did)
+    maxrank = d["nb"]
     L = tlr.TlrMatrix(ctx, d["n"], d["nb"], maxrank)
     out = []
     for theta, eps, prec in seq:
@@ -79,7 +84,7 @@ def sequences(ids, steps, seed, precisions):
 def test_pool_identical_alone_and_in_the_mix(ctx):
     import paper_2402_09356_gb300 as tlr
     sizes = [700, 1500, 2300, 3100, 1201]
-    pool = tlr.Pool(0, workers=3, nb=256)
+    pool = tlr.Pool(0, workers=3, nb=256, maxrank=FULL)
     ids, data = [], {}
     for j, n in enumerate(sizes):
         xy, z = make(n, 11 * j + 1, (1.0, 0.1, 0.5))
@@ -100,6 +105,7 @@ def test_pool_identical_alone_and_in_the_mix(ctx):
         perm = got["perm"].cpu().numpy()
         assert np.array_equal(perm, oracle.order(xy, "morton")[0])
         theta, eps, prec = seqs[d][0]
+        assert isinstance(mix[d][0], dict), ("first request failed", d, mix[d][0])
         exact = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
         assert abs(mix[d][0]["loglik"] - exact) <= 10 * eps * abs(exact), (d, mix[d][0]["loglik"], exact)
     pool.close()
@@ -109,10 +115,12 @@ def test_pool_tight_budget_evicts_and_stays_identical(ctx):
     import paper_2402_09356_gb300 as tlr
     sizes = [1800, 2600, 1000, 2600]
     nb = 200
-    fps = [tlr.tlr_pool_footprint(n, nb) for n in sizes]
-    # room for the resident data plus about two factors: every round evicts
-    budget = sum(f["base"] for f in fps) + 2 * max(f["factor"] + f["work"] for f in fps)
-    pool = tlr.Pool(0, workers=2, nb=nb, hbm_budget=budget)
+    fps = [tlr.tlr_pool_footprint(n, nb, nb) for n in sizes]
+    # room for the resident data and for the largest dataset to run alone: all
+    # four factors (about 160 MB) plus any workspace (at least 64 MiB) do not
+    # fit, so requests of different datasets evict one another
+    budget = sum(f["base"] for f in fps) + max(f["factor"] + f["work"] for f in fps)
+    pool = tlr.Pool(0, workers=2, nb=nb, maxrank=FULL, hbm_budget=budget)
     ids = []
     for j, n in enumerate(sizes):
         xy, z = make(n, 7 * j + 3, (1.0, 0.1, 1.0))
@@ -134,7 +142,7 @@ def test_pool_batched_many_small_datasets(ctx):
     import paper_2402_09356_gb300 as tlr
     rng = np.random.default_rng(4)
     sizes = rng.integers(300, 2500, 24)
-    pool = tlr.Pool(0, workers=8, nb=192)
+    pool = tlr.Pool(0, workers=8, nb=192, maxrank=FULL)
     ids = []
     thetas = []
     for j, n in enumerate(sizes):
@@ -156,7 +164,7 @@ def test_pool_mle_matches_tlr_mle_beside_other_traffic(ctx):
     import torch
     import paper_2402_09356_gb300 as tlr
     theta_true = (1.0, 0.1, 0.5)
-    pool = tlr.Pool(0, workers=3, nb=200)
+    pool = tlr.Pool(0, workers=3, nb=200, maxrank=FULL)
     xy, z = make(1600, 41, theta_true)
     did = tlr.tlr_pool_add(pool, xy, z, "morton")
     others = [tlr.tlr_pool_add(pool, *make(n, 50 + n, theta_true), "morton") for n in (900, 1400)]
@@ -176,8 +184,9 @@ def test_pool_mle_matches_tlr_mle_beside_other_traffic(ctx):
         tlr.tlr_pool_wait(pool, tk)
     th, ll, it = got["r"]
     d = tlr.tlr_pool_dataset(pool, did)
-    L = tlr.TlrMatrix(ctx, d["n"], d["nb"])
-    ref = tlr.tlr_mle(L, d["xy"], d["z"], tlr.Options(nb=d["nb"], eps=1e-7), start, lo, hi, tol=1e-7, max_iter=60)
+    L = tlr.TlrMatrix(ctx, d["n"], d["nb"], d["nb"])
+    ref = tlr.tlr_mle(L, d["xy"], d["z"], tlr.Options(nb=d["nb"], eps=1e-7, maxrank=d["nb"]), start, lo, hi,
+                      tol=1e-7, max_iter=60)
     torch.cuda.synchronize()
     assert ref["theta"] == th and ref["loglik"] == ll and ref["iters"] == it
     L.close()
@@ -186,7 +195,7 @@ def test_pool_mle_matches_tlr_mle_beside_other_traffic(ctx):
 
 def test_pool_tune_picks_a_candidate(ctx):
     import paper_2402_09356_gb300 as tlr
-    pool = tlr.Pool(0, workers=2, nb=256)
+    pool = tlr.Pool(0, workers=2, nb=256, maxrank=FULL)
     xy, z = make(2400, 9, (1.0, 0.1, 0.5))
     did = tlr.tlr_pool_add(pool, xy, z, "hilbert")
     best, ms = tlr.tlr_pool_tune(pool, did, (1.0, 0.1, 0.5), [160, 240, 400])
@@ -204,7 +213,7 @@ def test_pool_tune_picks_a_candidate(ctx):
 
 def test_pool_errors_are_per_request(ctx):
     import paper_2402_09356_gb300 as tlr
-    pool = tlr.Pool(0, workers=2, nb=128)
+    pool = tlr.Pool(0, workers=2, nb=128, maxrank=FULL)
     xy, z = make(500, 3, (1.0, 0.1, 0.5))
     did = tlr.tlr_pool_add(pool, xy, z, "morton")
     with pytest.raises(tlr.TlrError) as e:
