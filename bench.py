@@ -417,7 +417,7 @@ def run_reference(args):
 # ---- many datasets: batched evaluation (256 datasets) and serving -----------
 
 BATCH_BUCKETS = ((2000, 5000), (5000, 10000), (10000, 20001))
-BATCH_TILE_CANDIDATES = (256, 384, 512, 800)
+BATCH_TILE_CANDIDATES = (384, 512, 800, 1024)
 
 
 def batched_datasets(count: int, seed: int = 2024):
@@ -489,10 +489,18 @@ def run_batched(args):
         total = sum(times)
         out[name] = {"evals_per_s": count * args.steps / total, "s_per_step": total / args.steps,
                      "failed": fails, "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
-    rel = [abs(a - b) / abs(b) for ra, rb in zip(out["mixed"]["results"], out["fp64"]["results"])
-           for a, b in zip(ra, rb) if a is not None and b is not None]
+    rel, pairs = [], []
+    for k, (ra, rb) in enumerate(zip(out["mixed"]["results"], out["fp64"]["results"])):
+        for i, (a, b) in enumerate(zip(ra, rb)):
+            if a is not None and b is not None:
+                rel.append(abs(a - b) / abs(b))
+                pairs.append((rel[-1], int(sizes[i]), [round(float(v), 4) for v in walks[i][args.warmup + k]]))
+    pairs.sort(reverse=True)
+    accuracy = {"pairs": len(rel), "within_1e-6": int(sum(1 for r in rel if r <= 1e-6)),
+                "median": float(np.median(rel)) if rel else None,
+                "worst": [{"rel": r, "n": n, "theta": th} for r, n, th in pairs[:6]]}
     st = tlr.tlr_pool_stats(pool)
-    head = "mixed" if rel and max(rel) <= 1e-6 else "fp64"
+    head = "mixed" if rel and max(rel) <= 1e-6 else "fp64"  # every evaluated pair within 1e-6
     line = {"metric": "batched TLR l(theta) evals/s, %d datasets n~U[2000,20000]" % count,
             "value": out[head]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * out[head]["s_per_step"], "higher_is_better": True,
@@ -508,6 +516,7 @@ def run_batched(args):
             "fp64_path": {k: v for k, v in out["fp64"].items() if k != "results"},
             "mixed_path": {k: v for k, v in out["mixed"].items() if k != "results"},
             "rel_dl_mixed_vs_fp64_max": max(rel) if rel else None,
+            "mixed_vs_fp64": accuracy,
             "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
             "gpu_launches": out[head]["gpu_launches"]}
     print(json.dumps(line), flush=True)
@@ -578,13 +587,15 @@ def run_serving(args):
             steps_of[d] += 1
             tickets[q] = tlr.tlr_pool_submit(pool, ids[d], th, EPS, prec)
         lat, queue, run, fails = [], [], [], 0
+        lls = [None] * R
         by_n = {n: [] for n in SERVE_SIZES}
         for q in range(R):
             try:
-                _, tm = tlr.tlr_pool_wait(pool, tickets[q])
+                res, tm = tlr.tlr_pool_wait(pool, tickets[q])
             except tlr.TlrError:
                 fails += 1
                 continue
+            lls[q] = res["loglik"]
             lat.append(tm["latency_ms"])
             queue.append(tm["queue_ms"])
             run.append(tm["run_ms"])
@@ -603,7 +614,10 @@ def run_serving(args):
                      "by_n": {str(n): {"count": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99)}
                               for n, v in by_n.items()},
                      "mle": mle_out, "clocks": clk, "gpu_launches": int(tlr.tlr_launch_count() - launches0),
-                     "pool": tlr.tlr_pool_stats(pool)}
+                     "pool": tlr.tlr_pool_stats(pool), "lls": lls}
+    rel = [abs(a - b) / abs(b) for a, b in zip(out["mixed"]["lls"], out["fp64"]["lls"]) if a is not None and b is not None]
+    for name in out:
+        out[name].pop("lls")
     line = {"metric": "served TLR l(theta) evals/s and p50/p99 latency, 32 resident datasets",
             "value": out["mixed"]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": R, "warmup": 5,
             "ms_per_step": 1000.0 / out["mixed"]["evals_per_s"], "higher_is_better": True, "scaling": "weak",
@@ -615,6 +629,8 @@ def run_serving(args):
                        "workers": args.workers, "maxrank": args.maxrank, "rate": args.rate, "requests": R,
                        "latency": "host clock, submission to completion"},
             "fp64_path": out["fp64"], "mixed_path": out["mixed"], "setup_s": setup_s,
+            "mixed_vs_fp64": {"pairs": len(rel), "max": max(rel) if rel else None,
+                              "within_1e-6": int(sum(1 for r in rel if r <= 1e-6))},
             "clocks": out["mixed"]["clocks"], "gpu_launches": out["mixed"]["gpu_launches"]}
     print(json.dumps(line), flush=True)
     pool.close()

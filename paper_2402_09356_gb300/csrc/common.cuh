@@ -134,6 +134,10 @@ struct tlr_ctx {
     tlr::DevStatus *h_status = nullptr;   // pinned host mirror
     cudaStream_t aux = nullptr;           // second stream for concurrent tile work (high priority)
     cudaStream_t la = nullptr;            // look-ahead stream: the next column's panel update
+    // CTAs per SM the look-ahead panel GEMM may hold (shared memory reserved so
+    // that the critical-path kernels keep room); 0 = no reservation (several
+    // factorisations sharing the device)
+    int ahead_ctas_per_sm = 1;
     cudaEvent_t ev_la_fork = nullptr, ev_la_join = nullptr;
     cudaStream_t hp = nullptr;            // high-priority stream of the factorisation's compression
     cudaEvent_t ev_hp_fork = nullptr, ev_hp_join = nullptr;

@@ -298,6 +298,9 @@ int tlr_pool_create(int device, const tlr_pool_opts *opts, tlr_pool **out) {
     for (Worker &W : p->workers) {
         rc = tlr_ctx_create(device, &W.ctx);
         if (rc != TLR_OK) return cleanup(rc, "cannot create a worker context");
+        // several factorisations share the SMs: no look-ahead shared-memory
+        // reservation (it would hold every SM to one look-ahead CTA in total)
+        if (opts->workers > 1) W.ctx->ahead_ctas_per_sm = 0;
         if (cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking) != cudaSuccess)
             return cleanup(TLR_ERR_CUDA, "cannot create a worker stream");
     }

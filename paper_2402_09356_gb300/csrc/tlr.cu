@@ -27,7 +27,6 @@
 
 namespace tlr {
 
-constexpr int kAheadCtasPerSm = 1;
 
 // blockIdx.y: descriptor; blockIdx.x strides over its columns, threads over rows.
 __global__ void k_copy_batched(const CopyDesc *__restrict__ d) {
@@ -110,7 +109,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     // diagonal POTRF.  Two per SM left too little shared memory for the
     // compression's cluster kernels; a fixed subset of whole SMs starved the
     // compression's wide launches.
-    const int ahead_ctas = kAheadCtasPerSm;
+    const int ahead_ctas = ctx->ahead_ctas_per_sm;
     DevBuf panel_buf[2];
     panel_buf[0].alloc((size_t)nt * nb * nb * sizeof(double), st);
     if (ahead) panel_buf[1].alloc((size_t)nt * nb * nb * sizeof(double), st);
