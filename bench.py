@@ -42,6 +42,9 @@ EPS = 1e-7
 THETA0 = (1.0, 0.1, 0.5)
 ORDER = "hilbert"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch from ncu captures of unchanged kernels,
+# by (kernel, tile size); the capture and its command are in profiles/
+NCU_TRAFFIC = {("k_potrf_inv<16>", 800): (3.19e6, "profiles/k_potrf_inv_n16000.md")}
 
 
 def peaks():
@@ -298,10 +301,32 @@ def run_gpu(args):
                 "flops_counted": "FP64 work as executed: M J (2 s^3), norms per sweep (2 s^2), "
                                  "2 s per pair checked, 6 s per pair rotated"}
 
-    # the dominant kernel of the headline path: the larger device time per step
-    cand = [roof_panel(head), roof_jacobi(head)]
+    def roof_potrf(o):
+        # one launch per tile column on the side stream: L = chol(T_jj) and
+        # L^-1, m^3/3 + m^3/3 FP64 flops; its in-step time from the events
+        # around it on that stream
+        nt = (N_POINTS + NB - 1) // NB
+        ms_step = o["detail_ms"]["potrf"]
+        avg = ms_step / nt
+        ms = [min(NB, N_POINTS - t * NB) for t in range(nt)]
+        fl = sum(2.0 * m ** 3 / 3.0 for m in ms) / nt
+        achieved = fl / (avg / 1000.0) / 1e12 if avg > 0 else 0.0
+        occupied = 16 * 4 * sm_mhz * 1e6 / 1e12
+        traffic = NCU_TRAFFIC.get(("k_potrf_inv<16>", NB))
+        return {"bound": "alu", "kernel": "k_potrf_inv<16> (diagonal tile Cholesky + inverse, one 16-CTA cluster)",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if fp64_peak else None,
+                "traffic": traffic[0] if traffic else None,
+                "traffic_source": traffic[1] if traffic else None,
+                "peak_source": "FP64 DFMA pipe: %d SMs x 4 flop/clk x %.0f MHz (sampled SM clock)" % (n_sms, sm_mhz),
+                "frac_of_occupied_sms": achieved / occupied if occupied else None,
+                "launch_ms_avg": avg, "launches": nt * args.steps, "flops_per_launch": fl,
+                "total_ms": ms_step * args.steps}
+
+    # the dominant kernel of the headline path: the largest device time per step
+    cand = [roof_panel(head), roof_jacobi(head), roof_potrf(head)]
     roofline = max(cand, key=lambda r: r["total_ms"])
-    other = [r for r in cand if r is not roofline][0]
+    other = [r for r in cand if r is not roofline]
 
     def summary(o):
         res = o["results"]
