@@ -358,8 +358,9 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f64 storage, paired-f32 products" if head_name == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": "ordering study, n=%d (perturbed grid), Matern sigma2=1 beta=0.1 nu=0.5 "
-                               "walk start, %s, tile %d, eps %g, %s path" % (N_POINTS, ORDER, NB, EPS, head_name),
+        "config": {"workload": "ordering study, n=%d (perturbed grid), Matern sigma2=%g beta=%g nu=%g "
+                               "walk start, %s, tile %d, eps %g, %s path" % ((N_POINTS,) + tuple(THETA0) +
+                                                                            (ORDER, NB, EPS, head_name)),
                    "n": N_POINTS, "nb": NB, "eps": EPS, "ordering": ORDER, "theta0": list(THETA0),
                    "precision": head_name,
                    "theta_walk": "log-space, scale 0.05/step, seed 7",
@@ -662,7 +663,7 @@ def run_serving(args):
 
 
 def main():
-    global N_POINTS, NB, EPS, ORDER
+    global N_POINTS, NB, EPS, ORDER, THETA0
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -673,6 +674,7 @@ def main():
     ap.add_argument("--nb", type=int, default=NB)
     ap.add_argument("--eps", type=float, default=EPS)
     ap.add_argument("--order", default=ORDER)
+    ap.add_argument("--theta", default=None, help="walk start sigma2,beta,nu (default 1,0.1,0.5)")
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="precision paths to time (both for the headline; one for profiling runs)")
     ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serving"],
@@ -686,6 +688,8 @@ def main():
     ap.add_argument("--mle-iters", type=int, default=30, help="evaluations per MLE job (serving)")
     args = ap.parse_args()
     N_POINTS, NB, EPS, ORDER = args.n, args.nb, args.eps, args.order
+    if args.theta:
+        THETA0 = tuple(float(v) for v in args.theta.split(","))
     if args.impl == "reference":
         run_reference(args)
         return

@@ -12,7 +12,13 @@ bench's launch configuration), where the dense oracle likelihood is too slow:
 * exact l is invariant under any permutation of the locations (Sec. 3): the
   Hilbert and Morton results agree within twice the 10 eps |l| bound each
   meets, and the mixed path stays within 1e-6 |l| of the FP64 path.
+* both paths' l at full size within 10 eps |l| of the exact value that the
+  dense oracle computed once for this workload (tests/golden/
+  fullsize_loglik_n40000.json, written by make_fullsize_loglik.py).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -115,3 +121,15 @@ def test_fullsize_ordering_invariance_and_mixed(ctx, hilbert64):
         S = oracle.cov_block(block_xy(xyo, i), block_xy(xyo, j), THETA)
         assert np.linalg.norm(tiles.llt(i, j) - S, 2) <= 1.5 * EPS * THETA[0]
     Lx.close()
+
+
+def test_fullsize_loglik_against_exact_oracle(ctx, hilbert64, golden_dir):
+    import paper_2402_09356_gb300 as tlr
+    gold = json.load(open(os.path.join(golden_dir, "fullsize_loglik_n40000.json")))
+    assert gold["n"] == N and tuple(gold["theta"]) == THETA and gold["loc_seed"] == 1 and gold["z_seed"] == 2
+    exact = gold["loglik"]
+    _, r64, _ = hilbert64
+    assert abs(r64["loglik"] - exact) <= 10 * EPS * abs(exact), (r64["loglik"], exact)
+    Lx, rx, _ = factor(ctx, "hilbert", tlr.TLR_PREC_MIXED)
+    Lx.close()
+    assert abs(rx["loglik"] - exact) <= 10 * EPS * abs(exact), (rx["loglik"], exact)
