@@ -478,6 +478,9 @@ def run_batched(args):
         members = [i for i in range(count) if bucket_of[i] == b]
         if not members:
             continue
+        if args.batch_nb > 0:  # a fixed tile size instead of the tuner's choice
+            tuned[b] = {"best_nb": args.batch_nb, "ms": {}}
+            continue
         mid = (lo + hi) / 2
         rep = min(members, key=lambda i: abs(sizes[i] - mid))
         n = int(sizes[rep])
@@ -495,43 +498,63 @@ def run_batched(args):
     walks = [synth.theta_walk(tuple(th0[i]), args.warmup + args.steps, seed=900 + i, scale=0.05) for i in range(count)]
     out = {}
     clocks_all = {}
-    for name, prec in (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED)):
+    paths = (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED), ("auto", tlr.TLR_PREC_AUTO))
+    for name, prec in paths:
         for k in range(args.warmup):
             tlr.tlr_pool_loglik(pool, ids, [tuple(w[k]) for w in walks], eps=EPS, precision=prec)
         clocks = ClockSampler(0)
         torch.cuda.synchronize()
         launches0 = tlr.tlr_launch_count()
         clocks.start()
-        times, results, fails = [], [], 0
+        times, results, fails, used64 = [], [], 0, 0
         for k in range(args.steps):
             t0 = time.perf_counter()
             res, st = tlr.tlr_pool_loglik(pool, ids, [tuple(w[args.warmup + k]) for w in walks], eps=EPS,
                                           precision=prec)
             times.append(time.perf_counter() - t0)
             fails += sum(1 for x in st if x != 0)
-            results.append([r["loglik"] if x == 0 else None for r, x in zip(res, st)])
+            used64 += sum(1 for r, x in zip(res, st) if x == 0 and r["precision_used"] == tlr.TLR_PREC_FP64)
+            results.append([(r["loglik"], r["min_pivot2"]) if x == 0 else None for r, x in zip(res, st)])
         torch.cuda.synchronize()
         clocks_all[name] = clocks.stop()
         total = sum(times)
         out[name] = {"evals_per_s": count * args.steps / total, "s_per_step": total / args.steps,
-                     "failed": fails, "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
-    rel, pairs = [], []
-    for k, (ra, rb) in enumerate(zip(out["mixed"]["results"], out["fp64"]["results"])):
-        for i, (a, b) in enumerate(zip(ra, rb)):
-            if a is not None and b is not None:
-                rel.append(abs(a - b) / abs(b))
-                pairs.append((rel[-1], int(sizes[i]), [round(float(v), 4) for v in walks[i][args.warmup + k]]))
+                     "failed": fails, "fp64_results": used64,
+                     "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
+
+    def compare(name):
+        rel, pairs = [], []
+        for k, (ra, rb) in enumerate(zip(out[name]["results"], out["fp64"]["results"])):
+            for i, (a, b) in enumerate(zip(ra, rb)):
+                if a is not None and b is not None:
+                    rel.append(abs(a[0] - b[0]) / abs(b[0]))
+                    th = walks[i][args.warmup + k]
+                    pairs.append((rel[-1], a[1] / th[0], int(sizes[i]), [round(float(v), 4) for v in th]))
+        return rel, pairs
+
+    rel, pairs = compare("mixed")
+    rel_auto, _ = compare("auto")
+    # calibration of the auto rule: worst mixed-vs-FP64 difference among the
+    # evaluations whose smallest squared pivot (/ sigma2) is at least t
+    calib = {("%g" % t): {"kept": sum(1 for p in pairs if p[1] >= t),
+                          "max_rel": max([p[0] for p in pairs if p[1] >= t], default=None)}
+             for t in (1e-8, 1e-7, 1e-6, 1e-5, 1e-4, 1e-3)}
     pairs.sort(reverse=True)
     accuracy = {"pairs": len(rel), "within_1e-6": int(sum(1 for r in rel if r <= 1e-6)),
                 "median": float(np.median(rel)) if rel else None,
-                "worst": [{"rel": r, "n": n, "theta": th} for r, n, th in pairs[:6]]}
+                "worst": [{"rel": r, "min_pivot2": pv, "n": n, "theta": th} for r, pv, n, th in pairs[:6]],
+                "by_min_pivot2": calib}
+    accuracy_auto = {"pairs": len(rel_auto), "within_1e-6": int(sum(1 for r in rel_auto if r <= 1e-6)),
+                     "max": max(rel_auto) if rel_auto else None}
     st = tlr.tlr_pool_stats(pool)
-    head = "mixed" if rel and max(rel) <= 1e-6 else "fp64"  # every evaluated pair within 1e-6
+    # the fastest path whose every evaluated pair is within 1e-6 of the FP64 path
+    ok = [nm for nm, r in (("mixed", rel), ("auto", rel_auto)) if r and max(r) <= 1e-6]
+    head = max(ok, key=lambda nm: out[nm]["evals_per_s"]) if ok else "fp64"
     line = {"metric": "batched TLR l(theta) evals/s, %d datasets n~U[2000,20000]" % count,
             "value": out[head]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * out[head]["s_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 storage, paired-f32 products" if head == "mixed" else "f64", "data": "synthetic",
+            "dtype": "f64" if head == "fp64" else "f64 storage, paired-f32 products", "data": "synthetic",
             "config": {"workload": "batched: %d datasets, n ~ U[2000, 20000] jittered grids, theta ~ U(sigma2 "
                                    "[0.5,2], beta [0.02,0.3], nu [0.5,2.5]), Morton, eps %g, %d workers"
                                    % (count, EPS, args.workers),
@@ -541,8 +564,10 @@ def run_batched(args):
                        "l2": "inputs (all datasets' factors) larger than L2"},
             "fp64_path": {k: v for k, v in out["fp64"].items() if k != "results"},
             "mixed_path": {k: v for k, v in out["mixed"].items() if k != "results"},
+            "auto_path": {k: v for k, v in out["auto"].items() if k != "results"},
             "rel_dl_mixed_vs_fp64_max": max(rel) if rel else None,
             "mixed_vs_fp64": accuracy,
+            "auto_vs_fp64": accuracy_auto,
             "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
             "gpu_launches": out[head]["gpu_launches"]}
     print(json.dumps(line), flush=True)
@@ -682,6 +707,7 @@ def main():
                          "serving: a Poisson request stream over resident datasets")
     ap.add_argument("--workers", type=int, default=8, help="pool workers (batched / serving)")
     ap.add_argument("--datasets", type=int, default=256, help="datasets of the batched workload")
+    ap.add_argument("--batch-nb", type=int, default=0, help="fixed tile size for the batched workload (0: tuned)")
     ap.add_argument("--maxrank", type=int, default=0, help="rank slots per tile (batched / serving; 0 = nb/2)")
     ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream")
     ap.add_argument("--rate", type=float, default=500.0, help="arrival rate of the serving stream (1/s)")

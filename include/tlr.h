@@ -60,6 +60,16 @@ extern "C" {
  * significant bits); storage, the Matern evaluation, QR/SVD, the diagonal
  * POTRF, the log-determinant and the solve stay FP64. */
 #define TLR_PREC_MIXED 1
+/* Auto: the mixed path, then, if the factor shows an ill-conditioned
+ * covariance (smallest squared pivot min_i L_ii^2 below TLR_AUTO_PIVOT2 sigma2,
+ * i.e. some location nearly determined by the ones before it), the FP64 path
+ * again from the same starting rank map, whose result is returned.  The
+ * paired-FP32 rounding (about 1e-14 relative per product) is amplified by
+ * the covariance's conditioning; below the threshold it can exceed the
+ * 1e-6 |l| agreement with the FP64 path.  tlr_result.precision_used says
+ * which path the result comes from. */
+#define TLR_PREC_AUTO 2
+#define TLR_AUTO_PIVOT2 1e-6
 
 typedef struct tlr_ctx tlr_ctx; /* device, workspace pool, last error, timers */
 typedef struct tlr_mat tlr_mat; /* a TLR matrix or TLR Cholesky factor on the device */
@@ -89,6 +99,8 @@ typedef struct {
     int64_t dense_bytes;  /* Table 1 "Dense": lower off-diagonal tiles * nb^2 * 8 */
     double flops;         /* floating-point operations counted from the rank map */
     float ms_total;       /* device time of the call (CUDA events on `stream`) */
+    int32_t precision_used; /* TLR_PREC_FP64 or TLR_PREC_MIXED: the path the result comes from */
+    double min_pivot2;    /* min_i L_ii^2 over the factor's diagonal (a conditional variance) */
 } tlr_result;
 
 /* ---- context -------------------------------------------------------------- */

@@ -22,6 +22,8 @@ ORDERS = {"identity": 0, "random": 1, "morton": 2, "hilbert": 3, "kdtree": 4, "m
 TLR_ORDER_QUANTIZE = 1
 TLR_PREC_FP64 = 0
 TLR_PREC_MIXED = 1
+TLR_PREC_AUTO = 2
+TLR_AUTO_PIVOT2 = 1e-6
 
 
 class TlrError(RuntimeError):
@@ -44,7 +46,8 @@ class tlr_result(ctypes.Structure):
     _fields_ = [("loglik", ctypes.c_double), ("logdet", ctypes.c_double), ("quad", ctypes.c_double),
                 ("info", ctypes.c_int64), ("max_rank", ctypes.c_int32), ("mean_rank", ctypes.c_double),
                 ("offdiag_bytes", ctypes.c_int64), ("dense_bytes", ctypes.c_int64),
-                ("flops", ctypes.c_double), ("ms_total", ctypes.c_float)]
+                ("flops", ctypes.c_double), ("ms_total", ctypes.c_float), ("precision_used", ctypes.c_int32),
+                ("min_pivot2", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -439,12 +439,9 @@ int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *s
     });
 }
 
-static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
-                        const tlr_opts *opts, tlr_mat *L, tlr_result *out, cudaStream_t s) {
-    check_arg(xy && z && opts && L && out, "xy/z/opts/L/out");
-    check_arg(n > 0 && L->n == n && L->nb == opts->nb, "L does not match n/nb");
-    check_arg(opts->eps >= 0 && std::isfinite(opts->eps), "eps");
-    check_arg(opts->precision == TLR_PREC_FP64 || opts->precision == TLR_PREC_MIXED, "precision");
+// One evaluation on one precision path (df: paired-FP32 products).
+static void loglik_once(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
+                        const tlr_opts *opts, tlr_mat *L, tlr_result *out, cudaStream_t s, bool df) {
     MaternParams P = params_of(theta);
     std::memset(out, 0, sizeof *out);
     out->info = -1;
@@ -453,16 +450,17 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     status_reset(ctx, s);
     FactorStats st;
     long long inf = -1;
-    DevBuf acc(2 * sizeof(double), s), y((size_t)n * sizeof(double), s);
-    TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 2 * sizeof(double), s));
+    DevBuf acc(3 * sizeof(double), s), y((size_t)n * sizeof(double), s);
+    TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 3 * sizeof(double), s));
+    out->precision_used = df ? TLR_PREC_MIXED : TLR_PREC_FP64;
     try {
         factor(ctx, s, L, FactorMode::Matern, xy, &P, opts->eps * theta.sigma2, &st, &inf, z,
-               y.as<double>(), acc.as<double>(), opts->precision == TLR_PREC_MIXED);
+               y.as<double>(), acc.as<double>(), df);
     } catch (const Error &) {
         out->info = inf;
         throw;
     }
-    double h[2];
+    double h[3];
     TLR_CUDA_TRY(cudaMemcpyAsync(h, acc.as<double>(), sizeof h, cudaMemcpyDeviceToHost, s));
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_b, s));
     TLR_CUDA_TRY(cudaStreamSynchronize(s));
@@ -474,6 +472,7 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     }
     out->logdet = 2.0 * h[0];
     out->quad = h[1];
+    out->min_pivot2 = h[2] > 0.0 ? 1.0 / h[2] : INFINITY;
     out->loglik = -0.5 * (double)n * std::log(2.0 * M_PI) - 0.5 * out->logdet - 0.5 * out->quad;
     if (!std::isfinite(out->loglik)) throw make_error(TLR_ERR_NAN, "likelihood is not finite");
     int nt = L->nt;
@@ -502,6 +501,35 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     ctx->last_panel_launches = st.panel_launches;
     for (int k = 0; k < kStages; ++k) ctx->last_stage_ms[k] = st.stage_ms[k];
     for (int k = 0; k < kDetail; ++k) ctx->last_detail_ms[k] = st.detail_ms[k];
+}
+
+static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
+                        const tlr_opts *opts, tlr_mat *L, tlr_result *out, cudaStream_t s) {
+    check_arg(xy && z && opts && L && out, "xy/z/opts/L/out");
+    check_arg(n > 0 && L->n == n && L->nb == opts->nb, "L does not match n/nb");
+    check_arg(opts->eps >= 0 && std::isfinite(opts->eps), "eps");
+    check_arg(opts->precision == TLR_PREC_FP64 || opts->precision == TLR_PREC_MIXED ||
+                  opts->precision == TLR_PREC_AUTO, "precision");
+    if (opts->precision != TLR_PREC_AUTO) {
+        loglik_once(ctx, xy, z, n, theta, opts, L, out, s, opts->precision == TLR_PREC_MIXED);
+        return;
+    }
+    // auto: the mixed path; the FP64 path again, from the same starting rank
+    // map, where the factor shows an ill-conditioned covariance (or the mixed
+    // factorisation met a non-positive pivot)
+    const std::vector<int32_t> hint = L->h_ranks;
+    float ms_mixed = 0.f;
+    try {
+        loglik_once(ctx, xy, z, n, theta, opts, L, out, s, true);
+        if (out->min_pivot2 >= TLR_AUTO_PIVOT2 * theta.sigma2) return;
+        ms_mixed = out->ms_total;
+    } catch (const Error &e) {
+        if (e.code != TLR_ERR_NOT_SPD) throw;
+        TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    L->h_ranks = hint;
+    loglik_once(ctx, xy, z, n, theta, opts, L, out, s, false);
+    out->ms_total += ms_mixed;
 }
 
 int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,

@@ -442,19 +442,35 @@ void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *
                          ctx->d_status, row_base);
 }
 
-// acc[0] += sum_r log A[r, r]  (one block, fixed reduction order)
+// acc[0] += sum_r log A[r, r]  (one block, fixed reduction order); if maxinv
+// is not null, *maxinv = max(*maxinv, max_r 1 / A[r, r]^2) (the largest
+// inverse squared pivot, i.e. the smallest conditional variance seen so far;
+// positive doubles order like their bit patterns, so an integer atomicMax
+// keeps the result independent of launch order).
 __global__ void k_diag_logsum(const double *__restrict__ A, int lda, int m, double *acc,
-                              const DevStatus *st) {
-    __shared__ double part[256];
-    double s = 0.0;
-    for (int r = threadIdx.x; r < m; r += blockDim.x) s += log(A[(int64_t)r * lda + r]);
+                              const DevStatus *st, double *maxinv) {
+    __shared__ double part[256], pmax[256];
+    double s = 0.0, mx = 0.0;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        const double d = A[(int64_t)r * lda + r];
+        s += log(d);
+        mx = fmax(mx, 1.0 / (d * d));
+    }
     part[threadIdx.x] = s;
+    pmax[threadIdx.x] = mx;
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
-        if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        if (threadIdx.x < h) {
+            part[threadIdx.x] += part[threadIdx.x + h];
+            pmax[threadIdx.x] = fmax(pmax[threadIdx.x], pmax[threadIdx.x + h]);
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0 && !st->code) acc[0] += part[0];
+    if (threadIdx.x == 0 && !st->code) {
+        acc[0] += part[0];
+        if (maxinv && pmax[0] > 0.0 && pmax[0] <= 1.7e308)
+            atomicMax(reinterpret_cast<unsigned long long *>(maxinv), (unsigned long long)__double_as_longlong(pmax[0]));
+    }
 }
 
 // acc[0] += sum v_r^2 (one block, fixed reduction order)
@@ -471,8 +487,8 @@ __global__ void k_sumsq(const double *__restrict__ v, int m, double *acc) {
     if (threadIdx.x == 0) acc[0] += part[0];
 }
 
-void diag_logsum(cudaStream_t s, const double *A, int lda, int m, double *acc, const DevStatus *st) {
-    launch(k_diag_logsum, 1, 256, 0, s, A, lda, m, acc, st);
+void diag_logsum(cudaStream_t s, const double *A, int lda, int m, double *acc, const DevStatus *st, double *maxinv) {
+    launch(k_diag_logsum, 1, 256, 0, s, A, lda, m, acc, st, maxinv);
     TLR_CHECK_LAUNCH();
 }
 

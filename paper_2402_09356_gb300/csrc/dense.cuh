@@ -28,8 +28,10 @@ void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *
 void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int m,
                      const std::vector<RhsDesc> &rhs);
 
-// acc[0] += sum_r log A[r, r] (skipped once the status word holds an error).
-void diag_logsum(cudaStream_t s, const double *A, int lda, int m, double *acc, const DevStatus *st);
+// acc[0] += sum_r log A[r, r] (skipped once the status word holds an error);
+// maxinv (optional): running maximum of 1 / A[r, r]^2.
+void diag_logsum(cudaStream_t s, const double *A, int lda, int m, double *acc, const DevStatus *st,
+                 double *maxinv = nullptr);
 
 // acc[0] += |v|^2
 void sumsq(cudaStream_t s, const double *v, int m, double *acc);

@@ -515,7 +515,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             g.C = ytmp.as<double>(); g.ldc = nb;
             gemm_batched(ctx, st, false, false, std::vector<GemmProb>{g}, 1.0, 0.0);
             TLR_CUDA_TRY(cudaMemcpyAsync(yj, ytmp.as<double>(), mj * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            diag_logsum(st, Dj, nb, mj, acc, ctx->d_status);
+            diag_logsum(st, Dj, nb, mj, acc, ctx->d_status, acc + 2);
             sumsq(st, yj, mj, acc + 1);
             if (vty_pending > 0) {
                 GemmProb v{};

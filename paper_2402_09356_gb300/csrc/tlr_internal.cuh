@@ -63,7 +63,7 @@ void profile_events(tlr_ctx *ctx, int count);
 void upload_ranks(tlr_mat *M, cudaStream_t s);
 // TLR Cholesky.  With z, y and acc given, the forward solve of Eq. 1.2 is fused
 // in: y = L^-1 z (z, y device, ordered; may alias), acc[0] += sum log L_ii,
-// acc[1] += |y|^2.  With df (Matern mode only), the panel update and the
+// acc[1] += |y|^2, acc[2] = max(acc[2], max_i 1 / L_ii^2).  With df (Matern mode only), the panel update and the
 // compression's sampling and projection products run in paired-FP32
 // arithmetic; everything else stays FP64.
 void factor(tlr_ctx *ctx, cudaStream_t s, tlr_mat *M, FactorMode mode, const double *xy,

@@ -6,7 +6,8 @@ generation order, Z = synth.standard_normal(40000, seed=2), theta = (sigma2 1,
 beta 0.1, nu 0.5).  Exact l does not depend on the order of the locations
 (Sec. 3), so the value checks the TLR likelihood under any ordering.  The
 oracle builds the dense 40,000 x 40,000 covariance (12.8 GB) and factors it
-with LAPACK; about five minutes on eight cores.
+with LAPACK, single-threaded (a threaded OpenBLAS build of this size of
+problem crashed); about fifteen minutes.
 
 Usage: python tests/golden/make_fullsize_loglik.py
 """
@@ -14,6 +15,8 @@ import json
 import os
 import sys
 import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")  # before numpy loads OpenBLAS
 
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)

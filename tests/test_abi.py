@@ -53,7 +53,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(tlr_theta), sizeof(tlr_opts), sizeof(tlr_result), sizeof(tlr_pool_opts));
   printf("%zu %zu %zu %zu\\n", offsetof(tlr_opts, eps), offsetof(tlr_opts, precision),
          offsetof(tlr_result, info), offsetof(tlr_result, ms_total));
-  printf("%zu\\n", offsetof(tlr_pool_opts, hbm_budget));
+  printf("%zu %zu %zu\\n", offsetof(tlr_pool_opts, hbm_budget), offsetof(tlr_result, precision_used),
+         offsetof(tlr_result, min_pivot2));
   return 0;
 }
 """)
@@ -64,7 +65,8 @@ int main(void) {
     assert sizes[:4] == [ctypes.sizeof(tlr.tlr_theta), ctypes.sizeof(tlr.tlr_opts), ctypes.sizeof(tlr.tlr_result),
                          ctypes.sizeof(tlr.tlr_pool_opts)]
     assert sizes[4:] == [tlr.tlr_opts.eps.offset, tlr.tlr_opts.precision.offset, tlr.tlr_result.info.offset,
-                         tlr.tlr_result.ms_total.offset, tlr.tlr_pool_opts.hbm_budget.offset]
+                         tlr.tlr_result.ms_total.offset, tlr.tlr_pool_opts.hbm_budget.offset,
+                         tlr.tlr_result.precision_used.offset, tlr.tlr_result.min_pivot2.offset]
 
 
 def test_context_creation_fails_cleanly_without_gpu(lib):

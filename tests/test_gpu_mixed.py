@@ -71,3 +71,41 @@ def test_mixed_ragged_and_tiny(ctx, n, nb):
     r, _, perm = run(ctx, xy, z, theta, "hilbert", nb, eps, nb, tlr.TLR_PREC_MIXED)
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
     assert abs(r["loglik"] - ref) <= 10 * eps * abs(ref) + 1e-12
+
+
+AUTO_CASES = [
+    # n, nb, theta: rough to very smooth, short to long range
+    (1600, 200, (1.0, 0.1, 0.5)),
+    (900, 128, (1.0, 0.2, 2.0)),
+    (1200, 160, (1.5, 0.25, 2.5)),
+]
+
+
+def test_auto_precision_takes_mixed_or_fp64(ctx):
+    """TLR_PREC_AUTO returns, bit for bit, the mixed result when the factor's
+    smallest squared pivot is at least TLR_AUTO_PIVOT2 sigma2, else the FP64
+    result (both started from the same, empty, rank map)."""
+    import paper_2402_09356_gb300 as tlr
+    seen = set()
+    for n, nb, theta in AUTO_CASES:
+        xy = synth.jittered_grid(n, seed=n)
+        z = synth.standard_normal(n, seed=n + 3)
+        out = {}
+        for name, prec in (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED), ("auto", tlr.TLR_PREC_AUTO)):
+            try:
+                out[name] = run(ctx, xy, z, theta, "hilbert", nb, 1e-7, nb, prec)[0]
+            except tlr.TlrError as e:
+                out[name] = e.code
+        m = out["mixed"]
+        fallback = isinstance(m, int) or m["min_pivot2"] < tlr.TLR_AUTO_PIVOT2 * theta[0]
+        want = out["fp64"] if fallback else m
+        got = out["auto"]
+        if isinstance(want, int):
+            assert got == want, (n, theta, got, want)
+        else:
+            assert got["loglik"] == want["loglik"] and got["logdet"] == want["logdet"], (n, theta)
+            assert got["precision_used"] == (tlr.TLR_PREC_FP64 if fallback else tlr.TLR_PREC_MIXED)
+        seen.add(fallback)
+        if not isinstance(out["fp64"], int):
+            assert out["fp64"]["min_pivot2"] > 0
+    assert seen == {True, False}, "the cases should exercise both paths"
