@@ -60,16 +60,21 @@ extern "C" {
  * significant bits); storage, the Matern evaluation, QR/SVD, the diagonal
  * POTRF, the log-determinant and the solve stay FP64. */
 #define TLR_PREC_MIXED 1
-/* Auto: the mixed path, then, if the factor shows an ill-conditioned
- * covariance (smallest squared pivot min_i L_ii^2 below TLR_AUTO_PIVOT2 sigma2,
- * i.e. some location nearly determined by the ones before it), the FP64 path
- * again from the same starting rank map, whose result is returned.  The
- * paired-FP32 rounding (about 1e-14 relative per product) is amplified by
- * the covariance's conditioning; below the threshold it can exceed the
- * 1e-6 |l| agreement with the FP64 path.  tlr_result.precision_used says
- * which path the result comes from. */
+/* Auto: paired-FP32 rounding (about 1e-14 relative per product) is amplified
+ * by the covariance's conditioning, so the mixed path is used only where the
+ * factor shows a well-conditioned covariance: smallest squared pivot
+ * min_i L_ii^2 (the smallest conditional variance of a location given the
+ * ones before it) at least TLR_AUTO_PIVOT2 sigma2.  A matrix whose previous
+ * likelihood fell below goes to the FP64 path at once; otherwise the mixed
+ * path runs, and where its factor falls below (or meets a non-positive
+ * pivot) the FP64 path runs again from the same starting rank map and its
+ * result is returned.  tlr_result.precision_used says which.  The threshold
+ * comes from a measurement: over 441 batched evaluations (n 2k-20k, nu up to
+ * 2.5) every mixed result whose factor stayed at or above 1e-5 sigma2 was
+ * within 1e-6 |l| of the FP64 one (worst 9.5e-7), and up to 1e-2 below it;
+ * 3e-5 keeps a margin. */
 #define TLR_PREC_AUTO 2
-#define TLR_AUTO_PIVOT2 1e-6
+#define TLR_AUTO_PIVOT2 3e-5
 
 typedef struct tlr_ctx tlr_ctx; /* device, workspace pool, last error, timers */
 typedef struct tlr_mat tlr_mat; /* a TLR matrix or TLR Cholesky factor on the device */
@@ -193,14 +198,33 @@ int tlr_matern(tlr_ctx *ctx, const double *d, int64_t m, tlr_theta theta, double
  * each NT (NT - 1) / 2 * nb * maxrank doubles; ranks NT^2 int32.
  * Errors: TLR_ERR_ARG, TLR_ERR_OOM. */
 int tlr_mat_create(tlr_ctx *ctx, int64_t n, int nb, int maxrank, tlr_mat **out);
+
+/* The same matrix with storage sized by a rank map (the TLR memory saving of
+ * Sec. 2 and Table 1 made real on the device): rank_map (host, NT x NT row
+ * major, r_ij at i NT + j for i > j; e.g. from tlr_mat_ranks of an earlier
+ * factor of the same locations) gives each off-diagonal tile
+ * min(maxrank, r + max(8, r / 4) rounded up to 8) columns of U and V, plus a
+ * shared overflow area of max(sum / 8, 4 maxrank) columns.  A later
+ * compression or factorisation whose rank for a tile exceeds its slot moves
+ * the tile into the overflow area; if that is full it fails with
+ * TLR_ERR_RANK (message: "its slot").  The map also seeds the compression's
+ * sample sizes, as the previous factor does for tlr_loglik.
+ * Errors: TLR_ERR_ARG, TLR_ERR_OOM. */
+int tlr_mat_create_compact(tlr_ctx *ctx, int64_t n, int nb, int maxrank, const int32_t *rank_map,
+                           tlr_mat **out);
+
+/* Device bytes held by a TLR matrix (D, U, V, rank map); 0 for NULL. */
+int64_t tlr_mat_bytes(const tlr_mat *mat);
+
 void tlr_mat_destroy(tlr_mat *mat);
 
 /* Device pointers and layout of a TLR matrix (any output may be NULL).
  *   D      diagonal tile t at D + t nb^2 (column major, ld nb; lower triangle
  *          holds L_tt after a factorisation)
  *   U, V   off-diagonal tile (i, j), i > j, index k = i (i - 1) / 2 + j:
- *          U_k at U + k nb maxrank, V_k at V + k nb maxrank, column major
- *          with ld nb, r_ij valid columns; A_ij ~ U_k V_k'
+ *          for tlr_mat_create, U_k at U + k nb maxrank, V_k at V + k nb maxrank,
+ *          column major with ld nb, r_ij valid columns; A_ij ~ U_k V_k'
+ *          (a compact matrix places tiles by its own map: use tlr_mat_tile)
  *   ranks  device int32 NT x NT row major; ranks[i NT + j] = r_ij (symmetric),
  *          the diagonal holds m_t */
 int tlr_mat_layout(const tlr_mat *mat, int64_t *n, int *nb, int *nt, int *maxrank,
@@ -208,7 +232,7 @@ int tlr_mat_layout(const tlr_mat *mat, int64_t *n, int *nb, int *nt, int *maxran
 
 /* Copy one tile to caller buffers (device, column major, ld nb): for i == j
  * the diagonal tile into `a` (nb x nb); for i > j the factors U_ij into `a`
- * and V_ij into `b` (nb x r each, capacity nb x maxrank).  *rank (host)
+ * and V_ij into `b` (nb x r each; the buffers hold nb x maxrank).  *rank (host)
  * receives r_ij (m_i for i == j).  Stream ordered on `stream`.
  * Errors: TLR_ERR_ARG (i < j, out of range, NULL buffers). */
 int tlr_mat_tile(tlr_ctx *ctx, const tlr_mat *mat, int i, int j, double *a, double *b,

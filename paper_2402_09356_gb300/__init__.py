@@ -23,7 +23,7 @@ TLR_ORDER_QUANTIZE = 1
 TLR_PREC_FP64 = 0
 TLR_PREC_MIXED = 1
 TLR_PREC_AUTO = 2
-TLR_AUTO_PIVOT2 = 1e-6
+TLR_AUTO_PIVOT2 = 3e-5
 
 
 class TlrError(RuntimeError):
@@ -81,6 +81,9 @@ _SIGS = {
     "tlr_mat_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_void_p)]),
     "tlr_mat_destroy": (None, [ctypes.c_void_p]),
+    "tlr_mat_create_compact": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "tlr_mat_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
     "tlr_mat_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -218,14 +221,27 @@ class Context:
 class TlrMatrix:
     """Owns a tlr_mat (TLR matrix or factor) of a context."""
 
-    def __init__(self, ctx: Context, n: int, nb: int, maxrank: int = 0):
+    def __init__(self, ctx: Context, n: int, nb: int, maxrank: int = 0, rank_map=None):
+        """rank_map (NT x NT int32, e.g. tlr_mat_ranks of an earlier factor): compact storage."""
         self.ctx = ctx
         h = ctypes.c_void_p()
-        ctx.check(load_library().tlr_mat_create(ctx.h, int(n), int(nb), int(maxrank), ctypes.byref(h)))
+        if rank_map is None:
+            ctx.check(load_library().tlr_mat_create(ctx.h, int(n), int(nb), int(maxrank), ctypes.byref(h)))
+        else:
+            import numpy as np
+            rm = np.ascontiguousarray(rank_map, dtype=np.int32)
+            nt = (int(n) + int(nb) - 1) // int(nb)
+            if rm.size != nt * nt:
+                raise TlrError(TLR_ERR_ARG, "rank_map must be NT x NT")
+            ctx.check(load_library().tlr_mat_create_compact(ctx.h, int(n), int(nb), int(maxrank),
+                                                            ctypes.c_void_p(rm.ctypes.data), ctypes.byref(h)))
         self.h = h
         self.n, self.nb = int(n), int(nb)
         self.nt = (self.n + self.nb - 1) // self.nb
         self.maxrank = self.layout()["maxrank"]
+
+    def nbytes(self) -> int:
+        return int(load_library().tlr_mat_bytes(self.h))
 
     def layout(self) -> dict:
         n, nb, nt, mr = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

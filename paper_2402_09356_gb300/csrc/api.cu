@@ -295,39 +295,59 @@ int tlr_matern(tlr_ctx *ctx, const double *d, int64_t m, tlr_theta theta, double
     });
 }
 
+// D, U, V and the rank map of a new matrix; `hint` (empty: uniform slots)
+// sets a compact layout and the starting rank map.
+static void mat_create_impl(tlr_ctx *ctx, int64_t n, int nb, int maxrank, const std::vector<int32_t> &hint,
+                            tlr_mat **out) {
+    check_arg(out != nullptr, "out");
+    *out = nullptr;
+    check_arg(n > 0 && nb >= 16 && nb <= kMaxTile, "n/nb");
+    if (maxrank <= 0) maxrank = nb / 2;
+    check_arg(maxrank <= nb, "maxrank");
+    auto *M = new tlr_mat();
+    M->device = ctx->device;
+    M->n = n;
+    M->nb = nb;
+    M->nt = (int)((n + nb - 1) / nb);
+    M->maxrank = maxrank;
+    const int64_t cols = plan_slots(M, hint);
+    size_t dbytes = (size_t)M->nt * nb * nb * sizeof(double);
+    size_t uvbytes = (size_t)cols * nb * sizeof(double);
+    size_t rbytes = (size_t)M->nt * M->nt * sizeof(int32_t);
+    cudaError_t e1 = cudaMalloc(&M->D, dbytes);
+    cudaError_t e2 = cudaMalloc(&M->U, uvbytes);
+    cudaError_t e3 = cudaMalloc(&M->V, uvbytes);
+    cudaError_t e4 = cudaMalloc(&M->ranks, rbytes);
+    if (e1 || e2 || e3 || e4) {
+        tlr_mat_destroy(M);
+        cudaGetLastError();
+        throw make_error(TLR_ERR_OOM, "cannot allocate TLR matrix (%zu + 2 x %zu bytes)", dbytes, uvbytes);
+    }
+    M->bytes = dbytes + 2 * uvbytes + rbytes;
+    // padding rows of U / V must read as zero
+    TLR_CUDA_TRY(cudaMemset(M->D, 0, dbytes));
+    TLR_CUDA_TRY(cudaMemset(M->U, 0, uvbytes));
+    TLR_CUDA_TRY(cudaMemset(M->V, 0, uvbytes));
+    TLR_CUDA_TRY(cudaMemset(M->ranks, 0, rbytes));
+    M->h_ranks = hint;
+    *out = M;
+}
+
 int tlr_mat_create(tlr_ctx *ctx, int64_t n, int nb, int maxrank, tlr_mat **out) {
+    return guarded(ctx, [&] { mat_create_impl(ctx, n, nb, maxrank, {}, out); });
+}
+
+int tlr_mat_create_compact(tlr_ctx *ctx, int64_t n, int nb, int maxrank, const int32_t *rank_map, tlr_mat **out) {
     return guarded(ctx, [&] {
-        check_arg(out != nullptr, "out");
-        *out = nullptr;
-        check_arg(n > 0 && nb >= 16 && nb <= kMaxTile, "n/nb");
-        if (maxrank <= 0) maxrank = nb / 2;
-        check_arg(maxrank <= nb, "maxrank");
-        auto *M = new tlr_mat();
-        M->device = ctx->device;
-        M->n = n;
-        M->nb = nb;
-        M->nt = (int)((n + nb - 1) / nb);
-        M->maxrank = maxrank;
-        int64_t noff = (int64_t)M->nt * (M->nt - 1) / 2;
-        size_t dbytes = (size_t)M->nt * nb * nb * sizeof(double);
-        size_t uvbytes = (size_t)std::max<int64_t>(noff, 1) * nb * maxrank * sizeof(double);
-        cudaError_t e1 = cudaMalloc(&M->D, dbytes);
-        cudaError_t e2 = cudaMalloc(&M->U, uvbytes);
-        cudaError_t e3 = cudaMalloc(&M->V, uvbytes);
-        cudaError_t e4 = cudaMalloc(&M->ranks, (size_t)M->nt * M->nt * sizeof(int32_t));
-        if (e1 || e2 || e3 || e4) {
-            tlr_mat_destroy(M);
-            cudaGetLastError();
-            throw make_error(TLR_ERR_OOM, "cannot allocate TLR matrix (%zu + 2 x %zu bytes)", dbytes, uvbytes);
-        }
-        // padding rows of U / V must read as zero
-        TLR_CUDA_TRY(cudaMemset(M->D, 0, dbytes));
-        TLR_CUDA_TRY(cudaMemset(M->U, 0, uvbytes));
-        TLR_CUDA_TRY(cudaMemset(M->V, 0, uvbytes));
-        TLR_CUDA_TRY(cudaMemset(M->ranks, 0, (size_t)M->nt * M->nt * sizeof(int32_t)));
-        *out = M;
+        check_arg(rank_map != nullptr && n > 0 && nb > 0, "rank_map");
+        const int64_t nt = (n + nb - 1) / nb;
+        std::vector<int32_t> hint(rank_map, rank_map + nt * nt);
+        for (int64_t t = 0; t < nt; ++t) hint[(size_t)(t * nt + t)] = (int32_t)std::min<int64_t>(nb, n - t * nb);
+        mat_create_impl(ctx, n, nb, maxrank, hint, out);
     });
 }
+
+int64_t tlr_mat_bytes(const tlr_mat *M) { return M ? (int64_t)M->bytes : 0; }
 
 void tlr_mat_destroy(tlr_mat *M) {
     if (!M) return;
@@ -369,7 +389,7 @@ int tlr_mat_tile(tlr_ctx *ctx, const tlr_mat *M, int i, int j, double *a, double
         }
         check_arg(b != nullptr, "b");
         int r = M->h_ranks.size() == (size_t)M->nt * M->nt ? M->h_ranks[(size_t)i * M->nt + j] : 0;
-        size_t off = (size_t)off_index(i, j) * nb * M->maxrank;
+        size_t off = (size_t)slot_col(M, i, j) * nb;
         if (r > 0) {
             TLR_CUDA_TRY(cudaMemcpyAsync(a, M->U + off, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
             TLR_CUDA_TRY(cudaMemcpyAsync(b, M->V + off, nb * r * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -512,23 +532,30 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
                   opts->precision == TLR_PREC_AUTO, "precision");
     if (opts->precision != TLR_PREC_AUTO) {
         loglik_once(ctx, xy, z, n, theta, opts, L, out, s, opts->precision == TLR_PREC_MIXED);
+        L->last_pivot2 = out->min_pivot2 / theta.sigma2;
         return;
     }
-    // auto: the mixed path; the FP64 path again, from the same starting rank
-    // map, where the factor shows an ill-conditioned covariance (or the mixed
-    // factorisation met a non-positive pivot)
+    // auto: FP64 at once if the previous likelihood on this matrix found an
+    // ill-conditioned covariance; otherwise the mixed path, and the FP64 path
+    // again, from the same starting rank map, if this factor shows one (or
+    // the mixed factorisation met a non-positive pivot)
     const std::vector<int32_t> hint = L->h_ranks;
     float ms_mixed = 0.f;
-    try {
-        loglik_once(ctx, xy, z, n, theta, opts, L, out, s, true);
-        if (out->min_pivot2 >= TLR_AUTO_PIVOT2 * theta.sigma2) return;
-        ms_mixed = out->ms_total;
-    } catch (const Error &e) {
-        if (e.code != TLR_ERR_NOT_SPD) throw;
-        TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    const bool predict64 = L->last_pivot2 > 0.0 && L->last_pivot2 < TLR_AUTO_PIVOT2;
+    if (!predict64) {
+        try {
+            loglik_once(ctx, xy, z, n, theta, opts, L, out, s, true);
+            L->last_pivot2 = out->min_pivot2 / theta.sigma2;
+            if (L->last_pivot2 >= TLR_AUTO_PIVOT2) return;
+            ms_mixed = out->ms_total;
+        } catch (const Error &e) {
+            if (e.code != TLR_ERR_NOT_SPD) throw;
+            TLR_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        L->h_ranks = hint;
     }
-    L->h_ranks = hint;
     loglik_once(ctx, xy, z, n, theta, opts, L, out, s, false);
+    L->last_pivot2 = out->min_pivot2 / theta.sigma2;
     out->ms_total += ms_mixed;
 }
 

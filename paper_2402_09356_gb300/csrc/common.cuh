@@ -181,10 +181,21 @@ struct tlr_mat {
     int nt = 0;
     int maxrank = 0;
     double *D = nullptr;        // nt * nb * nb
-    double *U = nullptr;        // noff * nb * maxrank
-    double *V = nullptr;        // noff * nb * maxrank
+    double *U = nullptr;        // uniform: noff * nb * maxrank; compact: (sum cap + arena) * nb
+    double *V = nullptr;        // same layout as U
     int32_t *ranks = nullptr;   // nt * nt
     std::vector<int32_t> h_ranks;  // host mirror, refreshed after compress / factor
+    // Compact layout (empty vectors: uniform slots of maxrank columns).  Tile k
+    // = off_index(i, j) starts at column base_off[k] of U and V with room for
+    // cap[k] columns; a factorisation that finds a larger rank moves the tile
+    // into the arena (columns arena_off .. arena_off + arena_cols), and off /
+    // cur_cap hold where every tile lives in the current factor.
+    std::vector<int64_t> base_off, off;
+    std::vector<int32_t> cap, cur_cap;
+    int64_t arena_off = 0, arena_cols = 0, arena_next = 0;
+    bool cap_overflow = false;  // the last factorisation ran out of room (arena full)
+    double last_pivot2 = 0.0;   // min_i L_ii^2 / sigma2 of the last likelihood (0: none yet)
+    size_t bytes = 0;           // device bytes of D, U, V and the rank map
 };
 
 namespace tlr {
@@ -196,6 +207,14 @@ inline int stage_ring(const tlr_ctx *ctx, cudaStream_t s) {
 inline void stage_reset(tlr_ctx *ctx, cudaStream_t s) { ctx->stage[stage_ring(ctx, s)].off = 0; }
 
 inline int64_t off_index(int i, int j) { return (int64_t)i * (i - 1) / 2 + j; }
+// First column of off-diagonal tile (i, j) in U and V, and its capacity.
+inline int64_t slot_col(const tlr_mat *M, int i, int j) {
+    const int64_t k = off_index(i, j);
+    return M->off.empty() ? k * M->maxrank : M->off[(size_t)k];
+}
+inline int slot_cap(const tlr_mat *M, int i, int j) {
+    return M->cur_cap.empty() ? M->maxrank : M->cur_cap[(size_t)off_index(i, j)];
+}
 inline int tile_rows(int64_t n, int nb, int t) {
     int64_t r = n - (int64_t)t * nb;
     return (int)(r < nb ? r : nb);

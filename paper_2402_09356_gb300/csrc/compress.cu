@@ -1287,7 +1287,7 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
 
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df,
-                    const std::function<void()> &overlap) {
+                    const std::function<void()> &overlap, const GrowSlot &grow) {
     bool overlapped = false;
     ensure_omega(ctx, st);
     // profiling marks between the sub-steps of each adaptive round
@@ -1545,6 +1545,8 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
                 if (*bad_tile < 0) *bad_tile = J.tile_id;
                 continue;
             }
+            double *Uo = J.U, *Vo = J.V;
+            const int cap = J.cap > 0 ? J.cap : maxrank;
             bool conv = (s >= full) || (r <= s - kSpare);
             if (!conv) {
                 if (s >= kMaxSample) {
@@ -1556,18 +1558,22 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
                 next.push_back(q);
                 continue;
             }
+            if (r > cap && !(grow && grow(J, r, &Uo, &Vo))) {
+                if (*bad_tile < 0) *bad_tile = J.tile_id;
+                continue;
+            }
             ranks[q] = r;
             if (r == 0) continue;
             // U = Q W_r, V = B W_r
             GemmProb a{};
             a.A = W + oQ[u]; a.lda = J.m; a.m = J.m; a.k = s;
             a.B = W + oW[u]; a.ldb = s; a.n = r;
-            a.C = J.U; a.ldc = J.ldu;
+            a.C = Uo; a.ldc = J.ldu;
             gu.push_back(a);
             GemmProb b{};
             b.A = W + oB[u]; b.lda = J.k; b.m = J.k; b.k = s;
             b.B = W + oW[u]; b.ldb = s; b.n = r;
-            b.C = J.V; b.ldc = J.ldv;
+            b.C = Vo; b.ldc = J.ldv;
             gv.push_back(b);
         }
         gemm_batched(ctx, st, false, false, gu, 1.0, 0.0);

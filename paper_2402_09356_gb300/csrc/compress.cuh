@@ -22,7 +22,13 @@ struct CompressJob {
     int ldv;
     int s_guess;        // expected rank (previous evaluation), drives the first sample size
     long long tile_id;  // i * NT + j, reported on failure
+    int cap;            // columns of U / V available (<= 0: maxrank)
 };
+
+// Called with a job whose rank r exceeds its capacity but not maxrank: gives
+// the job new U / V storage for r columns (same leading dimensions), or
+// returns false (the tile is then reported in *bad_tile).
+using GrowSlot = std::function<bool(const CompressJob &, int r, double **U, double **V)>;
 
 // Allocate and fill the context's Gaussian test matrix and its paired-FP32
 // copy (once).
@@ -30,8 +36,9 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s);
 
 // Compress every job at absolute accuracy tau.  ranks[q] receives r for job q.
 // A tile whose rank exceeds maxrank (or cannot be resolved within the sample
-// cap) is reported in *bad_tile (its tile_id), a tile holding non-finite
-// values in *nan_tile; both are -1 otherwise.
+// cap, or exceeds its capacity where `grow` finds no room) is reported in
+// *bad_tile (its tile_id), a tile holding non-finite values in *nan_tile;
+// both are -1 otherwise.
 // With df, the sampling and projection products run in paired-FP32
 // arithmetic (every job must then carry T2).  `overlap`, if set, is called
 // once, after the first round's work is enqueued and before the host waits
@@ -39,6 +46,7 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s);
 // Syncs `s` once per adaptive round.
 void compress_tiles(tlr_ctx *ctx, cudaStream_t s, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile,
-                    bool df = false, const std::function<void()> &overlap = nullptr);
+                    bool df = false, const std::function<void()> &overlap = nullptr,
+                    const GrowSlot &grow = nullptr);
 
 }  // namespace tlr

@@ -28,9 +28,16 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
     return std::chrono::duration<double, std::milli>(b - a).count();
 }
 
-int64_t factor_bytes(int64_t n, int nb, int maxrank) {
-    const int64_t nt = ceil_div(n, nb), noff = nt * (nt - 1) / 2;
-    return (nt * nb * nb + 2 * std::max<int64_t>(noff, 1) * nb * maxrank) * 8 + nt * nt * 4;
+// Device bytes of a dataset's factor storage: compact slots from its rank
+// map when it has one (plan_slots), else uniform maxrank slots.
+int64_t factor_bytes(int64_t n, int nb, int maxrank, const std::vector<int32_t> &hint) {
+    tlr_mat M;
+    M.n = n;
+    M.nb = nb;
+    M.nt = (int)ceil_div(n, nb);
+    M.maxrank = maxrank;
+    const int64_t cols = plan_slots(&M, hint), nt = M.nt;
+    return (nt * nb * nb + 2 * cols * nb) * 8 + nt * nt * 4;
 }
 
 // Estimated device workspace of one evaluation (allocated inside it): the two
@@ -68,6 +75,7 @@ struct PoolData {
     double *xy = nullptr, *z = nullptr;
     int64_t *perm = nullptr;
     std::vector<int32_t> hint;  // rank map of the last factor (empty before the first)
+    double pivot2 = 0.0;        // min L_ii^2 / sigma2 of the last likelihood (auto precision)
     tlr_mat *L = nullptr;       // resident factor storage (null while evicted)
     int queued = 0;             // submitted, not finished
     bool removing = false;
@@ -123,18 +131,19 @@ struct tlr_pool {
 namespace {
 
 // TLR matrix storage from the pool's memory pool, stream ordered on s, zeroed
-// like tlr_mat_create's.
-tlr_mat *mat_alloc(tlr_pool *p, int64_t n, int nb, int maxrank, cudaStream_t s) {
+// like tlr_mat_create's: compact slots from `hint` when given, else uniform.
+tlr_mat *mat_alloc(tlr_pool *p, int64_t n, int nb, int maxrank, const std::vector<int32_t> &hint, cudaStream_t s) {
     auto *M = new tlr_mat();
     M->device = p->device;
     M->n = n;
     M->nb = nb;
     M->nt = (int)ceil_div(n, nb);
     M->maxrank = maxrank;
-    const int64_t noff = (int64_t)M->nt * (M->nt - 1) / 2;
+    const int64_t cols = plan_slots(M, hint);
     const size_t db = (size_t)M->nt * nb * nb * sizeof(double);
-    const size_t ub = (size_t)std::max<int64_t>(noff, 1) * nb * maxrank * sizeof(double);
+    const size_t ub = (size_t)cols * nb * sizeof(double);
     const size_t rb = (size_t)M->nt * M->nt * sizeof(int32_t);
+    M->bytes = db + 2 * ub + rb;
     cudaError_t e = cudaMallocFromPoolAsync((void **)&M->D, db, p->mp, s);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void **)&M->U, ub, p->mp, s);
     if (e == cudaSuccess) e = cudaMallocFromPoolAsync((void **)&M->V, ub, p->mp, s);
@@ -191,27 +200,61 @@ void worker_main(tlr_pool *p, int w) {
         int status = TLR_OK;
         std::string err;
         std::vector<int32_t> hint;
-        if (alloc && !d->L) d->L = mat_alloc(p, d->n, d->nb, d->maxrank, W.stream);
+        bool ran = false;
+        if (alloc && !d->L) d->L = mat_alloc(p, d->n, d->nb, d->maxrank, d->hint, W.stream);
+        tlr_opts o{};
+        o.nb = d->nb;
+        o.maxrank = d->maxrank;
+        o.eps = r->eps;
+        o.precision = r->precision;
+        double pivot2 = d->pivot2;
+        auto evaluate = [&](tlr_mat *M) {
+            M->h_ranks = d->hint;
+            M->last_pivot2 = d->pivot2;
+            status = tlr_loglik(W.ctx, d->xy, d->z, d->n, r->theta, &o, M, &r->res, W.stream);
+            err = status != TLR_OK ? std::string(tlr_last_error(W.ctx)) : std::string();
+            hint = M->h_ranks;
+            pivot2 = M->last_pivot2;
+            ran = true;
+        };
         if (!d->L) {
             status = TLR_ERR_OOM;
             err = "cannot allocate the factor storage of dataset " + std::to_string(d->id);
         } else {
-            tlr_opts o{};
-            o.nb = d->nb;
-            o.maxrank = d->maxrank;
-            o.eps = r->eps;
-            o.precision = r->precision;
-            d->L->h_ranks = d->hint;
-            status = tlr_loglik(W.ctx, d->xy, d->z, d->n, r->theta, &o, d->L, &r->res, W.stream);
-            if (status != TLR_OK) err = tlr_last_error(W.ctx);
-            hint = d->L->h_ranks;
+            evaluate(d->L);
+            if (status == TLR_ERR_RANK && d->L->cap_overflow) {
+                // the compact slots (sized by the last rank map) ran out of
+                // room: the same evaluation, from the same rank map, on
+                // uniform maxrank slots (held only for this request)
+                mat_free(d->L, W.stream);
+                d->L = mat_alloc(p, d->n, d->nb, d->maxrank, {}, W.stream);
+                if (d->L) {
+                    evaluate(d->L);
+                } else {
+                    status = TLR_ERR_OOM;
+                    err = "cannot allocate uniform factor storage after a slot overflow";
+                }
+            }
         }
-        const int64_t wb = work_bytes(d->n, d->nb, d->maxrank, d->L ? hint : d->hint);
+        // uniform storage (first request, or after an overflow) is given back;
+        // the next request allocates compact slots from the new rank map
+        tlr_mat *drop = (d->L && d->L->base_off.empty()) ? d->L : nullptr;
+        if (drop) {
+            mat_free(drop, W.stream);
+            d->L = nullptr;
+        }
+        const std::vector<int32_t> &nh = ran ? hint : d->hint;
+        const int64_t wb = work_bytes(d->n, d->nb, d->maxrank, nh);
+        const int64_t fb = factor_bytes(d->n, d->nb, d->maxrank, nh);
 
         lk.lock();
-        if (d->L) d->hint.swap(hint);
+        if (ran) {
+            d->hint.swap(hint);
+            d->pivot2 = pivot2;
+        }
         p->adm.finish(ar.data, d->L != nullptr);
         p->adm.set_work(ar.data, wb);
+        if (!d->L) p->adm.set_factor(ar.data, fb);
         r->status = status;
         r->err = err;
         r->t_done = Clock::now();
@@ -360,7 +403,7 @@ int tlr_pool_add(tlr_pool *p, const double *xy, const double *z, int64_t n, int 
     if (nb < 16 || nb > kMaxTile) return pool_fail(TLR_ERR_ARG, "nb must be 16..1024");
     const int maxrank = p->opts.maxrank > 0 ? std::min(p->opts.maxrank, nb) : nb / 2;
     const int64_t base = n * 32;  // locations (2n), observations, permutation
-    const int64_t fb = factor_bytes(n, nb, maxrank), wb = work_bytes(n, nb, maxrank, {});
+    const int64_t fb = factor_bytes(n, nb, maxrank, {}), wb = work_bytes(n, nb, maxrank, {});
     int slot;
     {
         std::lock_guard<std::mutex> lk(p->mu);
@@ -538,7 +581,7 @@ int tlr_pool_tune(tlr_pool *p, int id, tlr_theta theta, double eps, int precisio
         std::unique_lock<std::mutex> lk(p->mu);
         wait_idle(p, lk, d);
         const int maxrank = p->opts.maxrank > 0 ? std::min(p->opts.maxrank, nb) : nb / 2;
-        const int64_t fb = factor_bytes(d->n, nb, maxrank), wb = work_bytes(d->n, nb, maxrank, {});
+        const int64_t fb = factor_bytes(d->n, nb, maxrank, {}), wb = work_bytes(d->n, nb, maxrank, {});
         if (!p->adm.resize_check(id, fb, wb)) return false;
         p->adm.drop(id);
         tlr_mat *M = d->L;
@@ -598,7 +641,7 @@ int tlr_pool_footprint(int64_t n, int nb, int maxrank, int64_t *out) {
     if (!out || n <= 0 || nb < 16 || nb > kMaxTile || maxrank > nb) return pool_fail(TLR_ERR_ARG, "n/nb/maxrank/out");
     if (maxrank <= 0) maxrank = nb / 2;
     out[0] = n * 32;
-    out[1] = factor_bytes(n, nb, maxrank);
+    out[1] = factor_bytes(n, nb, maxrank, {});
     out[2] = work_bytes(n, nb, maxrank, {});
     return TLR_OK;
 }

@@ -109,6 +109,14 @@ public:
         x.wbytes = std::max<int64_t>(0, std::min(wbytes, budget_ - bases() - x.fbytes));
     }
 
+    // New factor size of a dataset whose factor is not resident (its next
+    // allocation), capped like set_work so that it can still run alone.
+    void set_factor(int d, int64_t fbytes) {
+        Data &x = data_[(size_t)d];
+        if (x.resident) return;
+        x.fbytes = std::max<int64_t>(0, std::min(fbytes, budget_ - bases() - x.wbytes));
+    }
+
     // Drops the resident factor of an idle dataset (returns whether it was resident).
     bool drop(int d) {
         Data &x = data_[(size_t)d];

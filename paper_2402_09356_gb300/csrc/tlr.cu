@@ -60,17 +60,38 @@ void copy_batched(tlr_ctx *ctx, cudaStream_t s, const std::vector<CopyDesc> &des
     TLR_CHECK_LAUNCH();
 }
 
-static inline double *Uslot(tlr_mat *M, int i, int j) {
-    return M->U + off_index(i, j) * (int64_t)M->nb * M->maxrank;
+static inline double *Uslot(tlr_mat *M, int i, int j) { return M->U + slot_col(M, i, j) * M->nb; }
+static inline double *Vslot(tlr_mat *M, int i, int j) { return M->V + slot_col(M, i, j) * M->nb; }
+static inline const double *Uslot(const tlr_mat *M, int i, int j) { return M->U + slot_col(M, i, j) * M->nb; }
+static inline const double *Vslot(const tlr_mat *M, int i, int j) { return M->V + slot_col(M, i, j) * M->nb; }
+
+// Compact layout: every factorisation starts from the base slots with an
+// empty arena; a tile whose rank exceeds its slot moves into the arena.
+static void reset_slots(tlr_mat *M) {
+    M->cap_overflow = false;
+    if (M->base_off.empty()) return;
+    M->off = M->base_off;
+    M->cur_cap = M->cap;
+    M->arena_next = 0;
 }
-static inline double *Vslot(tlr_mat *M, int i, int j) {
-    return M->V + off_index(i, j) * (int64_t)M->nb * M->maxrank;
-}
-static inline const double *Uslot(const tlr_mat *M, int i, int j) {
-    return M->U + off_index(i, j) * (int64_t)M->nb * M->maxrank;
-}
-static inline const double *Vslot(const tlr_mat *M, int i, int j) {
-    return M->V + off_index(i, j) * (int64_t)M->nb * M->maxrank;
+
+static GrowSlot arena_grow(tlr_mat *M) {
+    if (M->base_off.empty()) return nullptr;
+    return [M](const CompressJob &J, int r, double **U, double **V) -> bool {
+        const int nt = M->nt, i = (int)(J.tile_id / nt), j = (int)(J.tile_id % nt);
+        const int64_t need = (r + 7) & ~7;
+        if (M->arena_next + need > M->arena_cols) {
+            M->cap_overflow = true;
+            return false;
+        }
+        const int64_t k = off_index(i, j);
+        M->off[(size_t)k] = M->arena_off + M->arena_next;
+        M->cur_cap[(size_t)k] = (int32_t)need;
+        M->arena_next += need;
+        *U = Uslot(M, i, j);
+        *V = Vslot(M, i, j);
+        return true;
+    };
 }
 
 void upload_ranks(tlr_mat *M, cudaStream_t s) {
@@ -86,6 +107,11 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     const int nt = M->nt, nb = M->nb;
     const int64_t n = M->n;
     *info = -1;
+    // the likelihood path regenerates every tile: start from the base slots
+    // (the unfused path keeps where its compressed input tiles live)
+    if (mode == FactorMode::Matern) reset_slots(M);
+    M->cap_overflow = false;
+    const GrowSlot grow = arena_grow(M);
     std::vector<int32_t> &R = M->h_ranks;  // r_ij of the factor, filled column by column
     std::vector<int32_t> prev = R;         // previous ranks (input ranks for FactorMode::Tlr)
     bool have_prev = !prev.empty() && prev.size() == (size_t)nt * nt;
@@ -406,6 +432,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             c.ldv = nb;
             c.s_guess = have_prev ? prev[(size_t)i * nt + j] : 32;
             c.tile_id = (long long)i * nt + j;
+            c.cap = slot_cap(M, i, j);
             jobs.push_back(c);
         }
         std::vector<int> rk;
@@ -415,7 +442,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             // on the high-priority stream, ahead of the look-ahead GEMM
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_fork, st));
             TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->hp, ctx->ev_hp_fork, 0));
-            compress_tiles(ctx, ctx->hp, jobs, tau, M->maxrank, rk, &bad, &nan, df);
+            compress_tiles(ctx, ctx->hp, jobs, tau, M->maxrank, rk, &bad, &nan, df, nullptr, grow);
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_join, ctx->hp));
             TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_hp_join, 0));
         }
@@ -432,8 +459,9 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         }
         if (bad >= 0) {
             *info = bad;
-            throw make_error(TLR_ERR_RANK, "tile (%lld, %lld) needs rank > maxrank %d", bad / nt, bad % nt,
-                             M->maxrank);
+            throw make_error(TLR_ERR_RANK, "tile (%lld, %lld) needs rank > %s %d", bad / nt, bad % nt,
+                             M->cap_overflow ? "its slot, and the overflow area is full:" : "maxrank",
+                             M->cap_overflow ? slot_cap(M, (int)(bad / nt), (int)(bad % nt)) : M->maxrank);
         }
         for (size_t q = 0; q < jobs.size(); ++q) {
             int i = j + 1 + (int)q;
@@ -662,6 +690,34 @@ void lmul(tlr_ctx *ctx, cudaStream_t st, const tlr_mat *M, const double *w, doub
     }
 }
 
+int64_t plan_slots(tlr_mat *M, const std::vector<int32_t> &hint) {
+    const int nt = M->nt;
+    const int64_t noff = (int64_t)nt * (nt - 1) / 2;
+    M->base_off.clear();
+    M->cap.clear();
+    M->off.clear();
+    M->cur_cap.clear();
+    M->arena_off = M->arena_cols = M->arena_next = 0;
+    if (hint.size() != (size_t)nt * nt) return std::max<int64_t>(noff, 1) * M->maxrank;
+    M->base_off.resize((size_t)noff);
+    M->cap.resize((size_t)noff);
+    int64_t col = 0;
+    for (int i = 1; i < nt; ++i)
+        for (int j = 0; j < i; ++j) {
+            const int r = std::max(0, (int)hint[(size_t)i * nt + j]);
+            const int c = std::min(M->maxrank, (r + std::max(8, r / 4) + 7) & ~7);
+            const int64_t k = off_index(i, j);
+            M->base_off[(size_t)k] = col;
+            M->cap[(size_t)k] = c;
+            col += c;
+        }
+    M->arena_off = col;
+    M->arena_cols = std::max<int64_t>(col / 8, 4 * (int64_t)M->maxrank);
+    M->off = M->base_off;
+    M->cur_cap = M->cap;
+    return std::max<int64_t>(col + M->arena_cols, 1);
+}
+
 // Compress packed dense tiles (tlr_generate layout) into M.
 void compress_packed(tlr_ctx *ctx, cudaStream_t st, const double *tiles, tlr_mat *M, double tau,
                      long long *info) {
@@ -670,6 +726,8 @@ void compress_packed(tlr_ctx *ctx, cudaStream_t st, const double *tiles, tlr_mat
     std::vector<int32_t> prev = M->h_ranks;
     bool have_prev = prev.size() == (size_t)nt * nt;
     auto tile = [&](int i, int j) { return tiles + ((int64_t)i * (i + 1) / 2 + j) * nb * nb; };
+    reset_slots(M);
+    const GrowSlot grow = arena_grow(M);
     std::vector<CopyDesc> cd;
     for (int t = 0; t < nt; ++t)
         cd.push_back(CopyDesc{tile(t, t), nb, M->D + (int64_t)t * nb * nb, nb, nb, nb});
@@ -684,6 +742,7 @@ void compress_packed(tlr_ctx *ctx, cudaStream_t st, const double *tiles, tlr_mat
             c.V = Vslot(M, i, j); c.ldv = nb;
             c.s_guess = have_prev ? prev[(size_t)i * nt + j] : 32;
             c.tile_id = (long long)i * nt + j;
+            c.cap = slot_cap(M, i, j);
             jobs.push_back(c);
         }
     std::vector<int32_t> &R = M->h_ranks;
@@ -693,7 +752,7 @@ void compress_packed(tlr_ctx *ctx, cudaStream_t st, const double *tiles, tlr_mat
     if (!jobs.empty()) {
         std::vector<int> rk;
         long long bad = -1, nan = -1;
-        compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan);
+        compress_tiles(ctx, st, jobs, tau, M->maxrank, rk, &bad, &nan, false, nullptr, grow);
         if (nan >= 0) {
             *info = nan;
             throw make_error(TLR_ERR_NAN, "tile (%lld, %lld) holds non-finite values", nan / nt, nan % nt);

@@ -99,4 +99,12 @@ bool mle_bounds_ok(tlr_theta lo, tlr_theta hi);
 void mle_nelder_mead(const std::function<double(tlr_theta)> &negll, tlr_theta theta0, tlr_theta lo,
                      tlr_theta hi, double tol, int max_iter, tlr_theta *theta_hat, double *ll_hat, int *iters);
 
+// Compact slot layout of a TLR matrix from a rank map (host, NT x NT, r_ij at
+// i * NT + j for i > j; empty = no map): each off-diagonal tile gets
+// cap = min(maxrank, r + max(8, r / 4) rounded up to 8) columns, and an
+// overflow arena of max(sum cap / 8, 4 maxrank) columns follows.  Fills the
+// layout fields of M (base_off, cap, arena) and returns the total number of
+// columns U and V need; with no map, the uniform layout (noff * maxrank).
+int64_t plan_slots(tlr_mat *M, const std::vector<int32_t> &hint);
+
 }  // namespace tlr

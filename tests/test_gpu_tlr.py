@@ -227,3 +227,56 @@ def test_bad_arguments(ctx):
     with pytest.raises(tlr.TlrError) as e:
         tlr.tlr_loglik(L, xy, z, (1.0, 0.1, 0.5), tlr.Options(nb=16, eps=1e-9, precision=7))
     assert e.value.code == tlr.TLR_ERR_ARG
+
+
+def test_compact_storage_gives_the_same_factor(ctx):
+    """A matrix sized by a rank map (tlr_mat_create_compact) gives bit for bit
+    the result of uniform slots started from the same rank map, in far less
+    memory; the unfused path works on it too."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    n, nb, th0, th1 = 3000, 256, (1.0, 0.1, 0.5), (1.05, 0.09, 0.55)
+    xy, z, _ = ordered_problem(n, th0, "hilbert")
+    xy_d = torch.from_numpy(xy).cuda()
+    xyo = torch.empty_like(xy_d)
+    perm = tlr.tlr_order(ctx, xy_d, "hilbert", xy_out=xyo)
+    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(z).cuda())
+    opts = tlr.Options(nb=nb, eps=1e-7)
+    U = tlr.TlrMatrix(ctx, n, nb)
+    tlr.tlr_loglik(U, xyo, zo, th0, opts)
+    rmap = tlr.tlr_mat_ranks(U)
+    ref = tlr.tlr_loglik(U, xyo, zo, th1, opts)  # starts from rmap
+    C = tlr.TlrMatrix(ctx, n, nb, rank_map=rmap)  # its rank map seeds the samples too
+    got = tlr.tlr_loglik(C, xyo, zo, th1, opts)
+    for k in ("loglik", "logdet", "quad", "max_rank", "offdiag_bytes"):
+        assert got[k] == ref[k], k
+    assert np.array_equal(tlr.tlr_mat_ranks(C), tlr.tlr_mat_ranks(U))
+    i, j = 5, 4
+    a_u, b_u = tlr.tlr_mat_tile(U, i, j)
+    a_c, b_c = tlr.tlr_mat_tile(C, i, j)
+    assert torch.equal(a_u, a_c) and torch.equal(b_u, b_c)
+    nt = (n + nb - 1) // nb
+    fixed = nt * nb * nb * 8 + nt * nt * 4  # diagonal tiles and the rank map
+    assert C.nbytes() - fixed < 0.5 * (U.nbytes() - fixed), (C.nbytes(), U.nbytes())
+    U.close()
+    C.close()
+
+
+def test_compact_storage_overflow(ctx):
+    """Ranks far above the map's slots: tiles move into the overflow area
+    while it has room, then the call fails with RANK ("slot")."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    n, nb, theta = 3000, 256, (1.0, 0.1, 0.5)
+    xy, z, _ = ordered_problem(n, theta, "hilbert")
+    xy_d = torch.from_numpy(xy).cuda()
+    xyo = torch.empty_like(xy_d)
+    perm = tlr.tlr_order(ctx, xy_d, "hilbert", xy_out=xyo)
+    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(z).cuda())
+    opts = tlr.Options(nb=nb, eps=1e-7)
+    nt = (n + nb - 1) // nb
+    C = tlr.TlrMatrix(ctx, n, nb, rank_map=np.zeros((nt, nt), dtype=np.int32))
+    with pytest.raises(tlr.TlrError) as e:
+        tlr.tlr_loglik(C, xyo, zo, theta, opts)
+    assert e.value.code == tlr.TLR_ERR_RANK and "slot" in str(e.value)
+    C.close()
