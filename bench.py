@@ -469,11 +469,10 @@ def run_batched(args):
     import synth
     count = args.datasets
     sizes, th0 = batched_datasets(count)
-    pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
     t_setup = time.perf_counter()
     bucket_of = [next(b for b, (lo, hi) in enumerate(BATCH_BUCKETS) if lo <= n < hi) for n in sizes]
-    ids = [None] * count
     tuned = {}
+    tune_pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
     for b, (lo, hi) in enumerate(BATCH_BUCKETS):
         members = [i for i in range(count) if bucket_of[i] == b]
         if not members:
@@ -484,22 +483,30 @@ def run_batched(args):
         mid = (lo + hi) / 2
         rep = min(members, key=lambda i: abs(sizes[i] - mid))
         n = int(sizes[rep])
-        ids[rep] = tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=10 + rep), synth.standard_normal(n, seed=5000 + rep),
-                                    "morton")
-        best, ms = tlr.tlr_pool_tune(pool, ids[rep], tuple(th0[rep]), list(BATCH_TILE_CANDIDATES), eps=EPS,
+        rid = tlr.tlr_pool_add(tune_pool, synth.jittered_grid(n, seed=10 + rep),
+                               synth.standard_normal(n, seed=5000 + rep), "morton")
+        best, ms = tlr.tlr_pool_tune(tune_pool, rid, tuple(th0[rep]), list(BATCH_TILE_CANDIDATES), eps=EPS,
                                      precision=tlr.TLR_PREC_MIXED)
         tuned[b] = {"n": n, "best_nb": best, "ms": ms}
-    for i in range(count):
-        if ids[i] is None:
-            n = int(sizes[i])
-            ids[i] = tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=10 + i), synth.standard_normal(n, seed=5000 + i),
-                                      "morton", nb=tuned[bucket_of[i]]["best_nb"])
+    tune_pool.close()
+
+    def new_pool():
+        # every path gets a pool of its own, so that each dataset's rank-map
+        # history (the compression's sample sizes) comes from that path alone
+        pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
+        ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(int(sizes[i]), seed=10 + i),
+                                synth.standard_normal(int(sizes[i]), seed=5000 + i), "morton",
+                                nb=tuned[bucket_of[i]]["best_nb"]) for i in range(count)]
+        return pool, ids
+
     setup_s = time.perf_counter() - t_setup
     walks = [synth.theta_walk(tuple(th0[i]), args.warmup + args.steps, seed=900 + i, scale=0.05) for i in range(count)]
     out = {}
     clocks_all = {}
     paths = (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED), ("auto", tlr.TLR_PREC_AUTO))
+    pool_stats = {}
     for name, prec in paths:
+        pool, ids = new_pool()
         for k in range(args.warmup):
             tlr.tlr_pool_loglik(pool, ids, [tuple(w[k]) for w in walks], eps=EPS, precision=prec)
         clocks = ClockSampler(0)
@@ -521,6 +528,8 @@ def run_batched(args):
         out[name] = {"evals_per_s": count * args.steps / total, "s_per_step": total / args.steps,
                      "failed": fails, "fp64_results": used64,
                      "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
+        pool_stats[name] = tlr.tlr_pool_stats(pool)
+        pool.close()
 
     def compare(name):
         rel, pairs = [], []
@@ -546,7 +555,7 @@ def run_batched(args):
                 "by_min_pivot2": calib}
     accuracy_auto = {"pairs": len(rel_auto), "within_1e-6": int(sum(1 for r in rel_auto if r <= 1e-6)),
                      "max": max(rel_auto) if rel_auto else None}
-    st = tlr.tlr_pool_stats(pool)
+    st = pool_stats
     # the fastest path whose every evaluated pair is within 1e-6 of the FP64 path
     ok = [nm for nm, r in (("mixed", rel), ("auto", rel_auto)) if r and max(r) <= 1e-6]
     head = max(ok, key=lambda nm: out[nm]["evals_per_s"]) if ok else "fp64"
@@ -571,7 +580,6 @@ def run_batched(args):
             "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
             "gpu_launches": out[head]["gpu_launches"]}
     print(json.dumps(line), flush=True)
-    pool.close()
 
 
 SERVE_SIZES = (5000, 10000, 20000, 40000, 80000)
