@@ -589,6 +589,7 @@ int tlr_pool_tune(tlr_pool *p, int id, tlr_theta theta, double eps, int precisio
         d->nb = nb;
         d->maxrank = maxrank;
         d->hint.clear();
+        d->pivot2 = 0.0;
         p->adm.resize(id, fb, wb);
         lk.unlock();
         if (M) {
