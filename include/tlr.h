@@ -216,6 +216,10 @@ int tlr_mat_create_compact(tlr_ctx *ctx, int64_t n, int nb, int maxrank, const i
 /* Device bytes held by a TLR matrix (D, U, V, rank map); 0 for NULL. */
 int64_t tlr_mat_bytes(const tlr_mat *mat);
 
+/* Host only: the bytes tlr_mat_create (rank_map NULL) or
+ * tlr_mat_create_compact would allocate; -1 for invalid sizes. */
+int64_t tlr_mat_plan_bytes(int64_t n, int nb, int maxrank, const int32_t *rank_map);
+
 void tlr_mat_destroy(tlr_mat *mat);
 
 /* Device pointers and layout of a TLR matrix (any output may be NULL).

@@ -84,6 +84,7 @@ _SIGS = {
     "tlr_mat_create_compact": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "tlr_mat_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "tlr_mat_plan_bytes": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "tlr_mat_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -338,6 +339,16 @@ def tlr_matern(ctx: Context, d, theta, out=None, stream=None):
         out = torch.empty_like(d)
     ctx.check(load_library().tlr_matern(ctx.h, _ptr(d), d.numel(), _theta(theta), _ptr(out), _stream(stream)))
     return out
+
+
+def tlr_mat_plan_bytes(n: int, nb: int, maxrank: int = 0, rank_map=None) -> int:
+    """Bytes a uniform (rank_map None) or compact TLR matrix would hold (host only)."""
+    import numpy as np
+    ptr = ctypes.c_void_p(0)
+    if rank_map is not None:
+        rm = np.ascontiguousarray(rank_map, dtype=np.int32)
+        ptr = ctypes.c_void_p(rm.ctypes.data)
+    return int(load_library().tlr_mat_plan_bytes(int(n), int(nb), int(maxrank), ptr))
 
 
 def tlr_mat_ranks(mat: TlrMatrix):

@@ -349,6 +349,19 @@ int tlr_mat_create_compact(tlr_ctx *ctx, int64_t n, int nb, int maxrank, const i
 
 int64_t tlr_mat_bytes(const tlr_mat *M) { return M ? (int64_t)M->bytes : 0; }
 
+int64_t tlr_mat_plan_bytes(int64_t n, int nb, int maxrank, const int32_t *rank_map) {
+    if (n <= 0 || nb < 16 || nb > kMaxTile || maxrank > nb) return -1;
+    tlr_mat M;
+    M.n = n;
+    M.nb = nb;
+    M.nt = (int)((n + nb - 1) / nb);
+    M.maxrank = maxrank > 0 ? maxrank : nb / 2;
+    std::vector<int32_t> hint;
+    if (rank_map) hint.assign(rank_map, rank_map + (size_t)M.nt * M.nt);
+    const int64_t cols = plan_slots(&M, hint);
+    return ((int64_t)M.nt * nb * nb + 2 * cols * nb) * (int64_t)sizeof(double) + (int64_t)M.nt * M.nt * 4;
+}
+
 void tlr_mat_destroy(tlr_mat *M) {
     if (!M) return;
     cudaSetDevice(M->device);
