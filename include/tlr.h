@@ -70,9 +70,10 @@ extern "C" {
  * pivot) the FP64 path runs again from the same starting rank map and its
  * result is returned.  tlr_result.precision_used says which.  The threshold
  * comes from a measurement: over 441 batched evaluations (n 2k-20k, nu up to
- * 2.5) every mixed result whose factor stayed at or above 1e-5 sigma2 was
- * within 1e-6 |l| of the FP64 one (worst 9.5e-7), and up to 1e-2 below it;
- * 3e-5 keeps a margin. */
+ * 2.5, each path from its own rank-map history) every mixed result whose
+ * factor stayed at or above 1e-5 sigma2 was within 1e-6 |l| of the FP64 one
+ * (worst 4.2e-7; 4.5e-9 above 1e-4), and up to 5.6e-3 below it; 3e-5 keeps
+ * a margin. */
 #define TLR_PREC_AUTO 2
 #define TLR_AUTO_PIVOT2 3e-5
 
