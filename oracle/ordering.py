@@ -1,8 +1,8 @@
 """Oracle: spatial orderings of Sec. 3.  Test infrastructure only.
 
 Every ordering returns a permutation `perm` (int64): position k of the
-ordered problem holds original location perm[k].  Readings of the paper that
-the text leaves open (each one is listed in the design doc):
+ordered problem holds original location perm[k].  Readings of the paper where
+the text leaves a choice open:
 
 * Quantisation (Sec. 3.1, "Encoding"): each coordinate, clamped to [0, 1],
   is multiplied by 65535 (the largest 16-bit unsigned value) in one FP64
