@@ -1,4 +1,4 @@
-// Internal interfaces between the TLR driver (tlr.cu) and the C ABI (api.cu).
+// Internal interfaces between the TLR factorisation (tlr.cu), the pool (pool.cu) and the C ABI (api.cu).
 #pragma once
 
 #include <functional>
