@@ -144,12 +144,23 @@ void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long l
 // FP64 throughout.  A non-positive pivot sets NOT_SPD (info = row_base + row)
 // and every CTA leaves at the next barrier.
 constexpr int kPotrfThreads = 256;
+constexpr int kTileLoads = kBlk * kBlk / kPotrfThreads;  // operand elements per thread and tile
 
 // C (32 x 32, rows r0.., cols c0.. of a column-major matrix) -= A B' or A B:
 // a, b are 32 x 32 operand blocks already in shared memory as [row][k].
 __device__ __forceinline__ void tile_update32(double *C, int ldc, const double (*a)[kBlk + 1],
                                               const double (*b)[kBlk + 1], int rows, int cols, bool lower_only) {
     const int tid = threadIdx.x, tr = (tid & 15) * 2, tc = (tid >> 4) * 2;
+    // the C entries are read before the product, so that their latency
+    // overlaps with it (only this CTA updates this tile in this step)
+    double cv[2][2];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const int r = tr + x, c = tc + y;
+            cv[x][y] = (r < rows && c < cols && (!lower_only || c <= r)) ? __ldcg(C + (int64_t)c * ldc + r) : 0.0;
+        }
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 #pragma unroll 8
     for (int k = 0; k < kBlk; ++k) {
@@ -164,10 +175,7 @@ __device__ __forceinline__ void tile_update32(double *C, int ldc, const double (
 #pragma unroll
         for (int y = 0; y < 2; ++y) {
             const int r = tr + x, c = tc + y;
-            if (r < rows && c < cols && (!lower_only || c <= r)) {
-                double *p = C + (int64_t)c * ldc + r;
-                *p = __ldcg(p) - acc[x][y];
-            }
+            if (r < rows && c < cols && (!lower_only || c <= r)) C[(int64_t)c * ldc + r] = cv[x][y] - acc[x][y];
         }
 }
 
@@ -200,44 +208,49 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
             }
             if (tid == 0) s_bad = -1;
             __syncthreads();
-            if (tid < kBlk) {
-                const int r = tid;
-                for (int c = 0; c < w; ++c) {
-                    if (r == c) {
-                        const double d = sa[c][c];
-                        if (!(d > 0.0)) s_bad = c;
-                        else sa[c][c] = sqrt(d);
-                    }
-                    __syncwarp();
-                    if (s_bad >= 0) break;
-                    if (r > c && r < w) sa[r][c] /= sa[c][c];
-                    __syncwarp();
-                    if (r > c && r < w) {
-                        const double lrc = sa[r][c];
-                        for (int cc = c + 1; cc <= r; ++cc) sa[r][cc] -= lrc * sa[cc][c];
-                    }
-                    __syncwarp();
+            // right-looking Cholesky of the block, one column at a time, the
+            // updates spread over the CTA's threads
+            for (int c = 0; c < w; ++c) {
+                if (tid == 0) {
+                    const double d = sa[c][c];
+                    if (!(d > 0.0)) s_bad = c;
+                    else sa[c][c] = sqrt(d);
                 }
+                __syncthreads();
+                if (s_bad >= 0) break;  // read after the barrier: uniform
+                const double piv = sa[c][c];
+                for (int r = c + 1 + tid; r < w; r += kPotrfThreads) sa[r][c] /= piv;
+                __syncthreads();
+                const int nr = w - c - 1;
+                for (int e = tid; e < nr * nr; e += kPotrfThreads) {
+                    const int r = c + 1 + e % nr, cc = c + 1 + e / nr;
+                    if (cc <= r) sa[r][cc] -= sa[r][c] * sa[cc][c];
+                }
+                __syncthreads();
             }
-            __syncthreads();
             if (s_bad >= 0) {
                 if (tid == 0) {
                     set_status(st, TLR_ERR_NOT_SPD, row_base + p + s_bad);
                     __stcg(stop, 1LL);
                 }
             } else {
-                // inverse of the lower triangular block: column c of L^-1 by thread c
-                if (tid < kBlk) {
-                    const int c = tid;
-                    for (int r = 0; r < kBlk; ++r) {
+                // inverse of the lower triangular block, row by row: column c
+                // by the 8 lanes 8c .. 8c+7 (one warp holds four columns),
+                // each summing every 8th term, then a shuffle reduction
+                const int c = tid >> 3, q = tid & 7;
+                for (int r = 0; r < kBlk; ++r) {
+                    double part = 0.0;
+                    if (c < w && r < w && r > c)
+                        for (int k = c + q; k < r; k += 8) part = fma(sa[r][k], sl[k][c], part);
+                    part += __shfl_xor_sync(0xFFFFFFFFu, part, 4);
+                    part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
+                    part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
+                    if (q == 0) {
                         double v = 0.0;
-                        if (c < w && r < w && r >= c) {
-                            v = (r == c) ? 1.0 : 0.0;
-                            for (int k = c; k < r; ++k) v -= sa[r][k] * sl[k][c];
-                            v /= sa[r][r];
-                        }
+                        if (c < w && r < w && r >= c) v = ((r == c ? 1.0 : 0.0) - part) / sa[r][r];
                         sl[r][c] = v;
                     }
+                    __syncwarp();
                 }
                 __syncthreads();
                 for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
@@ -269,19 +282,41 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
         // 3. trailing update of the lower triangle, tiles (bi >= bj > kb)
         const int nt = nbk - kb - 1;
         const int ntiles = nt * (nt + 1) / 2;
-        for (int t = rank; t < ntiles; t += kCl) {
+        // the operands of a CTA's next tile are loaded into registers while it
+        // updates the current one (the panel is final in this step)
+        auto tile_of = [&](int t, int &I, int &Jb) {
             int bi = 0, rem = t;  // t -> (bi, bj), bi = kb+1+i, bj = kb+1+j, j <= i
             while (rem > bi) { rem -= bi + 1; ++bi; }
-            const int I = kb + 1 + bi, Jb = kb + 1 + rem;
+            I = kb + 1 + bi;
+            Jb = kb + 1 + rem;
+        };
+        double ra[kTileLoads], rb[kTileLoads];
+        auto fetch = [&](int t) {
+            int I, Jb;
+            tile_of(t, I, Jb);
+            const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
+#pragma unroll
+            for (int u = 0; u < kTileLoads; ++u) {
+                const int e = tid + u * kPotrfThreads, r = e % kBlk, k = e / kBlk;
+                ra[u] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
+                rb[u] = (r < cols && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + cj + r) : 0.0;
+            }
+        };
+        if (rank < ntiles) fetch(rank);
+        for (int t = rank; t < ntiles; t += kCl) {
+            int I, Jb;
+            tile_of(t, I, Jb);
             const int ri = I * kBlk, cj = Jb * kBlk;
             const int rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
             __syncthreads();
-            for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
-                const int r = e % kBlk, k = e / kBlk;
-                sa[r][k] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
-                sb[r][k] = (r < cols && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + cj + r) : 0.0;
+#pragma unroll
+            for (int u = 0; u < kTileLoads; ++u) {
+                const int e = tid + u * kPotrfThreads;
+                sa[e % kBlk][e / kBlk] = ra[u];
+                sb[e % kBlk][e / kBlk] = rb[u];
             }
             __syncthreads();
+            if (t + kCl < ntiles) fetch(t + kCl);
             tile_update32(A + (int64_t)cj * lda + ri, lda, sa, sb, rows, cols, I == Jb);
         }
         cl.sync();
@@ -315,18 +350,32 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
         cl.sync();
         // b. X[I, J] -= L[I, k] X[k, J] for row blocks I > k and column blocks J <= k
         const int nI = nbk - kb - 1, nJ = kb + 1, ntiles = nI * nJ;
+        double ra[kTileLoads], rb[kTileLoads];
+        auto fetch = [&](int t) {
+            const int I = kb + 1 + t % nI, Jb = t / nI;
+            const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
+#pragma unroll
+            for (int u = 0; u < kTileLoads; ++u) {
+                const int e = tid + u * kPotrfThreads, r = e % kBlk, k = e / kBlk;
+                ra[u] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
+                // b operand as [col][k]: X[p + k, cj + col]
+                rb[u] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
+            }
+        };
+        if (rank < ntiles) fetch(rank);
         for (int t = rank; t < ntiles; t += kCl) {
             const int I = kb + 1 + t % nI, Jb = t / nI;
             const int ri = I * kBlk, cj = Jb * kBlk;
             const int rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
             __syncthreads();
-            for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
-                const int r = e % kBlk, k = e / kBlk;
-                sa[r][k] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
-                // b operand as [col][k]: X[p + k, cj + col]
-                sb[r][k] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
+#pragma unroll
+            for (int u = 0; u < kTileLoads; ++u) {
+                const int e = tid + u * kPotrfThreads;
+                sa[e % kBlk][e / kBlk] = ra[u];
+                sb[e % kBlk][e / kBlk] = rb[u];
             }
             __syncthreads();
+            if (t + kCl < ntiles) fetch(t + kCl);
             tile_update32(X + (int64_t)cj * ldx + ri, ldx, sa, sb, rows, cols, false);
         }
         cl.sync();
