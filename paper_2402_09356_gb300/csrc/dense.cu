@@ -132,12 +132,15 @@ void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long l
 // (__ldcg: another CTA may have written the line in an earlier phase).  A
 // cluster barrier (release/acquire at cluster scope) separates dependent
 // phases.  With 32-wide blocks, block step k of the right-looking Cholesky:
-//   1. CTA 0 factors the diagonal block L_kk and inverts it (shared memory),
-//      the inverse kept in `dinv` for step 2 and for L^-1;
+//   1. CTA 0 factors the diagonal block L_kk and inverts it in shared memory
+//      with all its threads (a rank-1 update per column; the inverse row by
+//      row, eight lanes per column), the inverse kept in `dinv` for step 2
+//      and for L^-1;
 //   2. every thread of the cluster takes one row r below the block:
 //      A[r, k-block] <- A[r, k-block] L_kk^-T;
 //   3. the trailing lower triangle A_IJ -= P_I P_J' by 32 x 32 output tiles
-//      spread round-robin over the CTAs.
+//      spread round-robin over the CTAs, each CTA loading its next tile's
+//      operands into registers while it updates the current one.
 // Then X = L^-1 by right-looking substitution on X = I: block step k applies
 // X[k, :] <- L_kk^-1 X[k, :] (columns over all threads), then
 // X[I, :] -= L_Ik X[k, :] for the rows below (tiles over the CTAs).
