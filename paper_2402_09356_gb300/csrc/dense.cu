@@ -19,110 +19,7 @@ namespace tlr {
 namespace cg = cooperative_groups;
 
 constexpr int kBlk = 32;
-constexpr int kStrip = 64;  // column strips of the trailing update
 
-// Cholesky of the w x w diagonal block at (p0, p0) of A (lower part).
-__global__ void k_potrf_block(double *__restrict__ A, int lda, int m, int p0, DevStatus *st,
-                              long long row_base) {
-    __shared__ double S[kBlk][kBlk + 1];
-    __shared__ int bad;
-    if (st->code) return;
-    const int r = threadIdx.x;  // 32 threads
-    const int w = min(kBlk, m - p0);
-    double *B = A + (int64_t)p0 * lda + p0;
-    for (int c = 0; c < w; ++c) S[r][c] = (r < w) ? B[(int64_t)c * lda + r] : 0.0;
-    if (r == 0) bad = -1;
-    __syncthreads();
-    for (int c = 0; c < w; ++c) {
-        if (r == c) {
-            double d = S[c][c];
-            if (!(d > 0.0)) bad = c;
-            else S[c][c] = sqrt(d);
-        }
-        __syncthreads();
-        if (bad >= 0) break;
-        if (r > c && r < w) S[r][c] /= S[c][c];
-        __syncthreads();
-        if (r > c && r < w) {
-            double lrc = S[r][c];
-            for (int cc = c + 1; cc <= r; ++cc) S[r][cc] -= lrc * S[cc][c];
-        }
-        __syncthreads();
-    }
-    if (bad >= 0) {
-        if (r == 0) set_status(st, TLR_ERR_NOT_SPD, row_base + p0 + bad);
-        return;
-    }
-    if (r < w)
-        for (int c = 0; c <= r; ++c) B[(int64_t)c * lda + r] = S[r][c];
-}
-
-// A[r, p0:p0+w] <- A[r, p0:p0+w] L^-T for rows p0+w <= r < m (one thread per row).
-__global__ void k_trsm_right_lt(double *__restrict__ A, int lda, int m, int p0, const DevStatus *st) {
-    __shared__ double L[kBlk][kBlk + 1];
-    if (st->code) return;
-    const int w = min(kBlk, m - p0);
-    const double *Lb = A + (int64_t)p0 * lda + p0;
-    for (int e = threadIdx.x; e < kBlk * kBlk; e += blockDim.x) {
-        int rr = e % kBlk, cc = e / kBlk;
-        L[rr][cc] = (rr < w && cc < w && cc <= rr) ? Lb[(int64_t)cc * lda + rr] : 0.0;
-    }
-    __syncthreads();
-    int r = p0 + w + blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= m) return;
-    double x[kBlk];
-    double *row = A + (int64_t)p0 * lda + r;
-#pragma unroll
-    for (int c = 0; c < kBlk; ++c) {
-        if (c < w) {
-            double a = row[(int64_t)c * lda];
-#pragma unroll
-            for (int k = 0; k < c; ++k) a -= x[k] * L[c][k];
-            x[c] = a / L[c][c];
-        } else {
-            x[c] = 0.0;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < kBlk; ++c)
-        if (c < w) row[(int64_t)c * lda] = x[c];
-}
-
-__global__ void k_zero_upper(double *__restrict__ A, int lda, int m) {
-    int c = blockIdx.x;
-    for (int r = threadIdx.x; r < c && c < m; r += blockDim.x) A[(int64_t)c * lda + r] = 0.0;
-}
-
-void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long long row_base) {
-    for (int p0 = 0; p0 < m; p0 += kBlk) {
-        int w = std::min(kBlk, m - p0);
-        launch(k_potrf_block, 1, kBlk, 0, s, A, lda, m, p0, ctx->d_status, row_base);
-        int rest = m - p0 - w;
-        if (rest <= 0) break;
-        launch(k_trsm_right_lt, (unsigned)ceil_div(rest, 128), 128, 0, s, A, lda, m, p0, ctx->d_status);
-        TLR_CHECK_LAUNCH();
-        // trailing lower update A22 -= P P', one problem per 64-column strip
-        double *P = A + (int64_t)p0 * lda + p0 + w;
-        double *A22 = A + (int64_t)(p0 + w) * lda + p0 + w;
-        std::vector<GemmProb> probs;
-        for (int cb = 0; cb < rest; cb += kStrip) {
-            GemmProb g{};
-            g.A = P + cb;
-            g.B = P + cb;
-            g.C = A22 + (int64_t)cb * lda + cb;
-            g.m = rest - cb;
-            g.n = std::min(kStrip, rest - cb);
-            g.k = w;
-            g.lda = lda;
-            g.ldb = lda;
-            g.ldc = lda;
-            probs.push_back(g);
-        }
-        gemm_batched(ctx, s, false, true, probs, -1.0, 1.0);
-    }
-    launch(k_zero_upper, m, 128, 0, s, A, lda, m);
-    TLR_CHECK_LAUNCH();
-}
 
 // ---------------------------------------------------------------------------
 // Cholesky and inverse of one diagonal tile in a single launch.

@@ -13,11 +13,6 @@ struct RhsDesc {
     int ld;
 };
 
-// In-place Cholesky A = L L' of the m x m matrix A (lower triangle used and
-// returned, strict upper triangle zeroed).  A non-positive pivot sets the
-// context status to TLR_ERR_NOT_SPD with info = row_base + local row.
-void potrf_dense(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, long long row_base);
-
 // A = L L' in place (lower; strict upper zeroed) and X = L^-1 (m x m, lower,
 // ld ldx) in one launch on one thread-block cluster; m <= 1024.  A
 // non-positive pivot sets NOT_SPD (info = row_base + local row); X is then
