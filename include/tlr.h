@@ -402,7 +402,8 @@ typedef struct {
 int tlr_pool_create(int device, const tlr_pool_opts *opts, tlr_pool **out);
 
 /* Finish every queued request, stop the workers and free the pool's memory.
- * Results not yet collected by tlr_pool_wait are discarded.  NULL is ignored. */
+ * Results not yet collected by tlr_pool_wait are discarded.  No other call
+ * on the pool may run concurrently with it or follow it.  NULL is ignored. */
 void tlr_pool_destroy(tlr_pool *p);
 
 /* Message of the last failing tlr_pool_* call of the calling thread. */
