@@ -241,3 +241,23 @@ def test_pool_errors_are_per_request(ctx):
     with pytest.raises(tlr.TlrError):
         tlr.tlr_pool_submit(pool, did, (1.0, 0.1, 0.5))
     pool.close()
+
+
+def test_pool_compact_slot_overflow_falls_back_to_uniform(ctx):
+    """A request whose ranks outgrow the compact slots sized by the previous
+    request (here: eps 1e-3, then 1e-9) is rerun from the same rank map on
+    uniform slots; every result still equals the single-context sequence."""
+    import paper_2402_09356_gb300 as tlr
+    pool = tlr.Pool(0, workers=2, nb=256, maxrank=FULL)
+    xy, z = make(2600, 77, (1.0, 0.1, 0.5))
+    did = tlr.tlr_pool_add(pool, xy, z, "hilbert")
+    seq = [((1.0, 0.1, 0.5), 1e-3, tlr.TLR_PREC_FP64), ((1.0, 0.1, 0.5), 1e-9, tlr.TLR_PREC_FP64),
+           ((1.02, 0.1, 0.5), 1e-9, tlr.TLR_PREC_MIXED)]
+    got = run_mix(pool, {did: seq})[did]
+    ref = alone(ctx, pool, did, seq)
+    for k, (a, b) in enumerate(zip(got, ref)):
+        assert same(a, b), (k, a, b)
+    st = tlr.tlr_pool_stats(pool)
+    # uniform (first), compact, uniform (the overflow rerun), compact
+    assert st["allocations"] >= 3, st
+    pool.close()
