@@ -155,6 +155,33 @@ def test_unfused_path_generate_compress_potrf_solve(ctx):
     assert np.abs(back - zp).max() <= 1e-8 * np.abs(zp).max()
 
 
+def test_unfused_path_on_compact_storage(ctx):
+    """generate -> compress -> potrf -> solve on a matrix sized by the rank map
+    of a coarser first pass (tiles that outgrow their slots move into the
+    overflow area): the likelihood within the oracle bound, L (L^-1 z) = z."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    n, nb, theta, eps = 1600, 200, (1.0, 0.1, 0.5), 1e-9
+    xy, z, perm = ordered_problem(n, theta, "hilbert")
+    xyp, zp = oracle.permute_xy(xy, perm), z[perm]
+    ref = oracle.loglik_dense(xyp, zp, theta)
+    tiles = tlr.tlr_generate(ctx, torch.from_numpy(xyp).cuda(), nb, theta)
+    U = tlr.TlrMatrix(ctx, n, nb)
+    tlr.tlr_compress(U, tiles, eps * 10)  # a coarser pass: smaller ranks
+    rmap = tlr.tlr_mat_ranks(U)
+    U.close()
+    C = tlr.TlrMatrix(ctx, n, nb, rank_map=rmap)
+    tlr.tlr_compress(C, tiles, eps)
+    tlr.tlr_potrf(C, eps)
+    y, logdet, quad = tlr.tlr_solve(C, torch.from_numpy(zp).cuda())
+    ll = -0.5 * n * math.log(2 * math.pi) - 0.5 * logdet - 0.5 * quad
+    assert abs(ll - ref["loglik"]) <= 10 * eps * abs(ref["loglik"])
+    back = tlr.tlr_lmul(C, y).cpu().numpy()
+    assert np.abs(back - zp).max() <= 1e-8 * np.abs(zp).max()
+    assert C.nbytes() < tlr.tlr_mat_plan_bytes(n, nb)
+    C.close()
+
+
 def test_factor_ranks_match_schur_ranks(ctx):
     n, nb, theta, eps = 1600, 200, (1.0, 0.1, 0.5), 1e-7
     xy, z, perm = ordered_problem(n, theta, "morton")
