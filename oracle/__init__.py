@@ -24,6 +24,6 @@ from .covariance import besselk, besselk_scaled, matern, cov_matrix, cov_block, 
 from .ordering import (IDENTITY, RANDOM, MORTON, HILBERT, KDTREE, MAXMIN, NAMES,  # noqa: F401
                        quantize, dequantize, morton_code, hilbert_code, random_keys,
                        sort_codes, kdtree_perm, maxmin_perm, order, decode_xy)
-from .likelihood import (loglik_dense, loglik_from_cov, simulate_z, tile_bounds,  # noqa: F401
+from .likelihood import (loglik_dense, loglik_from_cov, loglik_from_factor, simulate_z, tile_bounds,  # noqa: F401
                          tile_singular_values, ranks_from_singular_values, tile_ranks,
                          factor_tile_ranks, dense_offdiag_bytes, tlr_offdiag_bytes)

@@ -4,7 +4,8 @@ Test infrastructure only.
 
 * loglik_dense: l = -n/2 log(2 pi) - 1/2 log|Sigma| - 1/2 Z' Sigma^-1 Z with
   Sigma built by the oracle's own Matern code, factored by LAPACK's Cholesky
-  (a library primitive), log|Sigma| = 2 sum log L_ii and Z' Sigma^-1 Z = |L^-1 Z|^2.
+  (a library primitive), log|Sigma| = 2 sum log L_ii and Z' Sigma^-1 Z = |L^-1 Z|^2
+  (loglik_from_factor: the same two terms from a factor already computed).
 * simulate_z: Z = L w with L the dense Cholesky factor of Sigma(theta) in the
   order the locations are given (generation order for the workloads).
 * tile_ranks: for every off-diagonal tile of Sigma the number of singular
@@ -28,14 +29,19 @@ import scipy.linalg
 from .covariance import cov_matrix
 
 
-def loglik_from_cov(sigma: np.ndarray, z: np.ndarray) -> dict:
-    n = sigma.shape[0]
-    L = np.linalg.cholesky(sigma)
+def loglik_from_factor(L: np.ndarray, z: np.ndarray) -> dict:
+    """Eq. 1.2 from the lower Cholesky factor L of Sigma (Sigma = L L'):
+    log|Sigma| = 2 sum log L_ii, Z' Sigma^-1 Z = |L^-1 Z|^2."""
+    n = L.shape[0]
     logdet = 2.0 * float(np.sum(np.log(np.diag(L))))
     y = scipy.linalg.solve_triangular(L, z, lower=True)
     quad = float(y @ y)
     ll = -0.5 * n * math.log(2.0 * math.pi) - 0.5 * logdet - 0.5 * quad
     return {"loglik": ll, "logdet": logdet, "quad": quad}
+
+
+def loglik_from_cov(sigma: np.ndarray, z: np.ndarray) -> dict:
+    return loglik_from_factor(np.linalg.cholesky(sigma), z)
 
 
 def loglik_dense(xy: np.ndarray, z: np.ndarray, theta) -> dict:

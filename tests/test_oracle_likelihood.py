@@ -138,3 +138,72 @@ def test_factor_tile_is_schur_complement():
     assert np.abs(schur - blk(L, i, j) @ blk(L, j, j).T).max() < 1e-13
     rf, _ = oracle.factor_tile_ranks(s, nb, 1e-9)
     assert rf[i, j] == np.count_nonzero(np.linalg.svd(schur, compute_uv=False) > 1e-9)
+
+
+def _tile_with_spectrum(rng, m, k, s):
+    """m x k tile sum_q s[q] u_q v_q' with orthonormal u, v (QR of Gaussians)."""
+    u, _ = np.linalg.qr(rng.standard_normal((m, len(s))))
+    v, _ = np.linalg.qr(rng.standard_normal((k, len(s))))
+    return (u * np.asarray(s)) @ v.T
+
+
+@pytest.mark.parametrize("sigma2, spectra, expected", [
+    # tau = eps * sigma2 = 2e-6: 1.5e-6 lies between eps and eps * sigma2, and
+    # the relative threshold eps * s_1 = 5e-6 would drop 3e-6 and 2.5e-6
+    (2.0, {(1, 0): [5.0, 1e-1, 3e-6, 2.5e-6, 1.5e-6, 5e-7],
+           (2, 0): [1.9e-6, 1e-7],
+           (2, 1): [1.0, 2.1e-6, 1.2e-6]}, {(1, 0): 4, (2, 0): 0, (2, 1): 2}),
+    # tau = 5e-7: 7e-7 and 6e-7 count although they are below eps = 1e-6
+    (0.5, {(1, 0): [1.0, 1e-3, 7e-7, 6e-7, 3e-7],
+           (2, 0): [8e-7, 4e-7],
+           (2, 1): [2e-2, 9e-7, 5.5e-7, 4.5e-7]}, {(1, 0): 4, (2, 0): 1, (2, 1): 3}),
+])
+def test_tile_ranks_constructed_spectra(sigma2, spectra, expected):
+    """Sec. 2-3: the rank of a tile is the number of its singular values above the
+    absolute threshold eps * sigma2 (reading of the accuracy threshold).  Tiles with
+    a known spectrum are placed in a block matrix; a threshold that drops sigma2,
+    is relative to the largest singular value, or counts the wrong blocks fails."""
+    eps, nb, n = 1e-6, 24, 3 * 24 - 5     # ragged last tile (19 rows)
+    rng = np.random.default_rng(11)
+    b = oracle.tile_bounds(n, nb)
+    S = np.zeros((n, n))
+    for t in range(3):
+        S[b[t][0]:b[t][1], b[t][0]:b[t][1]] = np.eye(b[t][1] - b[t][0])
+    for (i, j), s in spectra.items():
+        T = _tile_with_spectrum(rng, b[i][1] - b[i][0], b[j][1] - b[j][0], s)
+        S[b[i][0]:b[i][1], b[j][0]:b[j][1]] = T
+        S[b[j][0]:b[j][1], b[i][0]:b[i][1]] = T.T
+    r, sv = oracle.tile_ranks(S, nb, eps, sigma2)
+    for (i, j), want in expected.items():
+        assert r[i, j] == want and r[j, i] == want, ((i, j), r[i, j], want)
+        top = sorted(spectra[(i, j)], reverse=True)
+        assert np.allclose(sv[(i, j)][:len(top)], top, rtol=1e-9, atol=1e-15)
+    assert [r[t, t] for t in range(3)] == [24, 24, 19]   # diagonal tiles dense
+    # the Table 1 memory of this rank map: (m_i + m_j) r_ij doubles per tile
+    want_bytes = 8 * sum((b[i][1] - b[i][0] + b[j][1] - b[j][0]) * c for (i, j), c in expected.items())
+    assert oracle.tlr_offdiag_bytes(r, n, nb) == want_bytes
+
+
+def test_ranks_threshold_is_strict():
+    """A singular value equal to the threshold is dropped: the kept values are
+    those strictly above eps * sigma2 (values exact in binary)."""
+    sv = {(1, 0): np.array([1.0, 0.25, 0.25, 0.125]), (2, 0): np.array([0.25]),
+          (2, 1): np.array([0.5, 0.2500000000000001])}
+    r = oracle.ranks_from_singular_values(sv, 9, 3, 0.25)
+    assert (r[1, 0], r[2, 0], r[2, 1]) == (1, 0, 2)
+    assert (r[0, 1], r[0, 2], r[1, 2]) == (1, 0, 2)
+
+
+def test_loglik_from_factor_of_simulated_z():
+    """Eq. 1.2 on data drawn from the model, Z = L w: Z' Sigma^-1 Z = |w|^2
+    exactly, and log|Sigma| is LAPACK's log-determinant of Sigma."""
+    n = 300
+    xy = synth.jittered_grid(n, seed=4)
+    S = oracle.cov_matrix(xy, (1.7, 0.08, 1.0))
+    L = np.linalg.cholesky(S)
+    w = synth.standard_normal(n, seed=9)
+    r = oracle.loglik_from_factor(L, L @ w)
+    assert abs(r["quad"] - w @ w) <= 1e-10 * (w @ w)
+    sign, ld = np.linalg.slogdet(S)
+    assert sign == 1.0 and abs(r["logdet"] - ld) <= 1e-10 * abs(ld)
+    assert r["loglik"] == pytest.approx(-0.5 * n * math.log(2 * math.pi) - 0.5 * ld - 0.5 * (w @ w), rel=1e-10)
