@@ -144,6 +144,67 @@ def make_inputs(tlr, ctx, torch, dev, rank: int):
     return xy_h, xy, z
 
 
+def algorithmic_flops(ranks, n: int, nb: int) -> dict:
+    """The method's work per evaluation counted from a rank map (the factor's
+    r_ij, i > j), term by term as the TLR Cholesky of Sec. 2 needs it:
+      compression  4 m_i m_j r_ij per off-diagonal tile (RRQR-class);
+      POTRF        m_k^3 / 3 per diagonal tile;
+      TRSM         m_i m_k r_ik (V_ik <- L_kk^-1 V_ik);
+      SYRK         2 m_i m_k r_ik (D_ii -= U_ik (V_ik' V_ik) U_ik');
+      GEMM         2 m_k r_ik r_jk (V_ik' V_jk) + 8 m (r_ij + r_ik)^2 for the
+                   recompression of A_ij -= U_ik (V_ik' V_jk) U_jk', i > j > k.
+    Executed work differs (explicit inverses, densified panels, sampling)."""
+    import numpy as np
+    r = np.asarray(ranks, dtype=np.float64)
+    nt = r.shape[0]
+    m = np.array([min(nb, n - t * nb) for t in range(nt)], dtype=np.float64)
+    low = np.tril(r, -1)
+    comp = float((4.0 * m[:, None] * m[None, :] * low).sum())
+    potrf = float((m ** 3 / 3.0).sum())
+    trsm = float((m[:, None] * m[None, :] * low).sum())
+    syrk = 2.0 * trsm
+    gemm = 0.0
+    for k in range(nt - 2):
+        rk = low[k + 1:, k]                       # r_ik, i > k
+        mi = m[k + 1:]
+        prod = 2.0 * m[k] * np.outer(rk, rk)      # V_ik' V_jk, i > j > k
+        rij = low[k + 1:, k + 1:]                 # r_ij for rows i, cols j (both > k)
+        rec = 8.0 * mi[:, None] * (rij + rk[:, None]) ** 2
+        mask = np.tril(np.ones((nt - k - 1, nt - k - 1)), -1)
+        gemm += float(((prod + rec) * mask).sum())
+    total = comp + potrf + trsm + syrk + gemm
+    return {"total": total, "compression": comp, "potrf": potrf, "trsm": trsm, "syrk": syrk, "gemm": gemm}
+
+
+def draw_z_lw(tlr, ctx, xy_h, w_h, theta, order, nb):
+    """Data drawn from the model, Z = L(theta) w (generation order, host array):
+    L is the library's own TLR factor at eps 1e-9 (maxrank nb), so that the
+    quadratic term has the size the model gives it (|w|^2 ~ n).  A covariance
+    too ill-conditioned for that factor is retried at eps 1e-7; if that fails
+    too, Z = w is returned and the second value is False."""
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    n = w_h.size
+    xy = torch.from_numpy(xy_h).to(dev)
+    xyo = torch.empty_like(xy)
+    perm = tlr.tlr_order(ctx, xy, order, xy_out=xyo)
+    zero = torch.zeros(n, dtype=torch.float64, device=dev)
+    for eps in (1e-9, 1e-7):
+        L = tlr.TlrMatrix(ctx, n, nb, maxrank=nb)
+        try:
+            tlr.tlr_loglik(L, xyo, zero, tuple(theta), tlr.Options(nb=nb, eps=eps, maxrank=nb))
+            zo = tlr.tlr_lmul(L, tlr.tlr_gather(ctx, perm, torch.from_numpy(w_h).to(dev)))
+            z = torch.empty_like(zo)
+            z[perm] = zo
+            return z.cpu().numpy(), True
+        except tlr.TlrError:
+            torch.cuda.synchronize()
+        finally:
+            L.close()
+    return np.array(w_h, dtype=np.float64), False
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -220,6 +281,7 @@ def run_gpu(args):
         out["clocks"] = clocks.stop()
         out["launches"] = tlr.tlr_launch_count() - launches0
         out["times"] = [a.elapsed_time(b) for a, b in ev]
+        out["ranks"] = tlr.tlr_mat_ranks(L)  # the last step's factor
         out["value"], out["total_ms"] = aggregate(sum(out["times"]), args.steps, world, device=dev)
         if world > 1:
             torch.distributed.barrier()
@@ -302,14 +364,15 @@ def run_gpu(args):
                                  "2 s per pair checked, 6 s per pair rotated"}
 
     def roof_potrf(o):
-        # one launch per tile column on the side stream: L = chol(T_jj) and
-        # L^-1, m^3/3 + m^3/3 FP64 flops; its in-step time from the events
-        # around it on that stream
+        # one launch per tile column on the side stream: L = chol(T_jj) (the
+        # algorithmic m^3/3 FP64 flops) and L^-1 (another m^3/3, executed work
+        # that replaces the TRSM); its in-step time from the events around it
+        # on that stream
         nt = (N_POINTS + NB - 1) // NB
         ms_step = o["detail_ms"]["potrf"]
         avg = ms_step / nt
         ms = [min(NB, N_POINTS - t * NB) for t in range(nt)]
-        fl = sum(2.0 * m ** 3 / 3.0 for m in ms) / nt
+        fl = sum(m ** 3 / 3.0 for m in ms) / nt
         achieved = fl / (avg / 1000.0) / 1e12 if avg > 0 else 0.0
         occupied = 16 * 4 * sm_mhz * 1e6 / 1e12
         traffic = NCU_TRAFFIC.get(("k_potrf_inv<16>", NB))
@@ -321,12 +384,33 @@ def run_gpu(args):
                 "peak_source": "FP64 DFMA pipe: %d SMs x 4 flop/clk x %.0f MHz (sampled SM clock)" % (n_sms, sm_mhz),
                 "frac_of_occupied_sms": achieved / occupied if occupied else None,
                 "launch_ms_avg": avg, "launches": nt * args.steps, "flops_per_launch": fl,
+                "flops_counted": "algorithmic: m^3/3 (Cholesky of the diagonal tile)",
+                "executed_flops_per_launch": 2.0 * fl,
+                "executed_tflops": 2.0 * achieved,
+                "executed_note": "the launch also forms L^-1 (another m^3/3), used in place of a TRSM",
                 "total_ms": ms_step * args.steps}
 
     # the dominant kernel of the headline path: the largest device time per step
     cand = [roof_panel(head), roof_jacobi(head), roof_potrf(head)]
     roofline = max(cand, key=lambda r: r["total_ms"])
     other = [r for r in cand if r is not roofline]
+
+    def eval_roofline(o, name):
+        """Whole evaluation: the algorithmic flops of its rank map (Sec. 2 terms,
+        algorithmic_flops) over the measured time per evaluation, against the FP64
+        pipe and, on the mixed path, the pipe that runs its off-diagonal products."""
+        alg = algorithmic_flops(o["ranks"], N_POINTS, NB)
+        ms = o["total_ms"] / args.steps
+        achieved = alg["total"] / (ms / 1000.0) / 1e12
+        r = {"bound": "alu", "flops_algorithmic": alg["total"], "flops_by_term": alg,
+             "flops_executed": float(o["results"][-1]["flops"]), "ms_per_eval": ms, "achieved": achieved,
+             "unit": "TFLOP/s", "peak_fp64": fp64_peak, "frac_fp64": achieved / fp64_peak,
+             "counted_from": "rank map of the last timed evaluation"}
+        if name == "mixed":
+            r["peak_products"] = df_peak
+            r["frac_products"] = achieved / df_peak
+            r["peak_products_source"] = "paired-FP32 products on the FP32 pipe (see roofline_other)"
+        return r
 
     def summary(o):
         res = o["results"]
@@ -340,8 +424,26 @@ def run_gpu(args):
                                       "max_sweeps": cs["max_sweeps"],
                                       "mean_sweeps_fp32": cs["sweeps32"] / max(cs["tiles"], 1)},
                 "panel_tflops": roof_panel(o)["achieved"], "jacobi16": o["k16"], "gpu_launches": int(o["launches"]),
+                "eval_roofline": eval_roofline(o, "mixed" if o is mixed else "fp64"),
                 "loglik_last": res[-1]["loglik"], "max_rank_last": res[-1]["max_rank"],
                 "mean_rank_last": res[-1]["mean_rank"], "offdiag_mb_last": res[-1]["offdiag_bytes"] / 1e6}
+
+    # latency over many evaluations: the head path, theta continuing along the
+    # walk, each evaluation timed by CUDA events on the launching stream (L2
+    # flushed before each, outside the events)
+    lat = []
+    if args.latency_evals > 0:
+        lthetas = synth.theta_walk(THETA0, args.warmup + args.steps + args.latency_evals, seed=7, scale=0.05)
+        lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.latency_evals)]
+        for k in range(args.latency_evals):
+            flush.zero_()
+            lev[k][0].record(stream)
+            step(lthetas[args.warmup + args.steps + k], head_opts)
+            lev[k][1].record(stream)
+        torch.cuda.synchronize()
+        lat = [a.elapsed_time(b) for a, b in lev]
+    lat_src = lat if lat else head["times"]
 
     line = {
         "metric": METRIC,
@@ -351,8 +453,13 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": head["total_ms"] / args.steps,
-        "p50_ms": float(np.percentile(head["times"], 50)),
-        "p99_ms": float(np.percentile(head["times"], 99)),
+        "p50_ms": float(np.percentile(lat_src, 50)),
+        "p99_ms": float(np.percentile(lat_src, 99)),
+        "latency": {"evals": len(lat_src), "p50_ms": float(np.percentile(lat_src, 50)),
+                    "p90_ms": float(np.percentile(lat_src, 90)), "p99_ms": float(np.percentile(lat_src, 99)),
+                    "max_ms": float(max(lat_src)), "path": head_name,
+                    "how": "separate loop after the timed steps, theta continuing along the walk, CUDA events "
+                           "per evaluation, L2 flushed before each"},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -379,6 +486,20 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
+    # compact summary last, so that a truncated log tail still shows both paths
+    er = line[head_name + "_path"]["eval_roofline"] if line.get(head_name + "_path") else None
+    line["summary"] = {
+        "mixed_evals_per_s": mixed["value"] if mixed else None,
+        "fp64_evals_per_s": fp64["value"] if fp64 else None,
+        "mixed_ms": mixed["total_ms"] / args.steps if mixed else None,
+        "fp64_ms": fp64["total_ms"] / args.steps if fp64 else None,
+        "rel_dl_vs_fp64": rel_dl, "head": head_name,
+        "p50_ms": line["p50_ms"], "p99_ms": line["p99_ms"], "latency_evals": len(lat_src),
+        "e2e_evals_per_s": e2e_value,
+        "roofline": "%s %.4f of %s" % (roofline["kernel"].split(" ")[0], roofline["frac"] or 0.0, roofline["unit"]),
+        "eval_frac_fp64": er["frac_fp64"] if er else None,
+        "eval_tflops": er["achieved"] if er else None,
+        "loglik_last": head["results"][-1]["loglik"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     L.close()
@@ -387,11 +508,13 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def cpu_baseline_sample(n_sample: int = 6400, theta=THETA0):
+def cpu_baseline_sample(n_sample: int = 12800, theta=THETA0, single_thread_c1: bool = True):
     """The oracle (dense FP64 Cholesky likelihood) on a bounded sample, scaled to n = 40,000.
 
-    Sample: n = 6,400 (80 x 80 perturbed grid).  The covariance fill is scaled
-    by (40000/6400)^2, the Cholesky + solve by (40000/6400)^3.
+    Sample: n = 12,800 (the first n points of a perturbed 114 x 114 grid), about
+    10 s on 16 host cores.  The covariance fill is scaled by (40000/n)^2, the
+    Cholesky + solve by (40000/n)^3.  Also times the small workload (n = 1,600,
+    40 x 40 grid) on one thread in a child process.
     """
     import numpy as np
     import oracle
@@ -403,14 +526,69 @@ def cpu_baseline_sample(n_sample: int = 6400, theta=THETA0):
     t1 = time.perf_counter()
     oracle.loglik_from_cov(S, z)
     t2 = time.perf_counter()
+    del S
     f = N_POINTS / n_sample
     est = (t1 - t0) * f ** 2 + (t2 - t1) * f ** 3
     side = math.ceil(math.sqrt(n_sample))
-    return {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "dense FP64 oracle at n=%d (perturbed %dx%d grid, first n points): Matern fill %.2fs x "
-                      "(%d/%d)^2, Cholesky+solve %.2fs x (%d/%d)^3 -> %.1fs per n=%d evaluation"
-                      % (n_sample, side, side, t1 - t0, N_POINTS, n_sample, t2 - t1, N_POINTS, n_sample, est,
-                         N_POINTS)}
+    out = {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "dense FP64 oracle at n=%d (perturbed %dx%d grid, first n points): Matern fill %.2fs x "
+                     "(%d/%d)^2, Cholesky+solve %.2fs x (%d/%d)^3 -> %.1fs per n=%d evaluation"
+                     % (n_sample, side, side, t1 - t0, N_POINTS, n_sample, t2 - t1, N_POINTS, n_sample, est,
+                        N_POINTS),
+           "cpu_model": cpu_model()}
+    if single_thread_c1:
+        out["single_thread_n1600"] = oracle_single_thread(1600)
+    return out
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name") and ":" in line:
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_single_thread(n: int) -> dict:
+    """One dense oracle evaluation (fill + Cholesky + solve) on one thread, in a
+    child process whose OpenMP and BLAS pools are pinned to one thread."""
+    code = ("import sys, time, json; sys.path.insert(0, %r); import oracle, synth; "
+            "xy = synth.jittered_grid(%d, seed=1); z = synth.standard_normal(%d, seed=2); "
+            "oracle.loglik_dense(xy, z, %r); t = time.perf_counter(); "
+            "r = oracle.loglik_dense(xy, z, %r); print(json.dumps({'s': time.perf_counter() - t, "
+            "'loglik': r['loglik']}))" % (ROOT, n, n, tuple(THETA0), tuple(THETA0)))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        r = json.loads(p.stdout.strip().splitlines()[-1])
+        return {"n": n, "seconds": r["s"], "evals_per_s": 1.0 / r["s"], "threads": 1}
+    except Exception as e:  # reported, never fatal
+        return {"n": n, "error": str(e)[:200]}
+
+
+def run_oracle_fullsize(args):
+    """One real dense oracle evaluation at the full size (n = 40,000) on all
+    host cores, after no warm-up (one run of about 200 s; not part of the
+    default bench).  Prints one JSON line."""
+    import oracle
+    import synth
+    xy = synth.jittered_grid(N_POINTS, seed=1)
+    z = synth.standard_normal(N_POINTS, seed=2)
+    t0 = time.perf_counter()
+    S = oracle.cov_matrix(xy, THETA0)
+    t1 = time.perf_counter()
+    r = oracle.loglik_from_cov(S, z)
+    t2 = time.perf_counter()
+    print(json.dumps({"workload": "oracle-fullsize", "n": N_POINTS, "theta": list(THETA0),
+                      "fill_s": t1 - t0, "cholesky_solve_s": t2 - t1, "total_s": t2 - t0,
+                      "evals_per_s": 1.0 / (t2 - t0), "loglik": r["loglik"], "cores": os.cpu_count(),
+                      "cpu_model": cpu_model(),
+                      "threads": {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}}),
+          flush=True)
 
 
 def run_reference(args):
@@ -420,11 +598,11 @@ def run_reference(args):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        cpu_baseline_sample(n_sample=3200)
+        cpu_baseline_sample(n_sample=3200, single_thread_c1=False)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline_sample(n_sample=3200))
+        vals.append(cpu_baseline_sample(n_sample=3200, single_thread_c1=False))
     wall = time.perf_counter() - t0
     v = sum(x["value"] for x in vals) / len(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
@@ -438,6 +616,177 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
     print(json.dumps(line), flush=True)
+
+
+# ---- ordering study (Table 1, Sec. 5.2-5.3) ----------------------------------
+
+STUDY_ORDERS = ("random", "morton", "hilbert", "kdtree", "maxmin")
+STUDY_NU = (0.5, 1.0)
+STUDY_BETA = (0.03, 0.1, 0.3)
+STUDY_EPS = (1e-9, 1e-7, 1e-5)
+TABLE1_N = (10000, 20000, 30000, 40000)
+TABLE1_ORDERS = {"none": "random", "morton": "morton", "hilbert": "hilbert", "kdtree": "kdtree"}
+
+
+def table1_golden():
+    """Table 1's MB per (n, ordering, correlation) from tests/golden/table1_memory.txt."""
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table1_memory.txt")) as f:
+        for line in f:
+            if not line[:1].isdigit():
+                continue
+            n, order, *vals = line.split()
+            out[(int(n), order)] = [None if v == "NA" else float(v) for v in vals]
+    return out
+
+
+def run_ordering_study(args):
+    """The ordering study: every ordering x nu in {0.5, 1} x beta in {0.03, 0.1,
+    0.3} x eps in {1e-9, 1e-7, 1e-5} at n = 40,000, tile 800, FP64 path.  Per
+    point: time per evaluation (CUDA events, after one warm-up that sets the
+    rank map), l and its two terms, the factor's rank map (max / mean rank,
+    off-diagonal MB) and |dl| against the exact dense l where the oracle has it
+    (theta = (1, 0.1, 0.5) with the golden Z = L w), else against the same
+    ordering at eps = 1e-9.  Then Table 1's memory of the compressed covariance
+    (tile 1000, nu = 0.5, eps 1e-7) for n = 10k..40k beside the paper's values.
+    Z per theta: the golden Z where it exists, else Z = L w with L the
+    library's TLR factor at eps 1e-9 (Hilbert, maxrank nb), w seed 2.
+    A point whose tiles need more than maxrank = nb/2 is "NA" (Table 1's NA)."""
+    import numpy as np
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    import synth
+    dev = torch.device("cuda", 0)
+    ctx = tlr.Context(0)
+    stream = torch.cuda.current_stream()
+    n, nb = N_POINTS, NB
+    xy_h = synth.jittered_grid(n, seed=1)
+    w_h = synth.standard_normal(n, seed=2)
+    xy = torch.from_numpy(xy_h).to(dev)
+    w = torch.from_numpy(w_h).to(dev)
+    gold = None
+    gpath = os.path.join(ROOT, "tests", "golden", "fullsize_loglik_n%d.json" % n)
+    zpath = os.path.join(ROOT, "tests", "golden", "fullsize_z_n%d.npy" % n)
+    if os.path.exists(gpath) and os.path.exists(zpath):
+        gold = json.load(open(gpath))
+        gold["z_arr"] = np.load(zpath)
+    orders = [o for o in (args.study_orders.split(",") if args.study_orders else STUDY_ORDERS)]
+    rows, rank_maps = [], {}
+    t_all = time.perf_counter()
+
+    def draw_z(theta):
+        if gold is not None and tuple(gold["theta"]) == tuple(theta):
+            return torch.from_numpy(gold["z_arr"]).to(dev), gold
+        xyo = torch.empty_like(xy)
+        perm = tlr.tlr_order(ctx, xy, "hilbert", xy_out=xyo)
+        L = tlr.TlrMatrix(ctx, n, nb, maxrank=nb)
+        try:
+            tlr.tlr_loglik(L, xyo, torch.zeros(n, dtype=torch.float64, device=dev), theta,
+                           tlr.Options(nb=nb, eps=1e-9, maxrank=nb))
+            zo = tlr.tlr_lmul(L, tlr.tlr_gather(ctx, perm, w))
+            z = torch.empty_like(zo)
+            z[perm] = zo
+            return z, None
+        finally:
+            L.close()
+
+    for nu in STUDY_NU:
+        for beta in STUDY_BETA:
+            theta = (1.0, beta, nu)
+            try:
+                z, g = draw_z(theta)
+            except tlr.TlrError as e:
+                rows.append({"theta": list(theta), "error": "Z draw: " + str(e)[:120]})
+                continue
+            for order in orders:
+                xyo = torch.empty_like(xy)
+                perm = tlr.tlr_order(ctx, xy, order, xy_out=xyo)
+                zo = tlr.tlr_gather(ctx, perm, z)
+                ref9 = None
+                for eps in STUDY_EPS:
+                    row = {"order": order, "nu": nu, "beta": beta, "eps": eps}
+                    L = tlr.TlrMatrix(ctx, n, nb)
+                    opts = tlr.Options(nb=nb, eps=eps, precision=tlr.TLR_PREC_FP64)
+                    try:
+                        tlr.tlr_loglik(L, xyo, zo, theta, opts)  # warm-up: rank map
+                        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                              for _ in range(args.study_steps)]
+                        for a, b in ev:
+                            a.record(stream)
+                            r = tlr.tlr_loglik(L, xyo, zo, theta, opts)
+                            b.record(stream)
+                        torch.cuda.synchronize()
+                        ms = [a.elapsed_time(b) for a, b in ev]
+                        rk = tlr.tlr_mat_ranks(L)
+                        off = rk[np.tril_indices(rk.shape[0], -1)]
+                        row.update({"ms_per_eval": float(np.mean(ms)), "loglik": r["loglik"],
+                                    "logdet": r["logdet"], "quad": r["quad"], "max_rank": int(off.max()),
+                                    "mean_rank": float(off.mean()), "offdiag_mb": r["offdiag_bytes"] / 1e6,
+                                    "flops_algorithmic": algorithmic_flops(rk, n, nb)["total"]})
+                        rank_maps["%s nu=%g beta=%g eps=%g" % (order, nu, beta, eps)] = rk.tolist()
+                        if g is not None:
+                            row["dl_vs_exact"] = abs(r["loglik"] - g["loglik"])
+                            row["rel_dl_vs_exact"] = row["dl_vs_exact"] / abs(g["loglik"])
+                            row["dlogdet_vs_exact"] = abs(r["logdet"] - g["logdet"])
+                            row["dquad_vs_exact"] = abs(r["quad"] - g["quad"])
+                        if eps == STUDY_EPS[0]:
+                            ref9 = r["loglik"]
+                        elif ref9 is not None:
+                            row["dl_vs_eps1e-9"] = abs(r["loglik"] - ref9)
+                    except tlr.TlrError as e:
+                        row["status"] = "NA" if e.code == tlr.TLR_ERR_RANK else "error %d" % e.code
+                        row["error"] = str(e)[:120]
+                        torch.cuda.synchronize()
+                    finally:
+                        L.close()
+                    rows.append(row)
+    study_s = time.perf_counter() - t_all
+
+    # Table 1: memory of the compressed covariance, tile 1000, nu 0.5, eps 1e-7
+    paper = table1_golden()
+    t1 = []
+    t_tab = time.perf_counter()
+    for nn in (TABLE1_N if args.table1 else ()):
+        xy1 = torch.from_numpy(synth.jittered_grid(nn, seed=1)).to(dev)
+        for label, order in TABLE1_ORDERS.items():
+            xyo = torch.empty_like(xy1)
+            tlr.tlr_order(ctx, xy1, order, xy_out=xyo)
+            for c, beta in enumerate(STUDY_BETA):
+                theta = (1.0, beta, 0.5)
+                ent = {"n": nn, "ordering": label, "beta": beta,
+                       "paper_mb": paper.get((nn, label), [None] * 3)[c]}
+                M = tlr.TlrMatrix(ctx, nn, 1000)
+                try:
+                    tiles = tlr.tlr_generate(ctx, xyo, 1000, theta)
+                    tlr.tlr_compress(M, tiles, 1e-7 * theta[0])
+                    del tiles
+                    rk = tlr.tlr_mat_ranks(M)
+                    m = [min(1000, nn - t * 1000) for t in range(rk.shape[0])]
+                    mb = sum((m[i] + m[j]) * int(rk[i, j]) * 8 for i in range(len(m)) for j in range(i)) / 1e6
+                    ent["mb"] = mb
+                    if ent["paper_mb"]:
+                        ent["ratio_to_paper"] = mb / ent["paper_mb"]
+                except tlr.TlrError as e:
+                    ent["mb"] = "NA" if e.code == tlr.TLR_ERR_RANK else "error %d" % e.code
+                    torch.cuda.synchronize()
+                finally:
+                    M.close()
+                t1.append(ent)
+    table_s = time.perf_counter() - t_tab
+    out_dir = args.out_dir
+    os.makedirs(out_dir, exist_ok=True)
+    with open(os.path.join(out_dir, "ordering_study.json"), "w") as f:
+        json.dump({"rows": rows, "table1": t1, "rank_maps": rank_maps}, f)
+    ok = [r for r in rows if "ms_per_eval" in r]
+    line = {"workload": "ordering-study", "n": n, "nb": nb, "orders": orders, "points": len(rows),
+            "measured": len(ok), "na": sum(1 for r in rows if r.get("status") == "NA"),
+            "study_s": study_s, "table1_s": table_s, "rows_file": os.path.join(out_dir, "ordering_study.json"),
+            "rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()
+                      if k in ("order", "nu", "beta", "eps", "ms_per_eval", "max_rank", "mean_rank", "offdiag_mb",
+                               "rel_dl_vs_exact", "dl_vs_eps1e-9", "status")} for r in rows],
+            "table1": t1}
+    print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 # ---- many datasets: batched evaluation (256 datasets) and serving -----------
@@ -459,7 +808,8 @@ def batched_datasets(count: int, seed: int = 2024):
 
 def run_batched(args):
     """Batched workload: `--datasets` independent datasets (jittered grids,
-    first n points of a ceil(sqrt n)^2 grid, Z ~ N(0, I) seeded), Morton order,
+    first n points of a ceil(sqrt n)^2 grid, Z = L(theta_i) w_i drawn from each
+    dataset's own model with w_i ~ N(0, I) seeded), Morton order,
     eps 1e-7.  Tile size per n bucket picked by the pool's autotuner on one
     dataset of the bucket.  One step = every dataset evaluated once (one
     tlr_pool_loglik call), thetas moving along a per-dataset log-space walk."""
@@ -490,12 +840,21 @@ def run_batched(args):
         tuned[b] = {"n": n, "best_nb": best, "ms": ms}
     tune_pool.close()
 
+    # every dataset's data drawn from its own model, Z = L(theta_i) w_i
+    zctx = tlr.Context(0)
+    zs, z_white = [], 0
+    for i in range(count):
+        z, ok = draw_z_lw(tlr, zctx, synth.jittered_grid(int(sizes[i]), seed=10 + i),
+                          synth.standard_normal(int(sizes[i]), seed=5000 + i), th0[i], "morton", 512)
+        zs.append(z)
+        z_white += 0 if ok else 1
+    zctx.close()
+
     def new_pool():
         # every path gets a pool of its own, so that each dataset's rank-map
         # history (the compression's sample sizes) comes from that path alone
         pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
-        ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(int(sizes[i]), seed=10 + i),
-                                synth.standard_normal(int(sizes[i]), seed=5000 + i), "morton",
+        ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(int(sizes[i]), seed=10 + i), zs[i], "morton",
                                 nb=tuned[bucket_of[i]]["best_nb"]) for i in range(count)]
         return pool, ids
 
@@ -521,7 +880,8 @@ def run_batched(args):
             times.append(time.perf_counter() - t0)
             fails += sum(1 for x in st if x != 0)
             used64 += sum(1 for r, x in zip(res, st) if x == 0 and r["precision_used"] == tlr.TLR_PREC_FP64)
-            results.append([(r["loglik"], r["min_pivot2"]) if x == 0 else None for r, x in zip(res, st)])
+            results.append([(r["loglik"], r["min_pivot2"], r["logdet"]) if x == 0 else None
+                            for r, x in zip(res, st)])
         torch.cuda.synchronize()
         clocks_all[name] = clocks.stop()
         total = sum(times)
@@ -532,14 +892,20 @@ def run_batched(args):
         pool.close()
 
     def compare(name):
-        rel, pairs = [], []
+        rel, pairs, absd, dlogdet = [], [], [], []
         for k, (ra, rb) in enumerate(zip(out[name]["results"], out["fp64"]["results"])):
             for i, (a, b) in enumerate(zip(ra, rb)):
                 if a is not None and b is not None:
                     rel.append(abs(a[0] - b[0]) / abs(b[0]))
+                    absd.append(abs(a[0] - b[0]))
+                    dlogdet.append(abs(a[2] - b[2]) / abs(b[2]))
                     th = walks[i][args.warmup + k]
                     pairs.append((rel[-1], a[1] / th[0], int(sizes[i]), [round(float(v), 4) for v in th]))
+        compare.extra[name] = {"abs_dl_max": max(absd, default=None),
+                               "abs_dl_median": float(np.median(absd)) if absd else None,
+                               "rel_dlogdet_max": max(dlogdet, default=None)}
         return rel, pairs
+    compare.extra = {}
 
     rel, pairs = compare("mixed")
     rel_auto, _ = compare("auto")
@@ -552,9 +918,9 @@ def run_batched(args):
     accuracy = {"pairs": len(rel), "within_1e-6": int(sum(1 for r in rel if r <= 1e-6)),
                 "median": float(np.median(rel)) if rel else None,
                 "worst": [{"rel": r, "min_pivot2": pv, "n": n, "theta": th} for r, pv, n, th in pairs[:6]],
-                "by_min_pivot2": calib}
+                "by_min_pivot2": calib, **compare.extra["mixed"]}
     accuracy_auto = {"pairs": len(rel_auto), "within_1e-6": int(sum(1 for r in rel_auto if r <= 1e-6)),
-                     "max": max(rel_auto) if rel_auto else None}
+                     "max": max(rel_auto) if rel_auto else None, **compare.extra["auto"]}
     st = pool_stats
     # the fastest path whose every evaluated pair is within 1e-6 of the FP64 path
     ok = [nm for nm, r in (("mixed", rel), ("auto", rel_auto)) if r and max(r) <= 1e-6]
@@ -565,8 +931,10 @@ def run_batched(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if head == "fp64" else "f64 storage, paired-f32 products", "data": "synthetic",
             "config": {"workload": "batched: %d datasets, n ~ U[2000, 20000] jittered grids, theta ~ U(sigma2 "
-                                   "[0.5,2], beta [0.02,0.3], nu [0.5,2.5]), Morton, eps %g, %d workers"
-                                   % (count, EPS, args.workers),
+                                   "[0.5,2], beta [0.02,0.3], nu [0.5,2.5]), Z = L(theta) w, Morton, eps %g, "
+                                   "%d workers" % (count, EPS, args.workers),
+                       "z": "Z = L(theta_i) w_i from the library's TLR factor at eps 1e-9 (tile 512); "
+                            "%d datasets too ill-conditioned for it kept Z = w" % z_white,
                        "precision": head, "workers": args.workers, "maxrank": args.maxrank,
                        "tile_autotune": {str(BATCH_BUCKETS[b]): v for b, v in tuned.items()},
                        "timing": "host wall clock around each blocking tlr_pool_loglik (all datasets)",
@@ -587,7 +955,8 @@ SERVE_SIZES = (5000, 10000, 20000, 40000, 80000)
 
 def run_serving(args):
     """Serving workload: 32 resident datasets with n cycling through 5k, 10k,
-    20k, 40k, 80k (jittered grids, Z ~ N(0, I) seeded, Hilbert order, tile
+    20k, 40k, 80k (jittered grids, Z = L w drawn from the model at the walk's
+    start theta = (1, 0.1, 1.0), w ~ N(0, I) seeded, Hilbert order, tile
     800), a Poisson stream of `--requests` l(theta) requests at `--rate` per
     second on uniformly drawn datasets, theta following each dataset's own
     simplex-like walk in log(sigma2, beta, nu) around (1, 0.1, 1.0), and two
@@ -602,8 +971,13 @@ def run_serving(args):
     sizes = [SERVE_SIZES[i % len(SERVE_SIZES)] for i in range(nd)]
     pool = tlr.Pool(0, workers=args.workers, nb=NB, maxrank=args.maxrank)
     t_setup = time.perf_counter()
-    ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=300 + i), synth.standard_normal(n, seed=600 + i),
-                            "hilbert") for i, n in enumerate(sizes)]
+    zctx = tlr.Context(0)
+    zs = [draw_z_lw(tlr, zctx, synth.jittered_grid(n, seed=300 + i), synth.standard_normal(n, seed=600 + i),
+                    (1.0, 0.1, 1.0), "hilbert", NB) for i, n in enumerate(sizes)]
+    zctx.close()
+    z_white = sum(1 for _, ok in zs if not ok)
+    ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(n, seed=300 + i), zs[i][0], "hilbert")
+           for i, n in enumerate(sizes)]
     setup_s = time.perf_counter() - t_setup
     rng = np.random.default_rng(77)
     R = args.requests
@@ -686,7 +1060,9 @@ def run_serving(args):
                                    "Hilbert, tile %d, eps %g, Poisson %g req/s x %d requests + 2 MLE jobs, "
                                    "%d workers" % (NB, EPS, args.rate, R, args.workers),
                        "workers": args.workers, "maxrank": args.maxrank, "rate": args.rate, "requests": R,
-                       "latency": "host clock, submission to completion"},
+                       "latency": "host clock, submission to completion",
+                       "z": "Z = L(1, 0.1, 1.0) w from the library's TLR factor at eps 1e-9; %d kept Z = w"
+                            % z_white},
             "fp64_path": out["fp64"], "mixed_path": out["mixed"], "setup_s": setup_s,
             "mixed_vs_fp64": {"pairs": len(rel), "max": max(rel) if rel else None,
                               "within_1e-6": int(sum(1 for r in rel if r <= 1e-6))},
@@ -703,6 +1079,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--latency-evals", type=int, default=100,
+                    help="evaluations of the separate latency loop (p50/p99); 0 = use the timed steps")
     ap.add_argument("--n", type=int, default=N_POINTS, help="locations (profiling of smaller cases)")
     ap.add_argument("--nb", type=int, default=NB)
     ap.add_argument("--eps", type=float, default=EPS)
@@ -710,7 +1088,12 @@ def main():
     ap.add_argument("--theta", default=None, help="walk start sigma2,beta,nu (default 1,0.1,0.5)")
     ap.add_argument("--paths", default="both", choices=["both", "mixed", "fp64"],
                     help="precision paths to time (both for the headline; one for profiling runs)")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serving"],
+    ap.add_argument("--study-steps", type=int, default=2, help="timed evaluations per ordering-study point")
+    ap.add_argument("--study-orders", default="", help="comma-separated orderings of the study (default: all five)")
+    ap.add_argument("--no-table1", dest="table1", action="store_false", help="skip the Table 1 memory comparison")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"), help="where the study writes its tables")
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "batched", "serving", "ordering-study", "oracle-fullsize"],
                     help="headline: one n = 40,000 evaluation per step; batched: many datasets per step; "
                          "serving: a Poisson request stream over resident datasets")
     ap.add_argument("--workers", type=int, default=8, help="pool workers (batched / serving)")
@@ -727,12 +1110,17 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload == "oracle-fullsize":
+        run_oracle_fullsize(args)
+        return
     from paper_2402_09356_gb300 import build as lib_build
     lib_build.build()
     if args.workload == "batched":
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "ordering-study":
+        run_ordering_study(args)
     else:
         run_gpu(args)
 

@@ -328,11 +328,13 @@ int tlr_detail_times(tlr_ctx *ctx, double *ms, int count);
  * Errors: TLR_ERR_ARG. */
 int tlr_compress_times(tlr_ctx *ctx, double *ms);
 
-/* Counters of the compressions of the last tlr_loglik / tlr_potrf
- * factorisation, written to out[0..4]: tile compressions run (a tile redone
+/* Counters of the compressions of the last tlr_compress, tlr_loglik or
+ * tlr_potrf call, written to out[0..6]: tile compressions run (a tile redone
  * with a larger sample counts again), adaptive rounds, FP64 Jacobi sweeps
  * summed over the compressions, the largest FP64 sweep count of one
- * compression, and FP32 (preconditioning) Jacobi sweeps summed.
+ * compression, FP32 (preconditioning) Jacobi sweeps summed, and the QR and
+ * SVD jobs that ran on the global-memory kernels (samples too large for a
+ * cluster's shared memory).
  * Collected whether or not profiling is on.  Errors: TLR_ERR_ARG. */
 int tlr_compress_stats(tlr_ctx *ctx, int64_t *out);
 

@@ -10,7 +10,6 @@ if libtlr.so is missing or cannot be loaded, importing the functions raises.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 from dataclasses import dataclass
 
@@ -482,11 +481,11 @@ def tlr_kernel_stats(ctx: Context) -> dict:
             "jacobi16_clusters": int(a[3])}
 
 
-COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps", "sweeps32")
+COMPRESS_STATS = ("tiles", "rounds", "sweeps", "max_sweeps", "sweeps32", "qr_global", "svd_global")
 
 
 def tlr_compress_stats(ctx: Context) -> dict:
-    a = (ctypes.c_int64 * 5)()
+    a = (ctypes.c_int64 * len(COMPRESS_STATS))()
     ctx.check(load_library().tlr_compress_stats(ctx.h, a))
     return {k: int(a[i]) for i, k in enumerate(COMPRESS_STATS)}
 
@@ -500,10 +499,6 @@ def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1
                                 ctypes.byref(it), _stream(stream))
     mat.ctx.check(rc)
     return {"theta": (th.sigma2, th.beta, th.nu), "loglik": ll.value, "iters": it.value}
-
-
-def loglik_log2pi(n: int) -> float:
-    return -0.5 * n * math.log(2 * math.pi)
 
 
 # ---- many datasets: batched evaluation and serving ----------------------------

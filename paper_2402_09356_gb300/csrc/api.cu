@@ -617,7 +617,7 @@ int tlr_kernel_stats(tlr_ctx *ctx, double *out) {
 
 int tlr_compress_stats(tlr_ctx *ctx, int64_t *out) {
     if (!ctx || !out) return TLR_ERR_ARG;
-    for (int k = 0; k < 5; ++k) out[k] = ctx->comp_stats[k];
+    for (int k = 0; k < 7; ++k) out[k] = ctx->comp_stats[k];
     return TLR_OK;
 }
 

@@ -166,7 +166,7 @@ struct tlr_ctx {
     // GEMM, QR of B', SVD, host decision (incl. sync), U/V GEMMs
     std::vector<cudaEvent_t> comp_events;
     double comp_ms[7] = {0, 0, 0, 0, 0, 0, 0};
-    long long comp_stats[5] = {0, 0, 0, 0, 0};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum)
+    long long comp_stats[7] = {};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum), QR / SVD jobs on the global-memory kernels
     // the 16-CTA cluster Jacobi (profiling): device ms, FP64 flops, launches, clusters
     std::vector<cudaEvent_t> cls_time_events;
     double *d_potrf_scratch = nullptr;  // diagonal-block inverses of the cluster POTRF

@@ -1226,6 +1226,7 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
         }
         add_to_class(cls, big ? (QrKernel)k_qr_gm<16> : (QrKernel)k_qr_gm<8>, top, 6 * (size_t)J.s * sizeof(double),
                      J);
+        ctx->comp_stats[5] += 1;
     }
     launch_classes(ctx, st, cls, (ClassTiming *)nullptr);
 }
@@ -1254,6 +1255,7 @@ static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> 
         bytes = jacobi_gm_bytes(J.s, top);
         if (bytes > smem_cap((const void *)kg)) throw make_error(TLR_ERR_ARG, "sample size %d too large for this device", J.s);
         add_to_class(cls, kg, top, bytes, J);
+        ctx->comp_stats[6] += 1;
     }
     launch_classes(ctx, st, cls, timing, tau);
 }

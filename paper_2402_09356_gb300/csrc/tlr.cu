@@ -728,6 +728,7 @@ void compress_packed(tlr_ctx *ctx, cudaStream_t st, const double *tiles, tlr_mat
     auto tile = [&](int i, int j) { return tiles + ((int64_t)i * (i + 1) / 2 + j) * nb * nb; };
     reset_slots(M);
     const GrowSlot grow = arena_grow(M);
+    for (long long &v : ctx->comp_stats) v = 0;
     std::vector<CopyDesc> cd;
     for (int t = 0; t < nt; ++t)
         cd.push_back(CopyDesc{tile(t, t), nb, M->D + (int64_t)t * nb * nb, nb, nb, nb});

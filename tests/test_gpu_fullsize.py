@@ -1,5 +1,5 @@
-"""Parity at the full benchmark size (n = 40,000, tile 800, eps = 1e-7, the
-bench's launch configuration), where the dense oracle likelihood is too slow:
+"""Parity at the full benchmark size (n = 40,000, tile 800, the bench's launch
+configuration), where the dense oracle likelihood is too slow to run in a test:
 
 * sampled tiles of L L' against the oracle's covariance tiles.  In the
   left-looking factorisation tile (i, j) of L L' equals Sigma_ij minus the one
@@ -12,9 +12,11 @@ bench's launch configuration), where the dense oracle likelihood is too slow:
 * exact l is invariant under any permutation of the locations (Sec. 3): the
   Hilbert and Morton results agree within twice the 10 eps |l| bound each
   meets, and the mixed path stays within 1e-6 |l| of the FP64 path.
-* both paths' l at full size within 10 eps |l| of the exact value that the
-  dense oracle computed once for this workload (tests/golden/
-  fullsize_loglik_n40000.json, written by make_fullsize_loglik.py).
+* l, log|Sigma| and Z' Sigma^-1 Z of both paths, at eps = 1e-7 and 1e-9,
+  each within 10 eps of its own magnitude from the exact values the dense
+  oracle computed once for this workload with the data drawn from the model,
+  Z = L w (tests/golden/fullsize_loglik_n40000.json and fullsize_z_n40000.npy,
+  written by make_fullsize_loglik.py).
 """
 import json
 import os
@@ -31,17 +33,23 @@ N, NB, EPS, THETA = 40000, 800, 1e-7, (1.0, 0.1, 0.5)
 SAMPLED = [(0, 0), (1, 0), (2, 1), (25, 24), (30, 10), (49, 0), (49, 48)]
 
 
-def factor(ctx, order, precision):
+def golden_z(golden_dir):
+    return np.load(os.path.join(golden_dir, "fullsize_z_n40000.npy"))
+
+
+def factor(ctx, order, precision, eps=EPS, z=None):
+    """TLR factor of the workload; z (generation order) defaults to white noise,
+    which the tests that only look at the factor use."""
     import torch
     import paper_2402_09356_gb300 as tlr
     xy = synth.jittered_grid(N, seed=1)
-    w = synth.standard_normal(N, seed=2)
+    w = synth.standard_normal(N, seed=2) if z is None else z
     xy_d = torch.from_numpy(xy).cuda()
     xyo = torch.empty_like(xy_d)
     perm = tlr.tlr_order(ctx, xy_d, order, xy_out=xyo)
-    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(w).cuda())
+    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(np.ascontiguousarray(w)).cuda())
     L = tlr.TlrMatrix(ctx, N, NB)
-    r = tlr.tlr_loglik(L, xyo, zo, THETA, tlr.Options(nb=NB, eps=EPS, precision=precision))
+    r = tlr.tlr_loglik(L, xyo, zo, THETA, tlr.Options(nb=NB, eps=eps, precision=precision))
     return L, r, xyo.cpu().numpy()
 
 
@@ -106,12 +114,14 @@ def test_fullsize_logdet_from_diagonal(ctx, hilbert64):
     assert abs(2 * s - r["logdet"]) <= 1e-11 * abs(r["logdet"])
 
 
-def test_fullsize_ordering_invariance_and_mixed(ctx, hilbert64):
+def test_fullsize_ordering_invariance_and_mixed(ctx, golden_dir):
     import paper_2402_09356_gb300 as tlr
-    _, r64, _ = hilbert64
-    Lm, rm, _ = factor(ctx, "morton", tlr.TLR_PREC_FP64)
+    z = golden_z(golden_dir)
+    L6, r64, _ = factor(ctx, "hilbert", tlr.TLR_PREC_FP64, z=z)
+    L6.close()
+    Lm, rm, _ = factor(ctx, "morton", tlr.TLR_PREC_FP64, z=z)
     Lm.close()
-    Lx, rx, xyo = factor(ctx, "hilbert", tlr.TLR_PREC_MIXED)
+    Lx, rx, xyo = factor(ctx, "hilbert", tlr.TLR_PREC_MIXED, z=z)
     ref = abs(r64["loglik"])
     assert abs(rm["loglik"] - r64["loglik"]) <= 20 * EPS * ref, (rm["loglik"], r64["loglik"])
     assert abs(rx["loglik"] - r64["loglik"]) <= 1e-6 * ref, (rx["loglik"], r64["loglik"])
@@ -123,13 +133,18 @@ def test_fullsize_ordering_invariance_and_mixed(ctx, hilbert64):
     Lx.close()
 
 
-def test_fullsize_loglik_against_exact_oracle(ctx, hilbert64, golden_dir):
+@pytest.mark.parametrize("eps", [1e-7, 1e-9])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fullsize_loglik_terms_against_exact_oracle(ctx, golden_dir, eps, precision):
+    """Eq. 1.2 term by term at full size: l, log|Sigma| and Z' Sigma^-1 Z each
+    within 10 eps of its own magnitude from the dense oracle's exact values."""
     import paper_2402_09356_gb300 as tlr
     gold = json.load(open(os.path.join(golden_dir, "fullsize_loglik_n40000.json")))
     assert gold["n"] == N and tuple(gold["theta"]) == THETA and gold["loc_seed"] == 1 and gold["z_seed"] == 2
-    exact = gold["loglik"]
-    _, r64, _ = hilbert64
-    assert abs(r64["loglik"] - exact) <= 10 * EPS * abs(exact), (r64["loglik"], exact)
-    Lx, rx, _ = factor(ctx, "hilbert", tlr.TLR_PREC_MIXED)
-    Lx.close()
-    assert abs(rx["loglik"] - exact) <= 10 * EPS * abs(exact), (rx["loglik"], exact)
+    z = golden_z(golden_dir)
+    assert z.shape == (N,)
+    prec = tlr.TLR_PREC_FP64 if precision == "fp64" else tlr.TLR_PREC_MIXED
+    L, r, _ = factor(ctx, "hilbert", prec, eps=eps, z=z)
+    L.close()
+    for term in ("loglik", "logdet", "quad"):
+        assert abs(r[term] - gold[term]) <= 10 * eps * abs(gold[term]), (term, r[term], gold[term])

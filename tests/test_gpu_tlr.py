@@ -307,3 +307,85 @@ def test_compact_storage_overflow(ctx):
         tlr.tlr_loglik(C, xyo, zo, theta, opts)
     assert e.value.code == tlr.TLR_ERR_RANK and "slot" in str(e.value)
     C.close()
+
+
+def test_ranks_at_sigma2_not_one(ctx):
+    """The threshold is absolute and scales with sigma2 (Sec. 2-3, the accuracy
+    threshold): at sigma2 = 2.5 the compressed covariance tiles keep the
+    singular values above eps * sigma2, and the factor's tiles those of the
+    Schur complement above the same threshold."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    n, nb, theta, eps = 1600, 200, (2.5, 0.1, 0.5), 1e-7
+    xy, z, perm = ordered_problem(n, theta, "hilbert")
+    xyp = oracle.permute_xy(xy, perm)
+    S = oracle.cov_matrix(xyp, theta)
+    ref, sv = oracle.tile_ranks(S, nb, eps, sigma2=theta[0])
+    tiles = tlr.tlr_generate(ctx, torch.from_numpy(xyp).cuda(), nb, theta)
+    A = tlr.TlrMatrix(ctx, n, nb)
+    tlr.tlr_compress(A, tiles, eps * theta[0])
+    got = tlr.tlr_mat_ranks(A)
+    for (i, j), s in sv.items():
+        if got[i, j] != ref[i, j]:
+            assert near_threshold(s, ref[i, j], eps * theta[0]), (i, j, got[i, j], ref[i, j])
+    A.close()
+    # the same count at threshold eps (sigma2 dropped) differs somewhere
+    unscaled, _ = oracle.tile_ranks(S, nb, eps, sigma2=1.0)
+    assert (unscaled != ref).any()
+    reff, svf = oracle.factor_tile_ranks(S, nb, eps, sigma2=theta[0])
+    r, L, _ = gpu_loglik(ctx, xy, z, theta, "hilbert", nb, eps)
+    gotf = tlr.tlr_mat_ranks(L)
+    diff = 0
+    for (i, j), s in svf.items():
+        if gotf[i, j] != reff[i, j]:
+            diff += 1
+            assert abs(int(gotf[i, j]) - int(reff[i, j])) <= 2, (i, j, gotf[i, j], reff[i, j])
+    assert diff <= len(svf) // 4
+    exact = oracle.loglik_dense(xyp, z[perm], theta)["loglik"]
+    assert abs(r["loglik"] - exact) <= 10 * eps * abs(exact)
+    L.close()
+
+
+def overlapping_strips(nb, width, seed=21):
+    """2 nb locations: the first nb uniform in [0, (1 + width) / 2] x [0, 1], the
+    next nb in [(1 - width) / 2, 1] x [0, 1].  The off-diagonal tile couples the
+    two sets through their common strip, so its rank grows with the width."""
+    u = synth.uniform(seed, 4 * nb).reshape(4, nb)
+    half = 0.5 + width / 2
+    return np.concatenate([u[0] * half, 1.0 - u[1] * half, u[2], u[3]])
+
+
+def test_global_memory_fallback_kernels(ctx):
+    """Samples too large for a cluster's shared memory run on the global-memory
+    QR and Jacobi kernels.  Tile 1024 with an off-diagonal rank of 470 at eps
+    1e-7 (two overlapping strips of locations): the adaptive sample grows
+    56, 112, 224, 448, 512, and s = 448 and 512 exceed the cluster kernels'
+    shared memory.  Ranks and |T - U V'|_2 as in the shared-memory path, and l
+    against the dense oracle."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    nb, theta, eps = 1024, (1.0, 0.03, 0.5), 1e-7
+    xy = overlapping_strips(nb, 0.3)
+    n = 2 * nb
+    z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=6))
+    S = oracle.cov_matrix(xy, theta)            # identity order
+    ref, sv = oracle.tile_ranks(S, nb, eps)
+    assert 440 <= ref[1, 0] <= 490, ref[1, 0]
+    tiles = tlr.tlr_generate(ctx, torch.from_numpy(xy).cuda(), nb, theta)
+    A = tlr.TlrMatrix(ctx, n, nb, nb)
+    tlr.tlr_compress(A, tiles, eps)
+    st = tlr.tlr_compress_stats(ctx)
+    assert st["qr_global"] > 0 and st["svd_global"] > 0, st
+    got = tlr.tlr_mat_ranks(A)
+    if got[1, 0] != ref[1, 0]:
+        assert near_threshold(sv[(1, 0)], ref[1, 0], eps), (got[1, 0], ref[1, 0])
+    U, V = tlr.tlr_mat_tile(A, 1, 0)
+    E = S[nb:, :nb] - U.cpu().numpy() @ V.cpu().numpy().T
+    assert np.linalg.norm(E, 2) <= 1.1 * eps
+    A.close()
+    r, L, _ = gpu_loglik(ctx, xy, z, theta, "identity", nb, eps, maxrank=nb)
+    st = tlr.tlr_compress_stats(ctx)
+    assert st["qr_global"] > 0 and st["svd_global"] > 0, st
+    exact = oracle.loglik_dense(xy, z, theta)["loglik"]
+    assert abs(r["loglik"] - exact) <= 10 * eps * abs(exact), (r["loglik"], exact)
+    L.close()
