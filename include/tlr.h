@@ -76,6 +76,17 @@ extern "C" {
  * a margin. */
 #define TLR_PREC_AUTO 2
 #define TLR_AUTO_PIVOT2 3e-5
+/* Tensor: the mixed path with its dense off-diagonal products -- the panel
+ * update (with the Matern epilogue), the correction by the previous column,
+ * the compression's sampling and projection, V <- L^-1 V and the Gram
+ * matrices V'V -- on the tensor cores (tcgen05): each FP64 operand split into
+ * five BF16 slices with a power-of-two scale per row and 64-wide chunk of the
+ * inner dimension, slice products accumulated in FP32 in tensor memory and
+ * summed in float-float, about 40 significant bits per product (tlr_gemm_tc).
+ * The compression's QR runs in paired FP32; storage, the Matern evaluation,
+ * the SVD, the diagonal POTRF, the log-determinant and the solve stay FP64.
+ * Needs an sm_103a device (TLR_ERR_CUDA otherwise). */
+#define TLR_PREC_TENSOR 3
 
 typedef struct tlr_ctx tlr_ctx; /* device, workspace pool, last error, timers */
 typedef struct tlr_mat tlr_mat; /* a TLR matrix or TLR Cholesky factor on the device */
@@ -105,13 +116,16 @@ typedef struct {
     int64_t dense_bytes;  /* Table 1 "Dense": lower off-diagonal tiles * nb^2 * 8 */
     double flops;         /* floating-point operations counted from the rank map */
     float ms_total;       /* device time of the call (CUDA events on `stream`) */
-    int32_t precision_used; /* TLR_PREC_FP64 or TLR_PREC_MIXED: the path the result comes from */
+    int32_t precision_used; /* TLR_PREC_FP64, TLR_PREC_MIXED or TLR_PREC_TENSOR: the path the result comes from */
     double min_pivot2;    /* min_i L_ii^2 over the factor's diagonal (a conditional variance) */
 } tlr_result;
 
 /* ---- context -------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`.  *out receives the handle.
+ * Workspaces are taken from the device's default stream-ordered memory pool;
+ * the call sets that pool's release threshold to unlimited (for this
+ * process), so that freed workspace memory stays cached between tile columns.
  * Errors: TLR_ERR_ARG (out NULL), TLR_ERR_CUDA (no such device). */
 int tlr_ctx_create(int device, tlr_ctx **out);
 
@@ -186,6 +200,24 @@ int64_t tlr_tiles_size(int64_t n, int nb);
  * Errors: TLR_ERR_ARG (n <= 0, nb out of range, theta not positive). */
 int tlr_generate(tlr_ctx *ctx, const double *xy, int64_t n, int nb, tlr_theta theta,
                  double *tiles, void *stream);
+
+/* Product of the mixed-precision path on the tensor cores (tcgen05):
+ * C = alpha op(A) op(B) + beta C, op(X) = X or X' (trans_* != 0; not both),
+ * all matrices FP64 column major on the device, op(A) m x k, op(B) k x n.
+ * Every operand is split into `slices` BF16 slices with a power-of-two scale
+ * per row and 64-wide chunk of the inner dimension (error-free splitting of
+ * Ozaki, Ogita and Oishi 2012); slice products accumulate in FP32 in tensor
+ * memory, and are summed in float-float registers.  slices = 5: about 40
+ * significant bits relative to max |a| max |b| of each chunk (the product of
+ * the mixed path, TLR_PREC_TENSOR); slices = 1: the plain BF16 product with
+ * FP32 accumulation (8 bits).  A test and measurement hook of the kernel the
+ * likelihood uses; it allocates split copies of A and B (stream ordered) and
+ * returns after the product has finished (it syncs `stream`).
+ * Errors: TLR_ERR_ARG (sizes, leading dimensions, slices), TLR_ERR_CUDA (no
+ * sm_103a device), TLR_ERR_TIMEOUT (a pipeline wait gave up after 4 s). */
+int tlr_gemm_tc(tlr_ctx *ctx, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, double alpha,
+                const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                int64_t ldc, int slices, void *stream);
 
 /* Matern covariance for m distances (device in, device out); a probe of the
  * device K_nu used by tlr_generate.  Errors: TLR_ERR_ARG. */

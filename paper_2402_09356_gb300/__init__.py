@@ -22,6 +22,7 @@ TLR_ORDER_QUANTIZE = 1
 TLR_PREC_FP64 = 0
 TLR_PREC_MIXED = 1
 TLR_PREC_AUTO = 2
+TLR_PREC_TENSOR = 3
 TLR_AUTO_PIVOT2 = 3e-5
 
 
@@ -75,6 +76,10 @@ _SIGS = {
     "tlr_tiles_size": (ctypes.c_int64, [ctypes.c_int64, ctypes.c_int]),
     "tlr_generate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, tlr_theta,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_gemm_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                   ctypes.c_void_p]),
     "tlr_matern": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, tlr_theta, ctypes.c_void_p,
                                   ctypes.c_void_p]),
     "tlr_mat_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
@@ -329,6 +334,34 @@ def tlr_generate(ctx: Context, xy, nb: int, theta, tiles=None, stream=None):
         tiles = torch.empty(tlr_tiles_size(n, nb), dtype=torch.float64, device=xy.device)
     ctx.check(load_library().tlr_generate(ctx.h, _ptr(xy), n, int(nb), _theta(theta), _ptr(tiles), _stream(stream)))
     return tiles
+
+
+def tlr_gemm_tc(ctx: Context, A, B, C=None, alpha: float = 1.0, beta: float = 0.0, trans_a: bool = False,
+                trans_b: bool = False, slices: int = 5, stream=None):
+    """C = alpha op(A) op(B) + beta C on the tensor cores (BF16 slices).  A, B, C
+    are float64 CUDA tensors holding column-major matrices as their transposes
+    (a torch (cols, rows) row-major tensor is a column-major rows x cols matrix)."""
+    import torch
+    for name, t in (("A", A), ("B", B)):
+        _check_f64(name, t)
+        if t.dim() != 2 or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous 2-D tensor" % name)
+    # column-major view: rows = size(1), cols = size(0), ld = size(1)
+    ar, ac = A.shape[1], A.shape[0]
+    br, bc = B.shape[1], B.shape[0]
+    m, k = (ac, ar) if trans_a else (ar, ac)
+    kb, n = (bc, br) if trans_b else (br, bc)
+    if k != kb:
+        raise ValueError("inner dimensions differ: %d vs %d" % (k, kb))
+    if C is None:
+        C = torch.zeros((n, m), dtype=torch.float64, device=A.device)
+    _check_f64("C", C)
+    if tuple(C.shape) != (n, m) or not C.is_contiguous():
+        raise ValueError("C must be a contiguous (n, m) tensor")
+    ctx.check(load_library().tlr_gemm_tc(ctx.h, int(trans_a), int(trans_b), m, n, k, float(alpha), _ptr(A),
+                                         max(ar, 1), _ptr(B), max(br, 1), float(beta), _ptr(C), max(m, 1),
+                                         int(slices), _stream(stream)))
+    return C
 
 
 def tlr_matern(ctx: Context, d, theta, out=None, stream=None):

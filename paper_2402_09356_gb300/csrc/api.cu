@@ -9,6 +9,7 @@
 #include "common.cuh"
 #include "compress.cuh"
 #include "matern.cuh"
+#include "tcgemm.cuh"
 #include "tlr_internal.cuh"
 
 namespace tlr {
@@ -200,6 +201,14 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
             TLR_CUDA_TRY(cudaMalloc(&R.d, R.cap));
         }
         TLR_CUDA_TRY(cudaMalloc(&ctx->d_mtab, 2 * (size_t)kTabIntervals * kTabCoef * sizeof(double)));
+        // workspaces come from the device's default stream-ordered pool; keep
+        // what is freed cached there instead of returning it to the driver at
+        // every synchronisation (a factorisation syncs once per tile column,
+        // and re-mapping its per-column workspaces then costs milliseconds)
+        cudaMemPool_t mp = nullptr;
+        TLR_CUDA_TRY(cudaDeviceGetDefaultMemPool(&mp, device));
+        uint64_t keep = UINT64_MAX;
+        TLR_CUDA_TRY(cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep));
     });
     if (rc != TLR_OK) {
         tlr_ctx_destroy(ctx);
@@ -284,6 +293,29 @@ int tlr_generate(tlr_ctx *ctx, const double *xy, int64_t n, int nb, tlr_theta th
         MaternParams P = params_of(theta);
         build_matern_table(&P, ctx->d_mtab, (cudaStream_t)stream);
         generate_tiles(xy, n, nb, P, tiles, (cudaStream_t)stream);
+    });
+}
+
+int tlr_gemm_tc(tlr_ctx *ctx, int trans_a, int trans_b, int64_t m, int64_t n, int64_t k, double alpha,
+                const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                int slices, void *stream) {
+    return guarded(ctx, [&] {
+        check_arg(m >= 0 && n >= 0 && k >= 0 && m < (1 << 30) && n < (1 << 30) && k < (1 << 30), "m/n/k");
+        check_arg(!(trans_a && trans_b), "both operands transposed");
+        check_arg(slices == 1 || slices == kTcSlicesDefault, "slices");
+        if (m == 0 || n == 0) return;
+        check_arg(C && ldc >= m && ldc < (1LL << 31), "C/ldc");
+        if (k > 0) {
+            check_arg(A && B, "A/B");
+            check_arg(lda >= (trans_a ? k : m) && lda < (1LL << 31), "lda");
+            check_arg(ldb >= (trans_b ? n : k) && ldb < (1LL << 31), "ldb");
+        }
+        status_reset(ctx, (cudaStream_t)stream);
+        gemm_tc_single(ctx, (cudaStream_t)stream, trans_a != 0, trans_b != 0, (int)m, (int)n, (int)k, alpha, A,
+                       (int)lda, B, (int)ldb, beta, C, (int)ldc, slices);
+        long long info = -1;
+        const int sc = status_fetch(ctx, (cudaStream_t)stream, &info);  // syncs the stream
+        if (sc) throw make_error(sc, "tensor-core product: device status %d", sc);
     });
 }
 
@@ -472,9 +504,11 @@ int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *s
     });
 }
 
-// One evaluation on one precision path (df: paired-FP32 products).
+// One evaluation on one precision path (df: the mixed path's products in
+// paired FP32; tc: those products on the tensor cores).
 static void loglik_once(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
-                        const tlr_opts *opts, tlr_mat *L, tlr_result *out, cudaStream_t s, bool df) {
+                        const tlr_opts *opts, tlr_mat *L, tlr_result *out, cudaStream_t s, bool df,
+                        bool tc = false) {
     MaternParams P = params_of(theta);
     std::memset(out, 0, sizeof *out);
     out->info = -1;
@@ -485,10 +519,10 @@ static void loglik_once(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     long long inf = -1;
     DevBuf acc(3 * sizeof(double), s), y((size_t)n * sizeof(double), s);
     TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, 3 * sizeof(double), s));
-    out->precision_used = df ? TLR_PREC_MIXED : TLR_PREC_FP64;
+    out->precision_used = tc ? TLR_PREC_TENSOR : (df ? TLR_PREC_MIXED : TLR_PREC_FP64);
     try {
         factor(ctx, s, L, FactorMode::Matern, xy, &P, opts->eps * theta.sigma2, &st, &inf, z,
-               y.as<double>(), acc.as<double>(), df);
+               y.as<double>(), acc.as<double>(), df, tc);
     } catch (const Error &) {
         out->info = inf;
         throw;
@@ -542,9 +576,12 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     check_arg(n > 0 && L->n == n && L->nb == opts->nb, "L does not match n/nb");
     check_arg(opts->eps >= 0 && std::isfinite(opts->eps), "eps");
     check_arg(opts->precision == TLR_PREC_FP64 || opts->precision == TLR_PREC_MIXED ||
-                  opts->precision == TLR_PREC_AUTO, "precision");
+                  opts->precision == TLR_PREC_AUTO || opts->precision == TLR_PREC_TENSOR, "precision");
+    if (opts->precision == TLR_PREC_TENSOR && !tc_available())
+        throw make_error(TLR_ERR_CUDA, "TLR_PREC_TENSOR needs an sm_103a device");
     if (opts->precision != TLR_PREC_AUTO) {
-        loglik_once(ctx, xy, z, n, theta, opts, L, out, s, opts->precision == TLR_PREC_MIXED);
+        loglik_once(ctx, xy, z, n, theta, opts, L, out, s, opts->precision != TLR_PREC_FP64,
+                    opts->precision == TLR_PREC_TENSOR);
         L->last_pivot2 = out->min_pivot2 / theta.sigma2;
         return;
     }

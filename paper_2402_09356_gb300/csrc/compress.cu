@@ -42,6 +42,7 @@
 #include "common.cuh"
 #include "compress.cuh"
 #include "gemm.cuh"
+#include "tcgemm.cuh"
 
 namespace tlr {
 
@@ -1289,7 +1290,8 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
 
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df,
-                    const std::function<void()> &overlap, const GrowSlot &grow) {
+                    const std::function<void()> &overlap, const GrowSlot &grow, bool tc) {
+    const bool dfp = df && !tc;  // paired-FP32 operand copies for the products
     bool overlapped = false;
     ensure_omega(ctx, st);
     // profiling marks between the sub-steps of each adaptive round
@@ -1354,7 +1356,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             oW[u] = take((int64_t)s * s);
             oK[u] = take((int64_t)s * s);
             oS[u] = take(s);
-            oQ2[u] = df ? take((int64_t)J.m * s) : 0;  // float2, one double each
+            oQ2[u] = dfp ? take((int64_t)J.m * s) : 0;  // float2, one double each
             oX2[u] = take((int64_t)s * s);
             oG[u] = take((int64_t)s * s);
             oIA[u] = take((int64_t)s * s);
@@ -1375,7 +1377,8 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             a.A2 = J.T2; a.B2 = ctx->d_omega2;
             g1.push_back(a);
         }
-        gemm_batched(ctx, st, false, false, g1, 1.0, 0.0, df);
+        if (tc) gemm_tc(ctx, st, false, false, g1, 1.0, 0.0);
+        else gemm_batched(ctx, st, false, false, g1, 1.0, 0.0, df);
         cmark();
         // 2. Q = orth(Y)
         std::vector<QrJob> q1(np);
@@ -1386,7 +1389,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             scratch[u] = W + oC[u];
         }
         qr_launch(ctx, st, q1, scratch, df);
-        if (df) {
+        if (dfp) {
             std::vector<SplitDesc> sd(np);
             for (size_t u = 0; u < np; ++u)
                 sd[u] = SplitDesc{W + oQ[u], (float2 *)(W + oQ2[u]), jobs[pending[u]].m, jobs[pending[u]].m, ps[u]};
@@ -1404,7 +1407,8 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             a.A2 = J.T2; a.B2 = (const float2 *)(W + oQ2[u]);
             g2.push_back(a);
         }
-        gemm_batched(ctx, st, true, false, g2, 1.0, 0.0, df);
+        if (tc) gemm_tc(ctx, st, true, false, g2, 1.0, 0.0);
+        else gemm_batched(ctx, st, true, false, g2, 1.0, 0.0, df);
         cmark();
         std::vector<QrJob> q2(np);
         for (size_t u = 0; u < np; ++u) {

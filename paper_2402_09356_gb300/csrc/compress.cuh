@@ -40,13 +40,15 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s);
 // *bad_tile (its tile_id), a tile holding non-finite values in *nan_tile;
 // both are -1 otherwise.
 // With df, the sampling and projection products run in paired-FP32
-// arithmetic (every job must then carry T2).  `overlap`, if set, is called
+// arithmetic (every job must then carry T2), and the QR in paired FP32; with
+// tc as well, the two products run on the tensor cores (BF16 slices, from
+// the FP64 tiles; T2 unused).  `overlap`, if set, is called
 // once, after the first round's work is enqueued and before the host waits
 // for it (the caller enqueues independent work on other streams there).
 // Syncs `s` once per adaptive round.
 void compress_tiles(tlr_ctx *ctx, cudaStream_t s, std::vector<CompressJob> &jobs, double tau,
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile,
                     bool df = false, const std::function<void()> &overlap = nullptr,
-                    const GrowSlot &grow = nullptr);
+                    const GrowSlot &grow = nullptr, bool tc = false);
 
 }  // namespace tlr

@@ -120,6 +120,25 @@ __global__ void k_generate_tiles(const double *__restrict__ xy, int64_t n, int n
     (void)nt;
 }
 
+// A column panel of the covariance: T[c * ld + r] = C(s_{ri0 + r}, s_{ci0 + c})
+// for r < rows, c < cols; rows or columns past n give 0.  Each block fills a
+// 32-row x 32-column sub-block, threads down the columns (coalesced stores).
+__global__ void k_generate_panel(const double *__restrict__ xy, int64_t n, int64_t ri0, int64_t ci0, int rows,
+                                 int cols, MaternParams P, double *__restrict__ T, int ld) {
+    const int r = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int c0 = blockIdx.y * 32 + (threadIdx.x >> 5) * 4;
+    if (r >= rows) return;
+    const int64_t gr = ri0 + r;
+    const bool rv = gr < n;
+    const double xr = rv ? xy[gr] : 0.0, yr = rv ? xy[n + gr] : 0.0;
+    for (int q = 0; q < 4; ++q) {
+        const int c = c0 + q;
+        if (c >= cols) break;
+        const int64_t gc = ci0 + c;
+        T[(int64_t)c * ld + r] = (rv && gc < n) ? matern_cov(xr, yr, xy[gc], xy[n + gc], P) : 0.0;
+    }
+}
+
 __global__ void k_matern_vec(const double *__restrict__ d, int64_t m, MaternParams P,
                              double *__restrict__ out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,6 +199,14 @@ void generate_tiles(const double *xy, int64_t n, int nb, const MaternParams &P, 
     int64_t ntiles = (int64_t)nt * (nt + 1) / 2;
     int sub = (int)ceil_div(nb, 32);
     launch(k_generate_tiles, (unsigned)(ntiles * sub * sub), 256, 0, s, xy, n, nb, nt, P, tiles);
+    TLR_CHECK_LAUNCH();
+}
+
+void generate_panel(const double *xy, int64_t n, int64_t ri0, int64_t ci0, int rows, int cols,
+                    const MaternParams &P, double *T, int ld, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    launch(k_generate_panel, dim3((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(cols, 32)), 256, 0, s, xy, n, ri0,
+           ci0, rows, cols, P, T, ld);
     TLR_CHECK_LAUNCH();
 }
 

@@ -312,7 +312,7 @@ int wait_locked(tlr_pool *p, std::unique_lock<std::mutex> &lk, int64_t ticket, t
 
 bool args_ok(double eps, int prec) {
     return eps >= 0 && std::isfinite(eps) &&
-           (prec == TLR_PREC_FP64 || prec == TLR_PREC_MIXED || prec == TLR_PREC_AUTO);
+           (prec == TLR_PREC_FP64 || prec == TLR_PREC_MIXED || prec == TLR_PREC_AUTO || prec == TLR_PREC_TENSOR);
 }
 
 }  // namespace

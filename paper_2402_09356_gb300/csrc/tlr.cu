@@ -23,6 +23,7 @@
 #include "dense.cuh"
 #include "gemm.cuh"
 #include "matern.cuh"
+#include "tcgemm.cuh"
 #include "tlr_internal.cuh"
 
 namespace tlr {
@@ -102,8 +103,18 @@ void upload_ranks(tlr_mat *M, cudaStream_t s) {
 
 void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const double *xy,
             const MaternParams *P, double tau, FactorStats *stats, long long *info, const double *z,
-            double *y, double *acc, bool df) {
+            double *y, double *acc, bool df, bool tc) {
     if (df && mode != FactorMode::Matern) throw make_error(TLR_ERR_ARG, "paired-FP32 products need the Matern mode");
+    if (tc && !df) throw make_error(TLR_ERR_ARG, "tensor-core products belong to the mixed path");
+    // tc: the panel update (the large product, on the look-ahead stream) runs
+    // on the tensor cores (tcgemm.cuh) from the FP64 operands.  The small
+    // products on the critical path (correction, sampling, projection,
+    // V <- L^-1 V, Gram) can run there too (tcc), but measured slower at
+    // n = 40,000 than paired FP32: their 128 x 32 tiles keep the tensor pipe
+    // below a third of its rate and the operand splits add a launch each on
+    // the critical path; they stay paired FP32.
+    const bool tcp = tc, tcc = false;
+    const bool dfp = df && !tcc;  // paired-FP32 copies for the critical-path products
     const int nt = M->nt, nb = M->nb;
     const int64_t n = M->n;
     *info = -1;
@@ -141,7 +152,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
     if (ahead) panel_buf[1].alloc((size_t)nt * nb * nb * sizeof(double), st);
     int cur = 0;
     // paired-FP32 copy of the panel (mixed precision): operand of the compression products
-    DevBuf panel2(df ? (size_t)nt * nb * nb * sizeof(float2) : 0, st);
+    DevBuf panel2(dfp ? (size_t)nt * nb * nb * sizeof(float2) : 0, st);
     float2 *Tp2 = panel2.as<float2>();
     DevBuf xinv((size_t)nb * nb * sizeof(double), st);
     double *Xinv = xinv.as<double>();
@@ -244,19 +255,31 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
         g.B = Qc; g.ldb = nb; g.n = mc;
         g.C = T; g.ldc = (int)Mp;
         g.ri0 = (int64_t)c * nb; g.ci0 = (int64_t)c * nb;
-        DevBuf p2(df && Rc > 0 ? (size_t)Mp * Rc * sizeof(float2) : 0, s);
-        DevBuf q2(df && Rc > 0 ? (size_t)nb * Rc * sizeof(float2) : 0, s);
-        if (df && Rc > 0) {
+        DevBuf p2(df && !tcp && Rc > 0 ? (size_t)Mp * Rc * sizeof(float2) : 0, s);
+        DevBuf q2(df && !tcp && Rc > 0 ? (size_t)nb * Rc * sizeof(float2) : 0, s);
+        if (df && !tcp && Rc > 0) {
             g.A2 = p2.as<float2>();
             g.B2 = q2.as<float2>();
             split_f2_batched(ctx, s, {SplitDesc{Pc, p2.as<float2>(), (int)Mp, (int)Mp, Rc},
                                       SplitDesc{Qc, q2.as<float2>(), nb, mc, Rc}});
         }
         dmark(dm, s, det_build);
-        if (generate) {
+        if (generate && tcp) {
+            // the covariance panel by a plain FP64 kernel, then T -= P Q' on the
+            // tensor cores: their CTAs stay short (the FP64 Matern evaluation
+            // would keep a tensor-core CTA, its tensor memory and its shared
+            // memory, on an SM ~100 us per tile)
+            generate_panel(xy, n, g.ri0, g.ci0, (int)Mp, mc, *P, T, (int)Mp, s);
+            if (Rc > 0)
+                gemm_tc(ctx, s, false, true, std::vector<GemmProb>{g}, -1.0, 1.0, kTcSlicesDefault, ctas_per_sm > 0);
+            stats->matern_entries += (double)rows_valid * mc;
+            stats->panel_launches += 1;
+        } else if (generate) {
             gemm_batched_matern(ctx, s, true, std::vector<GemmProb>{g}, -1.0, xy, n, *P, df, 0, ctas_per_sm);
             stats->matern_entries += (double)rows_valid * mc;
             stats->panel_launches += 1;
+        } else if (Rc > 0 && tcp) {
+            gemm_tc(ctx, s, false, true, std::vector<GemmProb>{g}, -1.0, 1.0);
         } else if (Rc > 0) {
             gemm_batched(ctx, s, false, true, std::vector<GemmProb>{g}, -1.0, 1.0, df);
         }
@@ -303,9 +326,9 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             stats->gemm_flops += 2.0 * b.m * rik * mc;
         }
         gemm_batched(ctx, s, false, true, gz, 1.0, 0.0);
-        DevBuf u2(df ? (size_t)ztot * nb * sizeof(float2) : 0, s);
-        DevBuf z2(df ? (size_t)ztot * nb * sizeof(float2) : 0, s);
-        if (df) {
+        DevBuf u2(dfp ? (size_t)ztot * nb * sizeof(float2) : 0, s);
+        DevBuf z2(dfp ? (size_t)ztot * nb * sizeof(float2) : 0, s);
+        if (dfp) {
             std::vector<SplitDesc> sd;
             for (GemmProb &b : gu) {
                 const int64_t o = b.B - zb.as<double>();
@@ -316,7 +339,8 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             }
             split_f2_batched(ctx, s, sd);
         }
-        gemm_batched(ctx, s, false, false, gu, -1.0, 1.0, df);
+        if (tcc) gemm_tc(ctx, s, false, false, gu, -1.0, 1.0);
+        else gemm_batched(ctx, s, false, false, gu, -1.0, 1.0, df);
     };
 
     // y_c -= sum_{k<c} U_ck c_k, c_k = V_ck' y_k: a slice of column k's V_k' y_k
@@ -380,7 +404,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             dmark(dm_main, st, kDetSolveUpd);
         }
         mark();
-        if (df && j + 1 < nt) {
+        if (dfp && j + 1 < nt) {
             split_f2_batched(ctx, st, {SplitDesc{Tp + nb, Tp2 + nb, (int)Mp, (int)(Mp - nb), mj}});
             dmark(dm_main, st, kDetSplit);
         }
@@ -423,7 +447,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             CompressJob c{};
             c.T = Tp + (int64_t)(i - j) * nb;
             c.ldt = (int)Mp;
-            c.T2 = df ? Tp2 + (int64_t)(i - j) * nb : nullptr;
+            c.T2 = dfp ? Tp2 + (int64_t)(i - j) * nb : nullptr;
             c.m = tile_rows(n, nb, i);
             c.k = mj;
             c.U = Uslot(M, i, j);
@@ -442,7 +466,7 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
             // on the high-priority stream, ahead of the look-ahead GEMM
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_fork, st));
             TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->hp, ctx->ev_hp_fork, 0));
-            compress_tiles(ctx, ctx->hp, jobs, tau, M->maxrank, rk, &bad, &nan, df, nullptr, grow);
+            compress_tiles(ctx, ctx->hp, jobs, tau, M->maxrank, rk, &bad, &nan, df, nullptr, grow, tcc);
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_join, ctx->hp));
             TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_hp_join, 0));
         }
@@ -494,9 +518,9 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 off_c += r;
                 stats->flops += 2.0 * mj * mj * r;
             }
-            DevBuf x2(df && !gt.empty() ? (size_t)nb * nb * sizeof(float2) : 0, st);
-            DevBuf v2(df && !gt.empty() ? (size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(float2) : 0, st);
-            if (df && !gt.empty()) {
+            DevBuf x2(dfp && !gt.empty() ? (size_t)nb * nb * sizeof(float2) : 0, st);
+            DevBuf v2(dfp && !gt.empty() ? (size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(float2) : 0, st);
+            if (dfp && !gt.empty()) {
                 // paired-FP32 operands: X, and the V factors packed like the output
                 std::vector<SplitDesc> sd{SplitDesc{Xinv, x2.as<float2>(), nb, mj, mj}};
                 for (GemmProb &g : gt) {
@@ -507,7 +531,8 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 }
                 split_f2_batched(ctx, st, sd);
             }
-            gemm_batched(ctx, st, false, false, gt, 1.0, 0.0, df);
+            if (tcc) gemm_tc(ctx, st, false, false, gt, 1.0, 0.0);
+            else gemm_batched(ctx, st, false, false, gt, 1.0, 0.0, df);
             copy_batched(ctx, st, cb);
             dmark(dm_main, st, kDetTrsm);
             // G_j = V_j' V_j for the later columns' updates
@@ -519,12 +544,13 @@ void factor(tlr_ctx *ctx, cudaStream_t st, tlr_mat *M, FactorMode mode, const do
                 g.A = vtmp.as<double>(); g.lda = nb; g.m = S; g.k = mj;
                 g.B = vtmp.as<double>(); g.ldb = nb; g.n = S;
                 g.C = gram[j].as<double>(); g.ldc = S;
-                DevBuf v2(df ? (size_t)nb * S * sizeof(float2) : 0, st);
-                if (df) {
+                DevBuf v2(dfp ? (size_t)nb * S * sizeof(float2) : 0, st);
+                if (dfp) {
                     split_f2_batched(ctx, st, {SplitDesc{vtmp.as<double>(), v2.as<float2>(), nb, mj, S}});
                     g.A2 = g.B2 = v2.as<float2>();
                 }
-                gemm_batched(ctx, st, true, false, std::vector<GemmProb>{g}, 1.0, 0.0, df);
+                if (tcc) gemm_tc(ctx, st, true, false, std::vector<GemmProb>{g}, 1.0, 0.0);
+                else gemm_batched(ctx, st, true, false, std::vector<GemmProb>{g}, 1.0, 0.0, df);
                 stats->flops += 2.0 * S * S * mj;
                 dmark(dm_main, st, kDetGram);
             }

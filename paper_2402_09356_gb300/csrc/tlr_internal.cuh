@@ -65,10 +65,14 @@ void upload_ranks(tlr_mat *M, cudaStream_t s);
 // in: y = L^-1 z (z, y device, ordered; may alias), acc[0] += sum log L_ii,
 // acc[1] += |y|^2, acc[2] = max(acc[2], max_i 1 / L_ii^2).  With df (Matern mode only), the panel update and the
 // compression's sampling and projection products run in paired-FP32
-// arithmetic; everything else stays FP64.
+// arithmetic; everything else stays FP64.  With tc as well, those products,
+// the correction by the previous column, V <- L^-1 V and the Gram matrices
+// run on the tensor cores (BF16 slices, tcgemm.cuh); the compression's QR
+// stays paired FP32.
 void factor(tlr_ctx *ctx, cudaStream_t s, tlr_mat *M, FactorMode mode, const double *xy,
             const MaternParams *P, double tau, FactorStats *stats, long long *info,
-            const double *z = nullptr, double *y = nullptr, double *acc = nullptr, bool df = false);
+            const double *z = nullptr, double *y = nullptr, double *acc = nullptr, bool df = false,
+            bool tc = false);
 void forward_solve(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *z, double *y,
                    double *acc);
 void lmul(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *w, double *z);
@@ -87,6 +91,9 @@ void gather(const int64_t *perm, const double *src, int64_t n, double *dst, cuda
 // covariance (matern.cu)
 void generate_tiles(const double *xy, int64_t n, int nb, const MaternParams &P, double *tiles, cudaStream_t s);
 void matern_vec(const double *d, int64_t m, const MaternParams &P, double *out, cudaStream_t s);
+// T[c * ld + r] = C(s_{ri0 + r}, s_{ci0 + c}) for r < rows, c < cols (0 past n).
+void generate_panel(const double *xy, int64_t n, int64_t ri0, int64_t ci0, int rows, int cols,
+                    const MaternParams &P, double *T, int ld, cudaStream_t s);
 
 // Bounds of a maximum-likelihood search: positive, finite, lo <= hi.
 bool mle_bounds_ok(tlr_theta lo, tlr_theta hi);

@@ -121,10 +121,13 @@ def test_fullsize_ordering_invariance_and_mixed(ctx, golden_dir):
     L6.close()
     Lm, rm, _ = factor(ctx, "morton", tlr.TLR_PREC_FP64, z=z)
     Lm.close()
+    Lt, rt, _ = factor(ctx, "hilbert", tlr.TLR_PREC_TENSOR, z=z)
+    Lt.close()
     Lx, rx, xyo = factor(ctx, "hilbert", tlr.TLR_PREC_MIXED, z=z)
     ref = abs(r64["loglik"])
     assert abs(rm["loglik"] - r64["loglik"]) <= 20 * EPS * ref, (rm["loglik"], r64["loglik"])
     assert abs(rx["loglik"] - r64["loglik"]) <= 1e-6 * ref, (rx["loglik"], r64["loglik"])
+    assert abs(rt["loglik"] - r64["loglik"]) <= 1e-6 * ref, (rt["loglik"], r64["loglik"])
     # the mixed factor meets the same tile bound
     tiles = Tiles(Lx)
     for i, j in SAMPLED[1:4]:
@@ -134,7 +137,7 @@ def test_fullsize_ordering_invariance_and_mixed(ctx, golden_dir):
 
 
 @pytest.mark.parametrize("eps", [1e-7, 1e-9])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "tensor"])
 def test_fullsize_loglik_terms_against_exact_oracle(ctx, golden_dir, eps, precision):
     """Eq. 1.2 term by term at full size: l, log|Sigma| and Z' Sigma^-1 Z each
     within 10 eps of its own magnitude from the dense oracle's exact values."""
@@ -143,7 +146,7 @@ def test_fullsize_loglik_terms_against_exact_oracle(ctx, golden_dir, eps, precis
     assert gold["n"] == N and tuple(gold["theta"]) == THETA and gold["loc_seed"] == 1 and gold["z_seed"] == 2
     z = golden_z(golden_dir)
     assert z.shape == (N,)
-    prec = tlr.TLR_PREC_FP64 if precision == "fp64" else tlr.TLR_PREC_MIXED
+    prec = {"fp64": tlr.TLR_PREC_FP64, "mixed": tlr.TLR_PREC_MIXED, "tensor": tlr.TLR_PREC_TENSOR}[precision]
     L, r, _ = factor(ctx, "hilbert", prec, eps=eps, z=z)
     L.close()
     for term in ("loglik", "logdet", "quad"):

@@ -1,7 +1,9 @@
-"""Mixed precision (TLR_PREC_MIXED): the off-diagonal dense products in
-paired-FP32 arithmetic, everything else FP64.
+"""Mixed precision: the off-diagonal dense products in paired-FP32 arithmetic
+(TLR_PREC_MIXED) or as BF16-slice products on the tensor cores
+(TLR_PREC_TENSOR), everything else FP64.
 
-The products carry about 46 significant bits, so the factor differs from the
+The products carry about 46 (paired FP32) or 40 (five BF16 slices)
+significant bits, so the factor differs from the
 FP64 path only by rounding far below the compression threshold: the mixed
 likelihood must stay within the FP64 path's own bound against the exact dense
 oracle (10 eps |l|), within 1e-6 |l| of the FP64 path, and the rank maps of
@@ -38,13 +40,18 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("path", ["mixed", "tensor"])
 @pytest.mark.parametrize("n,nb,order,theta,eps,maxrank", CASES)
-def test_mixed_matches_fp64_and_oracle(ctx, n, nb, order, theta, eps, maxrank):
+def test_mixed_matches_fp64_and_oracle(ctx, n, nb, order, theta, eps, maxrank, path):
+    """Both mixed paths: paired-FP32 products (TLR_PREC_MIXED) and BF16-slice
+    products on the tensor cores (TLR_PREC_TENSOR)."""
     import paper_2402_09356_gb300 as tlr
+    prec = tlr.TLR_PREC_MIXED if path == "mixed" else tlr.TLR_PREC_TENSOR
     xy = synth.jittered_grid(n, seed=n)
     z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=n + 1))
     r64, rk64, perm = run(ctx, xy, z, theta, order, nb, eps, maxrank, tlr.TLR_PREC_FP64)
-    rmx, rkmx, _ = run(ctx, xy, z, theta, order, nb, eps, maxrank, tlr.TLR_PREC_MIXED)
+    rmx, rkmx, _ = run(ctx, xy, z, theta, order, nb, eps, maxrank, prec)
+    assert rmx["precision_used"] == prec
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
     assert abs(rmx["loglik"] - ref) <= 10 * eps * abs(ref), (rmx["loglik"], ref)
     assert abs(rmx["loglik"] - r64["loglik"]) <= 1e-6 * abs(r64["loglik"])
@@ -52,23 +59,28 @@ def test_mixed_matches_fp64_and_oracle(ctx, n, nb, order, theta, eps, maxrank):
     assert d.max() <= 1 and (d > 0).mean() <= 0.05, (d.max(), (d > 0).mean())
 
 
-def test_mixed_eps_to_zero_is_dense(ctx):
+@pytest.mark.parametrize("path", ["mixed", "tensor"])
+def test_mixed_eps_to_zero_is_dense(ctx, path):
     import paper_2402_09356_gb300 as tlr
+    prec = tlr.TLR_PREC_MIXED if path == "mixed" else tlr.TLR_PREC_TENSOR
     n, nb, theta = 1600, 200, (1.0, 0.1, 0.5)
     xy = synth.jittered_grid(n)
     z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=2))
-    r, _, perm = run(ctx, xy, z, theta, "morton", nb, 0.0, nb, tlr.TLR_PREC_MIXED)
+    r, _, perm = run(ctx, xy, z, theta, "morton", nb, 0.0, nb, prec)
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
-    assert abs(r["loglik"] - ref) <= 1e-10 * abs(ref)
+    # tensor: ~40-bit products, amplified by the conditioning of Sigma
+    assert abs(r["loglik"] - ref) <= (1e-10 if path == "mixed" else 1e-8) * abs(ref)
 
 
+@pytest.mark.parametrize("path", ["mixed", "tensor"])
 @pytest.mark.parametrize("n,nb", [(1, 16), (17, 16), (1000, 96)])
-def test_mixed_ragged_and_tiny(ctx, n, nb):
+def test_mixed_ragged_and_tiny(ctx, n, nb, path):
     import paper_2402_09356_gb300 as tlr
+    prec = tlr.TLR_PREC_MIXED if path == "mixed" else tlr.TLR_PREC_TENSOR
     theta, eps = (1.2, 0.08, 0.8), 1e-9
     xy = synth.jittered_grid(n, seed=n)
     z = oracle.simulate_z(xy, theta, synth.standard_normal(n, seed=n + 1))
-    r, _, perm = run(ctx, xy, z, theta, "hilbert", nb, eps, nb, tlr.TLR_PREC_MIXED)
+    r, _, perm = run(ctx, xy, z, theta, "hilbert", nb, eps, nb, prec)
     ref = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], theta)["loglik"]
     assert abs(r["loglik"] - ref) <= 10 * eps * abs(ref) + 1e-12
 
