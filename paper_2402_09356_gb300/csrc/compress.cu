@@ -52,6 +52,9 @@ constexpr int kOversample = 24;  // samples beyond the expected rank
 constexpr int kSpare = 20;       // fewer spare samples than this: redo with more
 constexpr int kQrThreads = 256;
 constexpr int kNw = kQrThreads / 32;
+// Threads of the shared-memory QR (512 measured slower at n = 40,000: the
+// step's barrier and exchange latency, not its dependent chains, bound it).
+constexpr int kQrSmThreads = 256;
 constexpr int kMaxSweeps = 40;
 
 template <class T>
@@ -103,15 +106,17 @@ struct QrJob {
 // interleaved groups over the spare warps (their partial dot products are
 // summed through shared memory).  Thread t handles row group t / width and
 // columns first + t % width + k * width.
+template <int kThreads>
 struct PanelSplit {
     int G, width;
     __device__ __forceinline__ explicit PanelSplit(int ncols) {
+        constexpr int kWarps = kThreads / 32;
         const int cw = (ncols + 31) / 32;
-        if (cw >= kNw || cw == 0) {
+        if (cw >= kWarps || cw == 0) {
             G = 1;
-            width = kQrThreads;
+            width = kThreads;
         } else {
-            G = kNw / cw;
+            G = kWarps / cw;
             width = 32 * cw;
         }
     }
@@ -177,12 +182,12 @@ struct QrArith<true> {
 };
 
 // Dot products d_cc = sum over local rows i >= lb of v[i] A(i, cc) for the
-// columns cc in [first, s), written to out[cc].  red: kQrThreads doubles.
-template <class Ar, class T>
+// columns cc in [first, s), written to out[cc].  red: kThreads doubles.
+template <int kThreads, class Ar, class T>
 __device__ __forceinline__ void panel_dots(const T *As, int ld, const T *v, int first, int s, int lb, int nr,
                                            double *red, double *out) {
     const int tid = threadIdx.x;
-    const PanelSplit ps(s - first);
+    const PanelSplit<kThreads> ps(s - first);
     const int g = tid / ps.width;
     if (ps.G == 1) {
         for (int cc = first + tid; cc < s; cc += ps.width) {
@@ -210,11 +215,11 @@ __device__ __forceinline__ void panel_dots(const T *As, int ld, const T *v, int 
 
 // A(i, cc) -= w[cc] v(i) for local rows i >= lb and columns cc in [first, s),
 // where v(i) = v[i] except v(ic) = vhead when ic is a local row.
-template <class Ar, class T>
+template <int kThreads, class Ar, class T>
 __device__ __forceinline__ void panel_update(T *As, int ld, const T *v, int ic, T vhead, const double *w, int first,
                                              int s, int lb, int nr) {
     const int tid = threadIdx.x;
-    const PanelSplit ps(s - first);
+    const PanelSplit<kThreads> ps(s - first);
     if (tid >= ps.G * ps.width) return;
     const int g = tid / ps.width;
     for (int cc = first + tid % ps.width; cc < s; cc += ps.width) {
@@ -236,9 +241,9 @@ __device__ __forceinline__ void panel_update(T *As, int ld, const T *v, int ic, 
 // Q = H_0 ... H_{s-1} [I; 0] is then accumulated backwards in place: before
 // H_c is applied, columns > c already hold their final values below row c,
 // and column c becomes H_c e_c (LAPACK's dorg2r ordering).
-// Shared memory: s * ld + 8 s + kQrThreads doubles.
+// Shared memory: s * ld + 8 s + kQrSmThreads doubles.
 template <int kCl, bool kDf>
-__global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict__ jobs) {
     using Ar = QrArith<kDf>;
     using T = typename Ar::T;
     static_assert(sizeof(T) == sizeof(double), "the panel element takes the bytes of one double");
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
     T *As = reinterpret_cast<T *>(sm);
     double *taus = sm + (size_t)s * ld, *betas = taus + s, *heads = betas + s;
     double *pd = heads + s, *prow = pd + 2 * s, *wv = prow + 2 * s, *red = wv + s;
-    for (int e = tid; e < nr * s; e += kQrThreads) {
+    for (int e = tid; e < nr * s; e += kQrSmThreads) {
         const int i = e % nr, j = e / nr;
         As[j * ld + i] = Ar::from(J.A[(int64_t)j * J.lda + r0 + i]);
     }
@@ -261,10 +266,10 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         double *pdc = pd + (c & 1) * s, *prc = prow + (c & 1) * s;
         const int lb = max(c - r0, 0), ic = c - r0;
         T *vc = As + c * ld;
-        panel_dots<Ar>(As, ld, vc, c, s, lb, nr, red, pdc);
+        panel_dots<kQrSmThreads, Ar>(As, ld, vc, c, s, lb, nr, red, pdc);
         const int owner = c / per;
         if (rank == owner)
-            for (int cc = c + tid; cc < s; cc += kQrThreads) prc[cc] = Ar::to(As[cc * ld + ic]);
+            for (int cc = c + tid; cc < s; cc += kQrSmThreads) prc[cc] = Ar::to(As[cc * ld + ic]);
         cl.sync();
         const double *orow = cl.map_shared_rank(prc, owner);
         double nrm2 = 0.0;
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         const double alpha = orow[c];
         double tau, beta, v0;
         householder(nrm2, alpha, tau, beta, v0);
-        for (int cc = c + 1 + tid; cc < s; cc += kQrThreads) {
+        for (int cc = c + 1 + tid; cc < s; cc += kQrSmThreads) {
             double d = 0.0;
 #pragma unroll
             for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pdc, k)[cc];
@@ -285,14 +290,14 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
             heads[c] = v0;
         }
         __syncthreads();
-        if (tau != 0.0) panel_update<Ar>(As, ld, vc, ic, Ar::from(v0), wv, c + 1, s, lb, nr);
+        if (tau != 0.0) panel_update<kQrSmThreads, Ar>(As, ld, vc, ic, Ar::from(v0), wv, c + 1, s, lb, nr);
         __syncthreads();
         if (tau != 0.0 && rank == owner && tid == 0) vc[ic] = Ar::from(v0);  // reflector head stored in place
     }
     cl.sync();  // every CTA is done reading the factorisation's partials
     if (J.Rt) {  // Rt(i, u) = R(u, i) for the own rows u < s
         const int nu = max(0, min(nr, s - r0));
-        for (int e = tid; e < nu * s; e += kQrThreads) {
+        for (int e = tid; e < nu * s; e += kQrSmThreads) {
             const int lu = e / s, i = e % s, u = r0 + lu;
             double v = 0.0;
             if (i > u) v = Ar::to(As[i * ld + lu]);
@@ -310,21 +315,21 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         if (tau != 0.0) {  // identical on every CTA of the cluster
             double *pdc = pd + (act & 1) * s;
             ++act;
-            panel_dots<Ar>(As, ld, vc, c + 1, s, lb, nr, red, pdc);
+            panel_dots<kQrSmThreads, Ar>(As, ld, vc, c + 1, s, lb, nr, red, pdc);
             cl.sync();
-            for (int cc = c + 1 + tid; cc < s; cc += kQrThreads) {
+            for (int cc = c + 1 + tid; cc < s; cc += kQrSmThreads) {
                 double d = 0.0;
 #pragma unroll
                 for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pdc, k)[cc];
                 wv[cc] = tau * d;
             }
             __syncthreads();
-            panel_update<Ar>(As, ld, vc, -1, Ar::from(0.0), wv, c + 1, s, lb, nr);
+            panel_update<kQrSmThreads, Ar>(As, ld, vc, -1, Ar::from(0.0), wv, c + 1, s, lb, nr);
             __syncthreads();
         }
         // column c of Q = H_c e_c
         const typename Ar::W tv = Ar::prep(tau * v0);
-        for (int i = tid; i < nr; i += kQrThreads) {
+        for (int i = tid; i < nr; i += kQrSmThreads) {
             T q;
             if (i < ic) q = Ar::from(0.0);
             else if (i == ic) q = Ar::from(1.0 - tau * v0 * v0);
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
         }
         __syncthreads();
     }
-    for (int e = tid; e < nr * s; e += kQrThreads) {
+    for (int e = tid; e < nr * s; e += kQrSmThreads) {
         const int i = e % nr, j = e / nr;
         J.Q[(int64_t)j * J.ldq + r0 + i] = Ar::to(As[j * ld + i]);
     }
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_sm(const QrJob *__restrict__ 
 
 static size_t qr_sm_bytes(int m, int s, int csize) {
     const int per = (m + csize - 1) / csize, ld = per | 1;
-    return ((size_t)s * ld + 8 * (size_t)s + kQrThreads) * sizeof(double);
+    return ((size_t)s * ld + 8 * (size_t)s + kQrSmThreads) * sizeof(double);
 }
 
 // QR in global memory (A factorised in place; Q and Rt as above), for panels
@@ -1022,10 +1027,11 @@ static size_t jacobi_gm_bytes(int s, int csize) {
 // Launch helpers.
 
 template <class K, class... Args>
-static void launch_cluster(K kernel, int csize, int nclusters, size_t smem, cudaStream_t st, Args... args) {
+static void launch_cluster(K kernel, int csize, int nclusters, int threads, size_t smem, cudaStream_t st,
+                           Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(nclusters * csize));
-    cfg.blockDim = dim3(kQrThreads);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1084,7 +1090,9 @@ static bool cluster16_ok() {
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int n1 = 0, n2 = 0;
-            if (cudaOccupancyMaxActiveClusters(&n1, k_qr_sm<16, false>, &cfg) == cudaSuccess &&
+            cudaLaunchConfig_t cfq = cfg;
+            cfq.blockDim = dim3(kQrSmThreads);
+            if (cudaOccupancyMaxActiveClusters(&n1, k_qr_sm<16, false>, &cfq) == cudaSuccess &&
                 cudaOccupancyMaxActiveClusters(&n2, k_jacobi_sm<16, kJacFull>, &cfg) == cudaSuccess && n1 > 0 && n2 > 0)
                 state = 1;
         }
@@ -1138,6 +1146,7 @@ struct LaunchClass {
     int csize;
     size_t smem = 0;
     std::vector<Job> jobs;
+    int threads = kQrThreads;
 };
 
 // Events around the launch of one class (profiling).
@@ -1175,7 +1184,8 @@ static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClas
         TLR_CUDA_TRY(cudaStreamWaitEvent(cs, ctx->cls_fork, 0));
         const bool timed = timing && timing->csize == use[k]->csize;
         if (timed) TLR_CUDA_TRY(cudaEventRecord(timing->e0, cs));
-        launch_cluster(use[k]->kernel, use[k]->csize, (int)use[k]->jobs.size(), use[k]->smem, cs, dj[k], extra...);
+        launch_cluster(use[k]->kernel, use[k]->csize, (int)use[k]->jobs.size(), use[k]->threads, use[k]->smem, cs, dj[k],
+                       extra...);
         if (timed) TLR_CUDA_TRY(cudaEventRecord(timing->e1, cs));
         TLR_CUDA_TRY(cudaEventRecord(ctx->cls_join[k], cs));
     }
@@ -1188,14 +1198,15 @@ static void launch_classes(tlr_ctx *ctx, cudaStream_t st, std::vector<LaunchClas
 }
 
 template <class Job, class K>
-static void add_to_class(std::vector<LaunchClass<Job, K>> &cls, K kernel, int csize, size_t smem, const Job &j) {
+static void add_to_class(std::vector<LaunchClass<Job, K>> &cls, K kernel, int csize, size_t smem, const Job &j,
+                         int threads = kQrThreads) {
     for (auto &c : cls)
         if (c.kernel == kernel && c.csize == csize) {
             c.smem = std::max(c.smem, smem);
             c.jobs.push_back(j);
             return;
         }
-    LaunchClass<Job, K> c{kernel, csize, smem, {j}};
+    LaunchClass<Job, K> c{kernel, csize, smem, {j}, threads};
     cls.push_back(c);
 }
 
@@ -1215,7 +1226,7 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
         QrKernel k = qr_sm_kernel(c, df);
         size_t bytes = qr_sm_bytes(J.m, J.s, c);
         if (bytes <= smem_cap((const void *)k)) {
-            add_to_class(cls, k, c, bytes, J);
+            add_to_class(cls, k, c, bytes, J, kQrSmThreads);
             continue;
         }
         // global-memory fallback: factorises its input in place

@@ -726,7 +726,13 @@ void launch_tc(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vector
     auto *dp = (const TcProb *)stage_push(ctx, tp.data(), tp.size() * sizeof(TcProb), s);
     auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
     if (ctas_per_sm > 0) {
-        constexpr size_t smem = tc_smem_bytes<S, 2>();
+        // more than half an SM's shared memory: one CTA of this product per SM,
+        // the rest of the SM open to a critical-path CTA (a second CTA of it
+        // would also wait for the tensor memory the first one holds)
+        int dev = 0, per_sm = 0;
+        TLR_CUDA_TRY(cudaGetDevice(&dev));
+        TLR_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        const size_t smem = std::max(tc_smem_bytes<S, 2>(), (size_t)per_sm / 2 + 1024);
         raise_smem(k_gemm_tc<S, 2, Epi>, smem);
         launch(k_gemm_tc<S, 2, Epi>, total, kTcThreads, smem, s, dp, dt, (int)act.size(), total, alpha, epi,
                ctx->d_status);
