@@ -28,19 +28,22 @@ constexpr int kBlk = 32;
 // memory, which for one tile is L2-resident, and every load goes to L2
 // (__ldcg: another CTA may have written the line in an earlier phase).  A
 // cluster barrier (release/acquire at cluster scope) separates dependent
-// phases.  With 32-wide blocks, block step k of the right-looking Cholesky:
-//   1. CTA 0 factors the diagonal block L_kk and inverts it in shared memory
-//      with all its threads (a rank-1 update per column; the inverse row by
-//      row, eight lanes per column), the inverse kept in `dinv` for step 2
-//      and for L^-1;
-//   2. every thread of the cluster takes one row r below the block:
-//      A[r, k-block] <- A[r, k-block] L_kk^-T;
-//   3. the trailing lower triangle A_IJ -= P_I P_J' by 32 x 32 output tiles
-//      spread round-robin over the CTAs, each CTA loading its next tile's
-//      operands into registers while it updates the current one.
-// Then X = L^-1 by right-looking substitution on X = I: block step k applies
-// X[k, :] <- L_kk^-1 X[k, :] (columns over all threads), then
-// X[I, :] -= L_Ik X[k, :] for the rows below (tiles over the CTAs).
+// phases.  The factorisation and the inverse X = L^-1 advance together, in
+// 32-wide block steps, two barriers a step.  Block step k:
+//   1. (all CTAs) the panel rows below the block, A[r, k] <- A[r, k] L_kk^-T,
+//      and the inverse's block row, X[k, :] <- L_kk^-1 X[k, :] (columns
+//      < end of block k; X starts as I), with L_kk^-1 from step k - 1;
+//   -- barrier --
+//   2. CTA 0 updates the next diagonal block, A_{k+1,k+1} -= L_{k+1,k}
+//      L_{k+1,k}', and factors and inverts it in shared memory (a rank-1
+//      update per column; the inverse row by row, eight lanes per column):
+//      the diagonal block of step k + 1 is ready when step k ends.  The other
+//      CTAs take, round robin, the rest of the trailing lower triangle,
+//      A_IJ -= L_Ik L_Jk' (I >= J > k), and the inverse's update
+//      X_IJ -= L_Ik X_kJ (I > k, J <= k), 32 x 32 output tiles, loading
+//      their next tile's operands into registers while they update the
+//      current one;
+//   -- barrier --
 // FP64 throughout.  A non-positive pivot sets NOT_SPD (info = row_base + row)
 // and every CTA leaves at the next barrier.
 constexpr int kPotrfThreads = 256;
@@ -79,6 +82,68 @@ __device__ __forceinline__ void tile_update32(double *C, int ldc, const double (
         }
 }
 
+// Cholesky of the w x w diagonal block at (p, p) of A by the calling CTA,
+// with the block's inverse: L_kk into A (lower; upper part of the block 0),
+// L_kk^-1 into Li (32 x 32, row major).  Returns the first failing column
+// (non-positive pivot) or -1, the same on every thread.
+__device__ int potrf_diag_block(double *A, int lda, int p, int w, double *Li, double (*sa)[kBlk + 1],
+                                double (*sl)[kBlk + 1], int *s_bad) {
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+        const int r = e % kBlk, c = e / kBlk;
+        sa[r][c] = (r < w && c < w && c <= r) ? __ldcg(A + (int64_t)(p + c) * lda + p + r) : 0.0;
+    }
+    if (tid == 0) *s_bad = -1;
+    __syncthreads();
+    // right-looking Cholesky of the block, one column at a time, the updates
+    // spread over the CTA's threads
+    for (int c = 0; c < w; ++c) {
+        if (tid == 0) {
+            const double d = sa[c][c];
+            if (!(d > 0.0)) *s_bad = c;
+            else sa[c][c] = sqrt(d);
+        }
+        __syncthreads();
+        if (*s_bad >= 0) break;  // read after the barrier: uniform
+        const double piv = sa[c][c];
+        for (int r = c + 1 + tid; r < w; r += kPotrfThreads) sa[r][c] /= piv;
+        __syncthreads();
+        const int nr = w - c - 1;
+        for (int e = tid; e < nr * nr; e += kPotrfThreads) {
+            const int r = c + 1 + e % nr, cc = c + 1 + e / nr;
+            if (cc <= r) sa[r][cc] -= sa[r][c] * sa[cc][c];
+        }
+        __syncthreads();
+    }
+    const int bad = *s_bad;
+    if (bad >= 0) return bad;
+    // inverse of the lower triangular block, row by row: column c by the 8
+    // lanes 8c .. 8c+7 (one warp holds four columns), each summing every 8th
+    // term, then a shuffle reduction
+    const int c = tid >> 3, q = tid & 7;
+    for (int r = 0; r < kBlk; ++r) {
+        double part = 0.0;
+        if (c < w && r < w && r > c)
+            for (int k = c + q; k < r; k += 8) part = fma(sa[r][k], sl[k][c], part);
+        part += __shfl_xor_sync(0xFFFFFFFFu, part, 4);
+        part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
+        part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
+        if (q == 0) {
+            double v = 0.0;
+            if (c < w && r < w && r >= c) v = ((r == c ? 1.0 : 0.0) - part) / sa[r][r];
+            sl[r][c] = v;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+        const int r = e % kBlk, cc = e / kBlk;
+        if (r < w && cc < w) A[(int64_t)(p + cc) * lda + p + r] = (cc <= r) ? sa[r][cc] : 0.0;
+        Li[r * kBlk + cc] = sl[r][cc];
+    }
+    return -1;
+}
+
 // `scratch`: 32 x 1024 doubles for the diagonal block inverses, then one
 // word through which CTA 0 tells the cluster to stop (the context's status
 // word may be set by kernels on other streams at any time, so the CTAs do not
@@ -94,75 +159,34 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
     const int nbk = (m + kBlk - 1) / kBlk;
     double *dinv = scratch;
     long long *stop = reinterpret_cast<long long *>(scratch + (int64_t)kBlk * kBlk * kBlk);
-    if (rank == 0 && tid == 0) __stcg(stop, __ldcg(&st->code) ? 1LL : 0LL);
+    // X = I; CTA 0 factors the first diagonal block
+    for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
+        const int r = (int)(e % m), c = (int)(e / m);
+        X[(int64_t)c * ldx + r] = (r == c) ? 1.0 : 0.0;
+    }
+    if (rank == 0) {
+        // one read of the status word decides for the whole CTA (another
+        // stream's kernel may set it at any time)
+        if (tid == 0) s_bad = __ldcg(&st->code) ? 1 : 0;
+        __syncthreads();
+        long long halt = s_bad ? 1LL : 0LL;
+        __syncthreads();
+        if (!halt) {
+            const int bad = potrf_diag_block(A, lda, 0, min(kBlk, m), dinv, sa, sl, &s_bad);
+            if (bad >= 0) {
+                if (tid == 0) set_status(st, TLR_ERR_NOT_SPD, row_base + bad);
+                halt = 1;
+            }
+        }
+        if (tid == 0) __stcg(stop, halt);
+    }
     cl.sync();
     if (__ldcg(stop)) return;
     for (int kb = 0; kb < nbk; ++kb) {
         const int p = kb * kBlk, w = min(kBlk, m - p);
-        double *Li = dinv + (int64_t)kb * kBlk * kBlk;  // L_kk^-1, [row][col] row major, 32 x 32
-        // 1. diagonal block
-        if (rank == 0) {
-            for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
-                const int r = e % kBlk, c = e / kBlk;
-                sa[r][c] = (r < w && c < w && c <= r) ? __ldcg(A + (int64_t)(p + c) * lda + p + r) : 0.0;
-            }
-            if (tid == 0) s_bad = -1;
-            __syncthreads();
-            // right-looking Cholesky of the block, one column at a time, the
-            // updates spread over the CTA's threads
-            for (int c = 0; c < w; ++c) {
-                if (tid == 0) {
-                    const double d = sa[c][c];
-                    if (!(d > 0.0)) s_bad = c;
-                    else sa[c][c] = sqrt(d);
-                }
-                __syncthreads();
-                if (s_bad >= 0) break;  // read after the barrier: uniform
-                const double piv = sa[c][c];
-                for (int r = c + 1 + tid; r < w; r += kPotrfThreads) sa[r][c] /= piv;
-                __syncthreads();
-                const int nr = w - c - 1;
-                for (int e = tid; e < nr * nr; e += kPotrfThreads) {
-                    const int r = c + 1 + e % nr, cc = c + 1 + e / nr;
-                    if (cc <= r) sa[r][cc] -= sa[r][c] * sa[cc][c];
-                }
-                __syncthreads();
-            }
-            if (s_bad >= 0) {
-                if (tid == 0) {
-                    set_status(st, TLR_ERR_NOT_SPD, row_base + p + s_bad);
-                    __stcg(stop, 1LL);
-                }
-            } else {
-                // inverse of the lower triangular block, row by row: column c
-                // by the 8 lanes 8c .. 8c+7 (one warp holds four columns),
-                // each summing every 8th term, then a shuffle reduction
-                const int c = tid >> 3, q = tid & 7;
-                for (int r = 0; r < kBlk; ++r) {
-                    double part = 0.0;
-                    if (c < w && r < w && r > c)
-                        for (int k = c + q; k < r; k += 8) part = fma(sa[r][k], sl[k][c], part);
-                    part += __shfl_xor_sync(0xFFFFFFFFu, part, 4);
-                    part += __shfl_xor_sync(0xFFFFFFFFu, part, 2);
-                    part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
-                    if (q == 0) {
-                        double v = 0.0;
-                        if (c < w && r < w && r >= c) v = ((r == c ? 1.0 : 0.0) - part) / sa[r][r];
-                        sl[r][c] = v;
-                    }
-                    __syncwarp();
-                }
-                __syncthreads();
-                for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
-                    const int r = e % kBlk, c = e / kBlk;
-                    if (r < w && c < w) A[(int64_t)(p + c) * lda + p + r] = (c <= r) ? sa[r][c] : 0.0;
-                    Li[r * kBlk + c] = sl[r][c];
-                }
-            }
-        }
-        cl.sync();
-        if (__ldcg(stop)) return;  // written by CTA 0 only, before the barrier
-        // 2. panel rows below the block: x <- a L_kk^-T, x_c = sum_{k<=c} a_k Linv[c][k]
+        const double *Li = dinv + (int64_t)kb * kBlk * kBlk;  // L_kk^-1, row major
+        // 1. panel rows below the block: x <- a L_kk^-T, x_c = sum_{k<=c} a_k Linv[c][k];
+        //    inverse block row: X[k-block, c] <- L_kk^-1 X[k-block, c], c < p + w
         for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) sl[e / kBlk][e % kBlk] = __ldcg(Li + e);
         __syncthreads();
         for (int r = p + w + gtid; r < m; r += gthreads) {
@@ -178,63 +202,7 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
                 A[(int64_t)(p + c) * lda + r] = x;
             }
         }
-        cl.sync();
-        // 3. trailing update of the lower triangle, tiles (bi >= bj > kb)
-        const int nt = nbk - kb - 1;
-        const int ntiles = nt * (nt + 1) / 2;
-        // the operands of a CTA's next tile are loaded into registers while it
-        // updates the current one (the panel is final in this step)
-        auto tile_of = [&](int t, int &I, int &Jb) {
-            int bi = 0, rem = t;  // t -> (bi, bj), bi = kb+1+i, bj = kb+1+j, j <= i
-            while (rem > bi) { rem -= bi + 1; ++bi; }
-            I = kb + 1 + bi;
-            Jb = kb + 1 + rem;
-        };
-        double ra[kTileLoads], rb[kTileLoads];
-        auto fetch = [&](int t) {
-            int I, Jb;
-            tile_of(t, I, Jb);
-            const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
-#pragma unroll
-            for (int u = 0; u < kTileLoads; ++u) {
-                const int e = tid + u * kPotrfThreads, r = e % kBlk, k = e / kBlk;
-                ra[u] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
-                rb[u] = (r < cols && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + cj + r) : 0.0;
-            }
-        };
-        if (rank < ntiles) fetch(rank);
-        for (int t = rank; t < ntiles; t += kCl) {
-            int I, Jb;
-            tile_of(t, I, Jb);
-            const int ri = I * kBlk, cj = Jb * kBlk;
-            const int rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < kTileLoads; ++u) {
-                const int e = tid + u * kPotrfThreads;
-                sa[e % kBlk][e / kBlk] = ra[u];
-                sb[e % kBlk][e / kBlk] = rb[u];
-            }
-            __syncthreads();
-            if (t + kCl < ntiles) fetch(t + kCl);
-            tile_update32(A + (int64_t)cj * lda + ri, lda, sa, sb, rows, cols, I == Jb);
-        }
-        cl.sync();
-    }
-    // zero the strict upper triangle; X = I
-    for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
-        const int r = (int)(e % m), c = (int)(e / m);
-        if (r < c) A[(int64_t)c * lda + r] = 0.0;
-        X[(int64_t)c * ldx + r] = (r == c) ? 1.0 : 0.0;
-    }
-    cl.sync();
-    for (int kb = 0; kb < nbk; ++kb) {
-        const int p = kb * kBlk, w = min(kBlk, m - p), ncols = p + w;
-        const double *Li = dinv + (int64_t)kb * kBlk * kBlk;
-        for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) sl[e / kBlk][e % kBlk] = __ldcg(Li + e);
-        __syncthreads();
-        // a. X[k-block, c] <- L_kk^-1 X[k-block, c] for the columns c < p + w
-        for (int c = gtid; c < ncols; c += gthreads) {
+        for (int c = gtid; c < p + w; c += gthreads) {
             double x[kBlk];
 #pragma unroll
             for (int k = 0; k < kBlk; ++k) x[k] = k < w ? __ldcg(X + (int64_t)c * ldx + p + k) : 0.0;
@@ -248,25 +216,47 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
             }
         }
         cl.sync();
-        // b. X[I, J] -= L[I, k] X[k, J] for row blocks I > k and column blocks J <= k
-        const int nI = nbk - kb - 1, nJ = kb + 1, ntiles = nI * nJ;
+        if (kb + 1 >= nbk) break;
+        // 2. trailing and inverse updates by this block column; CTA 0 also
+        //    prepares the next diagonal block
+        const int nt = nbk - kb - 1;            // block rows below
+        const int ntr = nt * (nt + 1) / 2;      // trailing tiles (I >= J > kb); tile 0 is (kb+1, kb+1)
+        const int ntot = ntr + nt * (kb + 1);   // + inverse tiles (I > kb, J <= kb)
+        // tile t -> operands: trailing (I, J): C = A_IJ, a = L_I,kb, b = L_J,kb (as [row][k]);
+        //                     inverse (I, J): C = X_IJ, a = L_I,kb, b = X_kb,J (as [col][k])
+        auto tile_of = [&](int t, bool &inv, int &I, int &Jb) {
+            if (t < ntr) {
+                int bi = 0, rem = t;
+                while (rem > bi) { rem -= bi + 1; ++bi; }
+                inv = false;
+                I = kb + 1 + bi;
+                Jb = kb + 1 + rem;
+            } else {
+                const int u = t - ntr;
+                inv = true;
+                I = kb + 1 + u % nt;
+                Jb = u / nt;
+            }
+        };
         double ra[kTileLoads], rb[kTileLoads];
         auto fetch = [&](int t) {
-            const int I = kb + 1 + t % nI, Jb = t / nI;
+            bool inv;
+            int I, Jb;
+            tile_of(t, inv, I, Jb);
             const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
 #pragma unroll
             for (int u = 0; u < kTileLoads; ++u) {
                 const int e = tid + u * kPotrfThreads, r = e % kBlk, k = e / kBlk;
                 ra[u] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
-                // b operand as [col][k]: X[p + k, cj + col]
-                rb[u] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
+                if (inv) rb[u] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
+                else rb[u] = (r < cols && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + cj + r) : 0.0;
             }
         };
-        if (rank < ntiles) fetch(rank);
-        for (int t = rank; t < ntiles; t += kCl) {
-            const int I = kb + 1 + t % nI, Jb = t / nI;
-            const int ri = I * kBlk, cj = Jb * kBlk;
-            const int rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
+        auto apply = [&](int t) {
+            bool inv;
+            int I, Jb;
+            tile_of(t, inv, I, Jb);
+            const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
             __syncthreads();
 #pragma unroll
             for (int u = 0; u < kTileLoads; ++u) {
@@ -275,10 +265,40 @@ k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevS
                 sb[e % kBlk][e / kBlk] = rb[u];
             }
             __syncthreads();
-            if (t + kCl < ntiles) fetch(t + kCl);
-            tile_update32(X + (int64_t)cj * ldx + ri, ldx, sa, sb, rows, cols, false);
+            return inv ? (X + (int64_t)cj * ldx + ri) : (A + (int64_t)cj * lda + ri);
+        };
+        if (rank == 0) {
+            // tile (kb+1, kb+1), then the next diagonal block
+            fetch(0);
+            double *C = apply(0);
+            tile_update32(C, lda, sa, sb, min(kBlk, m - (kb + 1) * kBlk), min(kBlk, m - (kb + 1) * kBlk), true);
+            __syncthreads();
+            const int pn = (kb + 1) * kBlk, wn = min(kBlk, m - pn);
+            const int bad = potrf_diag_block(A, lda, pn, wn, dinv + (int64_t)(kb + 1) * kBlk * kBlk, sa, sl, &s_bad);
+            if (bad >= 0 && tid == 0) {
+                set_status(st, TLR_ERR_NOT_SPD, row_base + pn + bad);
+                __stcg(stop, 1LL);
+            }
+        } else {
+            const int step = kCl - 1;
+            if (1 + rank - 1 < ntot) fetch(1 + rank - 1);
+            for (int t = 1 + rank - 1; t < ntot; t += step) {
+                bool inv;
+                int I, Jb;
+                tile_of(t, inv, I, Jb);
+                const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
+                double *C = apply(t);
+                if (t + step < ntot) fetch(t + step);
+                tile_update32(C, inv ? ldx : lda, sa, sb, rows, cols, !inv && I == Jb);
+            }
         }
         cl.sync();
+        if (__ldcg(stop)) return;  // written by CTA 0 only, before the barrier
+    }
+    // zero the strict upper triangle of the factor
+    for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
+        const int r = (int)(e % m), c = (int)(e / m);
+        if (r < c) A[(int64_t)c * lda + r] = 0.0;
     }
 }
 
