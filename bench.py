@@ -307,21 +307,16 @@ def run_gpu(args):
     head = runs[head_name]
     head_opts = tlr.Options(nb=NB, eps=EPS, precision=precisions[head_name])
 
-    # end to end through the public API with host buffers: pinned host inputs
-    # copied in every step, the result read back on the host
+    # end to end through the C ABI with HOST buffers (tlr_loglik_host): the
+    # pinned host inputs are copied to the device inside every call, ordered,
+    # permuted and evaluated; the result comes back on the host
     xy_pin = torch.from_numpy(xy_h).pin_memory()
     z_pin = z.cpu().pin_memory()
-    xy_dev = torch.empty_like(xy)
-    z_dev = torch.empty_like(z)
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        xy_dev.copy_(xy_pin, non_blocking=True)
-        z_dev.copy_(z_pin, non_blocking=True)
-        tlr.tlr_order(ctx, xy_dev, ORDER, perm=perm, xy_out=xyo)
-        tlr.tlr_gather(ctx, perm, z_dev, dst=zo)
-        tlr.tlr_loglik(L, xyo, zo, thetas[args.warmup + k], head_opts)  # result returned on the host
+        tlr.tlr_loglik_host(L, xy_pin, z_pin, thetas[args.warmup + k], head_opts, order=ORDER)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = world * e2e_steps / e2e_s
@@ -344,8 +339,9 @@ def run_gpu(args):
         fl = o["gemm_flops"] / launches
         achieved = fl / (avg / 1000.0) / 1e12 if avg > 0 else 0.0
         if o is tensor:
-            name = ("k_gemm_tc<5,2,TcEpiMatern> (panel update + Matern generation, tcgen05 products of 5 BF16 "
-                    "slices, 15 slice pairs)")
+            name = ("k_gemm_tc<5,2,TcEpiLinear> (panel update: FP64 covariance panel by k_generate_panel, operand "
+                    "splits, then T -= P Q' as tcgen05 products of 5 BF16 slices, 15 slice pairs; the time covers "
+                    "all three)")
             peak, src = tc_peak, ("bf16_tflops_sustained %.1f of MEASURED_PEAKS.json (%s) / 15 slice-pair "
                                   "products per FP64-equivalent product" % (pk["bf16_tflops_sustained"], pk_src))
         elif o is mixed:
@@ -500,6 +496,8 @@ def run_gpu(args):
         "rel_dl_vs_fp64_by_path": rel,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                "how": "tlr_loglik_host: host buffers in, copies, ordering and evaluation inside the call, "
+                       "host clock around the calls",
                 "h2d_bytes_per_step": int(xy_pin.numel() * 8 + z_pin.numel() * 8),
                 "d2h_bytes_per_step": 8 * 3},
         "gpu_launches": int(head["launches"]),
@@ -1115,7 +1113,7 @@ def main():
     ap.add_argument("--study-steps", type=int, default=2, help="timed evaluations per ordering-study point")
     ap.add_argument("--study-orders", default="", help="comma-separated orderings of the study (default: all five)")
     ap.add_argument("--no-table1", dest="table1", action="store_false", help="skip the Table 1 memory comparison")
-    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"), help="where the study writes its tables")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "study_out"), help="where the study writes its tables")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "batched", "serving", "ordering-study", "oracle-fullsize"],
                     help="headline: one n = 40,000 evaluation per step; batched: many datasets per step; "

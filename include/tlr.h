@@ -69,11 +69,11 @@ extern "C" {
  * path runs, and where its factor falls below (or meets a non-positive
  * pivot) the FP64 path runs again from the same starting rank map and its
  * result is returned.  tlr_result.precision_used says which.  The threshold
- * comes from a measurement: over 441 batched evaluations (n 2k-20k, nu up to
- * 2.5, each path from its own rank-map history) every mixed result whose
- * factor stayed at or above 1e-5 sigma2 was within 1e-6 |l| of the FP64 one
- * (worst 4.2e-7; 4.5e-9 above 1e-4), and up to 5.6e-3 below it; 3e-5 keeps
- * a margin. */
+ * comes from a measurement: over 444 batched evaluations (256 datasets, n
+ * 2k-20k, nu up to 2.5, data drawn from each dataset's model Z = L w, each
+ * path from its own rank-map history) every mixed result whose factor stayed
+ * at or above 1e-5 sigma2 was within 6.1e-9 |l| of the FP64 one (8.4e-7 at or
+ * above 1e-6), and up to 1.9e-4 below it; 3e-5 keeps a margin. */
 #define TLR_PREC_AUTO 2
 #define TLR_AUTO_PIVOT2 3e-5
 /* Tensor: the mixed path with its dense off-diagonal products -- the panel
@@ -324,6 +324,18 @@ int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *s
  * Errors: TLR_ERR_ARG, TLR_ERR_NOT_SPD, TLR_ERR_RANK, TLR_ERR_OOM, TLR_ERR_CUDA. */
 int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
                const tlr_opts *opts, tlr_mat *L, tlr_result *out, void *stream);
+
+/* The same evaluation from HOST buffers (Sec. 3 + Eq. 1.2 in one call): xy_host
+ * (2n doubles, SoA, generation order, in [0,1]^2) and z_host (n doubles, the
+ * same order) are copied to the device on `stream` (pinned memory makes the
+ * copies asynchronous; pageable memory works too), the locations are ordered
+ * by `order` (TLR_ORDER_*; seed for TLR_ORDER_RANDOM), locations and
+ * observations permuted, and l(theta) evaluated as tlr_loglik does.  The
+ * device copies are workspaces of the call.  *out is filled on the host; the
+ * call syncs `stream`.  Errors: those of tlr_order and tlr_loglik. */
+int tlr_loglik_host(tlr_ctx *ctx, const double *xy_host, const double *z_host, int64_t n, int order,
+                    uint64_t seed, tlr_theta theta, const tlr_opts *opts, tlr_mat *L, tlr_result *out,
+                    void *stream);
 
 /* ---- measurement ------------------------------------------------------------ */
 

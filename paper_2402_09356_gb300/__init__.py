@@ -106,6 +106,9 @@ _SIGS = {
     "tlr_loglik": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, tlr_theta,
                                   ctypes.POINTER(tlr_opts), ctypes.c_void_p, ctypes.POINTER(tlr_result),
                                   ctypes.c_void_p]),
+    "tlr_loglik_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                       ctypes.c_int, ctypes.c_uint64, tlr_theta, ctypes.POINTER(tlr_opts),
+                                       ctypes.c_void_p, ctypes.POINTER(tlr_result), ctypes.c_void_p]),
     "tlr_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int)]),
@@ -467,6 +470,34 @@ def tlr_loglik(mat: TlrMatrix, xy, z, theta, opts: Options, stream=None) -> dict
                                    ctypes.byref(res), _stream(stream))
     mat.ctx.check(rc, res.info)
     return res.as_dict()
+
+
+def tlr_loglik_host(mat: TlrMatrix, xy, z, theta, opts: Options, order="hilbert", seed: int = 3,
+                    stream=None) -> dict:
+    """l(theta) from host arrays (numpy float64 or pinned CPU tensors) in
+    generation order: the call copies them to the device, orders and
+    evaluates (Sec. 3, Eq. 1.2)."""
+    import numpy as np
+    xp, zp = _host_ptr(xy, 2 * mat.n), _host_ptr(z, mat.n)
+    res = tlr_result()
+    o = opts.c()
+    method = ORDERS[order] if isinstance(order, str) else int(order)
+    rc = load_library().tlr_loglik_host(mat.ctx.h, xp, zp, mat.n, method, int(seed), _theta(theta),
+                                        ctypes.byref(o), mat.h, ctypes.byref(res), _stream(stream))
+    mat.ctx.check(rc, res.info)
+    return res.as_dict()
+
+
+def _host_ptr(a, numel):
+    """Address of a contiguous float64 host array (numpy or CPU tensor) of numel elements."""
+    import numpy as np
+    if hasattr(a, "data_ptr"):
+        if a.device.type != "cpu" or str(a.dtype) != "torch.float64" or not a.is_contiguous() or a.numel() != numel:
+            raise TlrError(TLR_ERR_ARG, "host input must be a contiguous float64 CPU tensor of %d elements" % numel)
+        return ctypes.c_void_p(a.data_ptr())
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != numel:
+        raise TlrError(TLR_ERR_ARG, "host input must be a contiguous float64 array of %d elements" % numel)
+    return ctypes.c_void_p(a.ctypes.data)
 
 
 def tlr_profile(ctx: Context, enable: bool = True) -> dict:

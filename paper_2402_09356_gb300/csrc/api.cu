@@ -614,6 +614,35 @@ int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_t
     return guarded(ctx, [&] { loglik_impl(ctx, xy, z, n, theta, opts, L, out, (cudaStream_t)stream); });
 }
 
+int tlr_loglik_host(tlr_ctx *ctx, const double *xy_host, const double *z_host, int64_t n, int order, uint64_t seed,
+                    tlr_theta theta, const tlr_opts *opts, tlr_mat *L, tlr_result *out, void *stream) {
+    return guarded(ctx, [&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        check_arg(xy_host && z_host && n > 0 && n < ((int64_t)1 << 31), "xy_host/z_host/n");
+        check_arg(order >= TLR_ORDER_IDENTITY && order <= TLR_ORDER_MAXMIN, "order");
+        // device copies of the inputs, the ordering and the ordered inputs
+        DevBuf xy(2 * (size_t)n * sizeof(double), s), z((size_t)n * sizeof(double), s);
+        DevBuf perm((size_t)n * sizeof(int64_t), s), xyo(2 * (size_t)n * sizeof(double), s),
+            zo((size_t)n * sizeof(double), s);
+        TLR_CUDA_TRY(cudaMemcpyAsync(xy.as<double>(), xy_host, 2 * (size_t)n * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+        TLR_CUDA_TRY(cudaMemcpyAsync(z.as<double>(), z_host, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+        const double *x = xy.as<double>();
+        int64_t *p = perm.as<int64_t>();
+        switch (order) {
+        case TLR_ORDER_IDENTITY: order_identity(n, p, s); break;
+        case TLR_ORDER_RANDOM:
+        case TLR_ORDER_MORTON:
+        case TLR_ORDER_HILBERT: order_sfc(x, n, order, seed, p, nullptr, s); break;
+        case TLR_ORDER_KDTREE: order_kdtree(x, n, p, s); break;
+        case TLR_ORDER_MAXMIN: order_maxmin(x, n, p, s, ctx->num_sms); break;
+        }
+        permute_xy(x, p, n, 0, xyo.as<double>(), s);
+        gather(p, z.as<double>(), n, zo.as<double>(), s);
+        loglik_impl(ctx, xyo.as<double>(), zo.as<double>(), n, theta, opts, L, out, s);
+    });
+}
+
 int tlr_profile(tlr_ctx *ctx, int enable, double *gemm_ms, double *gemm_flops, double *matern_entries,
                 int *panel_launches) {
     if (!ctx) return TLR_ERR_ARG;

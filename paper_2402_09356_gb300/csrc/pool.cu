@@ -201,6 +201,7 @@ void worker_main(tlr_pool *p, int w) {
         std::string err;
         std::vector<int32_t> hint;
         bool ran = false;
+        int64_t extra = 0;  // storage charged for a retry on uniform slots
         if (alloc && !d->L) d->L = mat_alloc(p, d->n, d->nb, d->maxrank, d->hint, W.stream);
         tlr_opts o{};
         o.nb = d->nb;
@@ -225,14 +226,35 @@ void worker_main(tlr_pool *p, int w) {
             if (status == TLR_ERR_RANK && d->L->cap_overflow) {
                 // the compact slots (sized by the last rank map) ran out of
                 // room: the same evaluation, from the same rank map, on
-                // uniform maxrank slots (held only for this request)
-                mat_free(d->L, W.stream);
-                d->L = mat_alloc(p, d->n, d->nb, d->maxrank, {}, W.stream);
-                if (d->L) {
-                    evaluate(d->L);
+                // uniform maxrank slots (held only for this request).  The
+                // difference in storage is charged to the budget first,
+                // waiting for running requests or evicting idle factors.
+                const int64_t need = factor_bytes(d->n, d->nb, d->maxrank, {}) - (int64_t)d->L->bytes;
+                std::vector<int> ev2;
+                bool never = false, got = false;
+                std::vector<tlr_mat *> free2;
+                lk.lock();
+                while (!(got = p->adm.grow(ar.data, need, &ev2, &never)) && !never) p->cv_done.wait(lk);
+                for (int e : ev2) {
+                    PoolData *v = p->data[e].get();
+                    free2.push_back(v->L);
+                    v->L = nullptr;
+                }
+                lk.unlock();
+                for (tlr_mat *M : free2) mat_free(M, W.stream);
+                if (got) {
+                    extra = std::max<int64_t>(need, 0);
+                    mat_free(d->L, W.stream);
+                    d->L = mat_alloc(p, d->n, d->nb, d->maxrank, {}, W.stream);
+                    if (d->L) {
+                        evaluate(d->L);
+                    } else {
+                        status = TLR_ERR_OOM;
+                        err = "cannot allocate uniform factor storage after a slot overflow";
+                    }
                 } else {
                     status = TLR_ERR_OOM;
-                    err = "cannot allocate uniform factor storage after a slot overflow";
+                    err = "uniform factor storage after a slot overflow exceeds the HBM budget";
                 }
             }
         }
@@ -252,6 +274,7 @@ void worker_main(tlr_pool *p, int w) {
             d->hint.swap(hint);
             d->pivot2 = pivot2;
         }
+        p->adm.shrink(extra);
         p->adm.finish(ar.data, d->L != nullptr);
         p->adm.set_work(ar.data, wb);
         if (!d->L) p->adm.set_factor(ar.data, fb);

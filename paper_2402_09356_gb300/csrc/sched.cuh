@@ -177,6 +177,43 @@ public:
         return false;
     }
 
+    // Extra factor storage for the running request of dataset d (a retry on
+    // larger slots): charged at once if it fits, else after evicting idle
+    // factors of other datasets least recently used first.  Returns false if
+    // it cannot fit now; *never then says whether it cannot fit even with every
+    // other request finished and every idle factor evicted.
+    bool grow(int d, int64_t extra, std::vector<int> *evicted, bool *never) {
+        *never = false;
+        if (extra <= 0) return true;
+        const Data &x = data_[(size_t)d];
+        if (bases() + x.fbytes + x.wbytes + extra > budget_) {
+            *never = true;
+            return false;
+        }
+        int64_t idle = 0;
+        for (size_t e = 0; e < data_.size(); ++e)
+            if ((int)e != d && data_[e].resident && !data_[e].busy) idle += data_[e].fbytes;
+        if (used_ - idle + extra > budget_) return false;  // wait for running requests
+        while (used_ + extra > budget_) {
+            int victim = -1;
+            for (size_t e = 0; e < data_.size(); ++e)
+                if ((int)e != d && data_[e].resident && !data_[e].busy &&
+                    (victim < 0 || data_[e].last_use < data_[(size_t)victim].last_use))
+                    victim = (int)e;
+            data_[(size_t)victim].resident = false;
+            used_ -= data_[(size_t)victim].fbytes;
+            ++evictions_;
+            if (evicted) evicted->push_back(victim);
+        }
+        charge(extra);
+        return true;
+    }
+
+    // Releases extra storage taken by grow().
+    void shrink(int64_t extra) {
+        if (extra > 0) used_ -= extra;
+    }
+
     // The running request of dataset d has finished; `keep` false if its
     // factor storage was not kept (allocation failed).
     void finish(int d, bool keep = true) {

@@ -46,3 +46,31 @@ def test_mle_small_config(ctx):
     f_true = truth[0] * truth[1] ** (-2 * truth[2])
     assert abs(math.log(f_hat / f_true)) < 0.3                     # Eq. 5.1 quantity
     assert 4 <= res["iters"] <= 600
+
+
+@pytest.mark.parametrize("path", ["mixed", "tensor"])
+def test_mle_mixed_paths_match_fp64(ctx, path):
+    """The mixed-precision paths reach the FP64 path's estimate: every parameter
+    of theta-hat within 1e-3 (relative) of the FP64 search's, same data and
+    start (the accuracy target of the mixed-precision growth row)."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    n, nb, eps = 1600, 200, 1e-7
+    truth = (1.0, 0.1, 0.5)
+    xy = synth.jittered_grid(n, seed=41)
+    z = oracle.simulate_z(xy, truth, synth.standard_normal(n, seed=42))
+    xy_d = torch.from_numpy(xy).cuda()
+    xyo = torch.empty_like(xy_d)
+    perm = tlr.tlr_order(ctx, xy_d, "hilbert", xy_out=xyo)
+    zo = tlr.tlr_gather(ctx, perm, torch.from_numpy(z).cuda())
+    out = {}
+    for name, prec in (("fp64", tlr.TLR_PREC_FP64),
+                       (path, tlr.TLR_PREC_MIXED if path == "mixed" else tlr.TLR_PREC_TENSOR)):
+        L = tlr.TlrMatrix(ctx, n, nb)
+        out[name] = tlr.tlr_mle(L, xyo, zo, tlr.Options(nb=nb, eps=eps, precision=prec), theta0=(0.6, 0.05, 0.8),
+                                lo=(0.05, 0.005, 0.1), hi=(10.0, 2.0, 3.0), tol=1e-9, max_iter=600)
+        L.close()
+    a, b = out[path]["theta"], out["fp64"]["theta"]
+    for d in range(3):
+        assert abs(a[d] - b[d]) <= 1e-3 * abs(b[d]), (d, a, b)
+    assert abs(out[path]["loglik"] - out["fp64"]["loglik"]) <= 1e-6 * abs(out["fp64"]["loglik"])

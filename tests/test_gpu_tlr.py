@@ -389,3 +389,30 @@ def test_global_memory_fallback_kernels(ctx):
     exact = oracle.loglik_dense(xy, z, theta)["loglik"]
     assert abs(r["loglik"] - exact) <= 10 * eps * abs(exact), (r["loglik"], exact)
     L.close()
+
+
+def test_loglik_from_host_buffers(ctx):
+    """tlr_loglik_host (host inputs in generation order; copy, Sec. 3 ordering
+    and Eq. 1.2 inside one call) equals, bit for bit, the same evaluation from
+    device buffers, and meets the 10 eps bound against the dense oracle."""
+    import torch
+    import paper_2402_09356_gb300 as tlr
+    c = C1
+    xy, z, _ = ordered_problem(c["n"], c["theta"], c["order"])
+    r_dev, L, perm = gpu_loglik(ctx, xy, z, c["theta"], c["order"], c["nb"], c["eps"])
+    L.close()
+    M = tlr.TlrMatrix(ctx, c["n"], c["nb"])
+    r_host = tlr.tlr_loglik_host(M, xy, z, c["theta"], tlr.Options(nb=c["nb"], eps=c["eps"]), order=c["order"])
+    M.close()
+    M = tlr.TlrMatrix(ctx, c["n"], c["nb"])  # a fresh factor: the same starting rank map
+    pinned = tlr.tlr_loglik_host(M, torch.from_numpy(xy).pin_memory(), torch.from_numpy(z).pin_memory(),
+                                 c["theta"], tlr.Options(nb=c["nb"], eps=c["eps"]), order=c["order"])
+    M.close()
+    assert r_host["loglik"] == r_dev["loglik"] and r_host["logdet"] == r_dev["logdet"]
+    assert pinned["loglik"] == r_dev["loglik"]
+    ref = oracle.loglik_dense(xy, z, c["theta"])["loglik"]
+    assert abs(r_host["loglik"] - ref) <= 10 * c["eps"] * abs(ref)
+    with pytest.raises(tlr.TlrError) as e:
+        tlr.tlr_loglik_host(tlr.TlrMatrix(ctx, c["n"], c["nb"]), xy[:10], z, c["theta"],
+                            tlr.Options(nb=c["nb"], eps=c["eps"]))
+    assert e.value.code == tlr.TLR_ERR_ARG
