@@ -132,6 +132,36 @@ int tlr_ctx_create(int device, tlr_ctx **out);
 /* Destroy a context; frees its workspace.  NULL is ignored. */
 void tlr_ctx_destroy(tlr_ctx *ctx);
 
+/* Rank buckets of the compression (Sec. 2: the tiles of a column have uneven
+ * ranks).  Every tile is compressed from a random sample of s columns, s the
+ * tile's rank at the previous evaluation plus an oversampling margin; the
+ * QR and SVD stages of a tile run on a thread-block cluster whose size comes
+ * from the bucket s falls in: the first b with s <= qr_edge[b] (svd_edge[b]),
+ * entry 3 catching all larger s (its edge is ignored).  Tiles of one bucket
+ * share one launch.  Sizes are CTAs per cluster: 1, 2, 4, 8 or 16 (16 where
+ * the device runs clusters of 16, else 8; a size whose panel does not fit in
+ * shared memory grows to the next).  Larger clusters shorten one tile's
+ * compression (fewer rows per CTA), smaller ones need fewer SMs per tile and
+ * fewer barriers per flop: a single factorisation wants the first, many
+ * concurrent ones may want the second (tlr_pool_autotune).  The buckets
+ * change how the tile's QR and SVD are reduced, not what they compute: the
+ * results agree to rounding.  Default: QR s <= 64 -> 4, <= 128 -> 8, else
+ * 16; SVD s <= 48 -> 1, <= 96 -> 4, <= 160 -> 8, else 16. */
+typedef struct {
+    int32_t qr_edge[4];
+    int32_t qr_size[4];
+    int32_t svd_edge[4];
+    int32_t svd_size[4];
+} tlr_buckets;
+
+/* Set the context's rank buckets (NULL restores the default); applies to the
+ * calls that start after it.  Errors: TLR_ERR_ARG (a size not in {1, 2, 4, 8,
+ * 16}, or edges 0..2 not positive and nondecreasing). */
+int tlr_ctx_set_buckets(tlr_ctx *ctx, const tlr_buckets *b);
+
+/* The context's rank buckets.  Errors: TLR_ERR_ARG (NULL). */
+int tlr_ctx_get_buckets(const tlr_ctx *ctx, tlr_buckets *out);
+
 /* Message of the last failing call on `ctx` ("" if none).  Owned by ctx. */
 const char *tlr_last_error(const tlr_ctx *ctx);
 
@@ -324,6 +354,34 @@ int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *s
  * Errors: TLR_ERR_ARG, TLR_ERR_NOT_SPD, TLR_ERR_RANK, TLR_ERR_OOM, TLR_ERR_CUDA. */
 int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
                const tlr_opts *opts, tlr_mat *L, tlr_result *out, void *stream);
+
+/* Several evaluations of Eq. 1.2 advanced together on one context (the
+ * batched workload: many datasets whose tiles have uneven ranks, Sec. 2).
+ * Entry g evaluates l(theta[g]) for the ordered locations xy[g] and
+ * observations z[g] (device, n[g] each, as for tlr_loglik) with options
+ * opts[g] into L[g] and out[g].  The factorisations run column by column in
+ * lockstep, and each step of a column is one launch for all entries: the
+ * panel products with the Matern generation, the diagonal POTRF (one
+ * cluster per entry), every compression launch class (tiles of all entries
+ * bucketed by sample size), V <- L^-1 V, the Gram matrices and the solve.
+ * An entry whose factorisation finishes or fails drops out; the others go
+ * on.  Every entry's result is bit for bit what tlr_loglik returns for it
+ * alone (same L[g] rank map), including the TLR_PREC_AUTO choices.
+ *   count   1..32 entries; every entry has its own L[g]
+ *   opts    count options; all with the same precision (eps, nb, maxrank
+ *           per entry; opts[g].nb == L[g]'s tile size)
+ *   out     count results (host); ms_total is the device time of the whole
+ *           call (plus, under AUTO, of the call's mixed attempt)
+ *   status  count codes (host, may be NULL): TLR_OK, TLR_ERR_NOT_SPD,
+ *           TLR_ERR_RANK or TLR_ERR_NAN per entry (out[g].info as for
+ *           tlr_loglik); another error stops the call and is written to
+ *           every entry
+ * Returns TLR_OK, else the first failing entry's status (its message in
+ * tlr_last_error).  Syncs `stream`.  Errors: TLR_ERR_ARG, TLR_ERR_NOT_SPD,
+ * TLR_ERR_RANK, TLR_ERR_NAN, TLR_ERR_OOM, TLR_ERR_CUDA. */
+int tlr_loglik_batch(tlr_ctx *ctx, int count, const double *const *xy, const double *const *z, const int64_t *n,
+                     const tlr_theta *theta, const tlr_opts *opts, tlr_mat *const *L, tlr_result *out,
+                     int *status, void *stream);
 
 /* The same evaluation from HOST buffers (Sec. 3 + Eq. 1.2 in one call): xy_host
  * (2n doubles, SoA, generation order, in [0,1]^2) and z_host (n doubles, the

@@ -53,6 +53,14 @@ class tlr_result(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class tlr_buckets(ctypes.Structure):
+    _fields_ = [("qr_edge", ctypes.c_int32 * 4), ("qr_size", ctypes.c_int32 * 4),
+                ("svd_edge", ctypes.c_int32 * 4), ("svd_size", ctypes.c_int32 * 4)]
+
+    def as_dict(self) -> dict:
+        return {f: list(getattr(self, f)) for f, _ in self._fields_}
+
+
 class tlr_pool_opts(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("nb", ctypes.c_int32), ("maxrank", ctypes.c_int32),
                 ("flags", ctypes.c_uint32), ("hbm_budget", ctypes.c_int64)]
@@ -66,6 +74,8 @@ _SIGS = {
     "tlr_ctx_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "tlr_ctx_destroy": (None, [ctypes.c_void_p]),
     "tlr_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "tlr_ctx_set_buckets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "tlr_ctx_get_buckets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tlr_buckets)]),
     "tlr_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
                                  ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]),
@@ -106,6 +116,9 @@ _SIGS = {
     "tlr_loglik": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, tlr_theta,
                                   ctypes.POINTER(tlr_opts), ctypes.c_void_p, ctypes.POINTER(tlr_result),
                                   ctypes.c_void_p]),
+    "tlr_loglik_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tlr_loglik_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_int, ctypes.c_uint64, tlr_theta, ctypes.POINTER(tlr_opts),
                                        ctypes.c_void_p, ctypes.POINTER(tlr_result), ctypes.c_void_p]),
@@ -269,6 +282,23 @@ class TlrMatrix:
             self.close()
         except Exception:
             pass
+
+
+def tlr_ctx_set_buckets(ctx: Context, buckets=None):
+    """Rank buckets of the compression (tlr_buckets or a dict with its four
+    lists); None restores the default."""
+    if buckets is None:
+        ctx.check(load_library().tlr_ctx_set_buckets(ctx.h, None))
+        return
+    b = buckets if isinstance(buckets, tlr_buckets) else tlr_buckets(
+        *[(ctypes.c_int32 * 4)(*[int(v) for v in buckets[f]]) for f, _ in tlr_buckets._fields_])
+    ctx.check(load_library().tlr_ctx_set_buckets(ctx.h, ctypes.byref(b)))
+
+
+def tlr_ctx_get_buckets(ctx: Context) -> dict:
+    b = tlr_buckets()
+    ctx.check(load_library().tlr_ctx_get_buckets(ctx.h, ctypes.byref(b)))
+    return b.as_dict()
 
 
 def tlr_version() -> str:
@@ -470,6 +500,36 @@ def tlr_loglik(mat: TlrMatrix, xy, z, theta, opts: Options, stream=None) -> dict
                                    ctypes.byref(res), _stream(stream))
     mat.ctx.check(rc, res.info)
     return res.as_dict()
+
+
+def tlr_loglik_batch(mats, xys, zs, thetas, opts, stream=None):
+    """l(theta_g) (Eq. 1.2) for several ordered datasets on one context, their
+    factorisations advanced together (one launch per step for all).  mats,
+    xys, zs, thetas: sequences of equal length (1..32); opts: one Options or
+    one per entry (same precision).  Returns (results, statuses): a dict per
+    entry and its TLR status (entries that fail do not raise; an error of
+    the whole call does)."""
+    g = len(mats)
+    if not (len(xys) == len(zs) == len(thetas) == g):
+        raise TlrError(TLR_ERR_ARG, "mats, xys, zs and thetas must have equal lengths")
+    ctx = mats[0].ctx
+    ol = list(opts) if isinstance(opts, (list, tuple)) else [opts] * g
+    for m, x, z in zip(mats, xys, zs):
+        _check_f64("xy", x, 2 * m.n)
+        _check_f64("z", z, m.n)
+    P = ctypes.c_void_p * g
+    xa = P(*[x.data_ptr() for x in xys])
+    za = P(*[z.data_ptr() for z in zs])
+    la = P(*[m.h.value for m in mats])
+    na = (ctypes.c_int64 * g)(*[m.n for m in mats])
+    ta = (tlr_theta * g)(*[_theta(t) for t in thetas])
+    oa = (tlr_opts * g)(*[o.c() for o in ol])
+    res = (tlr_result * g)()
+    st = (ctypes.c_int * g)()
+    rc = load_library().tlr_loglik_batch(ctx.h, g, xa, za, na, ta, oa, la, res, st, _stream(stream))
+    if rc != TLR_OK and all(v == rc for v in st) and rc not in (TLR_ERR_NOT_SPD, TLR_ERR_RANK, TLR_ERR_NAN):
+        ctx.check(rc)
+    return [r.as_dict() for r in res], [int(v) for v in st]
 
 
 def tlr_loglik_host(mat: TlrMatrix, xy, z, theta, opts: Options, order="hilbert", seed: int = 3,

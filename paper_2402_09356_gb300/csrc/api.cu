@@ -173,9 +173,10 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
         if (device < 0 || device >= count) throw make_error(TLR_ERR_ARG, "no CUDA device %d", device);
         TLR_CUDA_TRY(cudaSetDevice(device));
         TLR_CUDA_TRY(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device));
-        TLR_CUDA_TRY(cudaMalloc(&ctx->d_status, sizeof(DevStatus)));
-        TLR_CUDA_TRY(cudaMemset(ctx->d_status, 0, sizeof(DevStatus)));
-        TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_status, sizeof(DevStatus), cudaHostAllocDefault));
+        // the context's word, then one per factorisation of a group call
+        TLR_CUDA_TRY(cudaMalloc(&ctx->d_status, (1 + kMaxGroup) * sizeof(DevStatus)));
+        TLR_CUDA_TRY(cudaMemset(ctx->d_status, 0, (1 + kMaxGroup) * sizeof(DevStatus)));
+        TLR_CUDA_TRY(cudaHostAlloc(&ctx->h_status, (1 + kMaxGroup) * sizeof(DevStatus), cudaHostAllocDefault));
         // the critical-path streams (diagonal POTRF, compression classes) get the
         // highest priority, so that the look-ahead panel GEMM fills in behind them
         int prio_lo = 0, prio_hi = 0;
@@ -250,6 +251,20 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
 }
 
 const char *tlr_last_error(const tlr_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tlr_ctx_set_buckets(tlr_ctx *ctx, const tlr_buckets *b) {
+    return guarded(ctx, [&] {
+        const tlr_buckets v = b ? *b : default_buckets();
+        check_arg(buckets_ok(v), "bucket sizes must be 1, 2, 4, 8 or 16 and edges positive, nondecreasing");
+        ctx->buckets = v;
+    });
+}
+
+int tlr_ctx_get_buckets(const tlr_ctx *ctx, tlr_buckets *out) {
+    if (!ctx || !out) return TLR_ERR_ARG;
+    *out = ctx->buckets;
+    return TLR_OK;
+}
 
 int tlr_order(tlr_ctx *ctx, const double *xy, int64_t n, int method, uint64_t seed, uint32_t flags,
               int64_t *perm, uint32_t *codes, double *xy_out, void *stream) {
@@ -504,6 +519,33 @@ int tlr_lmul(tlr_ctx *ctx, const tlr_mat *L, const double *w, double *z, void *s
     });
 }
 
+// Eq. 1.2 and the factor's rank statistics from acc = (sum log L_ii, |L^-1 z|^2,
+// max 1 / L_ii^2) of a finished factorisation.
+static void fill_result(tlr_result *out, int64_t n, const tlr_mat *L, const double *h, const FactorStats &st) {
+    out->logdet = 2.0 * h[0];
+    out->quad = h[1];
+    out->min_pivot2 = h[2] > 0.0 ? 1.0 / h[2] : INFINITY;
+    out->loglik = -0.5 * (double)n * std::log(2.0 * M_PI) - 0.5 * out->logdet - 0.5 * out->quad;
+    if (!std::isfinite(out->loglik)) throw make_error(TLR_ERR_NAN, "likelihood is not finite");
+    int nt = L->nt;
+    double sum = 0;
+    int cnt = 0, mx = 0;
+    int64_t bytes = 0;
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < i; ++j) {
+            int r = L->h_ranks[(size_t)i * nt + j];
+            sum += r;
+            ++cnt;
+            mx = std::max(mx, r);
+            bytes += (int64_t)(tile_rows(n, L->nb, i) + tile_rows(n, L->nb, j)) * r * 8;
+        }
+    out->max_rank = mx;
+    out->mean_rank = cnt ? sum / cnt : 0.0;
+    out->offdiag_bytes = bytes;
+    out->dense_bytes = (int64_t)nt * (nt - 1) / 2 * L->nb * L->nb * 8;
+    out->flops = st.flops;
+}
+
 // One evaluation on one precision path (df: the mixed path's products in
 // paired FP32; tc: those products on the tensor cores).
 static void loglik_once(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,
@@ -537,28 +579,7 @@ static void loglik_once(tlr_ctx *ctx, const double *xy, const double *z, int64_t
         out->info = sinfo;
         throw make_error(sc, "likelihood: device status %d (info %lld)", sc, sinfo);
     }
-    out->logdet = 2.0 * h[0];
-    out->quad = h[1];
-    out->min_pivot2 = h[2] > 0.0 ? 1.0 / h[2] : INFINITY;
-    out->loglik = -0.5 * (double)n * std::log(2.0 * M_PI) - 0.5 * out->logdet - 0.5 * out->quad;
-    if (!std::isfinite(out->loglik)) throw make_error(TLR_ERR_NAN, "likelihood is not finite");
-    int nt = L->nt;
-    double sum = 0;
-    int cnt = 0, mx = 0;
-    int64_t bytes = 0;
-    for (int i = 0; i < nt; ++i)
-        for (int j = 0; j < i; ++j) {
-            int r = L->h_ranks[(size_t)i * nt + j];
-            sum += r;
-            ++cnt;
-            mx = std::max(mx, r);
-            bytes += (int64_t)(tile_rows(n, L->nb, i) + tile_rows(n, L->nb, j)) * r * 8;
-        }
-    out->max_rank = mx;
-    out->mean_rank = cnt ? sum / cnt : 0.0;
-    out->offdiag_bytes = bytes;
-    out->dense_bytes = (int64_t)nt * (nt - 1) / 2 * L->nb * L->nb * 8;
-    out->flops = st.flops;
+    fill_result(out, n, L, h, st);
     float ms = 0.f;
     TLR_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b));
     out->ms_total = ms;
@@ -607,6 +628,195 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     loglik_once(ctx, xy, z, n, theta, opts, L, out, s, false);
     L->last_pivot2 = out->min_pivot2 / theta.sigma2;
     out->ms_total += ms_mixed;
+}
+
+// One entry of a batched evaluation (tlr_loglik_batch).
+struct BatchEntry {
+    const double *xy, *z;
+    int64_t n;
+    tlr_theta theta;
+    const tlr_opts *opts;
+    tlr_mat *L;
+    tlr_result *out;
+    int status = TLR_OK;
+    std::string msg;
+};
+
+static bool per_entry_error(int code) {
+    return code == TLR_ERR_NOT_SPD || code == TLR_ERR_RANK || code == TLR_ERR_NAN;
+}
+
+// The entries es on one precision path, their factorisations in lockstep
+// (factor_group).  A single entry takes loglik_once.  Failures that belong
+// to one entry (NOT_SPD, RANK, NAN) go to its status; others throw.  Each
+// entry's ms_total is the device time of the whole call.
+static void loglik_group_once(tlr_ctx *ctx, const std::vector<BatchEntry *> &es, cudaStream_t s, bool df, bool tc) {
+    const int G = (int)es.size();
+    if (G == 0) return;
+    if (G == 1) {
+        BatchEntry &e = *es[0];
+        try {
+            loglik_once(ctx, e.xy, e.z, e.n, e.theta, e.opts, e.L, e.out, s, df, tc);
+            e.status = TLR_OK;
+        } catch (const Error &err) {
+            if (!per_entry_error(err.code)) throw;
+            e.status = err.code;
+            e.msg = err.msg;
+        }
+        return;
+    }
+    const int cnt = kTabIntervals * kTabCoef;
+    std::vector<MaternParams> P(G);
+    std::vector<FactorStats> st(G);
+    std::vector<long long> info(G, -1);
+    int64_t ntot = 0;
+    for (BatchEntry *e : es) ntot += e->n;
+    TLR_CUDA_TRY(cudaEventRecord(ctx->ev_a, s));
+    DevBuf tabs((size_t)G * 2 * cnt * sizeof(double), s);
+    DevBuf acc((size_t)G * 3 * sizeof(double), s), y((size_t)ntot * sizeof(double), s);
+    TLR_CUDA_TRY(cudaMemsetAsync(ctx->d_status, 0, (size_t)(G + 1) * sizeof(DevStatus), s));
+    TLR_CUDA_TRY(cudaMemsetAsync(acc.as<double>(), 0, (size_t)G * 3 * sizeof(double), s));
+    std::vector<FactorItem> items(G);
+    int64_t yoff = 0;
+    for (int g = 0; g < G; ++g) {
+        BatchEntry &e = *es[(size_t)g];
+        std::memset(e.out, 0, sizeof *e.out);
+        e.out->info = -1;
+        e.out->precision_used = tc ? TLR_PREC_TENSOR : (df ? TLR_PREC_MIXED : TLR_PREC_FP64);
+        P[(size_t)g] = params_of(e.theta);
+        build_matern_table(&P[(size_t)g], tabs.as<double>() + (size_t)g * 2 * cnt, s);
+        FactorItem &F = items[(size_t)g];
+        F.M = e.L;
+        F.xy = e.xy;
+        F.P = &P[(size_t)g];
+        F.tau = e.opts->eps * e.theta.sigma2;
+        F.stats = &st[(size_t)g];
+        F.info = &info[(size_t)g];
+        F.z = e.z;
+        F.y = y.as<double>() + yoff;
+        F.acc = acc.as<double>() + 3 * g;
+        yoff += e.n;
+    }
+    factor_group(ctx, s, items, FactorMode::Matern, df, tc);
+    std::vector<double> h((size_t)G * 3);
+    TLR_CUDA_TRY(cudaMemcpyAsync(h.data(), acc.as<double>(), h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TLR_CUDA_TRY(cudaEventRecord(ctx->ev_b, s));
+    TLR_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    TLR_CUDA_TRY(cudaEventElapsedTime(&ms, ctx->ev_a, ctx->ev_b));
+    for (int g = 0; g < G; ++g) {
+        BatchEntry &e = *es[(size_t)g];
+        const FactorItem &F = items[(size_t)g];
+        e.out->ms_total = ms;
+        if (F.err != TLR_OK) {
+            e.status = F.err;
+            e.msg = F.msg;
+            e.out->info = info[(size_t)g];
+            continue;
+        }
+        try {
+            fill_result(e.out, e.n, e.L, h.data() + 3 * g, st[(size_t)g]);
+            e.status = TLR_OK;
+        } catch (const Error &err) {
+            e.status = err.code;
+            e.msg = err.msg;
+        }
+    }
+    ctx->last_gemm_ms = st[0].gemm_ms;
+    ctx->last_gemm_flops = st[0].gemm_flops;
+    ctx->last_matern_entries = st[0].matern_entries;
+    ctx->last_panel_launches = st[0].panel_launches;
+    for (int k = 0; k < kStages; ++k) ctx->last_stage_ms[k] = st[0].stage_ms[k];
+    for (int k = 0; k < kDetail; ++k) ctx->last_detail_ms[k] = st[0].detail_ms[k];
+}
+
+// The precision logic of loglik_impl over a batch: every entry computes what
+// tlr_loglik would compute for it alone (the same path choices, from the same
+// rank map); the entries of one path run as one group.
+static void loglik_group(tlr_ctx *ctx, std::vector<BatchEntry> &es, cudaStream_t s) {
+    const int prec = es[0].opts->precision;
+    if (prec == TLR_PREC_TENSOR && !tc_available())
+        throw make_error(TLR_ERR_CUDA, "TLR_PREC_TENSOR needs an sm_103a device");
+    std::vector<BatchEntry *> all;
+    for (BatchEntry &e : es) all.push_back(&e);
+    if (prec != TLR_PREC_AUTO) {
+        loglik_group_once(ctx, all, s, prec != TLR_PREC_FP64, prec == TLR_PREC_TENSOR);
+        for (BatchEntry *e : all)
+            if (e->status == TLR_OK) e->L->last_pivot2 = e->out->min_pivot2 / e->theta.sigma2;
+        return;
+    }
+    std::vector<std::vector<int32_t>> hint(es.size());
+    std::vector<float> ms_mixed(es.size(), 0.f);
+    std::vector<BatchEntry *> mixed, fp64;
+    for (size_t q = 0; q < es.size(); ++q) {
+        hint[q] = es[q].L->h_ranks;
+        const double p2 = es[q].L->last_pivot2;
+        (p2 > 0.0 && p2 < TLR_AUTO_PIVOT2 ? fp64 : mixed).push_back(&es[q]);
+    }
+    loglik_group_once(ctx, mixed, s, true, false);
+    for (BatchEntry *e : mixed) {
+        const size_t q = (size_t)(e - es.data());
+        if (e->status == TLR_OK) {
+            e->L->last_pivot2 = e->out->min_pivot2 / e->theta.sigma2;
+            if (e->L->last_pivot2 >= TLR_AUTO_PIVOT2) continue;
+            ms_mixed[q] = e->out->ms_total;
+        } else if (e->status != TLR_ERR_NOT_SPD) {
+            continue;
+        }
+        e->L->h_ranks = hint[q];
+        fp64.push_back(e);
+    }
+    std::sort(fp64.begin(), fp64.end());  // entry order
+    loglik_group_once(ctx, fp64, s, false, false);
+    for (BatchEntry *e : fp64) {
+        const size_t q = (size_t)(e - es.data());
+        if (e->status == TLR_OK) e->L->last_pivot2 = e->out->min_pivot2 / e->theta.sigma2;
+        e->out->ms_total += ms_mixed[q];
+    }
+}
+
+int tlr_loglik_batch(tlr_ctx *ctx, int count, const double *const *xy, const double *const *z, const int64_t *n,
+                     const tlr_theta *theta, const tlr_opts *opts, tlr_mat *const *L, tlr_result *out, int *status,
+                     void *stream) {
+    std::vector<BatchEntry> es;
+    int rc = guarded(ctx, [&] {
+        check_arg(count >= 1 && count <= kMaxGroup, "count must be 1..32");
+        check_arg(xy && z && n && theta && opts && L && out, "xy/z/n/theta/opts/L/out");
+        for (int g = 0; g < count; ++g) {
+            const tlr_opts *o = opts + g;
+            check_arg(xy[g] && z[g] && L[g], "xy[g]/z[g]/L[g]");
+            check_arg(n[g] > 0 && L[g]->n == n[g] && L[g]->nb == o->nb, "L[g] does not match n[g]/nb");
+            check_arg(o->eps >= 0 && std::isfinite(o->eps), "eps");
+            check_arg(o->precision == opts[0].precision, "one precision for all entries");
+            check_arg(o->precision == TLR_PREC_FP64 || o->precision == TLR_PREC_MIXED ||
+                          o->precision == TLR_PREC_AUTO || o->precision == TLR_PREC_TENSOR, "precision");
+            for (int h = 0; h < g; ++h) check_arg(L[h] != L[g], "every entry needs its own L");
+            BatchEntry e{};
+            e.xy = xy[g];
+            e.z = z[g];
+            e.n = n[g];
+            e.theta = theta[g];
+            e.opts = o;
+            e.L = L[g];
+            e.out = out + g;
+            es.push_back(e);
+        }
+        loglik_group(ctx, es, (cudaStream_t)stream);
+    });
+    if (rc != TLR_OK) {
+        if (status)
+            for (int g = 0; g < count; ++g) status[g] = rc;
+        return rc;
+    }
+    int first = TLR_OK;
+    for (int g = 0; g < count; ++g) {
+        if (status) status[g] = es[(size_t)g].status;
+        if (es[(size_t)g].status != TLR_OK && first == TLR_OK) {
+            first = es[(size_t)g].status;
+            ctx->err = es[(size_t)g].msg;
+        }
+    }
+    return first;
 }
 
 int tlr_loglik(tlr_ctx *ctx, const double *xy, const double *z, int64_t n, tlr_theta theta,

@@ -54,6 +54,23 @@ inline Error make_error(int code, const char *fmt, ...) {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Most factorisations advanced together in one call (tlr_loglik_batch).
+constexpr int kMaxGroup = 32;
+
+// Rank buckets of the compression (tlr_buckets): entries per table, default.
+constexpr int kBuckets = 4;
+inline tlr_buckets default_buckets() {
+    return tlr_buckets{{64, 128, INT32_MAX, INT32_MAX}, {4, 8, 16, 16}, {48, 96, 160, INT32_MAX}, {1, 4, 8, 16}};
+}
+inline bool buckets_ok(const tlr_buckets &b) {
+    auto size_ok = [](int32_t c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16; };
+    for (int k = 0; k < kBuckets; ++k)
+        if (!size_ok(b.qr_size[k]) || !size_ok(b.svd_size[k])) return false;
+    for (int k = 0; k + 1 < kBuckets - 1; ++k)
+        if (b.qr_edge[k] > b.qr_edge[k + 1] || b.svd_edge[k] > b.svd_edge[k + 1]) return false;
+    return b.qr_edge[0] > 0 && b.svd_edge[0] > 0;
+}
+
 // Number of kernels this library has launched (all contexts, all devices).
 extern std::atomic<long long> g_launch_count;
 
@@ -130,7 +147,7 @@ struct tlr_ctx {
     int device = 0;
     int num_sms = 0;
     std::string err;
-    tlr::DevStatus *d_status = nullptr;   // device status word
+    tlr::DevStatus *d_status = nullptr;   // device status words: the context's, then one per grouped factorisation
     tlr::DevStatus *h_status = nullptr;   // pinned host mirror
     cudaStream_t aux = nullptr;           // second stream for concurrent tile work (high priority)
     cudaStream_t la = nullptr;            // look-ahead stream: the next column's panel update
@@ -169,9 +186,11 @@ struct tlr_ctx {
     long long comp_stats[7] = {};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum), QR / SVD jobs on the global-memory kernels
     // the 16-CTA cluster Jacobi (profiling): device ms, FP64 flops, launches, clusters
     std::vector<cudaEvent_t> cls_time_events;
-    double *d_potrf_scratch = nullptr;  // diagonal-block inverses of the cluster POTRF
+    double *d_potrf_scratch = nullptr;  // diagonal-block inverses of the cluster POTRF (per job)
+    int potrf_scratch_jobs = 0;
     double k16_ms = 0.0, k16_flops = 0.0;
     long long k16_launches = 0, k16_clusters = 0;
+    tlr_buckets buckets = tlr::default_buckets();  // compression launch classes by sample size
 };
 
 struct tlr_mat {

@@ -465,6 +465,7 @@ struct SvdJob {
     int *rank;         // #{S > tau}, or -1 if any S is not finite
     int *sweeps;       // [0] FP64 sweeps, [1] FP32 sweeps, [2] FP64 pairs checked, [3] FP64 pairs rotated
     int s;
+    double tau;        // absolute accuracy of the tile
 };
 
 // Fast approximate reciprocal and reciprocal square root of a double (the
@@ -704,14 +705,14 @@ __device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols,
     }
 }
 
-__device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, double tau, int sweeps, int sweeps32) {
+__device__ void jacobi_rank(const SvdJob &J, const double *all_nrm, int sweeps, int sweeps32) {
     J.sweeps[0] = sweeps;
     J.sweeps[1] = sweeps32;
     J.sweeps[2] = J.sweeps[3] = 0;
     int r = 0;
     bool bad = false;
     for (int u = 0; u < J.s; ++u) {
-        r += all_nrm[u] > tau;
+        r += all_nrm[u] > J.tau;
         bad |= !(all_nrm[u] <= 1.7e308);
     }
     *J.rank = bad ? -1 : r;
@@ -740,7 +741,7 @@ constexpr int kRefineSteps = 3;  // FP64 Gram refinement steps after the FP32 sw
 // only, on the M1 found in `work`.
 enum { kJacFull = 0, kJacPrecond = 1, kJacFinish = 2 };
 template <int kCl, int kMode>
-__global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs, double tau) {
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     __shared__ int s_flag[2];
@@ -841,7 +842,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
     __syncthreads();
     jacobi_emit(J, D, gx, gy, b, all_nrm, lane, warp);
     if (rank == 0 && tid == 0) {
-        jacobi_rank(J, all_nrm, tau, sw64, sw32);
+        jacobi_rank(J, all_nrm, sw64, sw32);
         int chk = 0, rot = 0;
         for (int k = 0; k < kCl; ++k) {
             chk += cl.map_shared_rank(s_tally, k)[0];
@@ -907,9 +908,10 @@ struct EmitJob {
     int *rank;
     const unsigned long long *off;
     int s;
+    double tau;
 };
 
-__global__ void __launch_bounds__(kQrThreads) k_svd_emit(const EmitJob *__restrict__ jobs, double tau) {
+__global__ void __launch_bounds__(kQrThreads) k_svd_emit(const EmitJob *__restrict__ jobs) {
     extern __shared__ double nrm[];
     const EmitJob J = jobs[blockIdx.x];
     const int s = J.s, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -936,7 +938,7 @@ __global__ void __launch_bounds__(kQrThreads) k_svd_emit(const EmitJob *__restri
         int r = 0;
         bool bad = false;
         for (int u = 0; u < s; ++u) {
-            r += nrm[u] > tau;
+            r += nrm[u] > J.tau;
             bad |= !(nrm[u] <= 1.7e308);
         }
         const double off = __longlong_as_double((long long)*J.off);
@@ -954,7 +956,7 @@ static size_t jacobi_sm_bytes(int s, int csize) {
 // round are staged in shared memory and written back before the cluster
 // barrier.  Shared memory: two b x s blocks, their 2b squared norms, s norms.
 template <int kCl>
-__global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restrict__ jobs, double tau) {
+__global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     __shared__ int s_flag[2];
@@ -1014,7 +1016,7 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_gm(const SvdJob *__restri
     }
     __syncthreads();
     jacobi_emit(J, Ab, gx, gy, b, all_nrm, lane, warp);
-    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, tau, nsweep, 0);
+    if (rank == 0 && tid == 0) jacobi_rank(J, all_nrm, nsweep, 0);
     cl.sync();  // no CTA leaves while another may still read its flag
 }
 
@@ -1101,13 +1103,21 @@ static bool cluster16_ok() {
     return state == 1;
 }
 
-// Cluster sizes by sample size: the panel work per column shrinks with the
-// cluster, the barrier count does not, so small samples use small clusters.
-static int qr_cluster(int s) { return s <= 64 ? 4 : (s <= 128 ? 8 : 16); }
-static int svd_cluster(int s) { return s <= 48 ? 1 : (s <= 96 ? 4 : (s <= 160 ? 8 : 16)); }
+// Cluster sizes by sample size (the context's rank buckets): the panel work
+// per column shrinks with the cluster, the barrier count does not, so small
+// samples use small clusters.
+static int bucket_size(const int32_t *edge, const int32_t *size, int s) {
+    for (int b = 0; b + 1 < kBuckets; ++b)
+        if (s <= edge[b]) return size[b];
+    return size[kBuckets - 1];
+}
+static int qr_cluster(const tlr_ctx *ctx, int s) { return bucket_size(ctx->buckets.qr_edge, ctx->buckets.qr_size, s); }
+static int svd_cluster(const tlr_ctx *ctx, int s) {
+    return bucket_size(ctx->buckets.svd_edge, ctx->buckets.svd_size, s);
+}
 
 using QrKernel = void (*)(const QrJob *);
-using SvdKernel = void (*)(const SvdJob *, double);
+using SvdKernel = void (*)(const SvdJob *);
 
 template <bool kDf>
 static QrKernel qr_sm_kernel_t(int c) {
@@ -1219,7 +1229,7 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
     std::vector<LaunchClass<QrJob, QrKernel>> cls;
     for (size_t u = 0; u < jobs.size(); ++u) {
         QrJob J = jobs[u];
-        int c = qr_cluster(J.s);
+        int c = qr_cluster(ctx, J.s);
         if (c == 16 && !big) c = 8;
         int top = big ? 16 : 8;
         while (c < top && qr_sm_bytes(J.m, J.s, c) > smem_cap((const void *)qr_sm_kernel(c, df))) c *= 2;
@@ -1245,15 +1255,15 @@ static void qr_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<QrJob> &j
 
 // The SVD stage.  csize_of[u] receives the cluster size job u ran on (0 for
 // the global-memory variant); `timing` (optional) times one cluster size.
-static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs, double tau,
-                       std::vector<int> &csize_of, ClassTiming *timing, int mode) {
+static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> &jobs, std::vector<int> &csize_of,
+                       ClassTiming *timing, int mode) {
     csize_of.assign(jobs.size(), 0);
     const bool big = cluster16_ok();
     const int top = big ? 16 : 8;
     std::vector<LaunchClass<SvdJob, SvdKernel>> cls;
     for (size_t u = 0; u < jobs.size(); ++u) {
         const SvdJob &J = jobs[u];
-        int c = svd_cluster(J.s);
+        int c = svd_cluster(ctx, J.s);
         if (c > top) c = top;
         while (c < top && jacobi_sm_bytes(J.s, c) > smem_cap((const void *)svd_sm_kernel(c, mode))) c = std::max(2 * c, 4);
         SvdKernel k = svd_sm_kernel(c, mode);
@@ -1269,7 +1279,7 @@ static void svd_launch(tlr_ctx *ctx, cudaStream_t st, const std::vector<SvdJob> 
         add_to_class(cls, kg, top, bytes, J);
         ctx->comp_stats[6] += 1;
     }
-    launch_classes(ctx, st, cls, timing, tau);
+    launch_classes(ctx, st, cls, timing);
 }
 
 __global__ void k_gaussian(double *__restrict__ a, int64_t count, uint64_t seed) {
@@ -1299,9 +1309,9 @@ void ensure_omega(tlr_ctx *ctx, cudaStream_t s) {
     split_f2(s, ctx->d_omega, ctx->omega_rows, ctx->omega_rows, ctx->omega_cols, ctx->d_omega2);
 }
 
-void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau,
-                    int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df,
-                    const std::function<void()> &overlap, const GrowSlot &grow, bool tc) {
+void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, std::vector<int> &ranks,
+                   std::vector<int> &fail_order, bool df, const std::function<void()> &overlap, const GrowSlot &grow,
+                   bool tc) {
     const bool dfp = df && !tc;  // paired-FP32 operand copies for the products
     bool overlapped = false;
     ensure_omega(ctx, st);
@@ -1335,8 +1345,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
     } flush{ctx, ev};
     const int nj = (int)jobs.size();
     ranks.assign(nj, 0);
-    *bad_tile = -1;
-    *nan_tile = -1;
+    fail_order.clear();
     std::vector<int> sz(nj), pending;
     for (int q = 0; q < nj; ++q) {
         const CompressJob &J = jobs[q];
@@ -1431,7 +1440,8 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         // 4. SVD of R'
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
-            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u]};
+            sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u],
+                           jobs[pending[u]].tau};
         std::vector<int> svd_csize;
         ClassTiming t16;
         size_t ev_used = 0;
@@ -1440,7 +1450,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             t16.e0 = pooled_event(ctx, ev_used);
             t16.e1 = pooled_event(ctx, ev_used);
         }
-        svd_launch(ctx, st, sv, tau, svd_csize, ctx->profile ? &t16 : nullptr, kJacPrecond);
+        svd_launch(ctx, st, sv, svd_csize, ctx->profile ? &t16 : nullptr, kJacPrecond);
         // FP64 Gram refinement (batched over the tiles), then W, S and the rank
         std::vector<double *> xfin(np, nullptr);
         {
@@ -1467,6 +1477,7 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
                         a.B = X[u]; a.ldb = sz; a.n = sz;
                         a.C = W + oG[u]; a.ldc = sz;
                         gg.push_back(a);
+                        const double tau = jobs[pending[u]].tau;
                         rjobs.push_back(RefineJob{W + oG[u], W + oIA[u], d_off + u, 0.01 * tau * tau, sz});
                         GemmProb b{};
                         b.A = X[u]; b.lda = sz; b.m = sz; b.k = sz;
@@ -1485,11 +1496,11 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
                 }
                 std::vector<EmitJob> ej;
                 for (size_t u : rj) {
-                    ej.push_back(EmitJob{X[u], W + oW[u], W + oS[u], d_rank + u, d_off + u, ps[u]});
+                    ej.push_back(EmitJob{X[u], W + oW[u], W + oS[u], d_rank + u, d_off + u, ps[u], jobs[pending[u]].tau});
                     xfin[u] = X[u];
                 }
                 auto *de = (const EmitJob *)stage_push(ctx, ej.data(), ej.size() * sizeof(EmitJob), st);
-                launch(k_svd_emit, (unsigned)ej.size(), kQrThreads, (size_t)smax * sizeof(double), st, de, tau);
+                launch(k_svd_emit, (unsigned)ej.size(), kQrThreads, (size_t)smax * sizeof(double), st, de);
                 TLR_CHECK_LAUNCH();
             }
         }
@@ -1508,10 +1519,11 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             std::vector<SvdJob> fin;
             for (size_t u = 0; u < np; ++u)
                 if (h_rank[u] == -2)
-                    fin.push_back(SvdJob{W + oR[u], xfin[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u]});
+                    fin.push_back(SvdJob{W + oR[u], xfin[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u],
+                                         jobs[pending[u]].tau});
             if (!fin.empty()) {
                 std::vector<int> cs_fin;
-                svd_launch(ctx, st, fin, tau, cs_fin, nullptr, kJacFinish);
+                svd_launch(ctx, st, fin, cs_fin, nullptr, kJacFinish);
                 TLR_CUDA_TRY(cudaMemcpyAsync(h_rank.data(), d_rank, 5 * np * sizeof(int), cudaMemcpyDeviceToHost, st));
                 TLR_CUDA_TRY(cudaStreamSynchronize(st));
             }
@@ -1555,19 +1567,22 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
             int full = std::min(J.m, J.k);
             int r = h_rank[u];
             if (r < 0) {  // non-finite singular values
-                if (*nan_tile < 0) *nan_tile = J.tile_id;
+                ranks[q] = kCompNan;
+                fail_order.push_back(q);
                 continue;
             }
-            if (r > maxrank) {  // S are lower bounds of the tile's singular values
-                if (*bad_tile < 0) *bad_tile = J.tile_id;
+            if (r > J.maxrank) {  // S are lower bounds of the tile's singular values
+                ranks[q] = kCompBad;
+                fail_order.push_back(q);
                 continue;
             }
             double *Uo = J.U, *Vo = J.V;
-            const int cap = J.cap > 0 ? J.cap : maxrank;
+            const int cap = J.cap > 0 ? J.cap : J.maxrank;
             bool conv = (s >= full) || (r <= s - kSpare);
             if (!conv) {
                 if (s >= kMaxSample) {
-                    if (*bad_tile < 0) *bad_tile = J.tile_id;
+                    ranks[q] = kCompBad;
+                    fail_order.push_back(q);
                     continue;
                 }
                 int want = std::max(2 * s, ((r + kOversample + 7) / 8) * 8);
@@ -1576,7 +1591,8 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
                 continue;
             }
             if (r > cap && !(grow && grow(J, r, &Uo, &Vo))) {
-                if (*bad_tile < 0) *bad_tile = J.tile_id;
+                ranks[q] = kCompBad;
+                fail_order.push_back(q);
                 continue;
             }
             ranks[q] = r;
@@ -1600,6 +1616,23 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         pending.swap(next);
     }
     if (overlap && !overlapped) overlap();  // nothing was compressed
+}
+
+void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau, int maxrank,
+                    std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df,
+                    const std::function<void()> &overlap, const GrowSlot &grow, bool tc) {
+    for (CompressJob &J : jobs) {
+        J.tau = tau;
+        J.maxrank = maxrank;
+    }
+    std::vector<int> fails;
+    compress_jobs(ctx, st, jobs, ranks, fails, df, overlap, grow, tc);
+    *bad_tile = *nan_tile = -1;
+    for (int q : fails) {
+        long long *first = ranks[(size_t)q] == kCompNan ? nan_tile : bad_tile;
+        if (*first < 0) *first = jobs[(size_t)q].tile_id;
+        ranks[(size_t)q] = 0;
+    }
 }
 
 }  // namespace tlr

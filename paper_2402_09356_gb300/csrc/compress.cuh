@@ -23,7 +23,14 @@ struct CompressJob {
     int s_guess;        // expected rank (previous evaluation), drives the first sample size
     long long tile_id;  // i * NT + j, reported on failure
     int cap;            // columns of U / V available (<= 0: maxrank)
+    double tau;         // absolute accuracy (compress_jobs; compress_tiles sets it)
+    int maxrank;        // largest admissible rank (likewise)
+    int item;           // factorisation the tile belongs to (several in one call)
 };
+
+// Job outcomes of compress_jobs other than a rank.
+constexpr int kCompNan = -1;  // the tile holds non-finite values
+constexpr int kCompBad = -2;  // rank above maxrank, unresolved within the sample cap, or no room
 
 // Called with a job whose rank r exceeds its capacity but not maxrank: gives
 // the job new U / V storage for r columns (same leading dimensions), or
@@ -50,5 +57,13 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t s, std::vector<CompressJob> &jobs
                     int maxrank, std::vector<int> &ranks, long long *bad_tile, long long *nan_tile,
                     bool df = false, const std::function<void()> &overlap = nullptr,
                     const GrowSlot &grow = nullptr, bool tc = false);
+
+// The same for jobs that carry their own tau and maxrank (tiles of several
+// factorisations in one call: every launch class serves all of them).
+// ranks[q] receives r, or kCompNan / kCompBad; fail_order lists the failed
+// jobs in the order their failures were found.
+void compress_jobs(tlr_ctx *ctx, cudaStream_t s, std::vector<CompressJob> &jobs, std::vector<int> &ranks,
+                   std::vector<int> &fail_order, bool df = false, const std::function<void()> &overlap = nullptr,
+                   const GrowSlot &grow = nullptr, bool tc = false);
 
 }  // namespace tlr

@@ -148,9 +148,15 @@ __device__ int potrf_diag_block(double *A, int lda, int p, int w, double *Li, do
 // word through which CTA 0 tells the cluster to stop (the context's status
 // word may be set by kernels on other streams at any time, so the CTAs do not
 // each read it to decide).
+// One cluster per job (blockIdx.x / kCl): the diagonal tiles of several
+// factorisations in one launch (the jobs travel in the kernel parameters).
 template <int kCl>
-__global__ void __launch_bounds__(kPotrfThreads)
-k_potrf_inv(double *A, int lda, int m, double *X, int ldx, double *scratch, DevStatus *st, long long row_base) {
+__global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jobs) {
+    const PotrfJob J = jobs.job[blockIdx.x / kCl];
+    double *const A = J.A, *const X = J.X, *const scratch = J.scratch;
+    const int lda = J.lda, m = J.m, ldx = J.ldx;
+    DevStatus *const st = J.st;
+    const long long row_base = J.row_base;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank(), tid = threadIdx.x;
     const int gtid = rank * kPotrfThreads + tid, gthreads = kCl * kPotrfThreads;
@@ -378,11 +384,30 @@ void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int
     }
 }
 
-void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *X, int ldx, long long row_base) {
-    if (m <= 0) return;
-    if (m > kBlk * kBlk) throw make_error(TLR_ERR_ARG, "tile too large for the cluster POTRF (%d)", m);
-    if (!ctx->d_potrf_scratch)
-        TLR_CUDA_TRY(cudaMalloc(&ctx->d_potrf_scratch, ((size_t)kBlk * kBlk * kBlk + 8) * sizeof(double)));
+void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs) {
+    std::vector<PotrfJob> act;
+    for (const PotrfJob &J : jobs) {
+        if (J.m <= 0) continue;
+        if (J.m > kBlk * kBlk) throw make_error(TLR_ERR_ARG, "tile too large for the cluster POTRF (%d)", J.m);
+        act.push_back(J);
+    }
+    if (act.empty()) return;
+    if ((int)act.size() > kMaxGroup) throw make_error(TLR_ERR_ARG, "more than %d diagonal tiles in one launch", kMaxGroup);
+    // scratch per job: the diagonal-block inverses and the cluster's stop word
+    const size_t per = (size_t)kBlk * kBlk * kBlk + 8;
+    if ((int)act.size() > ctx->potrf_scratch_jobs) {
+        if (ctx->d_potrf_scratch) TLR_CUDA_TRY(cudaFree(ctx->d_potrf_scratch));  // syncs the device
+        ctx->d_potrf_scratch = nullptr;
+        ctx->potrf_scratch_jobs = 0;
+        const int want = std::max((int)act.size(), 2 * ctx->potrf_scratch_jobs);
+        TLR_CUDA_TRY(cudaMalloc(&ctx->d_potrf_scratch, per * want * sizeof(double)));
+        ctx->potrf_scratch_jobs = want;
+    }
+    PotrfBatch b{};
+    for (size_t q = 0; q < act.size(); ++q) {
+        b.job[q] = act[q];
+        b.job[q].scratch = ctx->d_potrf_scratch + per * q;
+    }
     static std::once_flag once;
     static int csize = 8;  // 16 CTAs where the device runs such clusters, else 8
     std::call_once(once, [] {
@@ -404,11 +429,13 @@ void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *
         cudaGetLastError();  // clear any error of the queries
     });
     if (csize == 16)
-        launch_clustered(k_potrf_inv<16>, 16, 1, kPotrfThreads, 0, s, A, lda, m, X, ldx, ctx->d_potrf_scratch,
-                         ctx->d_status, row_base);
+        launch_clustered(k_potrf_inv<16>, 16, (int)act.size(), kPotrfThreads, 0, s, b);
     else
-        launch_clustered(k_potrf_inv<8>, 8, 1, kPotrfThreads, 0, s, A, lda, m, X, ldx, ctx->d_potrf_scratch,
-                         ctx->d_status, row_base);
+        launch_clustered(k_potrf_inv<8>, 8, (int)act.size(), kPotrfThreads, 0, s, b);
+}
+
+void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *X, int ldx, long long row_base) {
+    potrf_inv_batched(ctx, s, {PotrfJob{A, lda, m, X, ldx, nullptr, ctx->d_status, row_base}});
 }
 
 // acc[0] += sum_r log A[r, r]  (one block, fixed reduction order); if maxinv

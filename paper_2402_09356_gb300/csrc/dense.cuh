@@ -19,6 +19,23 @@ struct RhsDesc {
 // not written.
 void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *X, int ldx, long long row_base);
 
+// The same for several tiles in one launch (one cluster each); every job
+// reports a non-positive pivot in its own status word st.  scratch is set by
+// the call.
+struct PotrfJob {
+    double *A;
+    int lda, m;
+    double *X;
+    int ldx;
+    double *scratch;
+    DevStatus *st;
+    long long row_base;
+};
+struct PotrfBatch {
+    PotrfJob job[kMaxGroup];
+};
+void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs);
+
 // B <- L^-1 B for every right-hand side matrix (L lower triangular m x m).
 void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int m,
                      const std::vector<RhsDesc> &rhs);

@@ -149,17 +149,15 @@ void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vec
     launch_gemm(ctx, s, ta, tb, probs, alpha, EpiLinear{beta}, df);
 }
 
-void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
-                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df, int max_ctas,
-                         int ctas_per_sm) {
-    if (!tb) throw make_error(TLR_ERR_ARG, "the Matern panel product takes B transposed");
-    EpiMatern e;
-    e.xy = xy;
-    e.n = n;
-    e.P = P;
-    std::vector<GemmProb> big;
-    for (const GemmProb &p : probs) big.push_back(p);
-    // the panel update is one large product: 64 x 64 tiles
+// The panel update is one large product: 64 x 64 tiles.  A capped grid
+// reserves more than half of an SM's shared memory per CTA (unused), so that
+// each of its CTAs holds an SM of its own; ctas_per_sm = k reserves more than
+// 1/(k+1) of it, so that at most k CTAs of this product share an SM and the
+// rest of every SM stays open to the critical-path kernels on the
+// high-priority streams.
+template <class Epi>
+static void launch_matern(tlr_ctx *ctx, cudaStream_t s, const std::vector<GemmProb> &big, double alpha,
+                          const Epi &e, bool df, int max_ctas, int ctas_per_sm) {
     if (big.empty()) return;
     std::vector<int> off(big.size() + 1, 0);
     for (size_t b = 0; b < big.size(); ++b)
@@ -170,11 +168,6 @@ void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vecto
     auto *dt = (const int *)stage_push(ctx, off.data(), off.size() * sizeof(int), s);
     int np = (int)big.size();
     const int grid = max_ctas > 0 ? std::min(total, max_ctas) : total;
-    // A capped grid reserves more than half of an SM's shared memory per CTA
-    // (unused), so that each of its CTAs holds an SM of its own; ctas_per_sm
-    // = k reserves more than 1/(k+1) of it, so that at most k CTAs of this
-    // product share an SM and the rest of every SM stays open to the
-    // critical-path kernels on the high-priority streams.
     size_t smem = 0;
     const int per = max_ctas > 0 ? 1 : ctas_per_sm;
     if (per > 0) {
@@ -187,14 +180,35 @@ void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vecto
         std::lock_guard<std::mutex> lock(mu);
         if (smem > set_to) {
             for (const void *k : {(const void *)k_gemm_df<64, 64, false, true, EpiMatern>,
-                                  (const void *)k_gemm_f64<64, 64, false, true, EpiMatern>})
+                                  (const void *)k_gemm_f64<64, 64, false, true, EpiMatern>,
+                                  (const void *)k_gemm_df<64, 64, false, true, EpiMaternMulti>,
+                                  (const void *)k_gemm_f64<64, 64, false, true, EpiMaternMulti>})
                 TLR_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             set_to = smem;
         }
     }
-    if (df) launch(k_gemm_df<64, 64, false, true, EpiMatern>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
-    else launch(k_gemm_f64<64, 64, false, true, EpiMatern>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
+    if (df) launch(k_gemm_df<64, 64, false, true, Epi>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
+    else launch(k_gemm_f64<64, 64, false, true, Epi>, grid, kGemmThreads, smem, s, dp, dt, np, total, alpha, e);
     TLR_CHECK_LAUNCH();
+}
+
+void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
+                         double alpha, const double *xy, int64_t n, const MaternParams &P, bool df, int max_ctas,
+                         int ctas_per_sm) {
+    if (!tb) throw make_error(TLR_ERR_ARG, "the Matern panel product takes B transposed");
+    EpiMatern e;
+    e.xy = xy;
+    e.n = n;
+    e.P = P;
+    launch_matern(ctx, s, probs, alpha, e, df, max_ctas, ctas_per_sm);
+}
+
+void gemm_batched_matern_multi(tlr_ctx *ctx, cudaStream_t s, const std::vector<GemmProb> &probs, double alpha,
+                               const std::vector<MaternItem> &items, bool df, int ctas_per_sm) {
+    if (probs.empty() || items.empty()) return;
+    EpiMaternMulti e;
+    e.items = (const MaternItem *)stage_push(ctx, items.data(), items.size() * sizeof(MaternItem), s);
+    launch_matern(ctx, s, probs, alpha, e, df, 0, ctas_per_sm);
 }
 
 }  // namespace tlr

@@ -24,6 +24,7 @@ struct GemmProb {
     int64_t ri0, ci0;  // epilogue data: first global row / column index
     const float2 *A2;  // paired-FP32 copies of A and B (same layout), for k_gemm_df
     const float2 *B2;
+    int item;          // EpiMaternMulti: the factorisation whose covariance the problem holds
 };
 
 constexpr int kGemmBK = 16, kGemmThreads = 256;
@@ -47,6 +48,25 @@ struct EpiMatern {
         int64_t gr = p.ri0 + r, gc = p.ci0 + c;
         if (gr >= n || gc >= n) return 0.0;
         return matern_cov(xy[gr], xy[n + gr], xy[gc], xy[n + gc], P) + ab;
+    }
+};
+
+// The Matern epilogue for the panels of several factorisations in one
+// launch: problem p takes its locations and parameters from items[p.item]
+// (the same arithmetic as EpiMatern).
+struct MaternItem {
+    const double *xy;
+    int64_t n;
+    MaternParams P;
+};
+struct EpiMaternMulti {
+    const MaternItem *items;
+    __device__ __forceinline__ double operator()(const GemmProb &p, int r, int c, double ab,
+                                                 const double *) const {
+        const MaternItem &it = items[p.item];
+        const int64_t n = it.n, gr = p.ri0 + r, gc = p.ci0 + c;
+        if (gr >= n || gc >= n) return 0.0;
+        return matern_cov(it.xy[gr], it.xy[n + gr], it.xy[gc], it.xy[n + gc], it.P) + ab;
     }
 };
 
@@ -301,5 +321,9 @@ void gemm_batched(tlr_ctx *ctx, cudaStream_t s, bool ta, bool tb, const std::vec
 void gemm_batched_matern(tlr_ctx *ctx, cudaStream_t s, bool tb, const std::vector<GemmProb> &probs,
                          double alpha, const double *xy, int64_t n, const MaternParams &P, bool df = false,
                          int max_ctas = 0, int ctas_per_sm = 0);
+// The same for problems of several factorisations (problem b generates from
+// items[b.item]; the table is copied to the device on s).
+void gemm_batched_matern_multi(tlr_ctx *ctx, cudaStream_t s, const std::vector<GemmProb> &probs, double alpha,
+                               const std::vector<MaternItem> &items, bool df, int ctas_per_sm = 0);
 
 }  // namespace tlr

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <functional>
+#include <string>
 
 #include "common.cuh"
 #include "matern.cuh"
@@ -73,6 +74,35 @@ void factor(tlr_ctx *ctx, cudaStream_t s, tlr_mat *M, FactorMode mode, const dou
             const MaternParams *P, double tau, FactorStats *stats, long long *info,
             const double *z = nullptr, double *y = nullptr, double *acc = nullptr, bool df = false,
             bool tc = false);
+
+// One factorisation of a group advanced together by factor_group.
+struct FactorItem {
+    tlr_mat *M = nullptr;
+    const double *xy = nullptr;       // Matern mode: ordered locations (device, SoA)
+    const MaternParams *P = nullptr;  // Matern mode: parameters with their table built
+    double tau = 0.0;                 // absolute compression accuracy
+    FactorStats *stats = nullptr;     // the first item's also receives the call's profiling times
+    long long *info = nullptr;
+    const double *z = nullptr;        // fused solve (optional), as for factor
+    double *y = nullptr;
+    double *acc = nullptr;
+    int err = TLR_OK;                 // output: the status that stopped this factorisation
+    std::string msg;
+};
+
+// The factorisations of `items` (at most kMaxGroup; one only in Tlr mode)
+// column by column in lockstep on one context: every step of column j is one
+// launch for all of them (panel products and generation, diagonal POTRF
+// clusters, every compression launch class, V <- L^-1 V, Gram matrices), so
+// the uneven-rank tiles of several factorisations share each launch.  Each
+// factorisation computes exactly what factor would compute for it alone.
+// A factorisation that meets a non-positive pivot, a non-finite tile or a
+// rank that does not fit stops with err / msg / *info set; the others go on.
+// Status words: with one item the context's word; with G > 1 items, word
+// 1 + g of ctx->d_status for item g (the caller resets words 0..G), word 0
+// for device-wide failures, which stop the call with an exception.
+void factor_group(tlr_ctx *ctx, cudaStream_t s, std::vector<FactorItem> &items, FactorMode mode, bool df,
+                  bool tc);
 void forward_solve(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *z, double *y,
                    double *acc);
 void lmul(tlr_ctx *ctx, cudaStream_t s, const tlr_mat *M, const double *w, double *z);
