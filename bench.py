@@ -815,6 +815,16 @@ def run_ordering_study(args):
 
 BATCH_BUCKETS = ((2000, 5000), (5000, 10000), (10000, 20001))
 BATCH_TILE_CANDIDATES = (384, 512, 800, 1024)
+# rank buckets of the compression (tlr_buckets): the default (latency: large
+# clusters for large samples) and a throughput map (half the CTAs per tile)
+BUCKETS_DEFAULT = {"qr_edge": [64, 128, 2 ** 31 - 1, 2 ** 31 - 1], "qr_size": [4, 8, 16, 16],
+                   "svd_edge": [48, 96, 160, 2 ** 31 - 1], "svd_size": [1, 4, 8, 16]}
+BUCKETS_THROUGHPUT = {"qr_edge": [64, 128, 2 ** 31 - 1, 2 ** 31 - 1], "qr_size": [2, 4, 8, 8],
+                      "svd_edge": [48, 96, 160, 2 ** 31 - 1], "svd_size": [1, 2, 4, 8]}
+# (group size, buckets) candidates of the batched workload's autotuner
+BATCH_CANDIDATES = ((1, "default"), (2, "default"), (4, "default"), (8, "default"), (16, "default"),
+                    (1, "throughput"), (8, "throughput"))
+BUCKET_MAPS = {"default": BUCKETS_DEFAULT, "throughput": BUCKETS_THROUGHPUT}
 
 
 def batched_datasets(count: int, seed: int = 2024):
@@ -872,22 +882,39 @@ def run_batched(args):
         z_white += 0 if ok else 1
     zctx.close()
 
-    def new_pool():
+    def new_pool(cfg):
         # every path gets a pool of its own, so that each dataset's rank-map
         # history (the compression's sample sizes) comes from that path alone
         pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
+        tlr.tlr_pool_configure(pool, cfg[0], BUCKET_MAPS[cfg[1]])
         ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(int(sizes[i]), seed=10 + i), zs[i], "morton",
                                 nb=tuned[bucket_of[i]]["best_nb"]) for i in range(count)]
         return pool, ids
 
+    # group size and rank buckets: the pool's throughput autotuner on every
+    # fourth dataset (mixed path; each candidate evaluates the subset twice)
+    pool, ids = new_pool((1, "default"))
+    sub_ids = ids[::4]
+    best, rates = tlr.tlr_pool_autotune(pool, sub_ids, [tuple(th0[i]) for i in range(0, count, 4)],
+                                        [(g, BUCKET_MAPS[b]) for g, b in BATCH_CANDIDATES], eps=EPS,
+                                        precision=tlr.TLR_PREC_MIXED, rounds=2)
+    pool.close()
+    cfg_tuned = BATCH_CANDIDATES[best]
+    autotune = {"subset": len(sub_ids), "rounds": 2, "precision": "mixed", "chosen": list(cfg_tuned),
+                "evals_per_s": {"group %d, %s buckets" % c: r for c, r in zip(BATCH_CANDIDATES, rates)},
+                "buckets": BUCKET_MAPS}
     setup_s = time.perf_counter() - t_setup
     walks = [synth.theta_walk(tuple(th0[i]), args.warmup + args.steps, seed=900 + i, scale=0.05) for i in range(count)]
     out = {}
     clocks_all = {}
-    paths = (("fp64", tlr.TLR_PREC_FP64), ("mixed", tlr.TLR_PREC_MIXED), ("auto", tlr.TLR_PREC_AUTO))
+    # every path with the tuned configuration, and the mixed path once more
+    # with the untuned one (group 1, default buckets) for comparison
+    paths = (("fp64", tlr.TLR_PREC_FP64, cfg_tuned), ("mixed", tlr.TLR_PREC_MIXED, cfg_tuned),
+             ("tensor", tlr.TLR_PREC_TENSOR, cfg_tuned), ("auto", tlr.TLR_PREC_AUTO, cfg_tuned),
+             ("mixed_untuned", tlr.TLR_PREC_MIXED, (1, "default")))
     pool_stats = {}
-    for name, prec in paths:
-        pool, ids = new_pool()
+    for name, prec, cfg in paths:
+        pool, ids = new_pool(cfg)
         for k in range(args.warmup):
             tlr.tlr_pool_loglik(pool, ids, [tuple(w[k]) for w in walks], eps=EPS, precision=prec)
         clocks = ClockSampler(0)
@@ -931,6 +958,11 @@ def run_batched(args):
 
     rel, pairs = compare("mixed")
     rel_auto, _ = compare("auto")
+    rel_tensor, _ = compare("tensor")
+    # the tuned and untuned mixed pools compute the same results up to the
+    # buckets' rounding (group size alone changes nothing)
+    same_untuned = [a == b for ra, rb in zip(out["mixed"]["results"], out["mixed_untuned"]["results"])
+                    for a, b in zip(ra, rb)]
     # calibration of the auto rule: worst mixed-vs-FP64 difference among the
     # evaluations whose smallest squared pivot (/ sigma2) is at least t
     calib = {("%g" % t): {"kept": sum(1 for p in pairs if p[1] >= t),
@@ -943,30 +975,40 @@ def run_batched(args):
                 "by_min_pivot2": calib, **compare.extra["mixed"]}
     accuracy_auto = {"pairs": len(rel_auto), "within_1e-6": int(sum(1 for r in rel_auto if r <= 1e-6)),
                      "max": max(rel_auto) if rel_auto else None, **compare.extra["auto"]}
+    accuracy_tensor = {"pairs": len(rel_tensor), "within_1e-6": int(sum(1 for r in rel_tensor if r <= 1e-6)),
+                       "max": max(rel_tensor) if rel_tensor else None, **compare.extra["tensor"]}
     st = pool_stats
     # the fastest path whose every evaluated pair is within 1e-6 of the FP64 path
-    ok = [nm for nm, r in (("mixed", rel), ("auto", rel_auto)) if r and max(r) <= 1e-6]
+    ok = [nm for nm, r in (("mixed", rel), ("tensor", rel_tensor), ("auto", rel_auto)) if r and max(r) <= 1e-6]
     head = max(ok, key=lambda nm: out[nm]["evals_per_s"]) if ok else "fp64"
     line = {"metric": "batched TLR l(theta) evals/s, %d datasets n~U[2000,20000]" % count,
             "value": out[head]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * out[head]["s_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if head == "fp64" else "f64 storage, paired-f32 products", "data": "synthetic",
+            "dtype": {"fp64": "f64", "tensor": "f64 storage, bf16-slice tensor-core panel products"}.get(
+                head, "f64 storage, paired-f32 products"), "data": "synthetic",
             "config": {"workload": "batched: %d datasets, n ~ U[2000, 20000] jittered grids, theta ~ U(sigma2 "
                                    "[0.5,2], beta [0.02,0.3], nu [0.5,2.5]), Z = L(theta) w, Morton, eps %g, "
-                                   "%d workers" % (count, EPS, args.workers),
+                                   "%d workers, group %d, %s buckets" % (count, EPS, args.workers, cfg_tuned[0],
+                                                                         cfg_tuned[1]),
                        "z": "Z = L(theta_i) w_i from the library's TLR factor at eps 1e-9 (tile 512); "
                             "%d datasets too ill-conditioned for it kept Z = w" % z_white,
                        "precision": head, "workers": args.workers, "maxrank": args.maxrank,
                        "tile_autotune": {str(BATCH_BUCKETS[b]): v for b, v in tuned.items()},
+                       "group_bucket_autotune": autotune,
                        "timing": "host wall clock around each blocking tlr_pool_loglik (all datasets)",
                        "l2": "inputs (all datasets' factors) larger than L2"},
             "fp64_path": {k: v for k, v in out["fp64"].items() if k != "results"},
             "mixed_path": {k: v for k, v in out["mixed"].items() if k != "results"},
             "auto_path": {k: v for k, v in out["auto"].items() if k != "results"},
+            "tensor_path": {k: v for k, v in out["tensor"].items() if k != "results"},
+            "mixed_untuned_path": {k: v for k, v in out["mixed_untuned"].items() if k != "results"},
+            "tuned_over_untuned": out["mixed"]["evals_per_s"] / out["mixed_untuned"]["evals_per_s"],
+            "mixed_tuned_equal_untuned": "%d of %d results bit for bit" % (sum(same_untuned), len(same_untuned)),
             "rel_dl_mixed_vs_fp64_max": max(rel) if rel else None,
             "mixed_vs_fp64": accuracy,
             "auto_vs_fp64": accuracy_auto,
+            "tensor_vs_fp64": accuracy_tensor,
             "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
             "gpu_launches": out[head]["gpu_launches"]}
     print(json.dumps(line), flush=True)

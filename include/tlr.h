@@ -572,6 +572,35 @@ int tlr_pool_mle(tlr_pool *p, int id, double eps, int precision, tlr_theta theta
 int tlr_pool_tune(tlr_pool *p, int id, tlr_theta theta, double eps, int precision, const int32_t *cands,
                   int ncand, int32_t *best, double *ms);
 
+/* Batched launches and rank buckets of the pool's workers.  group (1..32):
+ * a worker that admits a request also admits, up to `group` in all, the
+ * queued requests of the same precision that can start now (each under the
+ * admission rules above, in queue order), and evaluates them together with
+ * tlr_loglik_batch: each step of their factorisations' tile columns is one
+ * launch for all of them.  buckets (NULL: the default) become the rank
+ * buckets (tlr_ctx_set_buckets) of every worker's context.  Applies to
+ * requests admitted after the call; results do not depend on group (every
+ * result is the one tlr_loglik gives), and the buckets change them only by
+ * rounding.  Default: group 1, default buckets.  Errors: TLR_ERR_ARG. */
+int tlr_pool_configure(tlr_pool *p, int group, const tlr_buckets *buckets);
+
+/* The pool's current group size and buckets (either output may be NULL). */
+int tlr_pool_get_config(tlr_pool *p, int *group, tlr_buckets *buckets);
+
+/* Throughput autotuner of the batched workload (rank-bucket and group-size
+ * tuning): the `count` requests (ids[i], theta[i]) at eps / precision are
+ * evaluated once at the current configuration (which also sets the rank
+ * maps every candidate then starts from), then `rounds` times under each
+ * candidate c (group size groups[c], buckets[c]; buckets NULL keeps the
+ * current buckets), timed on the host clock from the first submission to
+ * the last result.  evals_per_s[c] (may be NULL) receives each candidate's
+ * successful evaluations per second; the pool keeps the fastest candidate,
+ * whose index goes to *best.  The datasets keep the rank maps of their last
+ * evaluation.  Errors: TLR_ERR_ARG (bad candidates or unknown datasets). */
+int tlr_pool_autotune(tlr_pool *p, int count, const int *ids, const tlr_theta *theta, double eps, int precision,
+                      int ncand, const int32_t *groups, const tlr_buckets *buckets, int rounds,
+                      double *evals_per_s, int *best);
+
 /* Device bytes the admission model charges for a dataset of n locations at
  * tile size nb and rank slots maxrank (<= 0: nb / 2), written to out[0..2]:
  * resident data (32 n: locations, observations, permutation), TLR factor
@@ -582,10 +611,11 @@ int tlr_pool_tune(tlr_pool *p, int id, tlr_theta theta, double eps, int precisio
 int tlr_pool_footprint(int64_t n, int nb, int maxrank, int64_t *out);
 
 /* Counters, written to out[0..count) (returns the number written, at most
- * 12): budget, bytes in use, peak bytes in use, resident dataset bytes,
+ * 14): budget, bytes in use, peak bytes in use, resident dataset bytes,
  * resident factor bytes, resident factors, evictions, requests completed,
  * requests queued, requests running, most requests running at once, factor
- * allocations.  Byte figures follow the admission model (factor storage
+ * allocations, group evaluations run (more than one request), requests
+ * those held.  Byte figures follow the admission model (factor storage
  * exact, workspace estimated). */
 int tlr_pool_stats(tlr_pool *p, int64_t *out, int count);
 

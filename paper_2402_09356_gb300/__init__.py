@@ -155,6 +155,12 @@ _SIGS = {
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
     "tlr_pool_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, tlr_theta, ctypes.c_double, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
+    "tlr_pool_configure": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "tlr_pool_get_config": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(tlr_buckets)]),
+    "tlr_pool_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_int)]),
     "tlr_pool_footprint": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "tlr_pool_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "tlr_sched_simulate": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
@@ -628,7 +634,8 @@ def tlr_mle(mat: TlrMatrix, xy, z, opts: Options, theta0, lo, hi, tol: float = 1
 # ---- many datasets: batched evaluation and serving ----------------------------
 
 POOL_STATS = ("budget", "used", "peak", "resident_data_bytes", "resident_factor_bytes", "resident_factors",
-              "evictions", "completed", "queued", "running", "max_running", "allocations")
+              "evictions", "completed", "queued", "running", "max_running", "allocations", "groups",
+              "grouped_requests")
 
 
 def _pool_check(rc: int):
@@ -771,6 +778,43 @@ def tlr_pool_tune(pool: Pool, id: int, theta, cands, eps: float = 1e-7, precisio
     _pool_check(load_library().tlr_pool_tune(pool.h, int(id), _theta(theta), float(eps), int(precision), ca, k,
                                              ctypes.byref(best), ms))
     return best.value, {int(cands[i]): ms[i] for i in range(k)}
+
+
+def _buckets(b):
+    if b is None or isinstance(b, tlr_buckets):
+        return b
+    return tlr_buckets(*[(ctypes.c_int32 * 4)(*[int(v) for v in b[f]]) for f, _ in tlr_buckets._fields_])
+
+
+def tlr_pool_configure(pool: Pool, group: int = 1, buckets=None):
+    """Requests a worker evaluates together (tlr_loglik_batch) and the rank
+    buckets of every worker's context (None: the default)."""
+    b = _buckets(buckets)
+    _pool_check(load_library().tlr_pool_configure(pool.h, int(group), None if b is None else ctypes.byref(b)))
+
+
+def tlr_pool_get_config(pool: Pool) -> dict:
+    g, b = ctypes.c_int(), tlr_buckets()
+    _pool_check(load_library().tlr_pool_get_config(pool.h, ctypes.byref(g), ctypes.byref(b)))
+    return {"group": g.value, "buckets": b.as_dict()}
+
+
+def tlr_pool_autotune(pool: Pool, ids, thetas, candidates, eps: float = 1e-7, precision: int = TLR_PREC_FP64,
+                      rounds: int = 1):
+    """Throughput tuning over candidates [(group, buckets or None), ...] on the
+    requests (ids[i], thetas[i]); the pool keeps the fastest.  Returns
+    (best index, evals/s per candidate)."""
+    k, c = len(ids), len(candidates)
+    ia = (ctypes.c_int * k)(*[int(i) for i in ids])
+    ta = (tlr_theta * k)(*[_theta(t) for t in thetas])
+    ga = (ctypes.c_int32 * c)(*[int(g) for g, _ in candidates])
+    cur = tlr_pool_get_config(pool)["buckets"]
+    ba = (tlr_buckets * c)(*[_buckets(b if b is not None else cur) for _, b in candidates])
+    rates = (ctypes.c_double * c)()
+    best = ctypes.c_int()
+    _pool_check(load_library().tlr_pool_autotune(pool.h, k, ia, ta, float(eps), int(precision), c, ga, ba,
+                                                 int(rounds), rates, ctypes.byref(best)))
+    return best.value, [rates[i] for i in range(c)]
 
 
 def tlr_pool_footprint(n: int, nb: int, maxrank: int = 0) -> dict:

@@ -630,18 +630,6 @@ static void loglik_impl(tlr_ctx *ctx, const double *xy, const double *z, int64_t
     out->ms_total += ms_mixed;
 }
 
-// One entry of a batched evaluation (tlr_loglik_batch).
-struct BatchEntry {
-    const double *xy, *z;
-    int64_t n;
-    tlr_theta theta;
-    const tlr_opts *opts;
-    tlr_mat *L;
-    tlr_result *out;
-    int status = TLR_OK;
-    std::string msg;
-};
-
 static bool per_entry_error(int code) {
     return code == TLR_ERR_NOT_SPD || code == TLR_ERR_RANK || code == TLR_ERR_NAN;
 }
@@ -775,6 +763,27 @@ static void loglik_group(tlr_ctx *ctx, std::vector<BatchEntry> &es, cudaStream_t
     }
 }
 
+}  // extern "C"
+
+void tlr::loglik_batch(tlr_ctx *ctx, std::vector<BatchEntry> &es, cudaStream_t s) {
+    const int count = (int)es.size();
+    check_arg(count >= 1 && count <= kMaxGroup, "count must be 1..32");
+    for (int g = 0; g < count; ++g) {
+        const BatchEntry &e = es[(size_t)g];
+        const tlr_opts *o = e.opts;
+        check_arg(e.xy && e.z && e.L && e.opts && e.out, "xy[g]/z[g]/L[g]/opts/out");
+        check_arg(e.n > 0 && e.L->n == e.n && e.L->nb == o->nb, "L[g] does not match n[g]/nb");
+        check_arg(o->eps >= 0 && std::isfinite(o->eps), "eps");
+        check_arg(o->precision == es[0].opts->precision, "one precision for all entries");
+        check_arg(o->precision == TLR_PREC_FP64 || o->precision == TLR_PREC_MIXED || o->precision == TLR_PREC_AUTO ||
+                      o->precision == TLR_PREC_TENSOR, "precision");
+        for (int h = 0; h < g; ++h) check_arg(es[(size_t)h].L != e.L, "every entry needs its own L");
+    }
+    loglik_group(ctx, es, s);
+}
+
+extern "C" {
+
 int tlr_loglik_batch(tlr_ctx *ctx, int count, const double *const *xy, const double *const *z, const int64_t *n,
                      const tlr_theta *theta, const tlr_opts *opts, tlr_mat *const *L, tlr_result *out, int *status,
                      void *stream) {
@@ -783,25 +792,17 @@ int tlr_loglik_batch(tlr_ctx *ctx, int count, const double *const *xy, const dou
         check_arg(count >= 1 && count <= kMaxGroup, "count must be 1..32");
         check_arg(xy && z && n && theta && opts && L && out, "xy/z/n/theta/opts/L/out");
         for (int g = 0; g < count; ++g) {
-            const tlr_opts *o = opts + g;
-            check_arg(xy[g] && z[g] && L[g], "xy[g]/z[g]/L[g]");
-            check_arg(n[g] > 0 && L[g]->n == n[g] && L[g]->nb == o->nb, "L[g] does not match n[g]/nb");
-            check_arg(o->eps >= 0 && std::isfinite(o->eps), "eps");
-            check_arg(o->precision == opts[0].precision, "one precision for all entries");
-            check_arg(o->precision == TLR_PREC_FP64 || o->precision == TLR_PREC_MIXED ||
-                          o->precision == TLR_PREC_AUTO || o->precision == TLR_PREC_TENSOR, "precision");
-            for (int h = 0; h < g; ++h) check_arg(L[h] != L[g], "every entry needs its own L");
             BatchEntry e{};
             e.xy = xy[g];
             e.z = z[g];
             e.n = n[g];
             e.theta = theta[g];
-            e.opts = o;
+            e.opts = opts + g;
             e.L = L[g];
             e.out = out + g;
             es.push_back(e);
         }
-        loglik_group(ctx, es, (cudaStream_t)stream);
+        loglik_batch(ctx, es, (cudaStream_t)stream);
     });
     if (rc != TLR_OK) {
         if (status)

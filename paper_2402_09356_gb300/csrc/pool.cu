@@ -99,6 +99,13 @@ struct Worker {
     cudaStream_t stream = nullptr;
 };
 
+// Tuning of a pool (tlr_pool_configure): requests a worker evaluates
+// together, and the rank buckets of every worker's context.
+struct PoolConfig {
+    int group = 1;
+    tlr_buckets buckets = default_buckets();
+};
+
 int pool_fail(int code, const std::string &msg) {
     t_pool_err = msg;
     return code;
@@ -124,6 +131,8 @@ struct tlr_pool {
     std::unordered_map<int64_t, std::unique_ptr<PoolReq>> reqs;
     int64_t next_ticket = 1;
     int64_t completed = 0, running = 0, max_running = 0, allocations = 0, resident_bytes = 0;
+    int64_t groups = 0, grouped = 0;  // group evaluations run, requests they held
+    PoolConfig cfg;
     std::vector<Worker> workers;
     std::vector<std::thread> threads;
 };
@@ -169,122 +178,205 @@ void mat_free(tlr_mat *M, cudaStream_t s) {
     delete M;
 }
 
+// One admitted request of a worker's group.
+struct Run {
+    Admission::Req ar{};
+    bool alloc = false;
+    PoolReq *r = nullptr;
+    PoolData *d = nullptr;
+    std::vector<tlr_mat *> to_free;
+    int status = TLR_OK;
+    std::string err;
+    std::vector<int32_t> hint;
+    bool ran = false;
+    int64_t extra = 0;  // storage charged for a retry on uniform slots
+    double pivot2 = 0.0;
+    tlr_opts o{};
+};
+
 void worker_main(tlr_pool *p, int w) {
     Worker &W = p->workers[(size_t)w];
     cudaSetDevice(p->device);
     std::unique_lock<std::mutex> lk(p->mu);
     for (;;) {
-        Admission::Req ar{};
-        bool alloc = false;
+        std::vector<Run> runs(1);
         std::vector<int> evicted;
-        while (!p->adm.admit(&ar, &alloc, &evicted)) {
+        while (!p->adm.admit(&runs[0].ar, &runs[0].alloc, &evicted)) {
             if (p->stop && p->adm.queued() == 0) return;
             p->cv_work.wait(lk);
         }
-        PoolReq *r = p->reqs[ar.ticket].get();
-        PoolData *d = p->data[ar.data].get();
+        // companions: queued requests of the same precision that can start
+        // now, evaluated together with the first (tlr_loglik_batch)
+        const PoolConfig cfg = p->cfg;
+        const int prec = p->reqs[runs[0].ar.ticket]->precision;
+        auto same_path = [&](const Admission::Req &q) { return p->reqs[q.ticket]->precision == prec; };
+        for (;;) {
+            if ((int)runs.size() >= cfg.group) break;
+            Run next;
+            if (!p->adm.admit(&next.ar, &next.alloc, &evicted, same_path)) break;
+            runs.push_back(std::move(next));
+        }
+        for (Run &u : runs) {
+            u.r = p->reqs[u.ar.ticket].get();
+            u.d = p->data[u.ar.data].get();
+            u.r->t_start = Clock::now();
+            p->max_running = std::max(p->max_running, ++p->running);
+            if (u.alloc) ++p->allocations;
+        }
         std::vector<tlr_mat *> to_free;
         for (int e : evicted) {
             PoolData *v = p->data[e].get();
             to_free.push_back(v->L);
             v->L = nullptr;
         }
-        r->t_start = Clock::now();
-        p->max_running = std::max(p->max_running, ++p->running);
-        if (alloc) ++p->allocations;
         lk.unlock();
 
         // The evicted factors' last requests have finished (their workers
         // synced), so their storage is free to go on this worker's stream.
         for (tlr_mat *M : to_free) mat_free(M, W.stream);
-        int status = TLR_OK;
-        std::string err;
-        std::vector<int32_t> hint;
-        bool ran = false;
-        int64_t extra = 0;  // storage charged for a retry on uniform slots
-        if (alloc && !d->L) d->L = mat_alloc(p, d->n, d->nb, d->maxrank, d->hint, W.stream);
-        tlr_opts o{};
-        o.nb = d->nb;
-        o.maxrank = d->maxrank;
-        o.eps = r->eps;
-        o.precision = r->precision;
-        double pivot2 = d->pivot2;
-        auto evaluate = [&](tlr_mat *M) {
+        W.ctx->buckets = cfg.buckets;
+        for (Run &u : runs) {
+            PoolData *d = u.d;
+            if (u.alloc && !d->L) d->L = mat_alloc(p, d->n, d->nb, d->maxrank, d->hint, W.stream);
+            u.o.nb = d->nb;
+            u.o.maxrank = d->maxrank;
+            u.o.eps = u.r->eps;
+            u.o.precision = u.r->precision;
+            u.pivot2 = d->pivot2;
+            if (!d->L) {
+                u.status = TLR_ERR_OOM;
+                u.err = "cannot allocate the factor storage of dataset " + std::to_string(d->id);
+            }
+        }
+        auto evaluate = [&](Run &u, tlr_mat *M) {
+            PoolData *d = u.d;
             M->h_ranks = d->hint;
             M->last_pivot2 = d->pivot2;
-            status = tlr_loglik(W.ctx, d->xy, d->z, d->n, r->theta, &o, M, &r->res, W.stream);
-            err = status != TLR_OK ? std::string(tlr_last_error(W.ctx)) : std::string();
-            hint = M->h_ranks;
-            pivot2 = M->last_pivot2;
-            ran = true;
+            u.status = tlr_loglik(W.ctx, d->xy, d->z, d->n, u.r->theta, &u.o, M, &u.r->res, W.stream);
+            u.err = u.status != TLR_OK ? std::string(tlr_last_error(W.ctx)) : std::string();
+            u.hint = M->h_ranks;
+            u.pivot2 = M->last_pivot2;
+            u.ran = true;
         };
-        if (!d->L) {
-            status = TLR_ERR_OOM;
-            err = "cannot allocate the factor storage of dataset " + std::to_string(d->id);
-        } else {
-            evaluate(d->L);
-            if (status == TLR_ERR_RANK && d->L->cap_overflow) {
-                // the compact slots (sized by the last rank map) ran out of
-                // room: the same evaluation, from the same rank map, on
-                // uniform maxrank slots (held only for this request).  The
-                // difference in storage is charged to the budget first,
-                // waiting for running requests or evicting idle factors.
-                const int64_t need = factor_bytes(d->n, d->nb, d->maxrank, {}) - (int64_t)d->L->bytes;
-                std::vector<int> ev2;
-                bool never = false, got = false;
-                std::vector<tlr_mat *> free2;
-                lk.lock();
-                while (!(got = p->adm.grow(ar.data, need, &ev2, &never)) && !never) p->cv_done.wait(lk);
-                for (int e : ev2) {
-                    PoolData *v = p->data[e].get();
-                    free2.push_back(v->L);
-                    v->L = nullptr;
+        {
+            std::vector<Run *> go;
+            for (Run &u : runs)
+                if (u.d->L) go.push_back(&u);
+            if (go.size() == 1) {
+                evaluate(*go[0], go[0]->d->L);
+            } else if (go.size() > 1) {
+                std::vector<BatchEntry> es;
+                for (Run *u : go) {
+                    PoolData *d = u->d;
+                    d->L->h_ranks = d->hint;
+                    d->L->last_pivot2 = d->pivot2;
+                    BatchEntry e;
+                    e.xy = d->xy;
+                    e.z = d->z;
+                    e.n = d->n;
+                    e.theta = u->r->theta;
+                    e.opts = &u->o;
+                    e.L = d->L;
+                    e.out = &u->r->res;
+                    es.push_back(e);
                 }
-                lk.unlock();
-                for (tlr_mat *M : free2) mat_free(M, W.stream);
-                if (got) {
-                    extra = std::max<int64_t>(need, 0);
-                    mat_free(d->L, W.stream);
-                    d->L = mat_alloc(p, d->n, d->nb, d->maxrank, {}, W.stream);
-                    if (d->L) {
-                        evaluate(d->L);
-                    } else {
-                        status = TLR_ERR_OOM;
-                        err = "cannot allocate uniform factor storage after a slot overflow";
-                    }
-                } else {
-                    status = TLR_ERR_OOM;
-                    err = "uniform factor storage after a slot overflow exceeds the HBM budget";
+                int call = TLR_OK;
+                std::string call_err;
+                try {
+                    loglik_batch(W.ctx, es, W.stream);
+                } catch (const Error &e) {
+                    call = e.code;
+                    call_err = e.msg;
+                } catch (const std::exception &e) {
+                    call = TLR_ERR_CUDA;
+                    call_err = e.what();
+                }
+                for (size_t g = 0; g < go.size(); ++g) {
+                    Run &u = *go[g];
+                    u.status = call != TLR_OK ? call : es[g].status;
+                    u.err = call != TLR_OK ? call_err : es[g].msg;
+                    u.hint = u.d->L->h_ranks;
+                    u.pivot2 = u.d->L->last_pivot2;
+                    u.ran = true;
                 }
             }
         }
-        // uniform storage (first request, or after an overflow) is given back;
-        // the next request allocates compact slots from the new rank map
-        tlr_mat *drop = (d->L && d->L->base_off.empty()) ? d->L : nullptr;
-        if (drop) {
-            mat_free(drop, W.stream);
-            d->L = nullptr;
+        for (Run &u : runs) {
+            PoolData *d = u.d;
+            if (!(d->L && u.status == TLR_ERR_RANK && d->L->cap_overflow)) continue;
+            // the compact slots (sized by the last rank map) ran out of
+            // room: the same evaluation, from the same rank map, on
+            // uniform maxrank slots (held only for this request).  The
+            // difference in storage is charged to the budget first,
+            // waiting for running requests or evicting idle factors.
+            const int64_t need = factor_bytes(d->n, d->nb, d->maxrank, {}) - (int64_t)d->L->bytes;
+            std::vector<int> ev2;
+            bool never = false, got = false;
+            std::vector<tlr_mat *> free2;
+            lk.lock();
+            while (!(got = p->adm.grow(u.ar.data, need, &ev2, &never)) && !never) p->cv_done.wait(lk);
+            for (int e : ev2) {
+                PoolData *v = p->data[e].get();
+                free2.push_back(v->L);
+                v->L = nullptr;
+            }
+            lk.unlock();
+            for (tlr_mat *M : free2) mat_free(M, W.stream);
+            if (got) {
+                u.extra = std::max<int64_t>(need, 0);
+                mat_free(d->L, W.stream);
+                d->L = mat_alloc(p, d->n, d->nb, d->maxrank, {}, W.stream);
+                if (d->L) {
+                    evaluate(u, d->L);
+                } else {
+                    u.status = TLR_ERR_OOM;
+                    u.err = "cannot allocate uniform factor storage after a slot overflow";
+                }
+            } else {
+                u.status = TLR_ERR_OOM;
+                u.err = "uniform factor storage after a slot overflow exceeds the HBM budget";
+            }
         }
-        const std::vector<int32_t> &nh = ran ? hint : d->hint;
-        const int64_t wb = work_bytes(d->n, d->nb, d->maxrank, nh);
-        const int64_t fb = factor_bytes(d->n, d->nb, d->maxrank, nh);
+        std::vector<int64_t> wb(runs.size()), fb(runs.size());
+        for (size_t q = 0; q < runs.size(); ++q) {
+            Run &u = runs[q];
+            PoolData *d = u.d;
+            // uniform storage (first request, or after an overflow) is given back;
+            // the next request allocates compact slots from the new rank map
+            tlr_mat *drop = (d->L && d->L->base_off.empty()) ? d->L : nullptr;
+            if (drop) {
+                mat_free(drop, W.stream);
+                d->L = nullptr;
+            }
+            const std::vector<int32_t> &nh = u.ran ? u.hint : d->hint;
+            wb[q] = work_bytes(d->n, d->nb, d->maxrank, nh);
+            fb[q] = factor_bytes(d->n, d->nb, d->maxrank, nh);
+        }
 
         lk.lock();
-        if (ran) {
-            d->hint.swap(hint);
-            d->pivot2 = pivot2;
+        for (size_t q = 0; q < runs.size(); ++q) {
+            Run &u = runs[q];
+            PoolData *d = u.d;
+            if (u.ran) {
+                d->hint.swap(u.hint);
+                d->pivot2 = u.pivot2;
+            }
+            p->adm.shrink(u.extra);
+            p->adm.finish(u.ar.data, d->L != nullptr);
+            p->adm.set_work(u.ar.data, wb[q]);
+            if (!d->L) p->adm.set_factor(u.ar.data, fb[q]);
+            u.r->status = u.status;
+            u.r->err = u.err;
+            u.r->t_done = Clock::now();
+            u.r->done = true;
+            --d->queued;
+            --p->running;
+            ++p->completed;
         }
-        p->adm.shrink(extra);
-        p->adm.finish(ar.data, d->L != nullptr);
-        p->adm.set_work(ar.data, wb);
-        if (!d->L) p->adm.set_factor(ar.data, fb);
-        r->status = status;
-        r->err = err;
-        r->t_done = Clock::now();
-        r->done = true;
-        --d->queued;
-        --p->running;
-        ++p->completed;
+        if (runs.size() > 1) {
+            ++p->groups;
+            p->grouped += (int64_t)runs.size();
+        }
         p->cv_done.notify_all();
         p->cv_work.notify_all();
     }
@@ -661,6 +753,66 @@ int tlr_pool_tune(tlr_pool *p, int id, tlr_theta theta, double eps, int precisio
     return TLR_OK;
 }
 
+int tlr_pool_configure(tlr_pool *p, int group, const tlr_buckets *b) {
+    if (!p || group < 1 || group > kMaxGroup) return pool_fail(TLR_ERR_ARG, "pool/group (1..32)");
+    const tlr_buckets v = b ? *b : default_buckets();
+    if (!buckets_ok(v)) return pool_fail(TLR_ERR_ARG, "bucket sizes must be 1, 2, 4, 8 or 16, edges nondecreasing");
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->cfg.group = group;
+    p->cfg.buckets = v;
+    return TLR_OK;
+}
+
+int tlr_pool_get_config(tlr_pool *p, int *group, tlr_buckets *b) {
+    if (!p) return pool_fail(TLR_ERR_ARG, "pool");
+    std::lock_guard<std::mutex> lk(p->mu);
+    if (group) *group = p->cfg.group;
+    if (b) *b = p->cfg.buckets;
+    return TLR_OK;
+}
+
+int tlr_pool_autotune(tlr_pool *p, int count, const int *ids, const tlr_theta *theta, double eps, int precision,
+                      int ncand, const int32_t *groups, const tlr_buckets *buckets, int rounds, double *evals_per_s,
+                      int *best) {
+    if (!p || count <= 0 || !ids || !theta || ncand <= 0 || !groups || rounds <= 0 || !best)
+        return pool_fail(TLR_ERR_ARG, "autotune arguments");
+    if (!args_ok(eps, precision)) return pool_fail(TLR_ERR_ARG, "eps/precision");
+    for (int c = 0; c < ncand; ++c) {
+        if (groups[c] < 1 || groups[c] > kMaxGroup) return pool_fail(TLR_ERR_ARG, "candidate group size");
+        if (buckets && !buckets_ok(buckets[c])) return pool_fail(TLR_ERR_ARG, "candidate buckets");
+    }
+    int old_group;
+    tlr_buckets old_b;
+    tlr_pool_get_config(p, &old_group, &old_b);
+    // every candidate starts from the same rank maps: one pass at the
+    // current configuration first (it also sets the maps of new datasets)
+    std::vector<tlr_result> out((size_t)count);
+    std::vector<int> st((size_t)count);
+    const int rc0 = tlr_pool_loglik(p, count, ids, theta, eps, precision, out.data(), st.data());
+    if (rc0 == TLR_ERR_ARG) return rc0;  // unknown dataset (message already set)
+    double best_rate = -1.0;
+    int best_c = -1;
+    for (int c = 0; c < ncand; ++c) {
+        tlr_pool_configure(p, groups[c], buckets ? buckets + c : &old_b);
+        const auto t0 = Clock::now();
+        int ok = 0;
+        for (int k = 0; k < rounds; ++k) {
+            tlr_pool_loglik(p, count, ids, theta, eps, precision, out.data(), st.data());
+            for (int q = 0; q < count; ++q) ok += st[(size_t)q] == TLR_OK;
+        }
+        const double sec = ms_between(t0, Clock::now()) / 1e3;
+        const double rate = sec > 0 ? ok / sec : 0.0;
+        if (evals_per_s) evals_per_s[c] = rate;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best_c = c;
+        }
+    }
+    tlr_pool_configure(p, groups[best_c], buckets ? buckets + best_c : &old_b);
+    *best = best_c;
+    return TLR_OK;
+}
+
 int tlr_pool_footprint(int64_t n, int nb, int maxrank, int64_t *out) {
     if (!out || n <= 0 || nb < 16 || nb > kMaxTile || maxrank > nb) return pool_fail(TLR_ERR_ARG, "n/nb/maxrank/out");
     if (maxrank <= 0) maxrank = nb / 2;
@@ -681,10 +833,10 @@ int tlr_pool_stats(tlr_pool *p, int64_t *out, int count) {
             ++nres;
         }
     }
-    const int64_t v[12] = {p->adm.budget(), p->adm.used(), p->adm.peak(), p->resident_bytes, fres, nres,
+    const int64_t v[14] = {p->adm.budget(), p->adm.used(), p->adm.peak(), p->resident_bytes, fres, nres,
                            p->adm.evictions(), p->completed, (int64_t)p->adm.queued(), p->running,
-                           p->max_running, p->allocations};
-    int k = std::min(count, 12);
+                           p->max_running, p->allocations, p->groups, p->grouped};
+    int k = std::min(count, 14);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
 }

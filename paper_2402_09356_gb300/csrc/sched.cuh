@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <deque>
+#include <functional>
 #include <vector>
 
 namespace tlr {
@@ -131,14 +132,18 @@ public:
     // Takes the next admissible request (see the policy above).  On success
     // *alloc says whether its factor storage must be allocated and `evicted`
     // receives the datasets whose factors were evicted to make room (their
-    // storage must be freed by the caller before allocating).
-    bool admit(Req *out, bool *alloc, std::vector<int> *evicted) {
+    // storage must be freed by the caller before allocating).  With `only`,
+    // requests for which it returns false are passed over (their datasets'
+    // later requests too, which keeps each dataset's order); a worker that
+    // evaluates several requests together takes its companions this way.
+    bool admit(Req *out, bool *alloc, std::vector<int> *evicted,
+               const std::function<bool(const Req &)> &only = nullptr) {
         bool mem_wait = false;
         seen_.assign(data_.size(), 0);
         for (auto it = queue_.begin(); it != queue_.end(); ++it) {
             const int d = it->data;
             Data &x = data_[(size_t)d];
-            if (seen_[(size_t)d] || x.busy) {
+            if (seen_[(size_t)d] || x.busy || (only && !only(*it))) {
                 seen_[(size_t)d] = 1;
                 continue;
             }

@@ -125,6 +125,21 @@ void matern_vec(const double *d, int64_t m, const MaternParams &P, double *out, 
 void generate_panel(const double *xy, int64_t n, int64_t ri0, int64_t ci0, int rows, int cols,
                     const MaternParams &P, double *T, int ld, cudaStream_t s);
 
+// One entry of a batched evaluation (tlr_loglik_batch): inputs, then the
+// entry's own status and message (NOT_SPD, RANK, NAN) on return.
+struct BatchEntry {
+    const double *xy = nullptr, *z = nullptr;
+    int64_t n = 0;
+    tlr_theta theta{};
+    const tlr_opts *opts = nullptr;
+    tlr_mat *L = nullptr;
+    tlr_result *out = nullptr;
+    int status = TLR_OK;
+    std::string msg;
+};
+// tlr_loglik_batch on entries (validated here); errors of the whole call throw.
+void loglik_batch(tlr_ctx *ctx, std::vector<BatchEntry> &es, cudaStream_t s);
+
 // Bounds of a maximum-likelihood search: positive, finite, lo <= hi.
 bool mle_bounds_ok(tlr_theta lo, tlr_theta hi);
 

@@ -81,10 +81,15 @@ def sequences(ids, steps, seed, precisions):
     return seqs
 
 
-def test_pool_identical_alone_and_in_the_mix(ctx):
+@pytest.mark.parametrize("group", [1, 4])
+def test_pool_identical_alone_and_in_the_mix(ctx, group):
+    """group > 1: workers evaluate up to `group` queued requests of one
+    precision together (tlr_loglik_batch); the results stay those of the
+    dataset's sequence alone."""
     import paper_2402_09356_gb300 as tlr
     sizes = [700, 1500, 2300, 3100, 1201]
     pool = tlr.Pool(0, workers=3, nb=256, maxrank=FULL)
+    tlr.tlr_pool_configure(pool, group)
     ids, data = [], {}
     for j, n in enumerate(sizes):
         xy, z = make(n, 11 * j + 1, (1.0, 0.1, 0.5))
@@ -95,6 +100,7 @@ def test_pool_identical_alone_and_in_the_mix(ctx):
     st = tlr.tlr_pool_stats(pool)
     assert st["completed"] == sum(len(s) for s in seqs.values())
     assert st["max_running"] >= 2
+    assert (st["grouped_requests"] > 0) == (group > 1)
     for d in ids:
         ref = alone(ctx, pool, d, seqs[d])
         for k, (a, b) in enumerate(zip(mix[d], ref)):
@@ -111,7 +117,8 @@ def test_pool_identical_alone_and_in_the_mix(ctx):
     pool.close()
 
 
-def test_pool_tight_budget_evicts_and_stays_identical(ctx):
+@pytest.mark.parametrize("group", [1, 3])
+def test_pool_tight_budget_evicts_and_stays_identical(ctx, group):
     import paper_2402_09356_gb300 as tlr
     sizes = [1800, 2600, 1000, 2600]
     nb = 200
@@ -121,6 +128,7 @@ def test_pool_tight_budget_evicts_and_stays_identical(ctx):
     # fit, so requests of different datasets evict one another
     budget = sum(f["base"] for f in fps) + max(f["factor"] + f["work"] for f in fps)
     pool = tlr.Pool(0, workers=2, nb=nb, maxrank=FULL, hbm_budget=budget)
+    tlr.tlr_pool_configure(pool, group)
     ids = []
     for j, n in enumerate(sizes):
         xy, z = make(n, 7 * j + 3, (1.0, 0.1, 1.0))
@@ -260,4 +268,40 @@ def test_pool_compact_slot_overflow_falls_back_to_uniform(ctx):
     st = tlr.tlr_pool_stats(pool)
     # uniform (first), compact, uniform (the overflow rerun), compact
     assert st["allocations"] >= 3, st
+    pool.close()
+
+
+def test_pool_autotune_keeps_the_fastest_candidate(ctx):
+    """Rank-bucket and group-size tuning on a batch of uneven datasets: every
+    candidate is timed, the pool keeps the fastest, and its results after
+    tuning match the dense oracle."""
+    import paper_2402_09356_gb300 as tlr
+    sizes = [1200, 2500, 1800, 3000, 900, 2200]
+    pool = tlr.Pool(0, workers=2, nb=256, maxrank=FULL)
+    ids, data = [], []
+    for j, n in enumerate(sizes):
+        xy, z = make(n, 5 * j + 2, (1.0, 0.1, 0.5))
+        ids.append(tlr.tlr_pool_add(pool, xy, z, "hilbert"))
+        data.append((xy, z))
+    thetas = [(1.0, 0.1, 0.5)] * len(ids)
+    small = {"qr_edge": [48, 96, 160, 0], "qr_size": [2, 4, 8, 8], "svd_edge": [48, 96, 160, 0],
+             "svd_size": [1, 2, 4, 8]}
+    cands = [(1, None), (3, None), (3, small)]
+    best, rates = tlr.tlr_pool_autotune(pool, ids, thetas, cands, eps=1e-9, precision=tlr.TLR_PREC_MIXED)
+    assert 0 <= best < len(cands) and all(r > 0 for r in rates)
+    assert rates[best] == max(rates)
+    cfg = tlr.tlr_pool_get_config(pool)
+    assert cfg["group"] == cands[best][0]
+    if cands[best][1] is not None:
+        assert cfg["buckets"]["qr_size"] == small["qr_size"]
+    res, st = tlr.tlr_pool_loglik(pool, ids, thetas, eps=1e-9, precision=tlr.TLR_PREC_MIXED)
+    assert st == [tlr.TLR_OK] * len(ids)
+    for d, (xy, z), r in zip(ids, data, res):
+        perm = tlr.tlr_pool_dataset(pool, d)["perm"].cpu().numpy()
+        exact = oracle.loglik_dense(oracle.permute_xy(xy, perm), z[perm], thetas[0])["loglik"]
+        assert abs(r["loglik"] - exact) <= 10 * 1e-9 * abs(exact)
+    with pytest.raises(tlr.TlrError):
+        tlr.tlr_pool_configure(pool, 0)
+    with pytest.raises(tlr.TlrError):
+        tlr.tlr_pool_autotune(pool, ids, thetas, [(40, None)])
     pool.close()
