@@ -117,6 +117,34 @@ def aggregate(total_ms: float, steps: int, world: int, device=None) -> tuple:
     return world * steps / (total_ms / 1000.0), total_ms
 
 
+def aggregate_units(units: float, seconds: float, world: int, device=None) -> tuple:
+    """Whole-job throughput of a sharded workload: every rank evaluated its own
+    `units` in `seconds`; the job's units are the sum over ranks and its time
+    the slowest rank's.  Returns (units_per_s, total_units, max_seconds)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        units, seconds = float(u.item()), float(t.item())
+    return units / seconds, units, seconds
+
+
+def shard_batched(sizes, world: int, maxrank: int = 0, nb: int = 512):
+    """Rank of every dataset of the batched workload: placed by HBM footprint
+    (tlr_pool_footprint at the nominal tile size: resident data, factor,
+    workspace) with the library's largest-first rule.  Every rank computes
+    the same placement; nothing is exchanged."""
+    import paper_2402_09356_gb300 as tlr
+    fp = []
+    for n in sizes:
+        f = tlr.tlr_pool_footprint(int(n), nb, maxrank if maxrank > 0 else 0)
+        fp.append(f["base"] + f["factor"] + f["work"])
+    return tlr.tlr_shard_place(fp, world), fp
+
+
 def dataset_seeds(rank: int) -> tuple:
     """Replica r evaluates its own dataset: locations seed 1 + r, w seed 2 + r."""
     return 1 + rank, 2 + rank
@@ -849,12 +877,25 @@ def run_batched(args):
     import torch
     import paper_2402_09356_gb300 as tlr
     import synth
-    count = args.datasets
-    sizes, th0 = batched_datasets(count)
+    # under torchrun every rank takes the datasets the footprint placement
+    # gives it (independent units, no collective on the data path) and the
+    # job's throughput is the sum of evaluations over the slowest rank's time
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    all_sizes, all_th0 = batched_datasets(args.datasets)
+    place, _ = shard_batched(all_sizes, world, args.maxrank)
+    mine = [i for i in range(args.datasets) if place[i] == rank]
+    sizes, th0 = all_sizes[mine], all_th0[mine]
+    count = len(mine)
     t_setup = time.perf_counter()
     bucket_of = [next(b for b, (lo, hi) in enumerate(BATCH_BUCKETS) if lo <= n < hi) for n in sizes]
     tuned = {}
-    tune_pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
+    tune_pool = tlr.Pool(local, workers=args.workers, nb=512, maxrank=args.maxrank)
     for b, (lo, hi) in enumerate(BATCH_BUCKETS):
         members = [i for i in range(count) if bucket_of[i] == b]
         if not members:
@@ -865,19 +906,19 @@ def run_batched(args):
         mid = (lo + hi) / 2
         rep = min(members, key=lambda i: abs(sizes[i] - mid))
         n = int(sizes[rep])
-        rid = tlr.tlr_pool_add(tune_pool, synth.jittered_grid(n, seed=10 + rep),
-                               synth.standard_normal(n, seed=5000 + rep), "morton")
+        rid = tlr.tlr_pool_add(tune_pool, synth.jittered_grid(n, seed=10 + mine[rep]),
+                               synth.standard_normal(n, seed=5000 + mine[rep]), "morton")
         best, ms = tlr.tlr_pool_tune(tune_pool, rid, tuple(th0[rep]), list(BATCH_TILE_CANDIDATES), eps=EPS,
                                      precision=tlr.TLR_PREC_MIXED)
         tuned[b] = {"n": n, "best_nb": best, "ms": ms}
     tune_pool.close()
 
     # every dataset's data drawn from its own model, Z = L(theta_i) w_i
-    zctx = tlr.Context(0)
+    zctx = tlr.Context(local)
     zs, z_white = [], 0
     for i in range(count):
-        z, ok = draw_z_lw(tlr, zctx, synth.jittered_grid(int(sizes[i]), seed=10 + i),
-                          synth.standard_normal(int(sizes[i]), seed=5000 + i), th0[i], "morton", 512)
+        z, ok = draw_z_lw(tlr, zctx, synth.jittered_grid(int(sizes[i]), seed=10 + mine[i]),
+                          synth.standard_normal(int(sizes[i]), seed=5000 + mine[i]), th0[i], "morton", 512)
         zs.append(z)
         z_white += 0 if ok else 1
     zctx.close()
@@ -885,9 +926,9 @@ def run_batched(args):
     def new_pool(cfg):
         # every path gets a pool of its own, so that each dataset's rank-map
         # history (the compression's sample sizes) comes from that path alone
-        pool = tlr.Pool(0, workers=args.workers, nb=512, maxrank=args.maxrank)
+        pool = tlr.Pool(local, workers=args.workers, nb=512, maxrank=args.maxrank)
         tlr.tlr_pool_configure(pool, cfg[0], BUCKET_MAPS[cfg[1]])
-        ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(int(sizes[i]), seed=10 + i), zs[i], "morton",
+        ids = [tlr.tlr_pool_add(pool, synth.jittered_grid(int(sizes[i]), seed=10 + mine[i]), zs[i], "morton",
                                 nb=tuned[bucket_of[i]]["best_nb"]) for i in range(count)]
         return pool, ids
 
@@ -904,7 +945,8 @@ def run_batched(args):
                 "evals_per_s": {"group %d, %s buckets" % c: r for c, r in zip(BATCH_CANDIDATES, rates)},
                 "buckets": BUCKET_MAPS}
     setup_s = time.perf_counter() - t_setup
-    walks = [synth.theta_walk(tuple(th0[i]), args.warmup + args.steps, seed=900 + i, scale=0.05) for i in range(count)]
+    walks = [synth.theta_walk(tuple(th0[i]), args.warmup + args.steps, seed=900 + mine[i], scale=0.05)
+             for i in range(count)]
     out = {}
     clocks_all = {}
     # every path with the tuned configuration, and the mixed path once more
@@ -917,7 +959,7 @@ def run_batched(args):
         pool, ids = new_pool(cfg)
         for k in range(args.warmup):
             tlr.tlr_pool_loglik(pool, ids, [tuple(w[k]) for w in walks], eps=EPS, precision=prec)
-        clocks = ClockSampler(0)
+        clocks = ClockSampler(local)
         torch.cuda.synchronize()
         launches0 = tlr.tlr_launch_count()
         clocks.start()
@@ -934,7 +976,10 @@ def run_batched(args):
         torch.cuda.synchronize()
         clocks_all[name] = clocks.stop()
         total = sum(times)
-        out[name] = {"evals_per_s": count * args.steps / total, "s_per_step": total / args.steps,
+        if world > 1:
+            torch.distributed.barrier()
+        rate, units, total = aggregate_units(count * args.steps, total, world, torch.device("cuda", local))
+        out[name] = {"evals_per_s": rate, "s_per_step": total / args.steps,
                      "failed": fails, "fp64_results": used64,
                      "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
         pool_stats[name] = tlr.tlr_pool_stats(pool)
@@ -981,7 +1026,7 @@ def run_batched(args):
     # the fastest path whose every evaluated pair is within 1e-6 of the FP64 path
     ok = [nm for nm, r in (("mixed", rel), ("tensor", rel_tensor), ("auto", rel_auto)) if r and max(r) <= 1e-6]
     head = max(ok, key=lambda nm: out[nm]["evals_per_s"]) if ok else "fp64"
-    line = {"metric": "batched TLR l(theta) evals/s, %d datasets n~U[2000,20000]" % count,
+    line = {"metric": "batched TLR l(theta) evals/s, %d datasets n~U[2000,20000]" % args.datasets,
             "value": out[head]["evals_per_s"], "unit": "evals/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * out[head]["s_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -989,7 +1034,7 @@ def run_batched(args):
                 head, "f64 storage, paired-f32 products"), "data": "synthetic",
             "config": {"workload": "batched: %d datasets, n ~ U[2000, 20000] jittered grids, theta ~ U(sigma2 "
                                    "[0.5,2], beta [0.02,0.3], nu [0.5,2.5]), Z = L(theta) w, Morton, eps %g, "
-                                   "%d workers, group %d, %s buckets" % (count, EPS, args.workers, cfg_tuned[0],
+                                   "%d workers, group %d, %s buckets" % (args.datasets, EPS, args.workers, cfg_tuned[0],
                                                                          cfg_tuned[1]),
                        "z": "Z = L(theta_i) w_i from the library's TLR factor at eps 1e-9 (tile 512); "
                             "%d datasets too ill-conditioned for it kept Z = w" % z_white,
@@ -1011,7 +1056,17 @@ def run_batched(args):
             "tensor_vs_fp64": accuracy_tensor,
             "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
             "gpu_launches": out[head]["gpu_launches"]}
-    print(json.dumps(line), flush=True)
+    if world > 1:
+        line["config"]["sharding"] = {"ranks": world, "datasets_per_rank": [int((place == r).sum())
+                                                                             for r in range(world)],
+                                      "placement": "largest footprint first onto the least-loaded rank",
+                                      "accuracy_and_autotune": "rank 0's datasets"}
+        line["n_gpus"] = world
+        line["scaling"] = "strong"
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 SERVE_SIZES = (5000, 10000, 20000, 40000, 80000)

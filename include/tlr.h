@@ -619,6 +619,18 @@ int tlr_pool_footprint(int64_t n, int nb, int maxrank, int64_t *out);
  * exact, workspace estimated). */
 int tlr_pool_stats(tlr_pool *p, int64_t *out, int count);
 
+/* Placement of datasets on the GPUs of a job (the batched and served
+ * workloads shard by dataset; no collective on the data path): dataset i,
+ * of HBM footprint bytes[i] (tlr_pool_footprint: resident data + factor +
+ * workspace), goes to rank_of[i] in 0..nranks-1.  Largest footprint first
+ * (ties: lower index), each onto the rank with the least bytes placed so far
+ * (ties: lower rank) among those whose budget[r] (NULL: unlimited) still has
+ * room: the longest-processing-time rule, whose heaviest rank carries at most
+ * 4/3 of the optimum when cost follows bytes (Graham 1969).  Deterministic:
+ * every rank computes the same placement without communicating.  Host only.
+ * Errors: TLR_ERR_ARG; TLR_ERR_OOM if some dataset fits no rank. */
+int tlr_shard_place(int count, const int64_t *bytes, int nranks, const int64_t *budget, int32_t *rank_of);
+
 /* The admission policy of the pool run as a discrete-event simulation on the
  * host (no device used): `workers` slots, `ndata` datasets with base, factor
  * and workspace bytes, and nreq requests (dataset req_data[i], arriving at

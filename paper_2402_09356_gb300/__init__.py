@@ -163,6 +163,8 @@ _SIGS = {
                                          ctypes.POINTER(ctypes.c_int)]),
     "tlr_pool_footprint": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "tlr_pool_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tlr_shard_place": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
     "tlr_sched_simulate": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -830,6 +832,18 @@ def tlr_pool_stats(pool: Pool) -> dict:
     if k < 0:
         _pool_check(k)
     return {POOL_STATS[i]: a[i] for i in range(k)}
+
+
+def tlr_shard_place(footprints, nranks: int, budgets=None):
+    """Rank of every dataset (host only): largest footprint first onto the
+    least-loaded rank with room (tlr_shard_place)."""
+    import numpy as np
+    b = np.ascontiguousarray(footprints, dtype=np.int64)
+    out = np.zeros(len(b), dtype=np.int32)
+    bud = None if budgets is None else np.ascontiguousarray(budgets, dtype=np.int64)
+    vp = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _pool_check(load_library().tlr_shard_place(len(b), vp(b), int(nranks), None if bud is None else vp(bud), vp(out)))
+    return out
 
 
 def tlr_sched_simulate(budget: int, workers: int, base, factor, work, req_data, req_arrival, req_cost):

@@ -3,6 +3,7 @@
 // evaluated by concurrent workers, each a host thread with its own context
 // and stream.  Every evaluation is an ordinary tlr_loglik call on the
 // dataset's own factor storage, started from the dataset's own rank map.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -839,6 +840,27 @@ int tlr_pool_stats(tlr_pool *p, int64_t *out, int count) {
     int k = std::min(count, 14);
     for (int i = 0; i < k; ++i) out[i] = v[i];
     return k;
+}
+
+int tlr_shard_place(int count, const int64_t *bytes, int nranks, const int64_t *budget, int32_t *rank_of) {
+    if (count < 0 || nranks < 1 || (count > 0 && (!bytes || !rank_of))) return pool_fail(TLR_ERR_ARG, "shard arguments");
+    for (int i = 0; i < count; ++i)
+        if (bytes[i] < 0) return pool_fail(TLR_ERR_ARG, "negative footprint");
+    std::vector<int> order((size_t)count);
+    for (int i = 0; i < count; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bytes[a] > bytes[b]; });
+    std::vector<int64_t> load((size_t)nranks, 0);
+    for (int i : order) {
+        int best = -1;
+        for (int r = 0; r < nranks; ++r) {
+            if (budget && load[(size_t)r] + bytes[i] > budget[r]) continue;
+            if (best < 0 || load[(size_t)r] < load[(size_t)best]) best = r;
+        }
+        if (best < 0) return pool_fail(TLR_ERR_OOM, "dataset " + std::to_string(i) + " fits no rank");
+        load[(size_t)best] += bytes[i];
+        rank_of[i] = best;
+    }
+    return TLR_OK;
 }
 
 int tlr_sched_simulate(int64_t budget, int workers, int ndata, const int64_t *base_bytes,
