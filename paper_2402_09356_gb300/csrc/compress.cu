@@ -41,6 +41,7 @@
 
 #include "common.cuh"
 #include "compress.cuh"
+#include "ff.cuh"
 #include "gemm.cuh"
 #include "tcgemm.cuh"
 
@@ -89,6 +90,25 @@ __device__ __forceinline__ void householder(double nrm2, double alpha, double &t
     }
 }
 
+// The same reflector in float-float arithmetic.  With beta = -sign(alpha) |x|
+// and v0 = alpha - beta, v'v = 2 |x| |v0|, so tau = 1 / (|x| |v0|); tau is
+// kept as its two factors rn = 1 / |x| and rv = 1 / |v0| (tau itself would
+// leave FP32's exponent range for |x| below ~1e-19), and every use multiplies
+// by them in an order that keeps the intermediate values near the data's
+// scale.  A column with |x| < 1e-30 (where the pairs' low words are already
+// subnormal) is taken as zero: no reflector.
+__device__ __forceinline__ void householder_ff(FF nrm2, FF alpha, FF &rn, FF &rv, FF &beta, FF &v0) {
+    rn = rv = beta = v0 = FF{0.f, 0.f};
+    const FF nrm = ff_sqrt(nrm2);
+    if (nrm.h >= 1e-30f) {
+        const FF snrm = alpha.h < 0.f ? ff_neg(nrm) : nrm;
+        beta = ff_neg(snrm);
+        v0 = ff_add(alpha, snrm);
+        rn = ff_div(FF{1.f, 0.f}, nrm);
+        rv = ff_div(FF{1.f, 0.f}, v0.h < 0.f ? ff_neg(v0) : v0);
+    }
+}
+
 struct QrJob {
     double *A;  // m x s input (ld lda); read only, except by the global-memory variant
     int lda;
@@ -126,7 +146,11 @@ struct PanelSplit {
 // element held as hi + lo, two FP32 words in the bytes of one double; dot
 // products accumulate with the TwoSum scheme of df_fma, updates a - w v form
 // the exact product of the high words by FMA and renormalise), which runs on
-// the FP32 pipe at about 46-bit accuracy.  Per-column scalars stay FP64.
+// the FP32 pipe at about 46-bit accuracy.  The per-column scalars (partial
+// dot products, the reflector's norm, tau, head and beta, the update weights)
+// are of type P: FP64, or float-float pairs (ff.cuh) in the paired variant,
+// so that its column steps issue no FP64 instruction (an FP64 warp
+// instruction holds GB300's FP64 pipe for 64 cycles, one active lane or 32).
 template <bool kDf>
 struct QrArith;
 template <>
@@ -145,6 +169,16 @@ struct QrArith<false> {
     };
     static __device__ __forceinline__ W prep(double w) { return W{w}; }
     static __device__ __forceinline__ T axmy(T a, const W &w, T v) { return fma(-w.w, v, a); }
+    // per-column scalars
+    using P = double;
+    static __device__ __forceinline__ P part(const Acc &a) { return a.d; }
+    static __device__ __forceinline__ P elem(T x) { return x; }
+    static __device__ __forceinline__ P padd(P a, P b) { return a + b; }
+    static __device__ __forceinline__ P pmul(P a, P b) { return a * b; }
+    static __device__ __forceinline__ bool nz(P a) { return a != 0.0; }
+    static __device__ __forceinline__ W prepP(P w) { return W{w}; }
+    static __device__ __forceinline__ T fromP(P x) { return x; }
+    static __device__ __forceinline__ double toD(P x) { return x; }
 };
 template <>
 struct QrArith<true> {
@@ -166,6 +200,15 @@ struct QrArith<true> {
         const float h = __double2float_rn(w);
         return W{h, __double2float_rn(w - (double)h)};
     }
+    using P = FF;
+    static __device__ __forceinline__ P part(const Acc &a) { return ff_two_sum(a.h, a.l); }
+    static __device__ __forceinline__ P elem(T x) { return FF{x.x, x.y}; }
+    static __device__ __forceinline__ P padd(P a, P b) { return ff_add(a, b); }
+    static __device__ __forceinline__ P pmul(P a, P b) { return ff_mul(a, b); }
+    static __device__ __forceinline__ bool nz(P a) { return a.h != 0.f; }
+    static __device__ __forceinline__ W prepP(P w) { return W{w.h, w.l}; }
+    static __device__ __forceinline__ T fromP(P x) { return make_float2(x.h, x.l); }
+    static __device__ __forceinline__ double toD(P x) { return (double)x.h + (double)x.l; }
     static __device__ __forceinline__ T axmy(T a, const W &w, T v) {
         const float ph = __fmul_rn(w.h, v.x);
         float pl = __fmaf_rn(w.h, v.x, -ph);
@@ -182,10 +225,10 @@ struct QrArith<true> {
 };
 
 // Dot products d_cc = sum over local rows i >= lb of v[i] A(i, cc) for the
-// columns cc in [first, s), written to out[cc].  red: kThreads doubles.
-template <int kThreads, class Ar, class T>
+// columns cc in [first, s), written to out[cc].  red: kThreads scalars.
+template <int kThreads, class Ar, class T, class P>
 __device__ __forceinline__ void panel_dots(const T *As, int ld, const T *v, int first, int s, int lb, int nr,
-                                           double *red, double *out) {
+                                           P *red, P *out) {
     const int tid = threadIdx.x;
     const PanelSplit<kThreads> ps(s - first);
     const int g = tid / ps.width;
@@ -194,7 +237,7 @@ __device__ __forceinline__ void panel_dots(const T *As, int ld, const T *v, int 
             const T *ac = As + cc * ld;
             typename Ar::Acc d;
             for (int i = lb; i < nr; ++i) Ar::acc(d, v[i], ac[i]);
-            out[cc] = Ar::val(d);
+            out[cc] = Ar::part(d);
         }
         return;
     }
@@ -203,27 +246,27 @@ __device__ __forceinline__ void panel_dots(const T *As, int ld, const T *v, int 
         const T *ac = As + cc * ld;
         typename Ar::Acc d;
         for (int i = lb + g; i < nr; i += ps.G) Ar::acc(d, v[i], ac[i]);
-        red[tid] = Ar::val(d);
+        red[tid] = Ar::part(d);
     }
     __syncthreads();
     if (tid < ps.width && cc < s) {
-        double d = 0.0;
-        for (int q = 0; q < ps.G; ++q) d += red[q * ps.width + tid];
+        P d{};
+        for (int q = 0; q < ps.G; ++q) d = Ar::padd(d, red[q * ps.width + tid]);
         out[cc] = d;
     }
 }
 
 // A(i, cc) -= w[cc] v(i) for local rows i >= lb and columns cc in [first, s),
 // where v(i) = v[i] except v(ic) = vhead when ic is a local row.
-template <int kThreads, class Ar, class T>
-__device__ __forceinline__ void panel_update(T *As, int ld, const T *v, int ic, T vhead, const double *w, int first,
+template <int kThreads, class Ar, class T, class P>
+__device__ __forceinline__ void panel_update(T *As, int ld, const T *v, int ic, T vhead, const P *w, int first,
                                              int s, int lb, int nr) {
     const int tid = threadIdx.x;
     const PanelSplit<kThreads> ps(s - first);
     if (tid >= ps.G * ps.width) return;
     const int g = tid / ps.width;
     for (int cc = first + tid % ps.width; cc < s; cc += ps.width) {
-        const typename Ar::W wc = Ar::prep(w[cc]);
+        const typename Ar::W wc = Ar::prepP(w[cc]);
         T *ac = As + cc * ld;
         for (int i = lb + g; i < nr; i += ps.G) ac[i] = Ar::axmy(ac[i], wc, i == ic ? vhead : v[i]);
     }
@@ -241,7 +284,7 @@ __device__ __forceinline__ void panel_update(T *As, int ld, const T *v, int ic, 
 // Q = H_0 ... H_{s-1} [I; 0] is then accumulated backwards in place: before
 // H_c is applied, columns > c already hold their final values below row c,
 // and column c becomes H_c e_c (LAPACK's dorg2r ordering).
-// Shared memory: s * ld + 8 s + kQrSmThreads doubles.
+// Shared memory: s * ld + 9 s + kQrSmThreads doubles.
 template <int kCl, bool kDf>
 __global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict__ jobs) {
     using Ar = QrArith<kDf>;
@@ -253,46 +296,62 @@ __global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict_
     const int m = J.m, s = J.s, tid = threadIdx.x;
     const int per = (m + kCl - 1) / kCl, ld = per | 1;
     const int r0 = min(m, rank * per), nr = min(m, r0 + per) - r0;
+    using P = typename Ar::P;
+    static_assert(sizeof(P) == sizeof(double), "a column scalar takes the bytes of one double");
     extern __shared__ double sm[];
     T *As = reinterpret_cast<T *>(sm);
-    double *taus = sm + (size_t)s * ld, *betas = taus + s, *heads = betas + s;
-    double *pd = heads + s, *prow = pd + 2 * s, *wv = prow + 2 * s, *red = wv + s;
+    // taus: tau (FP64), or 1 / |x| with rvs = 1 / |v0| (pairs; householder_ff)
+    P *taus = reinterpret_cast<P *>(sm + (size_t)s * ld), *betas = taus + s, *heads = betas + s, *rvs = heads + s;
+    P *pd = rvs + s, *prow = pd + 2 * s, *wv = prow + 2 * s, *red = wv + s;
     for (int e = tid; e < nr * s; e += kQrSmThreads) {
         const int i = e % nr, j = e / nr;
         As[j * ld + i] = Ar::from(J.A[(int64_t)j * J.lda + r0 + i]);
     }
     __syncthreads();
     for (int c = 0; c < s; ++c) {
-        double *pdc = pd + (c & 1) * s, *prc = prow + (c & 1) * s;
+        P *pdc = pd + (c & 1) * s, *prc = prow + (c & 1) * s;
         const int lb = max(c - r0, 0), ic = c - r0;
         T *vc = As + c * ld;
         panel_dots<kQrSmThreads, Ar>(As, ld, vc, c, s, lb, nr, red, pdc);
         const int owner = c / per;
         if (rank == owner)
-            for (int cc = c + tid; cc < s; cc += kQrSmThreads) prc[cc] = Ar::to(As[cc * ld + ic]);
+            for (int cc = c + tid; cc < s; cc += kQrSmThreads) prc[cc] = Ar::elem(As[cc * ld + ic]);
         cl.sync();
-        const double *orow = cl.map_shared_rank(prc, owner);
-        double nrm2 = 0.0;
-#pragma unroll
-        for (int k = 0; k < kCl; ++k) nrm2 += cl.map_shared_rank(pdc, k)[c];
-        const double alpha = orow[c];
-        double tau, beta, v0;
-        householder(nrm2, alpha, tau, beta, v0);
-        for (int cc = c + 1 + tid; cc < s; cc += kQrSmThreads) {
-            double d = 0.0;
-#pragma unroll
-            for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pdc, k)[cc];
-            wv[cc] = tau * (d + (v0 - alpha) * orow[cc]);
-        }
+        const P *orow = cl.map_shared_rank(prc, owner);
+        // the reflector's scalars once per CTA (every thread repeating the
+        // norm, square root and division would only repeat the same work)
         if (tid == 0) {
-            taus[c] = tau;
-            betas[c] = beta;
-            heads[c] = v0;
+            P nrm2{};
+#pragma unroll
+            for (int k = 0; k < kCl; ++k) nrm2 = Ar::padd(nrm2, cl.map_shared_rank(pdc, k)[c]);
+            const P alpha = orow[c];
+            if constexpr (kDf) {
+                householder_ff(nrm2, alpha, taus[c], rvs[c], betas[c], heads[c]);
+            } else {
+                double tau, beta, v0;
+                householder(nrm2, alpha, tau, beta, v0);
+                taus[c] = tau;
+                betas[c] = beta;
+                heads[c] = v0;
+            }
+            red[0] = alpha;
         }
         __syncthreads();
-        if (tau != 0.0) panel_update<kQrSmThreads, Ar>(As, ld, vc, ic, Ar::from(v0), wv, c + 1, s, lb, nr);
+        const P tau = taus[c], v0 = heads[c];
+        for (int cc = c + 1 + tid; cc < s; cc += kQrSmThreads) {
+            P d{};
+#pragma unroll
+            for (int k = 0; k < kCl; ++k) d = Ar::padd(d, cl.map_shared_rank(pdc, k)[cc]);
+            // w_cc = tau (d_cc + (v0 - alpha) A(c, cc)), v0 - alpha = -beta
+            if constexpr (kDf)
+                wv[cc] = ff_mul(ff_mul(ff_add(d, ff_mul(ff_neg(betas[c]), orow[cc])), tau), rvs[c]);
+            else
+                wv[cc] = tau * (d + (v0 - red[0]) * orow[cc]);
+        }
         __syncthreads();
-        if (tau != 0.0 && rank == owner && tid == 0) vc[ic] = Ar::from(v0);  // reflector head stored in place
+        if (Ar::nz(tau)) panel_update<kQrSmThreads, Ar>(As, ld, vc, ic, Ar::fromP(v0), wv, c + 1, s, lb, nr);
+        __syncthreads();
+        if (Ar::nz(tau) && rank == owner && tid == 0) vc[ic] = Ar::fromP(v0);  // reflector head stored in place
     }
     cl.sync();  // every CTA is done reading the factorisation's partials
     if (J.Rt) {  // Rt(i, u) = R(u, i) for the own rows u < s
@@ -301,7 +360,7 @@ __global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict_
             const int lu = e / s, i = e % s, u = r0 + lu;
             double v = 0.0;
             if (i > u) v = Ar::to(As[i * ld + lu]);
-            else if (i == u) v = betas[u];
+            else if (i == u) v = Ar::toD(betas[u]);
             J.Rt[(int64_t)u * s + i] = v;
         }
     }
@@ -309,30 +368,41 @@ __global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict_
     __syncthreads();
     int act = 0;
     for (int c = s - 1; c >= 0; --c) {
-        const double tau = taus[c], v0 = heads[c];
+        const P tau = taus[c], v0 = heads[c];
         const int lb = max(c - r0, 0), ic = c - r0;
         T *vc = As + c * ld;
-        if (tau != 0.0) {  // identical on every CTA of the cluster
-            double *pdc = pd + (act & 1) * s;
+        if (Ar::nz(tau)) {  // identical on every CTA of the cluster
+            P *pdc = pd + (act & 1) * s;
             ++act;
             panel_dots<kQrSmThreads, Ar>(As, ld, vc, c + 1, s, lb, nr, red, pdc);
             cl.sync();
             for (int cc = c + 1 + tid; cc < s; cc += kQrSmThreads) {
-                double d = 0.0;
+                P d{};
 #pragma unroll
-                for (int k = 0; k < kCl; ++k) d += cl.map_shared_rank(pdc, k)[cc];
-                wv[cc] = tau * d;
+                for (int k = 0; k < kCl; ++k) d = Ar::padd(d, cl.map_shared_rank(pdc, k)[cc]);
+                if constexpr (kDf) wv[cc] = ff_mul(ff_mul(d, tau), rvs[c]);
+                else wv[cc] = tau * d;
             }
             __syncthreads();
             panel_update<kQrSmThreads, Ar>(As, ld, vc, -1, Ar::from(0.0), wv, c + 1, s, lb, nr);
             __syncthreads();
         }
-        // column c of Q = H_c e_c
-        const typename Ar::W tv = Ar::prep(tau * v0);
+        // column c of Q = H_c e_c: tau v0 (= sign(v0) / |x| in pairs) times
+        // the reflector, 1 - tau v0^2 (= 1 - |v0| / |x|) at the head
+        typename Ar::W tv;
+        T qc;
+        if constexpr (kDf) {
+            const bool neg = v0.h < 0.f;
+            tv = Ar::prepP(neg ? ff_neg(tau) : tau);
+            qc = Ar::fromP(ff_add(FF{1.f, 0.f}, ff_neg(ff_mul(neg ? ff_neg(v0) : v0, tau))));
+        } else {
+            tv = Ar::prepP(tau * v0);
+            qc = Ar::from(1.0 - tau * v0 * v0);
+        }
         for (int i = tid; i < nr; i += kQrSmThreads) {
             T q;
             if (i < ic) q = Ar::from(0.0);
-            else if (i == ic) q = Ar::from(1.0 - tau * v0 * v0);
+            else if (i == ic) q = qc;
             else q = Ar::axmy(Ar::from(0.0), tv, vc[i]);
             vc[i] = q;
         }
@@ -347,7 +417,7 @@ __global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict_
 
 static size_t qr_sm_bytes(int m, int s, int csize) {
     const int per = (m + csize - 1) / csize, ld = per | 1;
-    return ((size_t)s * ld + 8 * (size_t)s + kQrSmThreads) * sizeof(double);
+    return ((size_t)s * ld + 9 * (size_t)s + kQrSmThreads) * sizeof(double);
 }
 
 // QR in global memory (A factorised in place; Q and Rt as above), for panels
@@ -386,13 +456,20 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_gm(const QrJob *__restrict__ 
         if (rank == owner)
             for (int cc = c + tid; cc < s; cc += kQrThreads) pr[cc] = A[(int64_t)cc * lda + c];
         cl.sync();
-        double nrm2 = 0.0;
-        for (int k = 0; k < kCl; ++k) nrm2 += cl.map_shared_rank(s_norm, k)[par];
         const double *orow = cl.map_shared_rank(pr, owner);
-        const double alpha = orow[c];
-        double tau, beta, v0;
-        householder(nrm2, alpha, tau, beta, v0);
-        if (tid == 0) { taus[c] = tau; betas[c] = beta; }
+        __shared__ double s_sc[2];  // alpha, v0 of the column (computed once per CTA)
+        if (tid == 0) {
+            double nrm2 = 0.0;
+            for (int k = 0; k < kCl; ++k) nrm2 += cl.map_shared_rank(s_norm, k)[par];
+            double tau_, beta_, v0_;
+            householder(nrm2, orow[c], tau_, beta_, v0_);
+            taus[c] = tau_;
+            betas[c] = beta_;
+            s_sc[0] = orow[c];
+            s_sc[1] = v0_;
+        }
+        __syncthreads();
+        const double tau = taus[c], alpha = s_sc[0], v0 = s_sc[1];
         if (tau != 0.0) {
             for (int cc = c + 1 + warp; cc < s; cc += kNw) {
                 double d = 0.0;

@@ -56,7 +56,6 @@ bool make_matern_params(double sigma2, double beta, double nu, MaternParams *P) 
     P->sigma2 = sigma2;
     P->inv_beta = 1.0 / beta;
     P->tab = nullptr;
-    P->tab2 = nullptr;
     P->nu = nu;
     int m = (int)std::floor(nu + 0.5);
     double mu = nu - m;

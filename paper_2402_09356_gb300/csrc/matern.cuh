@@ -49,7 +49,6 @@ constexpr int kTabCoef = kTabDeg + 1;
 struct MaternParams {
     double sigma2, inv_beta, nu;
     const double *tab;  // kTabIntervals x kTabCoef Chebyshev coefficients, or null (direct K_nu)
-    const float2 *tab2; // the same coefficients as (hi, lo) FP32 pairs (paired-FP32 evaluation), or null
     double mu;
     int m;
     double lead;       // 2^(1-nu) / Gamma(nu)
@@ -203,108 +202,6 @@ __device__ __forceinline__ double matern_cov(double xa, double ya, double xb, do
     double dx = xa - xb, dy = ya - yb;
     double s = dx * dx + dy * dy;
     if (s == 0.0) return P.sigma2;
-    return P.sigma2 * matern_corr_s(s, P);
-}
-
-// ---- the table in paired FP32 ("float-float", Dekker 1971): the same
-// Chebyshev interpolant of log C, evaluated with ~47-bit FP32 pairs on the
-// FP32 pipe (64 times GB300's FP64 rate), then exp in the same arithmetic.
-// Used by the covariance panels of the mixed-precision paths; the FP64 path
-// keeps matern_cov.
-struct FF {
-    float h, l;
-};
-__device__ __forceinline__ FF ff_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-    return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ FF ff_fast(float a, float b) {  // |a| >= |b|
-    const float s = __fadd_rn(a, b);
-    return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-    const FF s = ff_two_sum(a.h, b.h);
-    return ff_fast(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ FF ff_mul(FF a, FF b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, e);
-    e = __fmaf_rn(a.l, b.h, e);
-    return ff_fast(p, e);
-}
-
-// exp(y) for y <= ~0 in paired FP32: y = k ln2 + r with ln2 in three parts
-// (the first of 16 bits, so that k times it is exact for |k| < 2^8), then the
-// Taylor polynomial of exp(r), |r| <= ln2 / 2, to degree 12 (truncation below
-// 2^-47): degrees 7-12 in FP32 on r's high word, 0-6 in pairs.  Below -87
-// (under FP32's normal range) the result is 0.
-__device__ __forceinline__ FF ff_exp(FF y) {
-    if (y.h < -87.0f) return FF{0.f, 0.f};
-    const float k = rintf(__fmul_rn(y.h, 1.44269504f));
-    const float L1 = 0.693145751953125f, L2 = 1.428606765330187e-06f, L3 = 5.495603971894525e-14f;
-    FF r = ff_fast(__fsub_rn(y.h, __fmul_rn(k, L1)), y.l);       // y - k L1 (exact first word)
-    const float p2 = __fmul_rn(k, L2), p2e = __fmaf_rn(k, L2, -p2);  // k L2 exactly, as a pair
-    r = ff_add(r, FF{-p2, -p2e});
-    r = ff_add(r, FF{__fmul_rn(-k, L3), 0.f});
-    const float rh = r.h;
-    float q = 2.0876756e-09f;  // 1/12!
-    q = __fmaf_rn(q, rh, 2.5052108e-08f);
-    q = __fmaf_rn(q, rh, 2.755732e-07f);
-    q = __fmaf_rn(q, rh, 2.7557319e-06f);
-    q = __fmaf_rn(q, rh, 2.4801588e-05f);
-    q = __fmaf_rn(q, rh, 1.984127e-04f);  // ... + 1/7! (high word)
-    FF e{q, 0.f};
-    const FF c[7] = {FF{1.0f, 0.f}, FF{1.0f, 0.f}, FF{0.5f, 0.f}, FF{0.16666667f, -4.967054e-09f},
-                     FF{0.041666668f, -1.2417635e-09f}, FF{0.008333334f, -4.346172e-10f},
-                     FF{0.0013888889f, -3.3631094e-11f}};
-    e = ff_add(FF{-2.7255969e-12f, 0.f}, e);  // 1/7! low word
-#pragma unroll
-    for (int j = 6; j >= 0; --j) e = ff_add(c[j], ff_mul(r, e));
-    const int ki = (int)k;
-    return FF{ldexpf(e.h, ki), ldexpf(e.l, ki)};
-}
-
-// C(d)/sigma2 from s = d^2 through the paired-FP32 table; false (nothing
-// written) outside the table or on a flagged interval.
-__device__ __forceinline__ bool matern_corr_s_ff(double s, const MaternParams &P, double *out) {
-    if (!P.tab2) return false;
-    const long long bits = __double_as_longlong(s);
-    const int e = (int)((bits >> 52) & 0x7FF) - 1023;
-    if (e < kTabEmin || e > kTabEmax) return false;
-    const int sub = (int)((bits >> 50) & 3);
-    // t = 2 frac(4 u) - 1 from the 50 fraction bits below the two sub-interval bits
-    const long long f = bits & 0x3FFFFFFFFFFFFll;
-    const float th = __fsub_rn(__fmul_rn((float)(int)(f >> 26), 1.1920928955078125e-07f), 1.0f);  // 2^-23
-    const float tl = __fmul_rn((float)(int)(f & 0x3FFFFFFll), 1.7763568394002505e-15f);          // 2^-49
-    const FF t = ff_fast(th, tl);
-    const FF t2{__fmul_rn(2.0f, t.h), __fmul_rn(2.0f, t.l)};
-    const float2 *c = P.tab2 + ((e - kTabEmin) * kTabSub + sub) * kTabCoef;
-    const float2 c0 = __ldg(c);
-    if (c0.x != c0.x) return false;
-    FF b1{0.f, 0.f}, b2{0.f, 0.f};
-#pragma unroll
-    for (int j = kTabDeg; j >= 1; --j) {
-        const float2 cj = __ldg(c + j);
-        const FF b0 = ff_add(ff_add(FF{cj.x, cj.y}, ff_mul(t2, b1)), FF{-b2.h, -b2.l});
-        b2 = b1;
-        b1 = b0;
-    }
-    const FF lg = ff_add(ff_add(FF{c0.x, c0.y}, ff_mul(t, b1)), FF{-b2.h, -b2.l});
-    const FF ex = ff_exp(lg);
-    *out = (double)ex.h + (double)ex.l;
-    return true;
-}
-
-// Covariance between two locations, the table evaluated in paired FP32
-// (~1e-14 relative; matern_cov outside the table).
-__device__ __forceinline__ double matern_cov_ff(double xa, double ya, double xb, double yb,
-                                                const MaternParams &P) {
-    const double dx = xa - xb, dy = ya - yb;
-    const double s = dx * dx + dy * dy;
-    if (s == 0.0) return P.sigma2;
-    double c;
-    if (matern_corr_s_ff(s, P, &c)) return P.sigma2 * c;
     return P.sigma2 * matern_corr_s(s, P);
 }
 
