@@ -116,6 +116,7 @@ struct QrJob {
     int ldq;
     double *Rt;  // s x s output R' (ld s, lower triangular), or null
     int m, s;
+    float2 *Rt2;  // paired-FP32 variant: R' also as (hi, lo) pairs (ld s), or null
 };
 
 // ---------------------------------------------------------------------------
@@ -359,9 +360,17 @@ __global__ void __launch_bounds__(kQrSmThreads) k_qr_sm(const QrJob *__restrict_
         for (int e = tid; e < nu * s; e += kQrSmThreads) {
             const int lu = e / s, i = e % s, u = r0 + lu;
             double v = 0.0;
-            if (i > u) v = Ar::to(As[i * ld + lu]);
-            else if (i == u) v = Ar::toD(betas[u]);
+            T w = Ar::from(0.0);
+            if (i > u) {
+                w = As[i * ld + lu];
+                v = Ar::to(w);
+            } else if (i == u) {
+                w = Ar::fromP(betas[u]);
+                v = Ar::toD(betas[u]);
+            }
             J.Rt[(int64_t)u * s + i] = v;
+            if constexpr (kDf)
+                if (J.Rt2) J.Rt2[(int64_t)u * s + i] = w;
         }
     }
     if (!J.Q) return;
@@ -492,6 +501,10 @@ __global__ void __launch_bounds__(kQrThreads) k_qr_gm(const QrJob *__restrict__ 
             if (i < j) v = A[(int64_t)j * lda + i];
             else if (i == j) v = betas[i];
             J.Rt[(int64_t)i * s + j] = v;
+            if (J.Rt2) {
+                const float h = __double2float_rn(v);
+                J.Rt2[(int64_t)i * s + j] = make_float2(h, __double2float_rn(v - (double)h));
+            }
         }
     }
     if (!J.Q) return;
@@ -543,6 +556,7 @@ struct SvdJob {
     int *sweeps;       // [0] FP64 sweeps, [1] FP32 sweeps, [2] FP64 pairs checked, [3] FP64 pairs rotated
     int s;
     double tau;        // absolute accuracy of the tile
+    const float2 *Rt2; // R' as paired FP32 (the paired-FP32 precondition reads it), or null
 };
 
 // Fast approximate reciprocal and reciprocal square root of a double (the
@@ -625,9 +639,9 @@ __device__ __forceinline__ bool jacobi_rotate(T *x, T *y, T *nx, T *ny, int sdot
 // products, so that rounding alone never keeps a sweep alive.
 template <class T>
 __device__ __forceinline__ T jacobi_tol2(int s) {
-    const double u = std::is_same<T, double>::value ? 1.1102230246251565e-16 : 5.9604644775390625e-8;
-    const double tol = 8.0 * sqrt((double)s) * u;
-    return (T)(tol * tol);
+    const T u = std::is_same<T, double>::value ? T(1.1102230246251565e-16) : T(5.9604644775390625e-8);
+    const T tol = T(8) * sqrt((T)s) * u;
+    return tol * tol;
 }
 
 // Sort key of a column norm: non-finite values sort last.
@@ -777,7 +791,8 @@ __device__ __forceinline__ void jacobi_emit(const SvdJob &J, const double *cols,
         const double nv = all_nrm[u];
         const bool unit = nv > 0.0 && nv <= 1.7e308;
         const double *col = cols + q * s;
-        for (int r = lane; r < s; r += 32) J.W[(int64_t)pos * s + r] = unit ? col[r] / nv : col[r];
+        const double inv = unit ? 1.0 / nv : 1.0;  // one division per column, not per entry
+        for (int r = lane; r < s; r += 32) J.W[(int64_t)pos * s + r] = col[r] * inv;
         if (lane == 0) J.S[pos] = nv;
     }
 }
@@ -843,29 +858,62 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
         for (int e = tid; e < bsf; e += kQrThreads) {
             const int u = blk * b + e / s2, r = e % s2;
             float v = 0.0f;
-            if (u < s) v = r < s ? (float)J.Rt[(int64_t)u * s + r] : (r - s == u ? 1.0f : 0.0f);
+            if (u < s) {
+                if (r >= s) v = r - s == u ? 1.0f : 0.0f;
+                else v = J.Rt2 ? J.Rt2[(int64_t)u * s + r].x : (float)J.Rt[(int64_t)u * s + r];
+            }
             dst[e] = v;
         }
     }
     __syncthreads();
     sw32 = jacobi_sweeps<kCl, float>(cl, f0, stride_f, b, s, s2, kMaxSweeps32, g, cur, s_flag);
-    // B. M1 = M J for the held columns, 8 at a time; rows i = tid, tid + 256
+    // B. M1 = M J for the held columns, 8 at a time; rows i = tid, tid + 256.
+    // With the paired copy of M (paired-FP32 paths) the products run in
+    // float-float arithmetic on the FP32 pipe (J is exact in FP32; M1 then
+    // carries ~1e-14 of |M|, below the thresholds of those paths); else in
+    // FP64.  Warps whose rows all lie past s, and the second row when
+    // s <= 256, issue nothing (an FP64 warp instruction costs the same with
+    // no lane active).
     {
         const float *F = f0 + cur * stride_f;
         const int gx = block_at(px, g, nblk), gy = block_at(py, g, nblk);
-        for (int q0 = 0; q0 < 2 * b; q0 += 8) {
-            double acc[8][2];
+        const bool rows2 = s > kQrThreads, live = warp * 32 < s;
+        for (int q0 = 0; q0 < 2 * b && live; q0 += 8) {
+            double out[8][2];
+            if (J.Rt2) {
+                float h[8][2], l[8][2];
 #pragma unroll
-            for (int a = 0; a < 8; ++a) acc[a][0] = acc[a][1] = 0.0;
-            for (int k = 0; k < s; ++k) {
-                const double m0 = tid < s ? J.Rt[(int64_t)k * s + tid] : 0.0;
-                const double m1 = tid + kQrThreads < s ? J.Rt[(int64_t)k * s + tid + kQrThreads] : 0.0;
+                for (int a = 0; a < 8; ++a) h[a][0] = h[a][1] = l[a][0] = l[a][1] = 0.0f;
+                for (int k = 0; k < s; ++k) {
+                    const float2 m0 = tid < s ? J.Rt2[(int64_t)k * s + tid] : make_float2(0.f, 0.f);
+                    const float2 m1 = rows2 && tid + kQrThreads < s ? J.Rt2[(int64_t)k * s + tid + kQrThreads]
+                                                                    : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const int q = q0 + a;
+                        const float jk = q < 2 * b ? F[q * s2 + s + k] : 0.0f;
+                        df_fma(m0.x, m0.y, jk, 0.0f, h[a][0], l[a][0]);
+                        if (rows2) df_fma(m1.x, m1.y, jk, 0.0f, h[a][1], l[a][1]);
+                    }
+                }
 #pragma unroll
                 for (int a = 0; a < 8; ++a) {
-                    const int q = q0 + a;
-                    const double jk = q < 2 * b ? (double)F[q * s2 + s + k] : 0.0;
-                    acc[a][0] = fma(m0, jk, acc[a][0]);
-                    acc[a][1] = fma(m1, jk, acc[a][1]);
+                    out[a][0] = (double)h[a][0] + (double)l[a][0];
+                    out[a][1] = (double)h[a][1] + (double)l[a][1];
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 8; ++a) out[a][0] = out[a][1] = 0.0;
+                for (int k = 0; k < s; ++k) {
+                    const double m0 = tid < s ? J.Rt[(int64_t)k * s + tid] : 0.0;
+                    const double m1 = rows2 && tid + kQrThreads < s ? J.Rt[(int64_t)k * s + tid + kQrThreads] : 0.0;
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) {
+                        const int q = q0 + a;
+                        const double jk = q < 2 * b ? (double)F[q * s2 + s + k] : 0.0;
+                        out[a][0] = fma(m0, jk, out[a][0]);
+                        if (rows2) out[a][1] = fma(m1, jk, out[a][1]);
+                    }
                 }
             }
 #pragma unroll
@@ -874,8 +922,8 @@ __global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restri
                 if (q >= 2 * b) break;
                 const int u = (q < b ? gx : gy) * b + q % b;
                 if (u >= s) continue;
-                if (tid < s) J.work[(int64_t)u * s + tid] = acc[a][0];
-                if (tid + kQrThreads < s) J.work[(int64_t)u * s + tid + kQrThreads] = acc[a][1];
+                if (tid < s) J.work[(int64_t)u * s + tid] = out[a][0];
+                if (tid + kQrThreads < s) J.work[(int64_t)u * s + tid + kQrThreads] = out[a][1];
             }
         }
     }
@@ -1008,7 +1056,8 @@ __global__ void __launch_bounds__(kQrThreads) k_svd_emit(const EmitJob *__restri
         const double nv = nrm[u];
         const bool unit = nv > 0.0 && nv <= 1.7e308;
         const double *col = J.X + (int64_t)u * s;
-        for (int r = lane; r < s; r += 32) J.W[(int64_t)pos * s + r] = unit ? col[r] / nv : col[r];
+        const double inv = unit ? 1.0 / nv : 1.0;  // one division per column, not per entry
+        for (int r = lane; r < s; r += 32) J.W[(int64_t)pos * s + r] = col[r] * inv;
         if (lane == 0) J.S[pos] = nv;
     }
     if (tid == 0) {
@@ -1437,7 +1486,7 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
         const size_t np = pending.size();
         // workspace offsets (doubles)
         std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np), oQ2(np), oX2(np), oG(np),
-            oIA(np);
+            oIA(np), oR2(np);
         std::vector<int> ps(np);
         int64_t tot = 0;
         auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
@@ -1457,6 +1506,7 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
             oX2[u] = take((int64_t)s * s);
             oG[u] = take((int64_t)s * s);
             oIA[u] = take((int64_t)s * s);
+            oR2[u] = df ? take((int64_t)s * s) : 0;  // float2, one double each
         }
         DevBuf ws(tot * sizeof(double) + np * sizeof(unsigned long long) + 5 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
@@ -1510,7 +1560,7 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
         std::vector<QrJob> q2(np);
         for (size_t u = 0; u < np; ++u) {
             const CompressJob &J = jobs[pending[u]];
-            q2[u] = QrJob{W + oB[u], J.k, nullptr, 0, W + oR[u], J.k, ps[u]};
+            q2[u] = QrJob{W + oB[u], J.k, nullptr, 0, W + oR[u], J.k, ps[u], df ? (float2 *)(W + oR2[u]) : nullptr};
         }
         qr_launch(ctx, st, q2, scratch, df);
         cmark();
@@ -1518,7 +1568,7 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
         std::vector<SvdJob> sv(np);
         for (size_t u = 0; u < np; ++u)
             sv[u] = SvdJob{W + oR[u], W + oK[u], W + oW[u], W + oS[u], d_rank + u, d_rank + np + 4 * u, ps[u],
-                           jobs[pending[u]].tau};
+                           jobs[pending[u]].tau, df ? (const float2 *)(W + oR2[u]) : nullptr};
         std::vector<int> svd_csize;
         ClassTiming t16;
         size_t ev_used = 0;
