@@ -833,7 +833,7 @@ constexpr int kRefineSteps = 3;  // FP64 Gram refinement steps after the FP32 sw
 // only, on the M1 found in `work`.
 enum { kJacFull = 0, kJacPrecond = 1, kJacFinish = 2 };
 template <int kCl, int kMode>
-__global__ void __launch_bounds__(kQrThreads) k_jacobi_sm(const SvdJob *__restrict__ jobs) {
+__global__ void __launch_bounds__(kQrThreads, 2) k_jacobi_sm(const SvdJob *__restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     __shared__ int s_flag[2];
@@ -1486,7 +1486,7 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
         const size_t np = pending.size();
         // workspace offsets (doubles)
         std::vector<int64_t> oY(np), oQ(np), oB(np), oC(np), oR(np), oW(np), oK(np), oS(np), oQ2(np), oX2(np), oG(np),
-            oIA(np), oR2(np);
+            oIA(np), oR2(np), oB2(np), oW2(np);
         std::vector<int> ps(np);
         int64_t tot = 0;
         auto take = [&](int64_t cnt) { int64_t o = tot; tot += (cnt + 31) & ~31LL; return o; };
@@ -1507,6 +1507,8 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
             oG[u] = take((int64_t)s * s);
             oIA[u] = take((int64_t)s * s);
             oR2[u] = df ? take((int64_t)s * s) : 0;  // float2, one double each
+            oB2[u] = dfp ? take((int64_t)J.k * s) : 0;
+            oW2[u] = dfp ? take((int64_t)s * s) : 0;
         }
         DevBuf ws(tot * sizeof(double) + np * sizeof(unsigned long long) + 5 * np * sizeof(int) + 256, st);
         double *W = ws.as<double>();
@@ -1687,6 +1689,7 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
         }
         std::vector<int> next;
         std::vector<GemmProb> gu, gv;
+        std::vector<SplitDesc> suv;
         for (size_t u = 0; u < np; ++u) {
             int q = pending[u];
             const CompressJob &J = jobs[q];
@@ -1724,20 +1727,31 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
             }
             ranks[q] = r;
             if (r == 0) continue;
-            // U = Q W_r, V = B W_r
+            // U = Q W_r, V = B W_r (paired FP32 on the mixed paths: Q's paired
+            // copy exists, B and W_r are split here)
             GemmProb a{};
             a.A = W + oQ[u]; a.lda = J.m; a.m = J.m; a.k = s;
             a.B = W + oW[u]; a.ldb = s; a.n = r;
             a.C = Uo; a.ldc = J.ldu;
-            gu.push_back(a);
             GemmProb b{};
             b.A = W + oB[u]; b.lda = J.k; b.m = J.k; b.k = s;
             b.B = W + oW[u]; b.ldb = s; b.n = r;
             b.C = Vo; b.ldc = J.ldv;
+            if (dfp) {
+                float2 *b2 = (float2 *)(W + oB2[u]), *w2 = (float2 *)(W + oW2[u]);
+                suv.push_back(SplitDesc{W + oB[u], b2, J.k, J.k, s});
+                suv.push_back(SplitDesc{W + oW[u], w2, s, s, r});
+                a.A2 = (const float2 *)(W + oQ2[u]);
+                a.B2 = w2;
+                b.A2 = b2;
+                b.B2 = w2;
+            }
+            gu.push_back(a);
             gv.push_back(b);
         }
-        gemm_batched(ctx, st, false, false, gu, 1.0, 0.0);
-        gemm_batched(ctx, st, false, false, gv, 1.0, 0.0);
+        split_f2_batched(ctx, st, suv);
+        gemm_batched(ctx, st, false, false, gu, 1.0, 0.0, dfp);
+        gemm_batched(ctx, st, false, false, gv, 1.0, 0.0, dfp);
         cmark();
         // the workspace is released stream-ordered after these GEMMs
         pending.swap(next);
