@@ -184,6 +184,9 @@ int tlr_ctx_create(int device, tlr_ctx **out) {
         TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio_hi));
         TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->la, cudaStreamNonBlocking, prio_lo));
         TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->hp, cudaStreamNonBlocking, prio_hi));
+        TLR_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->sv, cudaStreamNonBlocking, prio_hi));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_sv_fork, cudaEventDisableTiming));
+        TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_sv_done, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_hp_fork, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_hp_join, cudaEventDisableTiming));
         TLR_CUDA_TRY(cudaEventCreateWithFlags(&ctx->ev_la_fork, cudaEventDisableTiming));
@@ -228,7 +231,9 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->la) cudaStreamDestroy(ctx->la);
     if (ctx->hp) cudaStreamDestroy(ctx->hp);
-    for (cudaEvent_t e : {ctx->ev_la_fork, ctx->ev_la_join, ctx->ev_hp_fork, ctx->ev_hp_join})
+    if (ctx->sv) cudaStreamDestroy(ctx->sv);
+    for (cudaEvent_t e : {ctx->ev_la_fork, ctx->ev_la_join, ctx->ev_hp_fork, ctx->ev_hp_join, ctx->ev_sv_fork,
+                          ctx->ev_sv_done})
         if (e) cudaEventDestroy(e);
     for (cudaStream_t c : ctx->cls_stream)
         if (c) cudaStreamDestroy(c);

@@ -157,6 +157,8 @@ struct tlr_ctx {
     int ahead_ctas_per_sm = 1;
     cudaEvent_t ev_la_fork = nullptr, ev_la_join = nullptr;
     cudaStream_t hp = nullptr;            // high-priority stream of the factorisation's compression
+    cudaStream_t sv = nullptr;            // the fused forward solve, beside the next column's work
+    cudaEvent_t ev_sv_fork = nullptr, ev_sv_done = nullptr;
     cudaEvent_t ev_hp_fork = nullptr, ev_hp_join = nullptr;
     // compression: one stream per launch class (cluster size), forked from and
     // joined to the calling stream
@@ -164,8 +166,8 @@ struct tlr_ctx {
     cudaStream_t cls_stream[kClassStreams] = {};
     cudaEvent_t cls_fork = nullptr, cls_join[kClassEvents] = {};
     cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_fork = nullptr, ev_join = nullptr;
-    // descriptor staging: ring 0 for the caller's stream, 1 for `aux`, 2 for `la`, 3 for `hp`
-    tlr::StageRing stage[4];
+    // descriptor staging: ring 0 for the caller's stream, 1 for `aux`, 2 for `la`, 3 for `hp`, 4 for `sv`
+    tlr::StageRing stage[5];
     // fixed Gaussian test matrices of the randomised range finder
     double *d_omega = nullptr;
     float2 *d_omega2 = nullptr;  // paired-FP32 copy of d_omega
@@ -220,7 +222,7 @@ struct tlr_mat {
 namespace tlr {
 
 inline int stage_ring(const tlr_ctx *ctx, cudaStream_t s) {
-    return s == ctx->aux ? 1 : (s == ctx->la ? 2 : (s == ctx->hp ? 3 : 0));
+    return s == ctx->aux ? 1 : (s == ctx->la ? 2 : (s == ctx->hp ? 3 : (s == ctx->sv ? 4 : 0)));
 }
 // Marks the ring of stream s empty; only valid right after a sync of s.
 inline void stage_reset(tlr_ctx *ctx, cudaStream_t s) { ctx->stage[stage_ring(ctx, s)].off = 0; }

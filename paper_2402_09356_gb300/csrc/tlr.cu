@@ -121,8 +121,6 @@ struct GroupItem {
     std::vector<DevBuf> gram, vty;
     std::vector<int> gram_n;
     std::vector<std::vector<int>> gram_off;
-    const double *vty_src = nullptr;
-    int vty_pending = 0;
     int r_of(int i, int k) const { return (int)M->h_ranks[(size_t)i * nt + k]; }
 };
 
@@ -213,6 +211,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
     TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
     TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->la, ctx->ev_fork, 0));
+    TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->sv, ctx->ev_fork, 0));
     // a compression job's tile belongs to items[J.item]
     const GrowSlot grow = [&](const CompressJob &J, int r, double **U, double **V) -> bool {
         const GrowSlot &gs = items[(size_t)J.item]->grow;
@@ -234,7 +233,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
         cudaEvent_t e;
         int idx;
     };
-    std::vector<DMark> dm_main, dm_aux, dm_la;
+    std::vector<DMark> dm_main, dm_aux, dm_la, dm_sv;
     auto dmark = [&](std::vector<DMark> &v, cudaStream_t s, int idx) {
         if (!ctx->profile) return;
         profile_events(ctx, prof_used + 1);
@@ -248,6 +247,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
         tlr_ctx *ctx;
         ~SideStreamGuard() {
             if (std::uncaught_exceptions()) {
+                cudaStreamSynchronize(ctx->sv);
                 cudaStreamSynchronize(ctx->la);
                 cudaStreamSynchronize(ctx->aux);
                 cudaStreamSynchronize(ctx->hp);
@@ -428,7 +428,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
     };
 
     // y_c -= sum_{k<c} U_ck c_k, c_k = V_ck' y_k: a slice of column k's V_k' y_k
-    auto solve_update = [&](const std::vector<GroupItem *> &us, int c) {
+    auto solve_update = [&](const std::vector<GroupItem *> &us, int c, cudaStream_t ss) {
         Hold hold;
         std::vector<CopyDesc> cq, cc;
         std::vector<GemmProb> gg;
@@ -441,8 +441,8 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
             for (int k = 0; k < c; ++k) off[k + 1] = off[k] + I.r_of(c, k);
             const int Rc = off[c];
             if (Rc <= 0) continue;
-            double *qb = hold_buf(hold, (size_t)nb * Rc * sizeof(double), st).as<double>();
-            double *cb = hold_buf(hold, (size_t)Rc * sizeof(double), st).as<double>();
+            double *qb = hold_buf(hold, (size_t)nb * Rc * sizeof(double), ss).as<double>();
+            double *cb = hold_buf(hold, (size_t)Rc * sizeof(double), ss).as<double>();
             for (int k = 0; k < c; ++k) {
                 const int r = I.r_of(c, k);
                 if (r <= 0) continue;
@@ -455,9 +455,9 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
             g.C = I.in->y + (int64_t)c * nb; g.ldc = nb;
             gg.push_back(g);
         }
-        copy_batched(ctx, st, cq);
-        copy_batched(ctx, st, cc);
-        gemm_batched(ctx, st, false, false, gg, -1.0, 1.0);
+        copy_batched(ctx, ss, cq);
+        copy_batched(ctx, ss, cc);
+        gemm_batched(ctx, ss, false, false, gg, -1.0, 1.0);
     };
 
     // status words of the call: one per factorisation (the context's word
@@ -472,6 +472,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
     };
 
     int cur = 0;
+    bool sv_pending = false;  // a solve on the solve stream may still read X
     for (int j = 0; j < nt_max; ++j) {
         std::vector<GroupItem *> act;
         for (auto &u : items)
@@ -513,15 +514,6 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
             panel_correct(corr, j, cur, st);
             dmark(dm_main, st, kDetCorrect);
         }
-        if (j > 0) {
-            std::vector<GroupItem *> sv;
-            for (GroupItem *u : act)
-                if (u->solve) sv.push_back(u);
-            if (!sv.empty()) {
-                solve_update(sv, j);
-                dmark(dm_main, st, kDetSolveUpd);
-            }
-        }
         mark();
         if (dfp) {
             std::vector<SplitDesc> sd;
@@ -553,6 +545,8 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
             copy_batched(ctx, st, cd);
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
             TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+            // the previous column's solve reads X = L^-1 on the solve stream
+            if (sv_pending) TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->aux, ctx->ev_sv_done, 0));
             if (ctx->profile) {
                 profile_events(ctx, prof_used + 1);
                 TLR_CUDA_TRY(cudaEventRecord(ctx->prof_events[prof_used], ctx->aux));
@@ -684,8 +678,6 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
                 // the packed V factors of column j, alive through the solve step
                 I.vtmp.alloc((size_t)nb * std::max<int64_t>(off_c, 1) * sizeof(double), st);
                 double *vt = I.vtmp.as<double>();
-                I.vty_src = nullptr;
-                I.vty_pending = 0;
                 float2 *x2 = nullptr, *v2 = nullptr;
                 if (dfp && off_c > 0) {
                     // paired-FP32 operands: X, and the V factors packed like the output
@@ -731,12 +723,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
                     gg.push_back(g);
                     stats->flops += 2.0 * S * S * mj;
                 }
-                if (I.solve && S > 0 && j + 1 < nt) {
-                    // V_j' y_j once y_j is final (after the solve step below)
-                    I.vty[j].alloc((size_t)S * sizeof(double), st);
-                    I.vty_src = vt;
-                    I.vty_pending = S;
-                }
+                if (I.solve && S > 0 && j + 1 < nt) I.vty[j].alloc((size_t)S * sizeof(double), st);
             }
             split_f2_batched(ctx, st, sd);
             if (tcc) gemm_tc(ctx, st, false, false, gt, 1.0, 0.0);
@@ -750,11 +737,23 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
                 dmark(dm_main, st, kDetGram);
             }
         }
+        // --- the fused forward solve of column j on its own stream (a5), beside
+        // the next column's panel correction and compression: y_j -= the
+        // products with the earlier columns, y_j <- L_jj^-1 y_j, the
+        // log-determinant and |y|^2 terms, and V_j' y_j for the later columns
         {
             std::vector<GroupItem *> sv;
             for (GroupItem *u : ok)
                 if (u->solve) sv.push_back(u);
             if (!sv.empty()) {
+                const cudaStream_t ss = ctx->sv;
+                TLR_CUDA_TRY(cudaEventRecord(ctx->ev_sv_fork, st));
+                TLR_CUDA_TRY(cudaStreamWaitEvent(ss, ctx->ev_sv_fork, 0));
+                dmark(dm_sv, ss, -1);
+                if (j > 0) {
+                    solve_update(sv, j, ss);
+                    dmark(dm_sv, ss, kDetSolveUpd);
+                }
                 std::vector<GemmProb> gy, gv;
                 for (GroupItem *u : sv) {
                     const int nb = u->nb;
@@ -764,36 +763,44 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
                     g.C = u->ytmp.as<double>(); g.ldc = nb;
                     gy.push_back(g);
                 }
-                gemm_batched(ctx, st, false, false, gy, 1.0, 0.0);
+                gemm_batched(ctx, ss, false, false, gy, 1.0, 0.0);
                 for (GroupItem *u : sv) {
-                    const int nb = u->nb, mj = tile_rows(u->n, nb, j);
+                    const int nb = u->nb, nt = u->nt, mj = tile_rows(u->n, nb, j);
                     double *yj = u->in->y + (int64_t)j * nb, *acc = u->in->acc;
-                    TLR_CUDA_TRY(cudaMemcpyAsync(yj, u->ytmp.as<double>(), mj * sizeof(double), cudaMemcpyDeviceToDevice, st));
-                    diag_logsum(st, u->M->D + (int64_t)j * nb * nb, nb, mj, acc, status_of(*u), acc + 2);
-                    sumsq(st, yj, mj, acc + 1);
-                    if (u->vty_pending > 0) {
-                        GemmProb v{};
-                        v.A = u->vty_src; v.lda = nb; v.m = u->vty_pending; v.k = mj;
-                        v.B = yj; v.ldb = nb; v.n = 1;
-                        v.C = u->vty[j].as<double>(); v.ldc = u->vty_pending;
-                        gv.push_back(v);
-                    }
+                    TLR_CUDA_TRY(cudaMemcpyAsync(yj, u->ytmp.as<double>(), mj * sizeof(double), cudaMemcpyDeviceToDevice, ss));
+                    diag_logsum(ss, u->M->D + (int64_t)j * nb * nb, nb, mj, acc, status_of(*u), acc + 2);
+                    sumsq(ss, yj, mj, acc + 1);
+                    if (j + 1 < nt && u->gram_n[j] > 0)
+                        for (int i = j + 1; i < nt; ++i) {
+                            const int r = u->r_of(i, j);
+                            if (r <= 0) continue;
+                            GemmProb v{};  // the slice of V_j' y_j of tile (i, j)
+                            v.A = Vslot(u->M, i, j); v.lda = nb; v.m = r; v.k = mj;
+                            v.B = yj; v.ldb = nb; v.n = 1;
+                            v.C = u->vty[j].as<double>() + u->gram_off[j][i]; v.ldc = r;
+                            gv.push_back(v);
+                        }
                 }
-                gemm_batched(ctx, st, true, false, gv, 1.0, 0.0);
-                dmark(dm_main, st, kDetSolve);
+                gemm_batched(ctx, ss, true, false, gv, 1.0, 0.0);
+                dmark(dm_sv, ss, kDetSolve);
+                TLR_CUDA_TRY(cudaEventRecord(ctx->ev_sv_done, ss));
+                sv_pending = true;
             }
         }
         for (GroupItem *u : ok) u->vtmp.release();
         mark();
         if (mode == FactorMode::Matern) cur ^= 1;
     }
-    // a factorisation that stopped may still have its look-ahead in flight
+    // a factorisation that stopped may still have its look-ahead in flight;
+    // the solve stream's last column
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_la_join, ctx->la));
     TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_la_join, 0));
+    TLR_CUDA_TRY(cudaEventRecord(ctx->ev_sv_done, ctx->sv));
+    TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_sv_done, 0));
     if (ctx->profile) {
-        for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la})
+        for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la, &dm_sv})
             if (!v->empty()) TLR_CUDA_TRY(cudaEventSynchronize(v->back().e));
-        for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la})
+        for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la, &dm_sv})
             for (size_t k = 1; k < v->size(); ++k) {
                 if ((*v)[k].idx < 0) continue;
                 float ms = 0.f;
