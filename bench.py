@@ -248,6 +248,13 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = tlr.Context(local)
+    if args.qr_sizes or args.svd_sizes:
+        bk = tlr.tlr_ctx_get_buckets(ctx)
+        if args.qr_sizes:
+            bk["qr_size"] = [int(v) for v in args.qr_sizes.split(",")]
+        if args.svd_sizes:
+            bk["svd_size"] = [int(v) for v in args.svd_sizes.split(",")]
+        tlr.tlr_ctx_set_buckets(ctx, bk)
     stream = torch.cuda.current_stream()
     xy_h, xy, z = make_inputs(tlr, ctx, torch, dev, rank)
     thetas = synth.theta_walk(THETA0, args.warmup + args.steps, seed=7, scale=0.05)
@@ -509,14 +516,15 @@ def run_gpu(args):
         "dtype": {"mixed": "f64 storage, paired-f32 products", "tensor": "f64 storage, bf16x5 tensor products",
                   "fp64": "f64"}[head_name],
         "data": "synthetic",
-        "config": {"workload": "ordering study, n=%d (perturbed grid), Matern sigma2=%g beta=%g nu=%g "
+        "config": {"workload": "TLR Matern log-likelihood, n=%d (perturbed grid), Matern sigma2=%g beta=%g nu=%g "
                                "walk start, %s, tile %d, eps %g, %s path" % ((N_POINTS,) + tuple(THETA0) +
                                                                             (ORDER, NB, EPS, head_name)),
                    "n": N_POINTS, "nb": NB, "eps": EPS, "ordering": ORDER, "theta0": list(THETA0),
                    "precision": head_name,
                    "theta_walk": "log-space, scale 0.05/step, seed 7",
                    "l2": "flushed between timed steps (256 MB write outside the events)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "rank_buckets": tlr.tlr_ctx_get_buckets(ctx)},
         "rel_dl_vs_fp64": rel_dl,
         "fp64_path": summary(fp64) if fp64 is not None else None,
         "mixed_path": summary(mixed) if mixed is not None else None,
@@ -1219,6 +1227,8 @@ def main():
     ap.add_argument("--datasets", type=int, default=256, help="datasets of the batched workload")
     ap.add_argument("--batch-nb", type=int, default=0, help="fixed tile size for the batched workload (0: tuned)")
     ap.add_argument("--maxrank", type=int, default=0, help="rank slots per tile (batched / serving; 0 = nb/2)")
+    ap.add_argument("--qr-sizes", default="", help="headline: cluster sizes of the QR rank buckets, e.g. 4,8,16,16")
+    ap.add_argument("--svd-sizes", default="", help="headline: cluster sizes of the SVD rank buckets, e.g. 1,4,8,16")
     ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream")
     ap.add_argument("--rate", type=float, default=500.0, help="arrival rate of the serving stream (1/s)")
     ap.add_argument("--mle-iters", type=int, default=30, help="evaluations per MLE job (serving)")
