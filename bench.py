@@ -44,7 +44,7 @@ ORDER = "hilbert"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from ncu captures of unchanged kernels,
 # by (kernel, tile size); the capture and its command are in profiles/
-NCU_TRAFFIC = {("k_potrf_inv<16>", 800): (3.04e6, "profiles/k_potrf_inv_n16000.md")}
+NCU_TRAFFIC = {}  # (kernel, tile) -> (DRAM bytes per launch, profile); none since the kernel's last change
 
 
 def peaks():
@@ -421,8 +421,9 @@ def run_gpu(args):
         fl = sum(m ** 3 / 3.0 for m in ms) / nt
         achieved = fl / (avg / 1000.0) / 1e12 if avg > 0 else 0.0
         occupied = 16 * 4 * sm_mhz * 1e6 / 1e12
-        traffic = NCU_TRAFFIC.get(("k_potrf_inv<16>", NB))
-        return {"bound": "alu", "kernel": "k_potrf_inv<16> (diagonal tile Cholesky + inverse, one 16-CTA cluster)",
+        traffic = NCU_TRAFFIC.get(("k_potrf_inv<16, 1>", NB))
+        return {"bound": "alu", "kernel": "k_potrf_inv<16, 1> (diagonal tile: Cholesky in FP64, its inverse in "
+                                          "float-float pairs on the paired paths; one 16-CTA cluster)",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak if fp64_peak else None,
                 "traffic": traffic[0] if traffic else None,

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "dense.cuh"
+#include "ff.cuh"
 #include "gemm.cuh"
 
 namespace tlr {
@@ -82,6 +83,45 @@ __device__ __forceinline__ void tile_update32(double *C, int ldc, const double (
         }
 }
 
+// The same update in float-float pairs (the inverse X on the paired paths):
+// C (pairs) -= A B with a, b pairs in shared memory as [row][k].
+__device__ __forceinline__ void tile_update32_ff(float2 *C, int ldc, const float2 (*a)[kBlk + 1],
+                                                 const float2 (*b)[kBlk + 1], int rows, int cols) {
+    const int tid = threadIdx.x, tr = (tid & 15) * 2, tc = (tid >> 4) * 2;
+    float2 cv[2][2];
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const int r = tr + x, c = tc + y;
+            cv[x][y] = (r < rows && c < cols) ? __ldcg(C + (int64_t)c * ldc + r) : make_float2(0.f, 0.f);
+        }
+    float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+    for (int k = 0; k < kBlk; ++k) {
+        const float2 a0 = a[tr][k], a1 = a[tr + 1][k], b0 = b[tc][k], b1 = b[tc + 1][k];
+        df_fma(a0.x, a0.y, b0.x, b0.y, h[0][0], l[0][0]);
+        df_fma(a0.x, a0.y, b1.x, b1.y, h[0][1], l[0][1]);
+        df_fma(a1.x, a1.y, b0.x, b0.y, h[1][0], l[1][0]);
+        df_fma(a1.x, a1.y, b1.x, b1.y, h[1][1], l[1][1]);
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const int r = tr + x, c = tc + y;
+            if (r < rows && c < cols) {
+                const FF d = ff_add(FF{cv[x][y].x, cv[x][y].y}, ff_neg(ff_two_sum(h[x][y], l[x][y])));
+                C[(int64_t)c * ldc + r] = make_float2(d.h, d.l);
+            }
+        }
+}
+
+__device__ __forceinline__ float2 ff_split(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
 // Cholesky of the w x w diagonal block at (p, p) of A by the calling CTA,
 // with the block's inverse: L_kk into A (lower; upper part of the block 0),
 // L_kk^-1 into Li (32 x 32, row major).  Returns the first failing column
@@ -150,7 +190,11 @@ __device__ int potrf_diag_block(double *A, int lda, int p, int w, double *Li, do
 // each read it to decide).
 // One cluster per job (blockIdx.x / kCl): the diagonal tiles of several
 // factorisations in one launch (the jobs travel in the kernel parameters).
-template <int kCl>
+// kFF: the inverse X in float-float pairs on the FP32 pipe (stored as pairs
+// in X's memory while the kernel runs, as doubles hi + lo at the end); the
+// Cholesky factor stays FP64.  The paired paths use X only in products they
+// run in paired FP32.
+template <int kCl, bool kFF>
 __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jobs) {
     const PotrfJob J = jobs.job[blockIdx.x / kCl];
     double *const A = J.A, *const X = J.X, *const scratch = J.scratch;
@@ -161,14 +205,19 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
     const int rank = (int)cl.block_rank(), tid = threadIdx.x;
     const int gtid = rank * kPotrfThreads + tid, gthreads = kCl * kPotrfThreads;
     __shared__ double sa[kBlk][kBlk + 1], sb[kBlk][kBlk + 1], sl[kBlk][kBlk + 1];
+    __shared__ float2 slf[kFF ? kBlk : 1][kBlk + 1];  // L_kk^-1 as pairs (kFF)
     __shared__ int s_bad;
+    float2 *const X2 = reinterpret_cast<float2 *>(X);
+    float2 (*const saf)[kBlk + 1] = reinterpret_cast<float2 (*)[kBlk + 1]>(sa);
+    float2 (*const sbf)[kBlk + 1] = reinterpret_cast<float2 (*)[kBlk + 1]>(sb);
     const int nbk = (m + kBlk - 1) / kBlk;
     double *dinv = scratch;
     long long *stop = reinterpret_cast<long long *>(scratch + (int64_t)kBlk * kBlk * kBlk);
     // X = I; CTA 0 factors the first diagonal block
     for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
         const int r = (int)(e % m), c = (int)(e / m);
-        X[(int64_t)c * ldx + r] = (r == c) ? 1.0 : 0.0;
+        if constexpr (kFF) X2[(int64_t)c * ldx + r] = make_float2(r == c ? 1.f : 0.f, 0.f);
+        else X[(int64_t)c * ldx + r] = (r == c) ? 1.0 : 0.0;
     }
     if (rank == 0) {
         // one read of the status word decides for the whole CTA (another
@@ -193,7 +242,11 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
         const double *Li = dinv + (int64_t)kb * kBlk * kBlk;  // L_kk^-1, row major
         // 1. panel rows below the block: x <- a L_kk^-T, x_c = sum_{k<=c} a_k Linv[c][k];
         //    inverse block row: X[k-block, c] <- L_kk^-1 X[k-block, c], c < p + w
-        for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) sl[e / kBlk][e % kBlk] = __ldcg(Li + e);
+        for (int e = tid; e < kBlk * kBlk; e += kPotrfThreads) {
+            const double v = __ldcg(Li + e);
+            sl[e / kBlk][e % kBlk] = v;
+            if constexpr (kFF) slf[e / kBlk][e % kBlk] = ff_split(v);
+        }
         __syncthreads();
         for (int r = p + w + gtid; r < m; r += gthreads) {
             double a[kBlk];
@@ -209,16 +262,32 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
             }
         }
         for (int c = gtid; c < p + w; c += gthreads) {
-            double x[kBlk];
+            if constexpr (kFF) {
+                float2 x[kBlk];
 #pragma unroll
-            for (int k = 0; k < kBlk; ++k) x[k] = k < w ? __ldcg(X + (int64_t)c * ldx + p + k) : 0.0;
+                for (int k = 0; k < kBlk; ++k)
+                    x[k] = k < w ? __ldcg(X2 + (int64_t)c * ldx + p + k) : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int r = 0; r < kBlk; ++r) {
-                if (r >= w) break;
-                double v = 0.0;
+                for (int r = 0; r < kBlk; ++r) {
+                    if (r >= w) break;
+                    float vh = 0.f, vl = 0.f;
 #pragma unroll
-                for (int k = 0; k <= r; ++k) v = fma(sl[r][k], x[k], v);
-                X[(int64_t)c * ldx + p + r] = v;
+                    for (int k = 0; k <= r; ++k) df_fma(slf[r][k].x, slf[r][k].y, x[k].x, x[k].y, vh, vl);
+                    const FF v = ff_two_sum(vh, vl);
+                    X2[(int64_t)c * ldx + p + r] = make_float2(v.h, v.l);
+                }
+            } else {
+                double x[kBlk];
+#pragma unroll
+                for (int k = 0; k < kBlk; ++k) x[k] = k < w ? __ldcg(X + (int64_t)c * ldx + p + k) : 0.0;
+#pragma unroll
+                for (int r = 0; r < kBlk; ++r) {
+                    if (r >= w) break;
+                    double v = 0.0;
+#pragma unroll
+                    for (int k = 0; k <= r; ++k) v = fma(sl[r][k], x[k], v);
+                    X[(int64_t)c * ldx + p + r] = v;
+                }
             }
         }
         cl.sync();
@@ -245,6 +314,7 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
             }
         };
         double ra[kTileLoads], rb[kTileLoads];
+        float2 rbf[kTileLoads];
         auto fetch = [&](int t) {
             bool inv;
             int I, Jb;
@@ -254,7 +324,9 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
             for (int u = 0; u < kTileLoads; ++u) {
                 const int e = tid + u * kPotrfThreads, r = e % kBlk, k = e / kBlk;
                 ra[u] = (r < rows && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + ri + r) : 0.0;
-                if (inv) rb[u] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
+                if (kFF && inv)
+                    rbf[u] = (r < cols && k < w) ? __ldcg(X2 + (int64_t)(cj + r) * ldx + p + k) : make_float2(0.f, 0.f);
+                else if (inv) rb[u] = (r < cols && k < w) ? __ldcg(X + (int64_t)(cj + r) * ldx + p + k) : 0.0;
                 else rb[u] = (r < cols && k < w) ? __ldcg(A + (int64_t)(p + k) * lda + cj + r) : 0.0;
             }
         };
@@ -267,8 +339,13 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
 #pragma unroll
             for (int u = 0; u < kTileLoads; ++u) {
                 const int e = tid + u * kPotrfThreads;
-                sa[e % kBlk][e / kBlk] = ra[u];
-                sb[e % kBlk][e / kBlk] = rb[u];
+                if (kFF && inv) {
+                    saf[e % kBlk][e / kBlk] = ff_split(ra[u]);
+                    sbf[e % kBlk][e / kBlk] = rbf[u];
+                } else {
+                    sa[e % kBlk][e / kBlk] = ra[u];
+                    sb[e % kBlk][e / kBlk] = rb[u];
+                }
             }
             __syncthreads();
             return inv ? (X + (int64_t)cj * ldx + ri) : (A + (int64_t)cj * lda + ri);
@@ -295,16 +372,21 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
                 const int ri = I * kBlk, cj = Jb * kBlk, rows = min(kBlk, m - ri), cols = min(kBlk, m - cj);
                 double *C = apply(t);
                 if (t + step < ntot) fetch(t + step);
-                tile_update32(C, inv ? ldx : lda, sa, sb, rows, cols, !inv && I == Jb);
+                if (kFF && inv) tile_update32_ff(reinterpret_cast<float2 *>(C), ldx, saf, sbf, rows, cols);
+                else tile_update32(C, inv ? ldx : lda, sa, sb, rows, cols, !inv && I == Jb);
             }
         }
         cl.sync();
         if (__ldcg(stop)) return;  // written by CTA 0 only, before the barrier
     }
-    // zero the strict upper triangle of the factor
+    // zero the strict upper triangle of the factor; the paired inverse to doubles
     for (int64_t e = gtid; e < (int64_t)m * m; e += gthreads) {
         const int r = (int)(e % m), c = (int)(e / m);
         if (r < c) A[(int64_t)c * lda + r] = 0.0;
+        if constexpr (kFF) {
+            const float2 v = X2[(int64_t)c * ldx + r];
+            X[(int64_t)c * ldx + r] = (double)v.x + (double)v.y;
+        }
     }
 }
 
@@ -384,7 +466,7 @@ void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int
     }
 }
 
-void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs) {
+void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs, bool ff_inverse) {
     std::vector<PotrfJob> act;
     for (const PotrfJob &J : jobs) {
         if (J.m <= 0) continue;
@@ -411,7 +493,10 @@ void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs)
     static std::once_flag once;
     static int csize = 8;  // 16 CTAs where the device runs such clusters, else 8
     std::call_once(once, [] {
-        if (cudaFuncSetAttribute(k_potrf_inv<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        if (cudaFuncSetAttribute(k_potrf_inv<16, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_potrf_inv<16, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(16);
             cfg.blockDim = dim3(kPotrfThreads);
@@ -423,15 +508,19 @@ void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs)
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int nclusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclusters, k_potrf_inv<16>, &cfg) == cudaSuccess && nclusters > 0)
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_potrf_inv<16, true>, &cfg) == cudaSuccess && nclusters > 0)
                 csize = 16;
         }
         cudaGetLastError();  // clear any error of the queries
     });
-    if (csize == 16)
-        launch_clustered(k_potrf_inv<16>, 16, (int)act.size(), kPotrfThreads, 0, s, b);
-    else
-        launch_clustered(k_potrf_inv<8>, 8, (int)act.size(), kPotrfThreads, 0, s, b);
+    const int nc = (int)act.size();
+    if (csize == 16) {
+        if (ff_inverse) launch_clustered(k_potrf_inv<16, true>, 16, nc, kPotrfThreads, 0, s, b);
+        else launch_clustered(k_potrf_inv<16, false>, 16, nc, kPotrfThreads, 0, s, b);
+    } else {
+        if (ff_inverse) launch_clustered(k_potrf_inv<8, true>, 8, nc, kPotrfThreads, 0, s, b);
+        else launch_clustered(k_potrf_inv<8, false>, 8, nc, kPotrfThreads, 0, s, b);
+    }
 }
 
 void potrf_inv(tlr_ctx *ctx, cudaStream_t s, double *A, int lda, int m, double *X, int ldx, long long row_base) {

@@ -34,7 +34,9 @@ struct PotrfJob {
 struct PotrfBatch {
     PotrfJob job[kMaxGroup];
 };
-void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs);
+// ff_inverse: X in float-float arithmetic (~1e-14 relative), the factor in
+// FP64 (the paired-FP32 paths, whose products with X are paired FP32).
+void potrf_inv_batched(tlr_ctx *ctx, cudaStream_t s, std::vector<PotrfJob> jobs, bool ff_inverse = false);
 
 // B <- L^-1 B for every right-hand side matrix (L lower triangular m x m).
 void trsm_left_lower(tlr_ctx *ctx, cudaStream_t s, const double *L, int ldl, int m,

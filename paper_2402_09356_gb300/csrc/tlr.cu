@@ -553,7 +553,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
                 aux_marks.push_back(ctx->prof_events[prof_used++]);
             }
             dmark(dm_aux, ctx->aux, -1);
-            potrf_inv_batched(ctx, ctx->aux, pj);  // one cluster launch per column of the group
+            potrf_inv_batched(ctx, ctx->aux, pj, df);  // one cluster launch per column of the group
             dmark(dm_aux, ctx->aux, kDetPotrf);
             if (ctx->profile) {
                 profile_events(ctx, prof_used + 1);
