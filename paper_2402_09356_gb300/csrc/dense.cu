@@ -122,6 +122,18 @@ __device__ __forceinline__ float2 ff_split(double v) {
     return make_float2(h, __double2float_rn(v - (double)h));
 }
 
+// 1 / sqrt(d) for d > 0 (normal): the PTX approximation, then two Newton
+// steps y <- y (3 - d y^2) / 2, each squaring the relative error (to about
+// an ulp).  One thread forms it per column of a diagonal block, where every
+// FP64 instruction holds the FP64 pipe for 64 cycles: this takes fewer
+// instructions than a square root followed by a quotient per entry.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    return y * fma(-0.5 * d * y, y, 1.5);
+}
+
 // Cholesky of the w x w diagonal block at (p, p) of A by the calling CTA,
 // with the block's inverse: L_kk into A (lower; upper part of the block 0),
 // L_kk^-1 into Li (32 x 32, row major).  Returns the first failing column
@@ -136,17 +148,24 @@ __device__ int potrf_diag_block(double *A, int lda, int p, int w, double *Li, do
     if (tid == 0) *s_bad = -1;
     __syncthreads();
     // right-looking Cholesky of the block, one column at a time, the updates
-    // spread over the CTA's threads
+    // spread over the CTA's threads; the pivot's reciprocal is kept in the
+    // padding column sa[c][kBlk] (the column is scaled by it, and the
+    // inverse below divides by the pivots through it)
     for (int c = 0; c < w; ++c) {
         if (tid == 0) {
             const double d = sa[c][c];
-            if (!(d > 0.0)) *s_bad = c;
-            else sa[c][c] = sqrt(d);
+            if (!(d > 0.0)) {
+                *s_bad = c;
+            } else {
+                const double y = rsqrt_newton(d);
+                sa[c][c] = d * y;
+                sa[c][kBlk] = y;
+            }
         }
         __syncthreads();
         if (*s_bad >= 0) break;  // read after the barrier: uniform
-        const double piv = sa[c][c];
-        for (int r = c + 1 + tid; r < w; r += kPotrfThreads) sa[r][c] /= piv;
+        const double rpiv = sa[c][kBlk];
+        for (int r = c + 1 + tid; r < w; r += kPotrfThreads) sa[r][c] *= rpiv;
         __syncthreads();
         const int nr = w - c - 1;
         for (int e = tid; e < nr * nr; e += kPotrfThreads) {
@@ -170,7 +189,7 @@ __device__ int potrf_diag_block(double *A, int lda, int p, int w, double *Li, do
         part += __shfl_xor_sync(0xFFFFFFFFu, part, 1);
         if (q == 0) {
             double v = 0.0;
-            if (c < w && r < w && r >= c) v = ((r == c ? 1.0 : 0.0) - part) / sa[r][r];
+            if (c < w && r < w && r >= c) v = ((r == c ? 1.0 : 0.0) - part) * sa[r][kBlk];
             sl[r][c] = v;
         }
         __syncwarp();
@@ -248,7 +267,10 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
             if constexpr (kFF) slf[e / kBlk][e % kBlk] = ff_split(v);
         }
         __syncthreads();
-        for (int r = p + w + gtid; r < m; r += gthreads) {
+        // rows and columns dealt to the CTAs in turn (gq = tid * kCl + rank), so
+        // that every CTA's FP64 pipe takes a share (a 32-term chain each)
+        const int gq = tid * kCl + rank;
+        for (int r = p + w + gq; r < m; r += gthreads) {
             double a[kBlk];
 #pragma unroll
             for (int k = 0; k < kBlk; ++k) a[k] = k < w ? __ldcg(A + (int64_t)(p + k) * lda + r) : 0.0;
@@ -261,7 +283,7 @@ __global__ void __launch_bounds__(kPotrfThreads) k_potrf_inv(const PotrfBatch jo
                 A[(int64_t)(p + c) * lda + r] = x;
             }
         }
-        for (int c = gtid; c < p + w; c += gthreads) {
+        for (int c = gq; c < p + w; c += gthreads) {
             if constexpr (kFF) {
                 float2 x[kBlk];
 #pragma unroll
