@@ -44,7 +44,7 @@ ORDER = "hilbert"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch from ncu captures of unchanged kernels,
 # by (kernel, tile size); the capture and its command are in profiles/
-NCU_TRAFFIC = {}  # (kernel, tile) -> (DRAM bytes per launch, profile); none since the kernel's last change
+NCU_TRAFFIC = {("k_potrf_inv<16, 1>", 800): (3.34e6, "profiles/k_potrf_inv_n16000.md")}
 
 
 def peaks():
