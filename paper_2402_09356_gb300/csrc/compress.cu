@@ -573,10 +573,22 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
 }
 
 // Squared norm of the first sdot entries of x (lanes stride 32; warp-uniform result).
+// FP32 columns are read as pairs of entries per lane (8-byte shared-memory
+// accesses, half the load instructions; the FP32 phase's columns hold 2 s
+// entries and start on 8-byte boundaries).
 template <class T>
 __device__ __forceinline__ T col_norm2(const T *x, int sdot, int lane) {
     T a = 0;
-    for (int r = lane; r < sdot; r += 32) a = fma(x[r], x[r], a);
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 *x2 = reinterpret_cast<const float2 *>(x);
+        for (int i = lane; 2 * i < sdot; i += 32) {
+            const float2 v = x2[i];
+            a = fmaf(v.x, v.x, a);
+            if (2 * i + 1 < sdot) a = fmaf(v.y, v.y, a);
+        }
+    } else {
+        for (int r = lane; r < sdot; r += 32) a = fma(x[r], x[r], a);
+    }
     return warp_sum(a);
 }
 
@@ -596,7 +608,16 @@ template <class T>
 __device__ __forceinline__ bool jacobi_rotate(T *x, T *y, T *nx, T *ny, int sdot, int srot, int lane, T tol2) {
     const T al = *nx, be = *ny;
     T ga = 0;
-    for (int r = lane; r < sdot; r += 32) ga = fma(x[r], y[r], ga);
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 *x2 = reinterpret_cast<const float2 *>(x), *y2 = reinterpret_cast<const float2 *>(y);
+        for (int i = lane; 2 * i < sdot; i += 32) {
+            const float2 u = x2[i], v = y2[i];
+            ga = fmaf(u.x, v.x, ga);
+            if (2 * i + 1 < sdot) ga = fmaf(u.y, v.y, ga);
+        }
+    } else {
+        for (int r = lane; r < sdot; r += 32) ga = fma(x[r], y[r], ga);
+    }
     ga = warp_sum(ga);
     if (ga == T(0) || ga * ga <= tol2 * (al * be)) return false;
     T c, sn, t;
@@ -618,10 +639,19 @@ __device__ __forceinline__ bool jacobi_rotate(T *x, T *y, T *nx, T *ny, int sdot
         c = rsqrtf(fmaf(t, t, 1.0f));
         sn = c * t;
     }
-    for (int r = lane; r < srot; r += 32) {
-        const T a = x[r], b = y[r];
-        x[r] = fma(c, a, -sn * b);
-        y[r] = fma(sn, a, c * b);
+    if constexpr (std::is_same<T, float>::value) {
+        float2 *x2 = reinterpret_cast<float2 *>(x), *y2 = reinterpret_cast<float2 *>(y);
+        for (int i = lane; 2 * i < srot; i += 32) {  // srot is even in the FP32 phase
+            const float2 a = x2[i], b = y2[i];
+            x2[i] = make_float2(fmaf(c, a.x, -sn * b.x), fmaf(c, a.y, -sn * b.y));
+            y2[i] = make_float2(fmaf(sn, a.x, c * b.x), fmaf(sn, a.y, c * b.y));
+        }
+    } else {
+        for (int r = lane; r < srot; r += 32) {
+            const T a = x[r], b = y[r];
+            x[r] = fma(c, a, -sn * b);
+            y[r] = fma(sn, a, c * b);
+        }
     }
     const T c2 = c * c, tg = T(2) * t * ga, tt = t * t;
     T al2 = c2 * (al - tg + tt * be), be2 = c2 * (be + tg + tt * al);
