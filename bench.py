@@ -1098,6 +1098,7 @@ def run_serving(args):
     nd = 32
     sizes = [SERVE_SIZES[i % len(SERVE_SIZES)] for i in range(nd)]
     pool = tlr.Pool(0, workers=args.workers, nb=NB, maxrank=args.maxrank)
+    tlr.tlr_pool_configure(pool, args.group)
     t_setup = time.perf_counter()
     zctx = tlr.Context(0)
     zs = [draw_z_lw(tlr, zctx, synth.jittered_grid(n, seed=300 + i), synth.standard_normal(n, seed=600 + i),
@@ -1187,7 +1188,8 @@ def run_serving(args):
             "config": {"workload": "serving: 32 resident datasets n in {5k,10k,20k,40k,80k}, nu=1.0 walk start, "
                                    "Hilbert, tile %d, eps %g, Poisson %g req/s x %d requests + 2 MLE jobs, "
                                    "%d workers" % (NB, EPS, args.rate, R, args.workers),
-                       "workers": args.workers, "maxrank": args.maxrank, "rate": args.rate, "requests": R,
+                       "workers": args.workers, "group": args.group, "maxrank": args.maxrank, "rate": args.rate,
+                       "requests": R,
                        "latency": "host clock, submission to completion",
                        "z": "Z = L(1, 0.1, 1.0) w from the library's TLR factor at eps 1e-9; %d kept Z = w"
                             % z_white},
@@ -1225,6 +1227,7 @@ def main():
                     help="headline: one n = 40,000 evaluation per step; batched: many datasets per step; "
                          "serving: a Poisson request stream over resident datasets")
     ap.add_argument("--workers", type=int, default=8, help="pool workers (batched / serving)")
+    ap.add_argument("--group", type=int, default=1, help="serving: requests a worker evaluates together")
     ap.add_argument("--datasets", type=int, default=256, help="datasets of the batched workload")
     ap.add_argument("--batch-nb", type=int, default=0, help="fixed tile size for the batched workload (0: tuned)")
     ap.add_argument("--maxrank", type=int, default=0, help="rank slots per tile (batched / serving; 0 = nb/2)")
