@@ -138,7 +138,11 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
     // n = 40,000 than paired FP32: their 128 x 32 tiles keep the tensor pipe
     // below a third of its rate and the operand splits add a launch each on
     // the critical path; they stay paired FP32.
-    const bool tcp = tc, tcc = false;
+    // The Gram matrices V_j' V_j (inner dimension the tile size, S x S
+    // outputs) are the one critical-path product measured faster there
+    // (13.6 -> 5.9 ms per evaluation at n = 40,000; all of them on the
+    // tensor cores: 469 -> 638 ms).
+    const bool tcp = tc, tcc = false, tcg = tc;
     const bool dfp = df && !tcc;  // paired-FP32 copies for the critical-path products
     const int G = (int)list.size();
     FactorStats *pstats = list[0].stats;  // profiling totals of the call
@@ -715,7 +719,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
                     g.A = vt; g.lda = nb; g.m = S; g.k = mj;
                     g.B = vt; g.ldb = nb; g.n = S;
                     g.C = I.gram[j].as<double>(); g.ldc = S;
-                    if (dfp) {
+                    if (dfp && !tcg) {
                         float2 *w2 = hold_buf(hold, (size_t)nb * S * sizeof(float2), st).as<float2>();
                         sg.push_back(SplitDesc{vt, w2, nb, mj, S});
                         g.A2 = g.B2 = w2;
@@ -732,7 +736,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
             dmark(dm_main, st, kDetTrsm);
             if (!gg.empty()) {
                 split_f2_batched(ctx, st, sg);
-                if (tcc) gemm_tc(ctx, st, true, false, gg, 1.0, 0.0);
+                if (tcg) gemm_tc(ctx, st, true, false, gg, 1.0, 0.0);
                 else gemm_batched(ctx, st, true, false, gg, 1.0, 0.0, df);
                 dmark(dm_main, st, kDetGram);
             }
