@@ -613,11 +613,22 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
         }
         std::vector<int> rk, fails;
         dmark(dm_main, st, kDetDiagCopy);
+        // the status words ride on the compression's own host read of its
+        // ranks: its first round waits for the side stream's POTRF and copies
+        // them, so that a tile column syncs the host once, not twice
+        const int nwords = own_words ? G + 1 : 1;
+        bool have_status = false;
+        const std::function<void()> read_status = [&]() {
+            TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->hp, ctx->ev_join, 0));
+            TLR_CUDA_TRY(cudaMemcpyAsync(ctx->h_status, ctx->d_status, nwords * sizeof(DevStatus),
+                                         cudaMemcpyDeviceToHost, ctx->hp));
+            have_status = true;
+        };
         if (!jobs.empty()) {
             // on the high-priority stream, ahead of the look-ahead GEMM
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_fork, st));
             TLR_CUDA_TRY(cudaStreamWaitEvent(ctx->hp, ctx->ev_hp_fork, 0));
-            compress_jobs(ctx, ctx->hp, jobs, rk, fails, df, nullptr, grow, tcc);
+            compress_jobs(ctx, ctx->hp, jobs, rk, fails, df, read_status, grow, tcc);
             TLR_CUDA_TRY(cudaEventRecord(ctx->ev_hp_join, ctx->hp));
             TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_hp_join, 0));
         }
@@ -625,11 +636,14 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
         dmark(dm_main, st, kDetCompress);
         TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join, 0));
         dmark(dm_main, st, kDetJoin);
-        // --- outcomes: the status words (syncs st, after the side stream's
-        // work), then non-finite tiles, then ranks that do not fit
-        const int nwords = own_words ? G + 1 : 1;
-        TLR_CUDA_TRY(cudaMemcpyAsync(ctx->h_status, ctx->d_status, nwords * sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
-        TLR_CUDA_TRY(cudaStreamSynchronize(st));
+        // --- outcomes: the status words (read with the ranks above, or here
+        // for a column with nothing to compress), then non-finite tiles, then
+        // ranks that do not fit
+        if (!have_status) {
+            TLR_CUDA_TRY(cudaMemcpyAsync(ctx->h_status, ctx->d_status, nwords * sizeof(DevStatus),
+                                         cudaMemcpyDeviceToHost, st));
+            TLR_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         if (own_words && ctx->h_status[0].code)  // a device-wide failure (bounded wait ran out)
             throw make_error(ctx->h_status[0].code, "TLR Cholesky: device status %d", ctx->h_status[0].code);
         for (GroupItem *u : act) {
