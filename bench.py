@@ -972,7 +972,7 @@ def run_batched(args):
         torch.cuda.synchronize()
         launches0 = tlr.tlr_launch_count()
         clocks.start()
-        times, results, fails, used64 = [], [], 0, 0
+        times, results, fails, used64, statuses = [], [], 0, 0, []
         for k in range(args.steps):
             t0 = time.perf_counter()
             res, st = tlr.tlr_pool_loglik(pool, ids, [tuple(w[args.warmup + k]) for w in walks], eps=EPS,
@@ -982,6 +982,7 @@ def run_batched(args):
             used64 += sum(1 for r, x in zip(res, st) if x == 0 and r["precision_used"] == tlr.TLR_PREC_FP64)
             results.append([(r["loglik"], r["min_pivot2"], r["logdet"]) if x == 0 else None
                             for r, x in zip(res, st)])
+            statuses.append([(int(x), int(r["precision_used"]) if x == 0 else None) for r, x in zip(res, st)])
         torch.cuda.synchronize()
         clocks_all[name] = clocks.stop()
         total = sum(times)
@@ -990,7 +991,8 @@ def run_batched(args):
         rate, units, total = aggregate_units(count * args.steps, total, world, torch.device("cuda", local))
         out[name] = {"evals_per_s": rate, "s_per_step": total / args.steps,
                      "failed": fails, "fp64_results": used64,
-                     "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results}
+                     "gpu_launches": int(tlr.tlr_launch_count() - launches0), "results": results,
+                     "statuses": statuses}
         pool_stats[name] = tlr.tlr_pool_stats(pool)
         pool.close()
 
@@ -1010,6 +1012,29 @@ def run_batched(args):
         return rel, pairs
     compare.extra = {}
 
+    def by_theta_region():
+        # failures, AUTO's FP64 redos and the mixed path's worst |dl| / |l|
+        # per region of the evaluated theta (range beta, smoothness nu)
+        def region(th):
+            b = "beta<0.1" if th[1] < 0.1 else ("beta<0.2" if th[1] < 0.2 else "beta>=0.2")
+            return b + (", nu<1.5" if th[2] < 1.5 else ", nu>=1.5")
+        reg = {}
+        for k in range(args.steps):
+            for i in range(count):
+                th = walks[i][args.warmup + k]
+                e = reg.setdefault(region(th), {"evals": 0, "failed": {nm: 0 for nm in ("fp64", "mixed", "tensor",
+                                                                                        "auto")},
+                                                "auto_fp64_results": 0, "mixed_rel_dl_max": 0.0})
+                e["evals"] += 1
+                for nm in e["failed"]:
+                    e["failed"][nm] += out[nm]["statuses"][k][i][0] != 0
+                e["auto_fp64_results"] += out["auto"]["statuses"][k][i][1] == tlr.TLR_PREC_FP64
+                a, b = out["mixed"]["results"][k][i], out["fp64"]["results"][k][i]
+                if a is not None and b is not None:
+                    e["mixed_rel_dl_max"] = max(e["mixed_rel_dl_max"], abs(a[0] - b[0]) / abs(b[0]))
+        return dict(sorted(reg.items()))
+
+    theta_regions = by_theta_region()
     rel, pairs = compare("mixed")
     rel_auto, _ = compare("auto")
     rel_tensor, _ = compare("tensor")
@@ -1052,17 +1077,18 @@ def run_batched(args):
                        "group_bucket_autotune": autotune,
                        "timing": "host wall clock around each blocking tlr_pool_loglik (all datasets)",
                        "l2": "inputs (all datasets' factors) larger than L2"},
-            "fp64_path": {k: v for k, v in out["fp64"].items() if k != "results"},
-            "mixed_path": {k: v for k, v in out["mixed"].items() if k != "results"},
-            "auto_path": {k: v for k, v in out["auto"].items() if k != "results"},
-            "tensor_path": {k: v for k, v in out["tensor"].items() if k != "results"},
-            "mixed_untuned_path": {k: v for k, v in out["mixed_untuned"].items() if k != "results"},
+            "fp64_path": {k: v for k, v in out["fp64"].items() if k not in ("results", "statuses")},
+            "mixed_path": {k: v for k, v in out["mixed"].items() if k not in ("results", "statuses")},
+            "auto_path": {k: v for k, v in out["auto"].items() if k not in ("results", "statuses")},
+            "tensor_path": {k: v for k, v in out["tensor"].items() if k not in ("results", "statuses")},
+            "mixed_untuned_path": {k: v for k, v in out["mixed_untuned"].items() if k not in ("results", "statuses")},
             "tuned_over_untuned": out["mixed"]["evals_per_s"] / out["mixed_untuned"]["evals_per_s"],
             "mixed_tuned_equal_untuned": "%d of %d results bit for bit" % (sum(same_untuned), len(same_untuned)),
             "rel_dl_mixed_vs_fp64_max": max(rel) if rel else None,
             "mixed_vs_fp64": accuracy,
             "auto_vs_fp64": accuracy_auto,
             "tensor_vs_fp64": accuracy_tensor,
+            "by_theta_region": theta_regions,
             "pool": st, "setup_s": setup_s, "clocks": clocks_all[head],
             "gpu_launches": out[head]["gpu_launches"]}
     if world > 1:
