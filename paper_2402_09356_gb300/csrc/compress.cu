@@ -633,9 +633,12 @@ __device__ __forceinline__ bool jacobi_rotate(T *x, T *y, T *nx, T *ny, int sdot
         c = c * fma(-0.5 * u * c, c, 1.5);
         sn = c * t;
     } else {
-        const float zeta = (be - al) / (2.0f * ga);
-        t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
-        if (t == 0.0f) return false;  // below FP32 resolution
+        // approximate reciprocals and square root: (c, c t) is orthogonal to
+        // FP32 accuracy for any t, so only convergence depends on them
+        const float zeta = __fdividef(be - al, 2.0f * ga), az = fabsf(zeta);
+        if (az >= 1e18f) return false;  // t below FP32 resolution
+        const float q = fmaf(zeta, zeta, 1.0f);
+        t = copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
         c = rsqrtf(fmaf(t, t, 1.0f));
         sn = c * t;
     }
@@ -781,15 +784,40 @@ __device__ int jacobi_sweeps(cg::cluster_group &cl, T *buf0, int stride, int b, 
                     break;
                 }
             }
-            // pull the blocks (and norms) of round g + 1 from their holders in round g
-            for (int slot = 0; slot < 2; ++slot) {
-                const int blk = block_at(slot ? py : px, g + 1, nblk);
-                const int p = pos_of(blk, g, nblk);
-                const int h = p < kCl ? p : nblk - 1 - p, hs = p < kCl ? 0 : 1;
-                const T *src = cl.map_shared_rank(buf(cur), h);
+            // pull the blocks (and norms) of round g + 1 from their holders in
+            // round g: kPull remote loads of each slot are issued before any
+            // store (the compiler cannot tell the remote source from the
+            // local destination, so a load-store loop waits out every round
+            // trip)
+            {
+                const T *src[2];
                 T *dst = buf(cur ^ 1);
-                for (int e = tid; e < bs; e += kQrThreads) dst[slot * bs + e] = src[hs * bs + e];
-                for (int e = tid; e < b; e += kQrThreads) dst[2 * bs + slot * b + e] = src[2 * bs + hs * b + e];
+                for (int slot = 0; slot < 2; ++slot) {
+                    const int blk = block_at(slot ? py : px, g + 1, nblk);
+                    const int p = pos_of(blk, g, nblk);
+                    const int h = p < kCl ? p : nblk - 1 - p, hs = p < kCl ? 0 : 1;
+                    src[slot] = cl.map_shared_rank(buf(cur), h) + hs * bs;
+                    const T *ns = cl.map_shared_rank(buf(cur), h) + 2 * bs + hs * b;
+                    for (int e = tid; e < b; e += kQrThreads) dst[2 * bs + slot * b + e] = ns[e];
+                }
+                constexpr int kPull = 4;
+                for (int e0 = tid; e0 < bs; e0 += kPull * kQrThreads) {
+                    T v[2][kPull];
+#pragma unroll
+                    for (int u = 0; u < kPull; ++u) {
+                        const int e = e0 + u * kQrThreads;
+                        v[0][u] = e < bs ? src[0][e] : T(0);
+                        v[1][u] = e < bs ? src[1][e] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPull; ++u) {
+                        const int e = e0 + u * kQrThreads;
+                        if (e < bs) {
+                            dst[e] = v[0][u];
+                            dst[bs + e] = v[1][u];
+                        }
+                    }
+                }
             }
             cur ^= 1;
             __syncthreads();
