@@ -244,6 +244,7 @@ void tlr_ctx_destroy(tlr_ctx *ctx) {
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->prof_events) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->cls_time_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->comp_events) cudaEventDestroy(e);
     for (StageRing &R : ctx->stage) {
         if (R.h) cudaFreeHost(R.h);
         if (R.d) cudaFree(R.d);

@@ -184,6 +184,8 @@ struct tlr_ctx {
     // compression sub-steps (when profiling): sample GEMM, QR of Y, projection
     // GEMM, QR of B', SVD, host decision (incl. sync), U/V GEMMs
     std::vector<cudaEvent_t> comp_events;
+    size_t comp_used = 0;                     // events of comp_events recorded since the last collect
+    std::vector<cudaEvent_t> comp_pending;    // complete rounds (8 marks each) not yet read
     double comp_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     long long comp_stats[7] = {};  // tiles, rounds, FP64 Jacobi sweeps (sum, max), FP32 sweeps (sum), QR / SVD jobs on the global-memory kernels
     // the 16-CTA cluster Jacobi (profiling): device ms, FP64 flops, launches, clusters

@@ -1499,11 +1499,12 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
     const bool dfp = df && !tc;  // paired-FP32 operand copies for the products
     bool overlapped = false;
     ensure_omega(ctx, st);
-    // profiling marks between the sub-steps of each adaptive round
+    // profiling marks between the sub-steps of each adaptive round, from a
+    // pool that is not reused before compress_profile_collect reads it
     std::vector<cudaEvent_t> ev;
     auto cmark = [&]() {
         if (!ctx->profile) return;
-        size_t k = ev.size();
+        const size_t k = ctx->comp_used++;
         while (ctx->comp_events.size() <= k) {
             cudaEvent_t e;
             TLR_CUDA_TRY(cudaEventCreate(&e));
@@ -1513,18 +1514,16 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
         ev.push_back(ctx->comp_events[k]);
     };
     // 8 marks per round: start, after sampling, QR of Y, projection, QR of B,
-    // SVD, host decision, U/V; summed into ctx->comp_ms when the call ends
+    // SVD, host decision, U/V; the complete rounds are handed on to
+    // compress_profile_collect (waiting for them here would hold the host
+    // until this call's last products end, and the stream that takes the
+    // next launches would idle)
     struct Flush {
         tlr_ctx *ctx;
         std::vector<cudaEvent_t> &ev;
         ~Flush() {
-            if (!ctx->profile || ev.empty()) return;
-            if (cudaEventSynchronize(ev.back()) != cudaSuccess) return;
-            for (size_t c = 0; c + 8 <= ev.size(); c += 8)
-                for (int k = 0; k < 7; ++k) {
-                    float ms = 0.f;
-                    if (cudaEventElapsedTime(&ms, ev[c + k], ev[c + k + 1]) == cudaSuccess) ctx->comp_ms[k] += ms;
-                }
+            if (!ctx->profile) return;
+            ctx->comp_pending.insert(ctx->comp_pending.end(), ev.begin(), ev.begin() + (ev.size() / 8) * 8);
         }
     } flush{ctx, ev};
     const int nj = (int)jobs.size();
@@ -1817,6 +1816,23 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs
     if (overlap && !overlapped) overlap();  // nothing was compressed
 }
 
+void compress_profile_reset(tlr_ctx *ctx) {
+    ctx->comp_pending.clear();
+    ctx->comp_used = 0;
+}
+
+void compress_profile_collect(tlr_ctx *ctx) {
+    const std::vector<cudaEvent_t> &ev = ctx->comp_pending;
+    for (size_t c = 0; c + 8 <= ev.size(); c += 8) {
+        TLR_CUDA_TRY(cudaEventSynchronize(ev[c + 7]));
+        for (int k = 0; k < 7; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[c + k], ev[c + k + 1]) == cudaSuccess) ctx->comp_ms[k] += ms;
+        }
+    }
+    compress_profile_reset(ctx);
+}
+
 void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &jobs, double tau, int maxrank,
                     std::vector<int> &ranks, long long *bad_tile, long long *nan_tile, bool df,
                     const std::function<void()> &overlap, const GrowSlot &grow, bool tc) {
@@ -1825,7 +1841,9 @@ void compress_tiles(tlr_ctx *ctx, cudaStream_t st, std::vector<CompressJob> &job
         J.maxrank = maxrank;
     }
     std::vector<int> fails;
+    compress_profile_reset(ctx);
     compress_jobs(ctx, st, jobs, ranks, fails, df, overlap, grow, tc);
+    if (ctx->profile) compress_profile_collect(ctx);
     *bad_tile = *nan_tile = -1;
     for (int q : fails) {
         long long *first = ranks[(size_t)q] == kCompNan ? nan_tile : bad_tile;

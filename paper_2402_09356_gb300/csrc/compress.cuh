@@ -66,4 +66,12 @@ void compress_jobs(tlr_ctx *ctx, cudaStream_t s, std::vector<CompressJob> &jobs,
                    std::vector<int> &fail_order, bool df = false, const std::function<void()> &overlap = nullptr,
                    const GrowSlot &grow = nullptr, bool tc = false);
 
+// Profiling (ctx->profile): compress_jobs records its sub-step marks without
+// waiting for them; compress_profile_collect waits for the marks recorded
+// since the last reset, adds their intervals to ctx->comp_ms and resets.
+// compress_tiles collects by itself; a caller of compress_jobs resets before
+// its first call and collects after its last.
+void compress_profile_reset(tlr_ctx *ctx);
+void compress_profile_collect(tlr_ctx *ctx);
+
 }  // namespace tlr

@@ -148,6 +148,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
     FactorStats *pstats = list[0].stats;  // profiling totals of the call
     int prof_used = 0;
     for (double &v : ctx->comp_ms) v = 0.0;
+    compress_profile_reset(ctx);
     for (long long &v : ctx->comp_stats) v = 0;
     ctx->k16_ms = ctx->k16_flops = 0.0;
     ctx->k16_launches = ctx->k16_clusters = 0;
@@ -816,6 +817,7 @@ void factor_group(tlr_ctx *ctx, cudaStream_t st, std::vector<FactorItem> &list, 
     TLR_CUDA_TRY(cudaEventRecord(ctx->ev_sv_done, ctx->sv));
     TLR_CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_sv_done, 0));
     if (ctx->profile) {
+        compress_profile_collect(ctx);
         for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la, &dm_sv})
             if (!v->empty()) TLR_CUDA_TRY(cudaEventSynchronize(v->back().e));
         for (std::vector<DMark> *v : {&dm_main, &dm_aux, &dm_la, &dm_sv})
